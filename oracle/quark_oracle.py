@@ -1,0 +1,520 @@
+"""FP64 CPU oracle of Quark's Update & Fuse steps and final LDM render.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
+leg of bench.py may import this module.  The CUDA path never does, and this module
+shares no code with it: it only reads the seeded inputs made by the synth module.
+
+Plain numpy float64, written from the paper step by step (Flynn et al., "Quark:
+Real-time, High-resolution, and General Neural View Synthesis", 2024):
+
+  encode        Sec. 3.2.1 and the "Encode Input Images" figure: a 3x3 conv (3 -> C,
+                zero pad, bias) at full resolution, then strided 2x2 mean pooling;
+                level k holds the k x k block mean of the conv output.
+  transition    Sec. 3.2.2 "Initialization" (broadcast learned v0, flat layers at the
+                depth anchors) and "Layer Collapse" (mean of adjacent layers plus a
+                residual MLP of their concatenation), then a x2 bilinear upsample when
+                the resolution changes (caption of the Update & Fuse figure).
+  depth         Sec. 3.2.3, Eq. (depth anchors) and Eq. (depth_activation).
+  back-project  Sec. 3.1 (operator P^T): unproject each LDM pixel at its layer depth,
+                project into each input view, bilinearly sample the view's feature map.
+  attention     Sec. 3.3: One-to-many attention, head_i = Attention(N(V) W_i^q, D, D),
+                MultiHead = concat(heads) W^O, V' = V + MultiHead(N(V), D); N = RMSNorm.
+  conv block    Sec. 3.3: V' = V + Conv(gelu(Conv(N(V)))), 3x3 per layer plane.
+  decode        Sec. 3.2.2 "Decoding": sigma = sigmoid(V W_sigma), c = sigmoid(V W_a),
+                depth by Eq. (depth_activation).
+  blend logits  Sec. 3.2.3: the one-to-many attention logits of the final block against
+                its update features, softmax delayed until after upsampling.
+  render        Sec. 3.1, Eq. (1): upsample the unactivated depth / density / blend
+                logits, activate, back-project the input images, blend with beta, over
+                composite (front to back, equivalent to the paper's back to front).
+
+Conventions (the paper is silent on them; the same readings bind the CUDA path):
+pixel centres at (x + 0.5, y + 0.5); camera x right, y down, z forward; world->camera
+X_c = R X_w + t; depth = camera z; level-k intrinsics diag(1/k, 1/k, 1) K; layer
+index l = 1..L with l = 1 farthest and l = L nearest; bilinear sampling with zero
+padding (grid_sample "zeros", align_corners=False); bilinear resizing with edge
+clamp; a sample with camera z <= 1e-6 in the source view is invalid and reads zero.
+
+Every computation runs on rectangular windows of a plane ("rects").  A full plane is
+one rect; sampled outputs of a large frame are computed by growing the requested rect
+backwards through each step's halo (render upsample, two 3x3 convs, x2 upsample).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+from scipy.special import erf
+
+Z_MIN = 1e-6
+RMS_EPS = 1e-6
+
+Rect = Tuple[int, int, int, int]  # y0, y1, x0, x1 (half-open), in plane coordinates
+
+
+# ---------------------------------------------------------------------------------------------
+# Elementwise definitions
+# ---------------------------------------------------------------------------------------------
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def gelu(x):
+    """erf form of gelu (the paper does not say which form; reading: exact erf)."""
+    return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+
+
+def rmsnorm(v, g):
+    """RMSNorm (Zhang & Sennrich 2019), the normalisation N of Sec. 3.3: g * v / rms(v)."""
+    return g * v / np.sqrt(np.mean(v * v, axis=-1, keepdims=True) + RMS_EPS)
+
+
+def depth_anchor(ell, L):
+    """Eq. (depth anchors): delta = (l - 0.5) / L for l = 1..L."""
+    return (np.asarray(ell, np.float64) - 0.5) / L
+
+
+def depth_activation(t, ell, L, near, far):
+    """Eq. (depth_activation): d = [(delta + 0.5/L tanh t)(1/near - 1/far) + 1/far]^-1."""
+    disparity = (depth_anchor(ell, L) + 0.5 / L * np.tanh(t)) * (1.0 / near - 1.0 / far) + 1.0 / far
+    return 1.0 / disparity
+
+
+def grow(r: Rect, n: int, H: int, W: int) -> Rect:
+    return (max(r[0] - n, 0), min(r[1] + n, H), max(r[2] - n, 0), min(r[3] + n, W))
+
+
+# ---------------------------------------------------------------------------------------------
+# Cameras and the back-projection geometry (Sec. 3.1, operator P^T)
+# ---------------------------------------------------------------------------------------------
+
+def scaled_K(cam, k: float) -> np.ndarray:
+    """Intrinsics of a grid k times coarser than the camera's own pixels."""
+    return np.diag([1.0 / k, 1.0 / k, 1.0]) @ cam.K
+
+
+def unproject(ys, xs, d, K_t, cam_t):
+    """World point of target pixel (ys, xs) at camera depth d (arrays broadcast together)."""
+    p = np.stack(np.broadcast_arrays(xs + 0.5, ys + 0.5, np.ones_like(xs, dtype=np.float64)), -1)
+    ray = p @ np.linalg.inv(K_t).T          # camera-space point at z = 1
+    Xc = ray * np.asarray(d)[..., None]      # scale to depth d
+    return (Xc - cam_t.t) @ cam_t.R          # R^T (X_c - t)
+
+
+def project(Xw, K_m, cam_m):
+    """Continuous pixel coordinates of world points in view m, and their validity (z > 1e-6)."""
+    Xc = Xw @ cam_m.R.T + cam_m.t
+    z = Xc[..., 2]
+    valid = z > Z_MIN
+    zs = np.where(valid, z, 1.0)
+    uvw = Xc @ K_m.T
+    return uvw[..., 0] / zs, uvw[..., 1] / zs, valid
+
+
+# ---------------------------------------------------------------------------------------------
+# Bilinear operators
+# ---------------------------------------------------------------------------------------------
+
+def bilinear_zero(fetch, u, v, valid):
+    """Bilinear sample at continuous pixel coords (u, v); taps outside the map read zero.
+
+    fetch(iy, ix) returns the texels at integer indices (zero outside the map), shape
+    idx.shape + (C,).  Invalid samples return zero."""
+    x = u - 0.5
+    y = v - 0.5
+    x0 = np.floor(x)
+    y0 = np.floor(y)
+    fx = (x - x0)[..., None]
+    fy = (y - y0)[..., None]
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    out = ((1 - fy) * (1 - fx) * fetch(y0, x0) + (1 - fy) * fx * fetch(y0, x0 + 1)
+           + fy * (1 - fx) * fetch(y0 + 1, x0) + fy * fx * fetch(y0 + 1, x0 + 1))
+    return np.where(valid[..., None], out, 0.0)
+
+
+def resize_taps(dst, ratio, n_src):
+    """Edge-clamped linear taps of a resize by `ratio` (pixel centres aligned):
+    src = (dst + 0.5) / ratio - 0.5.  Returns (i0, i1, w1)."""
+    src = (np.asarray(dst, np.float64) + 0.5) / ratio - 0.5
+    i0 = np.floor(src)
+    w1 = src - i0
+    i0 = i0.astype(np.int64)
+    return np.clip(i0, 0, n_src - 1), np.clip(i0 + 1, 0, n_src - 1), w1
+
+
+def resize_rect(src: np.ndarray, src_rect: Rect, H_src: int, W_src: int, ratio: int, out_rect: Rect):
+    """Bilinear resize (edge clamp) of src [..., h, w, C] held on src_rect, evaluated on out_rect."""
+    ys = np.arange(out_rect[0], out_rect[1])
+    xs = np.arange(out_rect[2], out_rect[3])
+    y0, y1, wy = resize_taps(ys, ratio, H_src)
+    x0, x1, wx = resize_taps(xs, ratio, W_src)
+    for a in (y0, y1):
+        assert a.min() >= src_rect[0] and a.max() < src_rect[1], "resize source rect too small"
+    for a in (x0, x1):
+        assert a.min() >= src_rect[2] and a.max() < src_rect[3], "resize source rect too small"
+    y0 -= src_rect[0]; y1 -= src_rect[0]; x0 -= src_rect[2]; x1 -= src_rect[2]
+    wy = wy[:, None, None]
+    wx = wx[None, :, None]
+    r0 = src[..., y0, :, :]
+    r1 = src[..., y1, :, :]
+    top = r0[..., :, x0, :] * (1 - wx) + r0[..., :, x1, :] * wx
+    bot = r1[..., :, x0, :] * (1 - wx) + r1[..., :, x1, :] * wx
+    return top * (1 - wy) + bot * wy
+
+
+def conv3x3_rect(x: np.ndarray, x_rect: Rect, H: int, W: int, w: np.ndarray, b: np.ndarray, out_rect: Rect):
+    """3x3 convolution, zero padding at the plane border, per leading index (layer).
+
+    x: [..., h, w, Cin] on x_rect; w: [3, 3, Cin, Cout] indexed [dy, dx]; returns
+    [..., out_h, out_w, Cout] on out_rect.  Every in-plane neighbour of out_rect must lie
+    in x_rect."""
+    oy0, oy1, ox0, ox1 = out_rect
+    need = (oy0 - 1, oy1 + 1, ox0 - 1, ox1 + 1)
+    lead = x.shape[:-3]
+    padded = np.zeros(lead + (need[1] - need[0], need[3] - need[2], x.shape[-1]))
+    # copy the in-plane part of the needed window
+    iy0, iy1 = max(need[0], 0), min(need[1], H)
+    ix0, ix1 = max(need[2], 0), min(need[3], W)
+    assert iy0 >= x_rect[0] and iy1 <= x_rect[1] and ix0 >= x_rect[2] and ix1 <= x_rect[3], "conv halo missing"
+    padded[..., iy0 - need[0]:iy1 - need[0], ix0 - need[2]:ix1 - need[2], :] = \
+        x[..., iy0 - x_rect[0]:iy1 - x_rect[0], ix0 - x_rect[2]:ix1 - x_rect[2], :]
+    oh, ow = oy1 - oy0, ox1 - ox0
+    out = np.zeros(lead + (oh, ow, w.shape[-1])) + b
+    for dy in range(3):
+        for dx in range(3):
+            out += padded[..., dy:dy + oh, dx:dx + ow, :] @ w[dy, dx]
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Encoder (Sec. 3.2.1): conv3x3 at full resolution, then 2x2 mean pooling per level
+# ---------------------------------------------------------------------------------------------
+
+def encode_box(image: np.ndarray, enc_w, enc_b, k: int, box: Rect) -> np.ndarray:
+    """Level-k feature map of one view on box (level coordinates): the k x k block mean of
+    F_1 = conv3x3(image) (zero pad, bias).  Returns [h, w, C]."""
+    H, W = image.shape[:2]
+    full = (box[0] * k, box[1] * k, box[2] * k, box[3] * k)
+    F1 = conv3x3_rect(image.astype(np.float64), (0, H, 0, W), H, W,
+                      enc_w.astype(np.float64), enc_b.astype(np.float64), full)
+    h, w = box[1] - box[0], box[3] - box[2]
+    return F1.reshape(h, k, w, k, -1).mean(axis=(1, 3))
+
+
+def encode_level(image, enc_w, enc_b, k):
+    """The whole level-k map of one view, [H/k, W/k, C]."""
+    H, W = image.shape[:2]
+    return encode_box(image, enc_w, enc_b, k, (0, H // k, 0, W // k))
+
+
+class LevelFetch:
+    """Texel fetch from level k of view m with zero padding; evaluates the encoder lazily on
+    the bounding box of the texels asked for (all fetches are declared first by `need`)."""
+
+    def __init__(self, image, enc_w, enc_b, k):
+        self.image, self.enc_w, self.enc_b, self.k = image, enc_w, enc_b, k
+        self.h, self.w = image.shape[0] // k, image.shape[1] // k
+        self.box = None
+        self.data = None
+
+    def prepare(self, ys_list, xs_list):
+        ys = np.concatenate([np.ravel(a) for a in ys_list])
+        xs = np.concatenate([np.ravel(a) for a in xs_list])
+        inside = (ys >= 0) & (ys < self.h) & (xs >= 0) & (xs < self.w)
+        if not inside.any():
+            self.box = (0, 0, 0, 0)
+            self.data = np.zeros((0, 0, self.enc_b.shape[0]))
+            return
+        box = (int(ys[inside].min()), int(ys[inside].max()) + 1, int(xs[inside].min()), int(xs[inside].max()) + 1)
+        self.box = box
+        self.data = encode_box(self.image, self.enc_w, self.enc_b, self.k, box)
+
+    def __call__(self, iy, ix):
+        inside = (iy >= 0) & (iy < self.h) & (ix >= 0) & (ix < self.w)
+        by = np.clip(iy - self.box[0], 0, max(self.data.shape[0] - 1, 0))
+        bx = np.clip(ix - self.box[2], 0, max(self.data.shape[1] - 1, 0))
+        if self.data.size == 0:
+            return np.zeros(iy.shape + (self.enc_b.shape[0],))
+        vals = self.data[by, bx]
+        return np.where(inside[..., None], vals, 0.0)
+
+
+def sample_views(fetchers: Sequence, cams, cam_t, k_t: float, k_m: float, d, ys, xs):
+    """Back-projection P^T (Sec. 3.1): for target pixels (ys, xs) at depth d, sample each view.
+
+    d: [L, h, w]; ys [h, 1], xs [1, w] target grid indices at scale k_t.  Returns Delta
+    [L, h, w, V, C]."""
+    K_t = scaled_K(cam_t, k_t)
+    Xw = unproject(ys[None], xs[None], d, K_t, cam_t)  # [L, h, w, 3]
+    coords = []
+    for m, cam in enumerate(cams):
+        u, v, valid = project(Xw, scaled_K(cam, k_m), cam)
+        coords.append((u, v, valid))
+        x0 = np.floor(u - 0.5).astype(np.int64)
+        y0 = np.floor(v - 0.5).astype(np.int64)
+        x0 = np.where(valid, x0, -2)
+        y0 = np.where(valid, y0, -2)
+        fetchers[m].prepare([y0, y0, y0 + 1, y0 + 1], [x0, x0 + 1, x0, x0 + 1])
+    out = []
+    for m in range(len(cams)):
+        u, v, valid = coords[m]
+        out.append(bilinear_zero(fetchers[m], u, v, valid))
+    return np.stack(out, axis=-2)
+
+
+# ---------------------------------------------------------------------------------------------
+# Fusion block pieces (Sec. 3.3)
+# ---------------------------------------------------------------------------------------------
+
+def one_to_many_attention(x, Delta, Wq, Wo, heads):
+    """MultiHead(x, Delta) with head_i = softmax(x W_i^q Delta^T / sqrt(C)) Delta (Sec. 3.3,
+    "Optimized Attention"); per-head query dimension C (appendix A).  Returns (out, p)."""
+    C = x.shape[-1]
+    outs, ps = [], []
+    for i in range(heads):
+        q = x @ Wq[:, i * C:(i + 1) * C]                          # [..., C]
+        logits = np.einsum("...c,...mc->...m", q, Delta) / math.sqrt(C)
+        logits = logits - logits.max(axis=-1, keepdims=True)
+        p = np.exp(logits)
+        p = p / p.sum(axis=-1, keepdims=True)
+        outs.append(np.einsum("...m,...mc->...c", p, Delta))
+        ps.append(p)
+    return np.concatenate(outs, axis=-1) @ Wo, np.stack(ps, axis=-2)
+
+
+def standard_attention(x, Delta, Wq, Wk, Wv, Wo, heads):
+    """Textbook multi-head cross attention (Sec. 3.3, Preliminaries; appendix A): queries x W^q,
+    keys Delta W^k, values Delta W^val, each split into `heads` heads of C/heads channels,
+    softmax(q k^T / sqrt(C/heads)) per head, concat, times W^O."""
+    C = x.shape[-1]
+    dh = C // heads
+    q = x @ Wq
+    k = Delta @ Wk
+    v = Delta @ Wv
+    outs = []
+    for i in range(heads):
+        sl = slice(i * dh, (i + 1) * dh)
+        logits = np.einsum("...c,...mc->...m", q[..., sl], k[..., sl]) / math.sqrt(dh)
+        logits = logits - logits.max(axis=-1, keepdims=True)
+        p = np.exp(logits)
+        p = p / p.sum(axis=-1, keepdims=True)
+        outs.append(np.einsum("...m,...mc->...c", p, v[..., sl]))
+    return np.concatenate(outs, axis=-1) @ Wo
+
+
+def layer_collapse(V, w1, b1, w2, b2):
+    """Layer Collapse (Sec. 3.2.2): pairs (l=2j-1, 2j) -> mean + MLP(concat); MLP = 2C -> C,
+    gelu, C -> C (the paper does not give the MLP depth; reading: one hidden layer)."""
+    a = V[0::2]
+    b = V[1::2]
+    cat = np.concatenate([a, b], axis=-1)
+    return 0.5 * (a + b) + gelu(cat @ w1 + b1) @ w2 + b2
+
+
+# ---------------------------------------------------------------------------------------------
+# One Update & Fuse step on windows
+# ---------------------------------------------------------------------------------------------
+
+@dataclass
+class StepResult:
+    rect_attn: Rect
+    V_in: np.ndarray       # [L, h, w, C] on rect_attn
+    V_attn: np.ndarray     # after the attention block, on rect_attn
+    depth_used: np.ndarray  # depth the views were sampled at, on rect_attn
+    Delta: np.ndarray      # [L, h, w, V, C]
+    x_norm: np.ndarray     # N(V_in) of the attention block
+    rect_out: Rect
+    V_out: np.ndarray      # after the conv block, on rect_out
+    t: np.ndarray          # raw depth logit [L, h, w]
+    s: np.ndarray          # raw density logit [L, h, w]
+    colour: np.ndarray     # [L, h, w, 3]
+    alpha: np.ndarray      # [L, h, w]
+    depth: np.ndarray      # [L, h, w]
+    beta_logits: Optional[np.ndarray]  # [L, h, w, V] on rect_attn (last scale only)
+
+
+def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
+                     rect_attn: Rect, rect_out: Rect, last: bool, mode: int = 0) -> StepResult:
+    f64 = lambda a: np.asarray(a, np.float64)
+    k, L = cfg.scales[j]
+    H, Wd = cfg.out_h // k, cfg.out_w // k
+    C = cfg.C
+    ys = np.arange(rect_attn[0], rect_attn[1])[:, None]
+    xs = np.arange(rect_attn[2], rect_attn[3])[None, :]
+    h, w = rect_attn[1] - rect_attn[0], rect_attn[3] - rect_attn[2]
+    ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
+
+    # ---- transition: initialisation, or layer collapse then x2 upsample ----
+    if j == 0:
+        V_in = np.broadcast_to(f64(W["v0"]), (L, h, w, C)).copy()
+        d = np.broadcast_to(1.0 / ((ell - 0.5) / L * (1 / cfg.near - 1 / cfg.far) + 1 / cfg.far), (L, h, w)).copy()
+    else:
+        kp, Lp = cfg.scales[j - 1]
+        Vp, rp = prev.V_out, prev.rect_out
+        if Lp == 2 * L:
+            Vp = layer_collapse(Vp, f64(W[f"col_w1_{j}"]), f64(W[f"col_b1_{j}"]),
+                                f64(W[f"col_w2_{j}"]), f64(W[f"col_b2_{j}"]))
+        else:
+            assert Lp == L
+        ratio = kp // k
+        V_in = resize_rect(Vp, rp, cfg.out_h // kp, cfg.out_w // kp, ratio, rect_attn)
+        t_in = V_in @ f64(W["w_d"]) + f64(W["b_d"])[0]
+        d = depth_activation(t_in, ell, L, cfg.near, cfg.far)
+
+    # ---- back-project the views' level-k features at the current depths ----
+    Delta = sample_views(fetchers[k], scene.cams, scene.target, k, k, d, ys, xs)  # [L,h,w,V,C]
+
+    # ---- fusion block: one-to-many attention ----
+    x = rmsnorm(V_in, f64(W[f"attn_g_{j}"]))
+    if mode == 0:
+        upd, _ = one_to_many_attention(x, Delta, f64(W[f"Wq_{j}"]), f64(W[f"Wo_{j}"]), cfg.heads)
+    else:
+        upd = standard_attention(x, Delta, f64(W[f"Wq_std_{j}"]), f64(W[f"Wk_std_{j}"]),
+                                 f64(W[f"Wv_std_{j}"]), f64(W[f"Wo_std_{j}"]), cfg.heads)
+    V_attn = V_in + upd
+
+    beta = None
+    if last:
+        qb = x @ f64(W["W_beta"])
+        beta = np.einsum("...c,...mc->...m", qb, Delta) / math.sqrt(C)
+
+    # ---- fusion block: residual conv block V + Conv(gelu(Conv(N(V)))) ----
+    n = rmsnorm(V_attn, f64(W[f"conv_g_{j}"]))
+    mid_rect = grow(rect_out, 1, H, Wd)
+    h1 = conv3x3_rect(n, rect_attn, H, Wd, f64(W[f"conv1_w_{j}"]), f64(W[f"conv1_b_{j}"]), mid_rect)
+    h2 = conv3x3_rect(gelu(h1), mid_rect, H, Wd, f64(W[f"conv2_w_{j}"]), f64(W[f"conv2_b_{j}"]), rect_out)
+    oy, ox = rect_out[0] - rect_attn[0], rect_out[2] - rect_attn[2]
+    V_out = V_attn[:, oy:oy + h2.shape[1], ox:ox + h2.shape[2]] + h2
+
+    # ---- decode the LDM attributes ----
+    ello = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
+    t = V_out @ f64(W["w_d"]) + f64(W["b_d"])[0]
+    s = V_out @ f64(W["w_sigma"]) + f64(W["b_sigma"])[0]
+    colour = sigmoid(V_out @ f64(W["W_a"]) + f64(W["b_a"]))
+    return StepResult(rect_attn, V_in, V_attn, d, Delta, x, rect_out, V_out, t, s, colour, sigmoid(s),
+                      depth_activation(t, ello, L, cfg.near, cfg.far), beta)
+
+
+# ---------------------------------------------------------------------------------------------
+# Final render (Sec. 3.1 Eq. 1, Sec. 3.2.3 Upsampling & Activation)
+# ---------------------------------------------------------------------------------------------
+
+def render_rect(cfg, scene, last: StepResult, out_rect: Rect, return_layers: bool = False):
+    """RGBA of the novel view on out_rect (full output resolution)."""
+    k, L = cfg.scales[-1]
+    Hl, Wl = cfg.out_h // k, cfg.out_w // k
+    s = k
+    rect_beta = last.rect_attn
+    ob = (last.rect_out[0] - rect_beta[0], last.rect_out[2] - rect_beta[2])
+    hb, wb = last.V_out.shape[1], last.V_out.shape[2]
+    beta_on_out = last.beta_logits[:, ob[0]:ob[0] + hb, ob[1]:ob[1] + wb]
+    t_up = resize_rect(last.t[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
+    s_up = resize_rect(last.s[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
+    b_up = resize_rect(beta_on_out, last.rect_out, Hl, Wl, s, out_rect)  # [L, h, w, V]
+    ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
+    d = depth_activation(t_up, ell, L, cfg.near, cfg.far)
+    alpha = sigmoid(s_up)
+    bl = b_up - b_up.max(axis=-1, keepdims=True)
+    beta = np.exp(bl)
+    beta = beta / beta.sum(axis=-1, keepdims=True)
+
+    ys = np.arange(out_rect[0], out_rect[1])[:, None]
+    xs = np.arange(out_rect[2], out_rect[3])[None, :]
+    K_t = scene.target.K
+    Xw = unproject(ys[None], xs[None], d, K_t, scene.target)
+    col = np.zeros(d.shape + (3,))
+    for m, cam in enumerate(scene.cams):
+        img = scene.images[m].astype(np.float64)
+        Hi, Wi = img.shape[:2]
+
+        def fetch(iy, ix, img=img, Hi=Hi, Wi=Wi):
+            inside = (iy >= 0) & (iy < Hi) & (ix >= 0) & (ix < Wi)
+            return np.where(inside[..., None], img[np.clip(iy, 0, Hi - 1), np.clip(ix, 0, Wi - 1)], 0.0)
+
+        u, v, valid = project(Xw, cam.K, cam)
+        col += beta[..., m:m + 1] * bilinear_zero(fetch, u, v, valid)
+    rgb = np.zeros(d.shape[1:] + (3,))
+    T = np.ones(d.shape[1:])
+    for li in range(L - 1, -1, -1):        # front (l = L, nearest) to back (l = 1)
+        rgb += (T * alpha[li])[..., None] * col[li]
+        T = T * (1.0 - alpha[li])
+    rgba = np.concatenate([rgb, (1.0 - T)[..., None]], axis=-1)
+    if return_layers:
+        return rgba, col, alpha, d, beta
+    return rgba
+
+
+def over_back_to_front(col, alpha):
+    """Over operator applied back to front (l = 1 first), as the paper states it (Sec. 3.1)."""
+    rgb = np.zeros(col.shape[1:])
+    a_acc = np.zeros(alpha.shape[1:])
+    for li in range(col.shape[0]):
+        rgb = alpha[li][..., None] * col[li] + (1 - alpha[li])[..., None] * rgb
+        a_acc = alpha[li] + (1 - alpha[li]) * a_acc
+    return np.concatenate([rgb, a_acc[..., None]], axis=-1)
+
+
+# ---------------------------------------------------------------------------------------------
+# Whole forward pass on a window of the output
+# ---------------------------------------------------------------------------------------------
+
+def plan_rects(cfg, out_rect: Rect):
+    """Windows each scale must compute so that out_rect of the final render is exact."""
+    n = cfg.n_scales
+    k, L = cfg.scales[-1]
+    Hl, Wl = cfg.out_h // k, cfg.out_w // k
+    ys = np.arange(out_rect[0], out_rect[1])
+    xs = np.arange(out_rect[2], out_rect[3])
+    y0, y1, _ = resize_taps(ys, k, Hl)
+    x0, x1, _ = resize_taps(xs, k, Wl)
+    need = (int(y0.min()), int(y1.max()) + 1, int(x0.min()), int(x1.max()) + 1)
+    rect_out = [None] * n
+    rect_attn = [None] * n
+    for j in range(n - 1, -1, -1):
+        kj, _ = cfg.scales[j]
+        H, W = cfg.out_h // kj, cfg.out_w // kj
+        rect_out[j] = need
+        rect_attn[j] = grow(need, 2, H, W)
+        if j > 0:
+            kp, _ = cfg.scales[j - 1]
+            ratio = kp // kj
+            Hp, Wp = cfg.out_h // kp, cfg.out_w // kp
+            ys = np.arange(rect_attn[j][0], rect_attn[j][1])
+            xs = np.arange(rect_attn[j][2], rect_attn[j][3])
+            a0, a1, _ = resize_taps(ys, ratio, Hp)
+            b0, b1, _ = resize_taps(xs, ratio, Wp)
+            need = (int(a0.min()), int(a1.max()) + 1, int(b0.min()), int(b1.max()) + 1)
+    return rect_attn, rect_out
+
+
+def make_fetchers(cfg, scene, W):
+    return {k: [LevelFetch(scene.images[m], np.asarray(W["enc_w"], np.float64),
+                           np.asarray(W["enc_b"], np.float64), k) for m in range(len(scene.cams))]
+            for k in cfg.levels()}
+
+
+def forward(cfg, W, scene, out_rect: Optional[Rect] = None, mode: int = 0):
+    """Novel-view RGBA on out_rect (default: the whole frame) plus every scale's step result."""
+    if out_rect is None:
+        out_rect = (0, cfg.out_h, 0, cfg.out_w)
+    rect_attn, rect_out = plan_rects(cfg, out_rect)
+    fetchers = make_fetchers(cfg, scene, W)
+    steps: List[StepResult] = []
+    prev = None
+    for j in range(cfg.n_scales):
+        prev = update_fuse_step(cfg, W, scene, fetchers, j, prev, rect_attn[j], rect_out[j],
+                                last=(j == cfg.n_scales - 1), mode=mode)
+        steps.append(prev)
+    rgba = render_rect(cfg, scene, steps[-1], out_rect)
+    return rgba, steps
+
+
+def encode_pyramid(cfg, W, scene) -> Dict[int, np.ndarray]:
+    """All levels of all views, {k: [V, H/k, W/k, C]} (small cases)."""
+    return {k: np.stack([encode_level(scene.images[m], np.asarray(W["enc_w"], np.float64),
+                                      np.asarray(W["enc_b"], np.float64), k)
+                         for m in range(len(scene.cams))]) for k in cfg.levels()}

@@ -1,0 +1,386 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the bench.
+
+This module only *makes inputs*: workload descriptions, pinhole cameras, input
+images (value-noise textures or a small ray-cast scene) and random-init network
+weights.  It holds none of the method's arithmetic (no reprojection, sampling,
+attention, convolution or compositing); each side implements those itself.
+
+Workloads follow the shapes of the paper's experiments (Sec. 1: 8 input views
+up to ~30 cm apart, 1080p output; Tables "Model description for Quark / Quark+":
+LDM layer counts 4..32, C = 32, 1..4 heads).  The paper's datasets and trained
+weights are not available, so seeded synthetic scenes and N(0, std) weights
+stand in for them.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------------------------
+# Workload description
+# --------------------------------------------------------------------------------------------
+
+ATTN_ONE_TO_MANY = 0
+ATTN_STANDARD = 1
+PREC_FP32 = 0
+PREC_BF16 = 1
+
+
+@dataclass
+class QuarkConfig:
+    """Shape of one Quark network instance.
+
+    scales: list of (k, L) from coarse to fine.  Scale j uses pyramid level k_j and an LDM
+    of L_j layers on a grid of (out_h / k_j, out_w / k_j) pixels.  Consecutive scales have
+    k_{j-1} / k_j in {1, 2} and L_{j-1} / L_j in {1, 2} (layer collapse, Sec. 3.2).
+    The final render upsamples the last scale by s = k_last (Sec. 3.2.3, factor s).
+    """
+
+    C: int = 16
+    heads: int = 1
+    scales: List[Tuple[int, int]] = field(default_factory=lambda: [(2, 4)])
+    near: float = 1.0
+    far: float = 10.0
+    out_h: int = 48
+    out_w: int = 64
+    attn_mode: int = ATTN_ONE_TO_MANY
+    precision: int = PREC_FP32
+
+    @property
+    def n_scales(self) -> int:
+        return len(self.scales)
+
+    @property
+    def upsample_s(self) -> int:
+        return self.scales[-1][0]
+
+    def ldm_shape(self, j: int) -> Tuple[int, int, int]:
+        k, L = self.scales[j]
+        return L, self.out_h // k, self.out_w // k
+
+    def levels(self) -> List[int]:
+        return sorted({k for k, _ in self.scales})
+
+    def replace(self, **kw) -> "QuarkConfig":
+        return dataclasses.replace(self, **kw)
+
+
+@dataclass
+class Camera:
+    """Pinhole camera, world->camera extrinsics X_c = R X_w + t; x right, y down, z forward."""
+
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    R: np.ndarray  # (3, 3) float64
+    t: np.ndarray  # (3,) float64
+
+    @property
+    def K(self) -> np.ndarray:
+        return np.array([[self.fx, 0.0, self.cx], [0.0, self.fy, self.cy], [0.0, 0.0, 1.0]])
+
+    @property
+    def centre(self) -> np.ndarray:
+        return -self.R.T @ self.t
+
+
+def look_at(centre: Sequence[float], target: Sequence[float]) -> Tuple[np.ndarray, np.ndarray]:
+    """Rotation/translation of a camera at `centre` aimed at `target` (y down, z forward)."""
+    c = np.asarray(centre, np.float64)
+    z = np.asarray(target, np.float64) - c
+    z = z / np.linalg.norm(z)
+    down = np.array([0.0, 1.0, 0.0])
+    x = np.cross(down, z)
+    x = x / np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z])
+    return R, -R @ c
+
+
+def make_camera(width, height, f, centre, target=None, cx=None, cy=None) -> Camera:
+    if target is None:
+        R, t = np.eye(3), -np.asarray(centre, np.float64)
+    else:
+        R, t = look_at(centre, target)
+    return Camera(width, height, float(f), float(f),
+                  float(width / 2 if cx is None else cx), float(height / 2 if cy is None else cy), R, t)
+
+
+# --------------------------------------------------------------------------------------------
+# Value noise (input textures only)
+# --------------------------------------------------------------------------------------------
+
+def _lattice(rng: np.random.Generator, n: int) -> np.ndarray:
+    return rng.random((n, n, 3))
+
+
+def value_noise_2d(lat: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Smooth (smoothstep-interpolated) periodic value noise; lat is (n, n, 3) in [0, 1)."""
+    n = lat.shape[0]
+    u0 = np.floor(u)
+    v0 = np.floor(v)
+    fu = u - u0
+    fv = v - v0
+    fu = fu * fu * (3 - 2 * fu)
+    fv = fv * fv * (3 - 2 * fv)
+    i0 = u0.astype(np.int64) % n
+    j0 = v0.astype(np.int64) % n
+    i1 = (i0 + 1) % n
+    j1 = (j0 + 1) % n
+    a = lat[j0, i0]
+    b = lat[j0, i1]
+    c = lat[j1, i0]
+    d = lat[j1, i1]
+    fu = fu[..., None]
+    fv = fv[..., None]
+    return (a * (1 - fu) + b * fu) * (1 - fv) + (c * (1 - fu) + d * fu) * fv
+
+
+def fbm_2d(rng: np.random.Generator, u: np.ndarray, v: np.ndarray, octaves: int,
+           lattice_n: int = 64) -> np.ndarray:
+    """Sum of `octaves` value-noise octaves (frequency x2, amplitude x0.5), normalised to [0, 1]."""
+    out = np.zeros(u.shape + (3,))
+    amp, tot, freq = 1.0, 0.0, 1.0
+    for _ in range(octaves):
+        lat = _lattice(rng, lattice_n)
+        out += amp * value_noise_2d(lat, u * freq, v * freq)
+        tot += amp
+        amp *= 0.5
+        freq *= 2.0
+    return out / tot
+
+
+# --------------------------------------------------------------------------------------------
+# Scenes
+# --------------------------------------------------------------------------------------------
+
+@dataclass
+class Scene:
+    images: np.ndarray           # (V, H, W, 3) float32 in [0, 1]
+    cams: List[Camera]           # input views
+    target: Camera               # novel view (output resolution)
+    depth: Optional[np.ndarray] = None  # (V, H, W) ground-truth z of the ray-cast scene
+
+
+def scene_noise_pair(seed: int = 1234, V: int = 2, W: int = 64, H: int = 48, f: float = 60.0,
+                     baseline: float = 0.1, octaves: int = 3, period: float = 16.0,
+                     out_w: Optional[int] = None, out_h: Optional[int] = None) -> Scene:
+    """Smooth value-noise images (base period `period` px), cameras spaced `baseline` apart on x,
+    all looking down +z (R = I), novel view at the midpoint of the rig."""
+    rng = np.random.default_rng(seed)
+    ys, xs = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    imgs = []
+    for _ in range(V):
+        imgs.append(fbm_2d(rng, xs / period, ys / period, octaves, lattice_n=max(8, int(np.ceil(max(W, H) / period)) + 2)))
+    images = np.stack(imgs).astype(np.float32)
+    xs_c = np.linspace(0.0, baseline * (V - 1), V)
+    cams = [make_camera(W, H, f, (x, 0.0, 0.0)) for x in xs_c]
+    ow = W if out_w is None else out_w
+    oh = H if out_h is None else out_h
+    sx, sy = ow / W, oh / H
+    target = Camera(ow, oh, f * sx, f * sy, W / 2 * sx, H / 2 * sy, np.eye(3),
+                    -np.array([xs_c.mean(), 0.0, 0.0]))
+    return Scene(images, cams, target)
+
+
+def _ray_dirs(cam: Camera) -> np.ndarray:
+    ys, xs = np.meshgrid(np.arange(cam.height, dtype=np.float64) + 0.5,
+                         np.arange(cam.width, dtype=np.float64) + 0.5, indexing="ij")
+    d_cam = np.stack([(xs - cam.cx) / cam.fx, (ys - cam.cy) / cam.fy, np.ones_like(xs)], -1)
+    return d_cam @ cam.R  # camera -> world (R^T d), z_cam = 1 along each ray
+
+
+def scene_raycast(seed: int = 1234, V: int = 8, W: int = 1920, H: int = 1080, f: float = 1400.0,
+                  arc: float = 0.6, radius: float = 10.0, n_planes: int = 10, n_spheres: int = 10,
+                  zmin: float = 1.0, zmax: float = 100.0, octaves: int = 5,
+                  out_w: Optional[int] = None, out_h: Optional[int] = None) -> Scene:
+    """Ray-cast scene: `n_planes` textured quads and `n_spheres` textured spheres placed uniformly in
+    inverse depth over [zmin, zmax] m in front of the rig, over a textured backdrop plane at zmax.
+    Cameras sit evenly on an `arc` m arc of a circle of `radius` m around (0, 0, radius), aimed at it;
+    the novel view is the arc midpoint.  One ray per pixel, no antialiasing."""
+    rng = np.random.default_rng(seed)
+    centre = np.array([0.0, 0.0, radius])
+    half = arc / radius / 2.0
+    thetas = np.linspace(-half, half, V)
+    cams = []
+    for th in thetas:
+        c = np.array([radius * np.sin(th), 0.0, radius - radius * np.cos(th)])
+        R, t = look_at(c, centre)
+        cams.append(Camera(W, H, f, f, W / 2, H / 2, R, t))
+    ow = W if out_w is None else out_w
+    oh = H if out_h is None else out_h
+    target = Camera(ow, oh, f * ow / W, f * oh / H, ow / 2, oh / 2, np.eye(3), np.zeros(3))
+
+    tan_x = (W / 2) / f
+    tan_y = (H / 2) / f
+    prims = []
+    for i in range(n_planes + n_spheres):
+        z = 1.0 / rng.uniform(1.0 / zmax, 1.0 / zmin)
+        px = rng.uniform(-0.8, 0.8) * tan_x * z
+        py = rng.uniform(-0.8, 0.8) * tan_y * z
+        size = rng.uniform(0.05, 0.25) * tan_x * z
+        tex = rng.integers(0, 2**31)
+        if i < n_planes:
+            # quad with normal tilted away from -z, spanned by two unit axes
+            nrm = np.array([rng.uniform(-0.4, 0.4), rng.uniform(-0.4, 0.4), -1.0])
+            nrm /= np.linalg.norm(nrm)
+            a1 = np.cross(np.array([0.0, 1.0, 0.0]), nrm)
+            a1 /= np.linalg.norm(a1)
+            a2 = np.cross(nrm, a1)
+            prims.append(("quad", np.array([px, py, z]), nrm, a1, a2, size, tex))
+        else:
+            prims.append(("sphere", np.array([px, py, z]), size * 0.7, tex))
+    back_tex = rng.integers(0, 2**31)
+
+    images, depths = [], []
+    for cam in cams:
+        o = cam.centre
+        d = _ray_dirs(cam).reshape(-1, 3)
+        best = np.full(d.shape[0], np.inf)
+        col = np.zeros((d.shape[0], 3))
+        # backdrop z = zmax (world); ray param s along d
+        s_back = (zmax - o[2]) / d[:, 2]
+        hit = s_back > 0
+        best[hit] = s_back[hit]
+        P = o + d * best[:, None]
+        col[:] = fbm_2d(np.random.default_rng(back_tex), P[:, 0] / 4.0, P[:, 1] / 4.0, octaves)
+        for pr in prims:
+            if pr[0] == "quad":
+                _, c0, nrm, a1, a2, size, tex = pr
+                den = d @ nrm
+                s = ((c0 - o) @ nrm) / np.where(np.abs(den) < 1e-12, 1e-12, den)
+                P = o + d * s[:, None]
+                lu = (P - c0) @ a1
+                lv = (P - c0) @ a2
+                m = (s > 0) & (s < best) & (np.abs(lu) < size) & (np.abs(lv) < size)
+                if np.any(m):
+                    best[m] = s[m]
+                    col[m] = fbm_2d(np.random.default_rng(tex), lu[m] / size * 4.0, lv[m] / size * 4.0, octaves)
+            else:
+                _, c0, r, tex = pr
+                oc = o - c0
+                b = d @ oc
+                a = np.einsum("ij,ij->i", d, d)
+                cc = oc @ oc - r * r
+                disc = b * b - a * cc
+                ok = disc > 0
+                s = np.full(d.shape[0], np.inf)
+                s[ok] = (-b[ok] - np.sqrt(disc[ok])) / a[ok]
+                m = ok & (s > 0) & (s < best)
+                if np.any(m):
+                    best[m] = s[m]
+                    P = o + d[m] * s[m, None] - c0
+                    lon = np.arctan2(P[:, 0], -P[:, 2])
+                    lat = np.arcsin(np.clip(P[:, 1] / r, -1, 1))
+                    col[m] = fbm_2d(np.random.default_rng(tex), lon * 3.0, lat * 3.0, octaves)
+        images.append(col.reshape(H, W, 3))
+        # the ray direction has unit camera-z, so the ray parameter equals camera depth
+        depths.append(best.reshape(H, W))
+    return Scene(np.stack(images).astype(np.float32), cams, target, np.stack(depths).astype(np.float32))
+
+
+def perturb_target(scene: Scene, rng: np.random.Generator, jitter: float) -> Camera:
+    """Novel view jittered by U(-jitter, jitter) m per axis, same orientation."""
+    c = scene.target.centre + rng.uniform(-jitter, jitter, 3)
+    return dataclasses.replace(scene.target, t=-scene.target.R @ c)
+
+
+# --------------------------------------------------------------------------------------------
+# Weights
+# --------------------------------------------------------------------------------------------
+
+def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
+    """Every tensor of the network, row-vector convention (y = x @ W + b).
+
+    enc_w (3, 3, 3, C): 3x3 encoder conv [dy, dx, c_in, c_out]; enc_b (C,)
+    v0 (C,): learned initial feature (Sec. 3.2.2, Initialization)
+    per scale j: attn_g_j (C,), Wq_j (C, h*C), Wo_j (h*C, C)          one-to-many attention (Sec. 3.3)
+                 conv_g_j (C,), conv1_w_j (3,3,C,C), conv1_b_j, conv2_w_j, conv2_b_j   residual conv block
+                 col_w1_j (2C, C), col_b1_j (C,), col_w2_j (C, C), col_b2_j (C,)      layer collapse MLP
+                 Wq_std_j, Wk_std_j, Wv_std_j, Wo_std_j (C, C)         standard cross-attention mode
+    w_d (C,), b_d (1,), w_sigma (C,), b_sigma (1,), W_a (C, 3), b_a (3,)   LDM decoders
+    W_beta (C, C): blend-weight query projection of the final block (Sec. 3.2.3)
+    """
+    C, h = cfg.C, cfg.heads
+    s = {"enc_w": (3, 3, 3, C), "enc_b": (C,), "v0": (C,)}
+    for j in range(cfg.n_scales):
+        s.update({
+            f"attn_g_{j}": (C,), f"Wq_{j}": (C, h * C), f"Wo_{j}": (h * C, C),
+            f"conv_g_{j}": (C,), f"conv1_w_{j}": (3, 3, C, C), f"conv1_b_{j}": (C,),
+            f"conv2_w_{j}": (3, 3, C, C), f"conv2_b_{j}": (C,),
+            f"col_w1_{j}": (2 * C, C), f"col_b1_{j}": (C,), f"col_w2_{j}": (C, C), f"col_b2_{j}": (C,),
+            f"Wq_std_{j}": (C, C), f"Wk_std_{j}": (C, C), f"Wv_std_{j}": (C, C), f"Wo_std_{j}": (C, C),
+        })
+    s.update({"w_d": (C,), "b_d": (1,), "w_sigma": (C,), "b_sigma": (1,), "W_a": (C, 3), "b_a": (3,),
+              "W_beta": (C, C)})
+    return s
+
+
+def make_weights(cfg: QuarkConfig, seed: int = 5678, std: float = 0.02, sharp: bool = False) -> Dict[str, np.ndarray]:
+    """Random-init weights.  Default: every tensor N(0, std) (gains 1 + N(0, std)).
+
+    sharp=True draws fan-in-scaled weights (N(0, 1/fan_in) x gain, with the query and blend
+    projections x4) so that the softmax over views, the blend weights, the depth tanh and
+    the gelu are far from their linear regimes."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, shp in weight_shapes(cfg).items():
+        if not sharp:
+            if name.startswith(("attn_g", "conv_g")):
+                w = 1.0 + std * rng.standard_normal(shp)
+            else:
+                w = std * rng.standard_normal(shp)
+        else:
+            if name.startswith(("attn_g", "conv_g")):
+                w = 1.0 + 0.2 * rng.standard_normal(shp)
+            elif name in ("v0",):
+                w = rng.standard_normal(shp)
+            elif name.startswith(("enc_b", "conv1_b", "conv2_b", "col_b")) or name in ("b_d", "b_sigma", "b_a"):
+                w = 0.3 * rng.standard_normal(shp)
+            else:
+                fan_in = int(np.prod(shp[:-1])) if len(shp) > 1 else shp[0]
+                gain = 4.0 if name.startswith(("Wq", "W_beta")) else (2.0 if name in ("w_d", "w_sigma") else 1.0)
+                w = gain * rng.standard_normal(shp) / np.sqrt(fan_in)
+        out[name] = w.astype(np.float32)
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# The workloads
+# --------------------------------------------------------------------------------------------
+
+def config_small() -> QuarkConfig:
+    """V=2 views 64x48, f=60, 16-channel level-2 map from one 3x3 conv, LDM 32x24 L=4,
+    depths in inverse depth over 1..10 m, C=16, one head, output 64x48 (s=2)."""
+    return QuarkConfig(C=16, heads=1, scales=[(2, 4)], near=1.0, far=10.0, out_h=48, out_w=64)
+
+
+def scene_small(seed: int = 1234) -> Scene:
+    return scene_noise_pair(seed=seed)
+
+
+def config_1080p() -> QuarkConfig:
+    """V=8 views 1920x1080, scales (k, L) = (8,32),(4,16),(2,8),(1,4), C=32, two heads,
+    near 1 m, far 100 m, 1080p output (s=1)."""
+    return QuarkConfig(C=32, heads=2, scales=[(8, 32), (4, 16), (2, 8), (1, 4)], near=1.0, far=100.0,
+                       out_h=1080, out_w=1920)
+
+
+def scene_1080p(seed: int = 1234, V: int = 8, W: int = 1920, H: int = 1080) -> Scene:
+    return scene_raycast(seed=seed, V=V, W=W, H=H, f=1400.0 * W / 1920.0)
+
+
+def config_grad() -> QuarkConfig:
+    """Differentiation workload: V=4 views 512x512, scales (2,16), (1,8), C=32, two heads."""
+    return QuarkConfig(C=32, heads=2, scales=[(2, 16), (1, 8)], near=1.0, far=100.0, out_h=512, out_w=512)
+
+
+def scene_grad(seed: int) -> Scene:
+    return scene_raycast(seed=seed, V=4, W=512, H=512, f=400.0, arc=0.3)
