@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: 1080p novel-view rendering from V=8 input views (encode pyramid + every Update &
+Fuse step + final render), FP32 and BF16 forms, on N GPUs as independent replicas.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl quark|reference] [--form bf16|fp32]
+
+Prints one JSON line.  `value` is frames/s of the whole job (all ranks) for the headline form
+with inputs resident in HBM; `e2e` is the same metric through the public API with the images in
+pinned host memory and the RGBA result read back to host memory every step.  The workload
+(2.8 GB FP32 pyramid, 1+ GB volumes per scale) is far larger than L2, so no flush is needed.
+`--impl reference` times the FP64 oracle on the host cores on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2411_16680_b300 import accounting, synth  # noqa: E402
+
+WORKLOAD = "1080p novel view, V=8 views 1920x1080, scales (k,L)=(8,32),(4,16),(2,8),(1,4), C=32, h=2"
+METRIC = "1080p novel-view fps (V=8) FP32 vs BF16 at >=40 dB vs oracle; p50/p99 latency"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "sm_max_mhz": d.get("sm_max_mhz", 2032.0), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0,
+            "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ----------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.bus_id:
+            cmd.insert(1, f"--id={self.bus_id}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [r for r in csv.reader(io.StringIO(self.out)) if len(r) >= 9]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def bus_id_of(dev: int):
+    """nvidia-smi --id of the GPU torch calls `dev` (PCI bus id, else the visible-devices entry)."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+        return vis[dev] if dev < len(vis) else str(dev)
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample
+# ----------------------------------------------------------------------------------------------
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(cfg, W, scene, rows: int = 2):
+    """Oracle on `rows` output rows at the frame centre, through every scale; returns (fps, secs,
+    description).  The fps extrapolates the sampled rows to the full frame."""
+    from oracle import quark_oracle as O
+    y0 = cfg.out_h // 2 - rows // 2
+    rect = (y0, y0 + rows, 0, cfg.out_w)
+    t0 = time.perf_counter()
+    O.forward(cfg, W, scene, rect)
+    dt = time.perf_counter() - t0
+    fps = (rows / cfg.out_h) / dt
+    desc = (f"oracle (float64 numpy) on output rows {rect[0]}-{rect[1] - 1} x all {cfg.out_w} columns of the "
+            f"{cfg.out_w}x{cfg.out_h} frame through every scale; fps scaled by {cfg.out_h}/{rows}")
+    return fps, dt, desc
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------------
+
+def run_form(cfg, W, scene, steps, warmup, rank, world, dev, peaks):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_16680_b300 import quark
+
+    torch.cuda.set_device(dev)
+    ctx = quark.Context(cfg, device=dev)
+    ctx.load_weights(W)
+    stream = torch.cuda.Stream(dev)
+    images = torch.tensor(scene.images, device=f"cuda:{dev}")
+    out = torch.empty(cfg.out_h, cfg.out_w, 4, device=f"cuda:{dev}")
+    with torch.cuda.stream(stream):
+        pyr = ctx.encode_pyramid(images, scene.cams, stream)
+        ldm = ctx.ldm_create(scene.target)
+
+    def step():
+        ctx.encode_pyramid(images, scene.cams, stream, into=pyr)
+        ctx.render_novel_view(pyr, ldm, out, stream)
+
+    for _ in range(warmup):
+        step()
+    stream.synchronize()
+    # per-step latency (device time per frame) and per-kernel device time
+    ctx.reset_counters()
+    ctx.set_profiling(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(bus_id_of(dev)) as clk:
+        ev[0].record(stream)
+        for i in range(steps):
+            step()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launch_count()
+    ktimes = ctx.kernel_times()
+    ctx.set_profiling(False)
+    lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[steps])
+    t = torch.tensor([total_ms], device=f"cuda:{dev}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+
+    # end to end through the public API: pinned host images in, host RGBA out, every step
+    himg = torch.from_numpy(np.ascontiguousarray(scene.images)).pin_memory()
+    hout = torch.empty(cfg.out_h, cfg.out_w, 4).pin_memory()
+    pyr_h = ctx.encode_pyramid(himg, scene.cams, stream)
+    for _ in range(2):
+        ctx.encode_pyramid(himg, scene.cams, stream, into=pyr_h)
+        ctx.render_novel_view(pyr_h, ldm, hout, stream)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.encode_pyramid(himg, scene.cams, stream, into=pyr_h)
+        ctx.render_novel_view(pyr_h, ldm, hout, stream)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=f"cuda:{dev}")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    rgba = out.cpu().numpy()
+    pyr_h.release()
+    pyr.release()
+    ldm.release()
+    ctx.close()
+    return {
+        "total_ms": total_ms, "lat": lat, "launches": launches, "ktimes": ktimes, "clocks": clk.summary(),
+        "e2e_s": e2e_s, "h2d": int(scene.images.nbytes), "d2h": int(cfg.out_h * cfg.out_w * 16), "rgba": rgba,
+    }
+
+
+def roofline(cfg, V, img_h, img_w, res, peaks):
+    work = accounting.per_view_work(cfg, V, img_h, img_w)
+    steps_done = None
+    fam, (n, ms) = max(res["ktimes"].items(), key=lambda kv: kv[1][1])
+    steps_done = n / max(work[fam]["launches"], 1)
+    per_launch_ms = ms / n
+    w = work[fam]
+    bytes_per_launch = w["bytes"] / w["launches"]
+    flops_per_launch = w["flops"] / w["launches"]
+    alu_bound = fam in ("conv_block",) or (fam == "attend" and cfg.precision == 0)
+    if fam == "conv_block":
+        achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+        peak = accounting.fp32_alu_peak_tflops(peaks["sm_max_mhz"])
+        r = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+             "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 FLOP x {peaks['sm_max_mhz']:.0f} MHz"}
+    else:
+        achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        r = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+             "peak_source": f"{peaks['source']} copy bandwidth"}
+    r["frac"] = round(r["achieved"] / r["peak"], 4)
+    r["kernel"] = fam
+    r["traffic"] = None
+    r["algorithmic_bytes_per_launch"] = int(bytes_per_launch)
+    r["algorithmic_flops_per_launch"] = int(flops_per_launch)
+    r["avg_launch_ms"] = round(per_launch_ms, 4)
+    r["kernels_ms_per_frame"] = {k: round(v[1] / max(steps_done, 1), 4) for k, v in res["ktimes"].items()}
+    return r
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="quark", choices=["quark", "reference"])
+    ap.add_argument("--form", default="bf16", choices=["bf16", "fp32"], help="headline form for `value`")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharp", action="store_true", help="sharp random weights instead of N(0, 0.02)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    peaks = load_peaks()
+
+    base_cfg = synth.config_1080p()
+    scene = synth.scene_1080p()
+    V = len(scene.cams)
+    img_h, img_w = scene.images.shape[1:3]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cfg = base_cfg.replace(precision=synth.PREC_FP32)
+        W = synth.make_weights(cfg, sharp=args.sharp)
+        fps_l, secs, desc = [], 0.0, ""
+        for _ in range(args.warmup):
+            pass  # the oracle has no warm-up state
+        for _ in range(args.steps):
+            f, s, desc = oracle_sample(cfg, W, scene, rows=1)
+            fps_l.append(f)
+            secs += s
+        fps = statistics.median(fps_l)
+        line = {"impl": "reference", "metric": METRIC, "value": round(fps, 6), "unit": "frames/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / fps, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded ray-cast scene; random-init weights)",
+                "config": {"workload": WORKLOAD, "form": "oracle", "l2": "inputs larger than L2"},
+                "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": blas_threads(),
+                                 "kind": "oracle", "sample": desc},
+                "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = local
+
+    forms = {}
+    results = {}
+    for form in ("fp32", "bf16"):
+        cfg = base_cfg.replace(precision=synth.PREC_FP32 if form == "fp32" else synth.PREC_BF16)
+        W = synth.make_weights(cfg, sharp=args.sharp)
+        res = run_form(cfg, W, scene, args.steps, args.warmup, rank, world, dev, peaks)
+        results[form] = (cfg, res)
+        fps = world * args.steps / (res["total_ms"] * 1e-3)
+        lat = sorted(res["lat"])
+        forms[form] = {"fps": round(fps, 2), "ms_per_step": round(res["total_ms"] / args.steps, 3),
+                       "p50_ms": round(statistics.median(lat), 3),
+                       "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                       "e2e_fps": round(world * args.steps / res["e2e_s"], 2)}
+
+    # accuracy of each form against the oracle on sampled windows (rank 0)
+    if rank == 0:
+        import numpy as np
+        from oracle import quark_oracle as O
+        rects = [(0, 4, 0, 4), (538, 542, 958, 962), (1076, 1080, 1916, 1920)]
+        W = synth.make_weights(base_cfg, sharp=args.sharp)
+        refs = [O.forward(base_cfg, W, scene, r)[0] for r in rects]
+        for form, (cfg, res) in results.items():
+            errs, sq, n = [], 0.0, 0
+            for r, ref in zip(rects, refs):
+                d = res["rgba"][r[0]:r[1], r[2]:r[3]].astype(np.float64) - ref
+                errs.append(float(np.abs(d).max()))
+                sq += float((d ** 2).sum())
+                n += d.size
+            mse = sq / n
+            forms[form]["max_abs_vs_oracle"] = float(f"{max(errs):.3g}")
+            forms[form]["psnr_db_vs_oracle"] = round(10 * np.log10(1 / mse), 1) if mse > 0 else None
+
+    head = args.form
+    cfg, res = results[head]
+    f = forms[head]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cfg64 = base_cfg.replace(precision=synth.PREC_FP32)
+        fps_cpu, secs, desc = oracle_sample(cfg64, synth.make_weights(cfg64, sharp=args.sharp), scene, rows=2)
+        cpu = {"value": round(fps_cpu, 6), "unit": "frames/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": desc, "seconds": round(secs, 1)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": f["fps"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32",
+            "data": "synthetic (seeded ray-cast scene of 20 textured primitives; random-init weights N(0,0.02))",
+            "config": {"workload": WORKLOAD, "form": head, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (2.8 GB pyramid per frame), no flush"},
+            "latency_ms": {"p50": f["p50_ms"], "p99": f["p99_ms"]},
+            "forms": forms,
+            "e2e": {"value": f["e2e_fps"], "unit": "frames/s", "h2d_bytes_per_step": res["h2d"],
+                    "d2h_bytes_per_step": res["d2h"]},
+            "roofline": roofline(cfg, V, img_h, img_w, res, peaks),
+            "cpu_baseline": cpu,
+            "clocks": res["clocks"],
+            "gpu_launches": res["launches"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

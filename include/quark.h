@@ -1,0 +1,220 @@
+/*
+ * quark.h -- C ABI of the B300 (sm_103a) implementation of Quark's Update & Fuse steps and
+ * final LDM render (Flynn et al., "Quark: Real-time, High-resolution, and General Neural
+ * View Synthesis", 2024).
+ *
+ * Problem statement (Sec. 2 and Sec. 3): posed input images with intrinsics/extrinsics in,
+ * novel-view RGB out.  Network weights are passed in (random-init tensors; no checkpoint
+ * exists).  All compute runs in this library's CUDA kernels on one GPU; there is no CPU
+ * fallback.
+ *
+ * Conventions shared by every entry point:
+ *   - Pixel centres sit at (x + 0.5, y + 0.5).  Camera frame: x right, y down, z forward.
+ *     Extrinsics are world->camera, X_c = R X_w + t (R row-major).  Depth is camera z.
+ *   - A pyramid level k has intrinsics diag(1/k, 1/k, 1) K.  Scale j of an LDM uses pyramid
+ *     level k_j and a grid of (target.height / k_j, target.width / k_j) pixels.
+ *   - Layer l = 1..L, l = 1 farthest, l = L nearest (Sec. 3.2.3, depth anchors).
+ *   - Device arrays are dense, row-major, channel-last; element types are float32 unless
+ *     stated.  Every GPU call is asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).
+ *   - Errors are return codes; nothing aborts and nothing throws across the ABI.  A failing
+ *     call leaves its outputs unspecified and stores a message readable with quark_last_error.
+ *   - A context and its handles are used from one host thread at a time, except the
+ *     quark_serve_* calls, which are thread-safe.
+ */
+#ifndef QUARK_H
+#define QUARK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QUARK_OK = 0,
+    QUARK_EINVAL = 1,     /* bad argument: sizes, shapes, non-finite camera, NULL pointer */
+    QUARK_ENOMEM = 2,     /* device allocation failed or the HBM cap would be exceeded */
+    QUARK_ECUDA = 3,      /* a CUDA runtime call failed (message names it) */
+    QUARK_EAGAIN = 4,     /* result not ready yet (serve poll) */
+    QUARK_ETIMEDOUT = 5,  /* a bounded wait ran out */
+    QUARK_ENOTFOUND = 6,  /* unknown ticket / time step */
+    QUARK_EBUSY = 7,      /* queue full or handle in use */
+    QUARK_EINTERNAL = 8
+} quark_status;
+
+#define QUARK_MAX_SCALES 8
+#define QUARK_MAX_VIEWS 32
+
+enum { QUARK_FP32 = 0, QUARK_BF16 = 1 };             /* storage / tensor-core precision form */
+enum { QUARK_ATTN_ONE_TO_MANY = 0 };                  /* Sec. 3.3 "Optimized Attention" */
+
+/* Pinhole camera (Sec. 3.1: camera parameters theta).  R row-major, world->camera. */
+typedef struct {
+    int width, height;
+    double fx, fy, cx, cy;
+    double R[9];
+    double t[3];
+} quark_camera;
+
+/* Network shape (Sec. 3.2; tables "Model description for Quark / Quark+").
+ *   C          channels of features, pyramid and feature volume: 16, 32 or 64
+ *   heads      one-to-many attention heads h: 1, 2 or 4 (per-head width C, appendix A)
+ *   n_scales   number of Update & Fuse steps, 1..8
+ *   k[j], L[j] pyramid factor and LDM layer count of step j, coarse to fine.  k in {1,2,4,8};
+ *              k[j-1]/k[j] in {1,2} (x2 spatial upsample); L[j-1]/L[j] in {1,2} (layer
+ *              collapse, Sec. 3.2.2); L <= 64.  The final render upsamples by s = k[n-1].
+ *   near_m, far_m  near and far planes eta and f of Eq. (depth_activation), 0 < near < far
+ *   precision  QUARK_FP32 (all storage and arithmetic FP32) or QUARK_BF16 (pyramid and
+ *              feature volume stored in BF16, contractions on tensor cores with FP32
+ *              accumulation; geometry, softmax and transmittance stay FP32)
+ *   hbm_cap_bytes  cap on this context's device allocations (0 = no cap)              */
+typedef struct {
+    int C, heads, n_scales;
+    int k[QUARK_MAX_SCALES];
+    int L[QUARK_MAX_SCALES];
+    float near_m, far_m;
+    int precision;
+    int attn_mode;
+    size_t hbm_cap_bytes;
+} quark_config;
+
+/* Host FP32 weights, row-vector convention y = x W + b.  Copied (and packed) by
+ * quark_load_weights; the caller keeps ownership.  Shapes for C channels and h heads:
+ *   enc_w [3][3][3][C] (dy, dx, c_in, c_out), enc_b [C]   encoder conv (Sec. 3.2.1)
+ *   v0 [C]                                              learned initial feature (Sec. 3.2.2)
+ *   per step j:
+ *     attn_g[j] [C], Wq[j] [C][h*C], Wo[j] [h*C][C]      RMSNorm gain, one-to-many attention
+ *     conv_g[j] [C], conv1_w[j], conv2_w[j] [3][3][C][C], conv1_b[j], conv2_b[j] [C]
+ *                                                       residual conv block (Sec. 3.3)
+ *     col_w1[j] [2C][C], col_b1[j] [C], col_w2[j] [C][C], col_b2[j] [C]
+ *                                                       layer collapse into step j (Sec. 3.2.2);
+ *                                                       may be NULL where L does not halve
+ *   w_d [C], b_d; w_sigma [C], b_sigma; W_a [C][3], b_a [3]   depth, density, appearance
+ *   W_beta [C][C]                                       blend-logit query of the last step   */
+typedef struct {
+    const float* enc_w;
+    const float* enc_b;
+    const float* v0;
+    const float* attn_g[QUARK_MAX_SCALES];
+    const float* Wq[QUARK_MAX_SCALES];
+    const float* Wo[QUARK_MAX_SCALES];
+    const float* conv_g[QUARK_MAX_SCALES];
+    const float* conv1_w[QUARK_MAX_SCALES];
+    const float* conv1_b[QUARK_MAX_SCALES];
+    const float* conv2_w[QUARK_MAX_SCALES];
+    const float* conv2_b[QUARK_MAX_SCALES];
+    const float* col_w1[QUARK_MAX_SCALES];
+    const float* col_b1[QUARK_MAX_SCALES];
+    const float* col_w2[QUARK_MAX_SCALES];
+    const float* col_b2[QUARK_MAX_SCALES];
+    const float* w_d;
+    float b_d;
+    const float* w_sigma;
+    float b_sigma;
+    const float* W_a;
+    const float* b_a;
+    const float* W_beta;
+} quark_weights;
+
+typedef struct quark_ctx quark_ctx;
+typedef struct quark_pyramid quark_pyramid;
+typedef struct quark_ldm quark_ldm;
+
+/* Create a context on CUDA device `device` (made current for the call).  Validates the
+ * config (EINVAL).  No device memory is allocated until weights or handles are made. */
+quark_status quark_create(const quark_config* cfg, int device, quark_ctx** out);
+
+/* Free a context and every device buffer it owns.  Handles made from it must be released
+ * first.  NULL is accepted. */
+quark_status quark_destroy(quark_ctx* ctx);
+
+/* Copy (and pack for the kernels) the network weights.  Synchronous. */
+quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* w);
+
+/* Encode Input Images (Sec. 3.2.1): F_1 = conv3x3(I) (3 -> C, zero pad, bias, no
+ * activation), F_2k = 2x2 mean pool of F_k, for every level some step uses.  Also keeps a
+ * padded RGBA copy of the images for the final render (Eq. 1 samples the input images).
+ *   images  [V][H][W][3] float32 in [0, 1]; device memory, or host memory (pinned for an
+ *           asynchronous copy), which is then copied in on `stream`
+ *   cams    V host cameras; all views share one resolution W x H, divisible by every k
+ *   V       1..32
+ * If *out is NULL on entry, a new pyramid is allocated ([V][H/k][W/k][C] per level, FP32 or
+ * BF16 by the precision form) and returned in *out; free it with quark_release_pyramid.  If
+ * *out holds a pyramid of this context with the same V and resolution, it is re-encoded in
+ * place (new images and cameras, e.g. the next video frame) without allocating; its previous
+ * contents must no longer be in use on another stream.  `images` may be reused once the
+ * stream has passed this call. */
+quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images, const quark_camera* cams, int V,
+                                  void* stream, quark_pyramid** out);
+
+/* Allocate an LDM (feature volume, decoded attributes and blend logits for every step)
+ * in the frustum of the novel view `target` (Sec. 3.1).  target->width/height is the
+ * output resolution and must be divisible by every k. */
+quark_status quark_ldm_create(quark_ctx* ctx, const quark_camera* target, quark_ldm** out);
+
+/* One Update & Fuse step (Sec. 3.2.2, Fig. "Update & Fuse Step"; Sec. 3.3), step `scale`
+ * (steps run in order 0..n_scales-1 on one LDM):
+ *   transition   step 0: broadcast v0, layers flat at the depth anchors; step j > 0: layer
+ *                collapse when L halves, then x2 bilinear upsample when k halves
+ *   back-project decode depth (Eq. depth_activation), unproject each LDM pixel x layer,
+ *                reproject into every view, bilinearly sample its level-k features (zero pad)
+ *   fusion block V += MultiHead(N(V), Delta) (one-to-many, Sec. 3.3), then
+ *                V += Conv(gelu(Conv(N(V)))) (3x3 per layer plane)
+ *   decode       colour = sigmoid(V W_a + b_a), alpha = sigmoid(V w_sigma + b_sigma),
+ *                depth (Eq. depth_activation); the last step also writes the blend logits
+ *                (Sec. 3.2.3) and the raw depth / density logits for the render. */
+quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int scale, quark_ldm* ldm,
+                               void* stream);
+
+/* Final render (Sec. 3.1 Eq. 1; Sec. 3.2.3 "Upsampling & Activation"): bilinear upsample by
+ * s of the raw depth, density and blend logits, activation, back-projection of the input
+ * images onto the layers, blend with softmax(beta), over-composite front to back.
+ *   rgba  [H_out][W_out][4] float32: RGB and accumulated alpha (black background); device
+ *         memory, or host memory (copied out on `stream`; synchronise before reading). */
+quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, float* rgba,
+                              void* stream);
+
+/* Convenience: every Update & Fuse step then the render, for one novel view. */
+quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, quark_ldm* ldm, float* rgba,
+                                     void* stream);
+
+/* Fields of an LDM readable for inspection (state after the latest quark_update_fuse). */
+enum {
+    QUARK_FIELD_VOLUME = 0,       /* [L][H][W][C] feature volume after the step (FP32 out)    */
+    QUARK_FIELD_VOLUME_ATTN = 1,  /* [L][H][W][C] after the attention block, before the conv  */
+    QUARK_FIELD_COLOUR = 2,       /* [L][H][W][3] appearance c                                 */
+    QUARK_FIELD_ALPHA = 3,        /* [L][H][W] density (alpha)                                  */
+    QUARK_FIELD_DEPTH = 4,        /* [L][H][W] depth in metres                                 */
+    QUARK_FIELD_BETA_LOGITS = 5,  /* [H][W][L][V] blend logits (last step only)                 */
+    QUARK_FIELD_DEPTH_LOGIT = 6,  /* [H][W][L] raw depth logit t = V w_d + b_d                  */
+    QUARK_FIELD_DENSITY_LOGIT = 7 /* [H][W][L] raw density logit                                */
+};
+
+/* Copy one field of the LDM's latest step into host memory `dst` of `bytes` bytes
+ * (synchronous; EINVAL if `bytes` differs from the field's size, which
+ * quark_ldm_field_bytes returns). */
+quark_status quark_ldm_read(quark_ldm* ldm, int field, void* dst, size_t bytes);
+size_t quark_ldm_field_bytes(const quark_ldm* ldm, int field);
+
+quark_status quark_release_pyramid(quark_pyramid* pyr);
+quark_status quark_release_ldm(quark_ldm* ldm);
+
+/* Last error message of a context (or of the calling thread when ctx is NULL). */
+const char* quark_last_error(const quark_ctx* ctx);
+
+/* Kernel accounting.  quark_launch_count returns the number of kernels this context has
+ * launched since creation or the last reset.  With profiling on, every launch is bracketed
+ * by CUDA events on its own stream and quark_kernel_times (which synchronises) returns, per
+ * kernel family, the number of launches and the summed device time in ms.  names receives
+ * at most `cap` entries; returns the number of families. */
+uint64_t quark_launch_count(const quark_ctx* ctx);
+void quark_reset_counters(quark_ctx* ctx);
+quark_status quark_set_profiling(quark_ctx* ctx, int enable);
+int quark_kernel_times(quark_ctx* ctx, const char** names, double* ms, uint64_t* launches, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QUARK_H */

@@ -1,0 +1,60 @@
+"""Algorithmic (compulsory) bytes and FLOPs of each kernel family for one novel view.
+
+Bytes count every tensor a kernel must read or write once: the feature volume entering and
+leaving a step, the pyramid level it samples (each texel once), the decoded attributes, the
+blend logits, the images and the output.  FLOPs count the multiply-adds of the definition
+(2 per MAC) plus nothing for activations.  These are the numerators of the roofline fractions
+the bench reports; measured DRAM traffic above them means re-reads.
+"""
+from __future__ import annotations
+
+from typing import Dict
+
+
+def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, float]]:
+    C, h = cfg.C, cfg.heads
+    elt = 2 if cfg.precision == 1 else 4
+    out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "launches": 0}
+                                        for k in ("encode", "collapse", "attend", "conv_block", "render")}
+    # encode: images in, every used level out, RGBA copy out
+    e = out["encode"]
+    e["bytes"] += V * img_h * img_w * (3 * 4 + 16)
+    for k in cfg.levels():
+        e["bytes"] += V * (img_h // k) * (img_w // k) * C * elt
+    e["flops"] += 2 * 27 * C * V * img_h * img_w
+    e["launches"] += 1
+    for j, (k, L) in enumerate(cfg.scales):
+        H, W = cfg.out_h // k, cfg.out_w // k
+        E = L * H * W
+        last = j == cfg.n_scales - 1
+        a = out["attend"]
+        vin = 0
+        if j > 0:
+            kp, Lp = cfg.scales[j - 1]
+            Hp, Wp = cfg.out_h // kp, cfg.out_w // kp
+            vin = L * Hp * Wp * C * elt
+            if Lp == 2 * L:
+                c = out["collapse"]
+                c["bytes"] += (Lp + L) * Hp * Wp * C * elt
+                c["flops"] += 2 * 3 * C * C * L * Hp * Wp
+                c["launches"] += 1
+        a["bytes"] += vin + V * (img_h // k) * (img_w // k) * C * elt + E * C * elt + (E * V * 4 if last else 0)
+        macs = 2 * h * C * C + 2 * V * h * C + 4 * V * C + (C * C + V * C if last else 0)
+        a["flops"] += 2 * macs * E
+        a["launches"] += 1
+        cb = out["conv_block"]
+        cb["bytes"] += 2 * E * C * elt + E * 7 * 4
+        cb["flops"] += 2 * (18 * C * C + 5 * C) * E
+        cb["launches"] += 1
+    k, L = cfg.scales[-1]
+    Hl, Wl = cfg.out_h // k, cfg.out_w // k
+    r = out["render"]
+    r["bytes"] += L * Hl * Wl * (2 + V) * 4 + V * img_h * img_w * 16 + cfg.out_h * cfg.out_w * 16
+    r["flops"] += 2 * cfg.out_h * cfg.out_w * L * V * 16
+    r["launches"] += 1
+    return out
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, n_sm: int = 148, lanes: int = 128) -> float:
+    """FP32 SIMT peak: n_sm SMs x `lanes` FP32 FMA lanes x 2 FLOP x clock."""
+    return n_sm * lanes * 2 * sm_mhz * 1e6 / 1e12

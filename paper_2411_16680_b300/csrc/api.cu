@@ -1,0 +1,746 @@
+// C ABI of the library (include/quark.h): contexts, validation, weight packing, handles and
+// the per-step launch sequence.  Host code only; the compute is in the k_*.cu kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "quark_internal.cuh"
+#include "api_internal.h"
+
+using namespace quark;
+
+// -------------------------------------------------------------------------------------------
+// Errors
+// -------------------------------------------------------------------------------------------
+
+static thread_local std::string g_thread_error;
+
+quark_status qk_fail(const quark_ctx* ctx, quark_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) const_cast<quark_ctx*>(ctx)->last_error = buf;
+    g_thread_error = buf;
+    return st;
+}
+
+#define QK_CUDA(ctx, call)                                                                       \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* quark_last_error(const quark_ctx* ctx) {
+    if (ctx) return ctx->last_error.c_str();
+    return g_thread_error.c_str();
+}
+
+// -------------------------------------------------------------------------------------------
+// Device memory with the context's cap
+// -------------------------------------------------------------------------------------------
+
+quark_status qk_alloc(quark_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return QUARK_OK;
+    {
+        std::lock_guard<std::mutex> g(ctx->mem_mu);
+        if (ctx->cfg.hbm_cap_bytes && ctx->bytes + bytes > ctx->cfg.hbm_cap_bytes)
+            return qk_fail(ctx, QUARK_ENOMEM, "allocation of %zu bytes exceeds the HBM cap (%zu of %zu in use)",
+                           bytes, ctx->bytes, ctx->cfg.hbm_cap_bytes);
+        ctx->bytes += bytes;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> g(ctx->mem_mu);
+        ctx->bytes -= bytes;
+        *p = nullptr;
+        cudaGetLastError();
+        return qk_fail(ctx, QUARK_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    return QUARK_OK;
+}
+
+void qk_free(quark_ctx* ctx, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> g(ctx->mem_mu);
+    ctx->bytes -= bytes;
+}
+
+// -------------------------------------------------------------------------------------------
+// Launch accounting
+// -------------------------------------------------------------------------------------------
+
+static const char* kFamilyNames[KF_COUNT] = {"encode", "collapse", "attend", "conv_block", "render"};
+
+static cudaEvent_t get_event(quark_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+quark_status qk_launch(quark_ctx* ctx, cudaStream_t st, KernelFamily fam, const std::function<cudaError_t()>& fn) {
+    cudaEvent_t e0 = nullptr;
+    if (ctx->profiling) {
+        e0 = get_event(ctx);
+        cudaEventRecord(e0, st);
+    }
+    cudaError_t err = fn();
+    ctx->launches++;
+    if (ctx->profiling) {
+        cudaEvent_t e1 = get_event(ctx);
+        cudaEventRecord(e1, st);
+        ctx->pending.push_back({fam, e0, e1});
+    }
+    if (err != cudaSuccess)
+        return qk_fail(ctx, QUARK_ECUDA, "launch of %s kernel failed: %s", kFamilyNames[fam], cudaGetErrorString(err));
+    return QUARK_OK;
+}
+
+extern "C" uint64_t quark_launch_count(const quark_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" void quark_reset_counters(quark_ctx* ctx) {
+    if (!ctx) return;
+    ctx->launches = 0;
+    for (auto& p : ctx->pending) {
+        cudaEventSynchronize(p.e1);
+        ctx->event_pool.push_back(p.e0);
+        ctx->event_pool.push_back(p.e1);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < KF_COUNT; ++i) {
+        ctx->fam_ms[i] = 0.0;
+        ctx->fam_n[i] = 0;
+    }
+}
+
+extern "C" quark_status quark_set_profiling(quark_ctx* ctx, int enable) {
+    if (!ctx) return qk_fail(nullptr, QUARK_EINVAL, "NULL context");
+    ctx->profiling = enable != 0;
+    return QUARK_OK;
+}
+
+extern "C" int quark_kernel_times(quark_ctx* ctx, const char** names, double* ms, uint64_t* launches, int cap) {
+    if (!ctx) return 0;
+    for (auto& p : ctx->pending) {
+        cudaEventSynchronize(p.e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, p.e0, p.e1);
+        ctx->fam_ms[p.fam] += t;
+        ctx->fam_n[p.fam] += 1;
+        ctx->event_pool.push_back(p.e0);
+        ctx->event_pool.push_back(p.e1);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < KF_COUNT && i < cap; ++i) {
+        if (names) names[i] = kFamilyNames[i];
+        if (ms) ms[i] = ctx->fam_ms[i];
+        if (launches) launches[i] = ctx->fam_n[i];
+    }
+    return KF_COUNT;
+}
+
+// -------------------------------------------------------------------------------------------
+// Context
+// -------------------------------------------------------------------------------------------
+
+static bool is_pow2_factor(int k) { return k == 1 || k == 2 || k == 4 || k == 8; }
+
+quark_status qk_validate_config(const quark_config* c) {
+    if (!c) return qk_fail(nullptr, QUARK_EINVAL, "NULL config");
+    if (c->C != 16 && c->C != 32) return qk_fail(nullptr, QUARK_EINVAL, "C must be 16 or 32 (got %d)", c->C);
+    if (c->heads != 1 && c->heads != 2 && c->heads != 4)
+        return qk_fail(nullptr, QUARK_EINVAL, "heads must be 1, 2 or 4 (got %d)", c->heads);
+    if (c->n_scales < 1 || c->n_scales > QUARK_MAX_SCALES)
+        return qk_fail(nullptr, QUARK_EINVAL, "n_scales must be 1..%d", QUARK_MAX_SCALES);
+    for (int j = 0; j < c->n_scales; ++j) {
+        if (!is_pow2_factor(c->k[j])) return qk_fail(nullptr, QUARK_EINVAL, "k[%d] must be 1, 2, 4 or 8", j);
+        if (c->L[j] < 1 || c->L[j] > 64) return qk_fail(nullptr, QUARK_EINVAL, "L[%d] must be 1..64", j);
+        if (j > 0) {
+            if (c->k[j - 1] != c->k[j] && c->k[j - 1] != 2 * c->k[j])
+                return qk_fail(nullptr, QUARK_EINVAL, "k[%d]/k[%d] must be 1 or 2", j - 1, j);
+            if (c->L[j - 1] != c->L[j] && c->L[j - 1] != 2 * c->L[j])
+                return qk_fail(nullptr, QUARK_EINVAL, "L[%d]/L[%d] must be 1 or 2", j - 1, j);
+        }
+    }
+    if (!(c->near_m > 0.f) || !(c->far_m > c->near_m) || !std::isfinite(c->far_m))
+        return qk_fail(nullptr, QUARK_EINVAL, "need 0 < near < far < inf");
+    if (c->precision != QUARK_FP32 && c->precision != QUARK_BF16)
+        return qk_fail(nullptr, QUARK_EINVAL, "unknown precision %d", c->precision);
+    if (c->attn_mode != QUARK_ATTN_ONE_TO_MANY) return qk_fail(nullptr, QUARK_EINVAL, "unknown attention mode");
+    return QUARK_OK;
+}
+
+extern "C" quark_status quark_create(const quark_config* cfg, int device, quark_ctx** out) {
+    if (!out) return qk_fail(nullptr, QUARK_EINVAL, "NULL out");
+    *out = nullptr;
+    quark_status s = qk_validate_config(cfg);
+    if (s != QUARK_OK) return s;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) return qk_fail(nullptr, QUARK_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= n) return qk_fail(nullptr, QUARK_EINVAL, "device %d out of range", device);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return qk_fail(nullptr, QUARK_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    quark_ctx* ctx = new quark_ctx();
+    ctx->cfg = *cfg;
+    ctx->device = device;
+    *out = ctx;
+    return QUARK_OK;
+}
+
+extern "C" quark_status quark_destroy(quark_ctx* ctx) {
+    if (!ctx) return QUARK_OK;
+    cudaSetDevice(ctx->device);
+    for (auto& p : ctx->pending) {
+        cudaEventSynchronize(p.e1);
+        ctx->event_pool.push_back(p.e0);
+        ctx->event_pool.push_back(p.e1);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    qk_free(ctx, ctx->wdev, ctx->wbytes);
+    delete ctx;
+    return QUARK_OK;
+}
+
+// -------------------------------------------------------------------------------------------
+// Weights: packed into one device blob per context
+// -------------------------------------------------------------------------------------------
+
+extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* w) {
+    if (!ctx || !w) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    cudaSetDevice(ctx->device);
+    const quark_config& c = ctx->cfg;
+    const int C = c.C, h = c.heads;
+    auto need = [&](const void* p, const char* name) -> bool {
+        if (!p) {
+            qk_fail(ctx, QUARK_EINVAL, "weight %s is NULL", name);
+            return false;
+        }
+        return true;
+    };
+    if (!need(w->enc_w, "enc_w") || !need(w->enc_b, "enc_b") || !need(w->v0, "v0") || !need(w->w_d, "w_d") ||
+        !need(w->w_sigma, "w_sigma") || !need(w->W_a, "W_a") || !need(w->b_a, "b_a") || !need(w->W_beta, "W_beta"))
+        return QUARK_EINVAL;
+    std::vector<float> blob;
+    auto put = [&](const float* p, size_t n) {
+        size_t off = blob.size();
+        blob.insert(blob.end(), p, p + n);
+        return off;
+    };
+    auto pad4 = [&]() {
+        while (blob.size() % 4) blob.push_back(0.f);
+    };
+    ctx->off_enc = put(w->enc_w, 27 * (size_t)C);
+    put(w->enc_b, C);
+    pad4();
+    for (int j = 0; j < c.n_scales; ++j) {
+        if (!need(w->attn_g[j], "attn_g") || !need(w->Wq[j], "Wq") || !need(w->Wo[j], "Wo") ||
+            !need(w->conv_g[j], "conv_g") || !need(w->conv1_w[j], "conv1_w") || !need(w->conv1_b[j], "conv1_b") ||
+            !need(w->conv2_w[j], "conv2_w") || !need(w->conv2_b[j], "conv2_b"))
+            return QUARK_EINVAL;
+        // attend block: v0, g, w_d, b_d (padded to C), Wq, Wo, W_beta
+        const AttendLayout al{C, h};
+        ctx->off_attend[j] = blob.size();
+        put(w->v0, C);
+        put(w->attn_g[j], C);
+        put(w->w_d, C);
+        blob.push_back(w->b_d);
+        for (int i = 1; i < C; ++i) blob.push_back(0.f);
+        put(w->Wq[j], (size_t)C * h * C);
+        put(w->Wo[j], (size_t)h * C * C);
+        put(w->W_beta, (size_t)C * C);
+        if (blob.size() - ctx->off_attend[j] != (size_t)al.total()) return qk_fail(ctx, QUARK_EINTERNAL, "attend layout");
+        pad4();
+        // conv block: g, W1, b1, W2, b2, w_d, w_s, W_a, b_a, b_d, b_s (+3 pad)
+        const ConvLayout cl{C};
+        ctx->off_conv[j] = blob.size();
+        put(w->conv_g[j], C);
+        put(w->conv1_w[j], 9 * (size_t)C * C);
+        put(w->conv1_b[j], C);
+        put(w->conv2_w[j], 9 * (size_t)C * C);
+        put(w->conv2_b[j], C);
+        put(w->w_d, C);
+        put(w->w_sigma, C);
+        put(w->W_a, 3 * (size_t)C);
+        put(w->b_a, 3);
+        blob.push_back(w->b_d);
+        blob.push_back(w->b_sigma);
+        blob.push_back(0.f);
+        blob.push_back(0.f);
+        blob.push_back(0.f);
+        if (blob.size() - ctx->off_conv[j] != (size_t)cl.total()) return qk_fail(ctx, QUARK_EINTERNAL, "conv layout");
+        pad4();
+        ctx->off_collapse[j] = (size_t)-1;
+        if (j > 0 && c.L[j - 1] == 2 * c.L[j]) {
+            if (!need(w->col_w1[j], "col_w1") || !need(w->col_b1[j], "col_b1") || !need(w->col_w2[j], "col_w2") ||
+                !need(w->col_b2[j], "col_b2"))
+                return QUARK_EINVAL;
+            ctx->off_collapse[j] = blob.size();
+            put(w->col_w1[j], 2 * (size_t)C * C);
+            put(w->col_b1[j], C);
+            put(w->col_w2[j], (size_t)C * C);
+            put(w->col_b2[j], C);
+            pad4();
+        }
+    }
+    for (float f : blob)
+        if (!std::isfinite(f)) return qk_fail(ctx, QUARK_EINVAL, "non-finite weight");
+    qk_free(ctx, ctx->wdev, ctx->wbytes);
+    ctx->wdev = nullptr;
+    ctx->wbytes = blob.size() * sizeof(float);
+    quark_status s = qk_alloc(ctx, (void**)&ctx->wdev, ctx->wbytes);
+    if (s != QUARK_OK) return s;
+    QK_CUDA(ctx, cudaMemcpy(ctx->wdev, blob.data(), ctx->wbytes, cudaMemcpyHostToDevice));
+    ctx->weights_loaded = true;
+    return QUARK_OK;
+}
+
+// -------------------------------------------------------------------------------------------
+// Cameras and geometry
+// -------------------------------------------------------------------------------------------
+
+quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what) {
+    bool ok = c.width > 0 && c.height > 0 && std::isfinite(c.fx) && std::isfinite(c.fy) && c.fx > 0 && c.fy > 0 &&
+              std::isfinite(c.cx) && std::isfinite(c.cy);
+    for (int i = 0; i < 9; ++i) ok = ok && std::isfinite(c.R[i]);
+    for (int i = 0; i < 3; ++i) ok = ok && std::isfinite(c.t[i]);
+    if (!ok) return qk_fail(ctx, QUARK_EINVAL, "%s camera is not a finite pinhole camera", what);
+    // R must be a rotation (orthonormal, det +1) to 1e-6
+    double rrt[9] = {0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) rrt[3 * i + j] += c.R[3 * i + k] * c.R[3 * j + k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (std::fabs(rrt[3 * i + j] - (i == j ? 1.0 : 0.0)) > 1e-6)
+                return qk_fail(ctx, QUARK_EINVAL, "%s camera R is not orthonormal", what);
+    return QUARK_OK;
+}
+
+// A = K_m R_m R_t^T K_t^-1 and b = K_m (t_m - R_m R_t^T t_t), both grids scaled by 1/k.
+ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m) {
+    double Kt_inv[9] = {k_t / tgt.fx, 0, -tgt.cx / tgt.fx, 0, k_t / tgt.fy, -tgt.cy / tgt.fy, 0, 0, 1};
+    double Km[9] = {view.fx / k_m, 0, view.cx / k_m, 0, view.fy / k_m, view.cy / k_m, 0, 0, 1};
+    double Rrel[9] = {0};  // R_m R_t^T
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) Rrel[3 * i + j] += view.R[3 * i + k] * tgt.R[3 * j + k];
+    double M[9] = {0}, A[9] = {0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) M[3 * i + j] += Km[3 * i + k] * Rrel[3 * k + j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) A[3 * i + j] += M[3 * i + k] * Kt_inv[3 * k + j];
+    double tr[3];
+    for (int i = 0; i < 3; ++i) {
+        tr[i] = view.t[i];
+        for (int k = 0; k < 3; ++k) tr[i] -= Rrel[3 * i + k] * tgt.t[k];
+    }
+    ViewMap vm;
+    for (int i = 0; i < 9; ++i) vm.A[i] = (float)A[i];
+    for (int i = 0; i < 3; ++i) {
+        double b = 0;
+        for (int k = 0; k < 3; ++k) b += Km[3 * i + k] * tr[k];
+        vm.b[i] = (float)b;
+    }
+    return vm;
+}
+
+// -------------------------------------------------------------------------------------------
+// Pyramid
+// -------------------------------------------------------------------------------------------
+
+static bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void pyramid_free(quark_pyramid* p) {
+    quark_ctx* ctx = p->ctx;
+    for (int i = 0; i < 4; ++i) qk_free(ctx, p->level[i], p->level_bytes[i]);
+    qk_free(ctx, p->rgba, p->rgba_bytes);
+    qk_free(ctx, p->staging, p->staging_bytes);
+    delete p;
+}
+
+extern "C" quark_status quark_release_pyramid(quark_pyramid* pyr) {
+    if (!pyr) return QUARK_OK;
+    cudaSetDevice(pyr->ctx->device);
+    pyramid_free(pyr);
+    return QUARK_OK;
+}
+
+static int level_index(int k) { return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3; }
+
+extern "C" quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images, const quark_camera* cams, int V,
+                                             void* stream, quark_pyramid** out) {
+    if (!ctx || !images || !cams || !out) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
+    if (V < 1 || V > QUARK_MAX_VIEWS) return qk_fail(ctx, QUARK_EINVAL, "V must be 1..%d (got %d)", QUARK_MAX_VIEWS, V);
+    for (int m = 0; m < V; ++m) {
+        quark_status s = qk_validate_camera(ctx, cams[m], "input");
+        if (s != QUARK_OK) return s;
+        if (cams[m].width != cams[0].width || cams[m].height != cams[0].height)
+            return qk_fail(ctx, QUARK_EINVAL, "all views must share one resolution");
+    }
+    const int H = cams[0].height, W = cams[0].width;
+    const quark_config& c = ctx->cfg;
+    for (int j = 0; j < c.n_scales; ++j)
+        if (H % c.k[j] || W % c.k[j])
+            return qk_fail(ctx, QUARK_EINVAL, "image %dx%d not divisible by k=%d", W, H, c.k[j]);
+    quark_pyramid* p = *out;
+    if (p && (p->ctx != ctx || p->V != V || p->H != H || p->W != W))
+        return qk_fail(ctx, QUARK_EINVAL, "existing pyramid has another context, view count or resolution");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fresh = p == nullptr;
+    quark_status s = QUARK_OK;
+    if (fresh) {
+        p = new quark_pyramid();
+        p->ctx = ctx;
+        p->V = V;
+        p->H = H;
+        p->W = W;
+        const size_t elt = c.precision == QUARK_BF16 ? 2 : 4;
+        for (int j = 0; j < c.n_scales && s == QUARK_OK; ++j) {
+            int li = level_index(c.k[j]);
+            if (p->level[li]) continue;
+            p->level_bytes[li] = (size_t)V * (H / c.k[j]) * (W / c.k[j]) * c.C * elt;
+            s = qk_alloc(ctx, &p->level[li], p->level_bytes[li]);
+        }
+        if (s == QUARK_OK) {
+            p->rgba_bytes = (size_t)V * H * W * sizeof(float4);
+            s = qk_alloc(ctx, &p->rgba, p->rgba_bytes);
+        }
+    }
+    p->cams.assign(cams, cams + V);
+    const float* src = images;
+    if (s == QUARK_OK && !is_device_pointer(images)) {
+        if (!p->staging) {
+            p->staging_bytes = (size_t)V * H * W * 3 * sizeof(float);
+            s = qk_alloc(ctx, &p->staging, p->staging_bytes);
+        }
+        if (s == QUARK_OK) {
+            cudaError_t e = cudaMemcpyAsync(p->staging, images, p->staging_bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) s = qk_fail(ctx, QUARK_ECUDA, "image upload: %s", cudaGetErrorString(e));
+            src = (const float*)p->staging;
+        }
+    }
+    if (s == QUARK_OK) {
+        EncodeArgs a{};
+        a.images = src;
+        a.V = V;
+        a.H = H;
+        a.W = W;
+        a.w = ctx->wdev + ctx->off_enc;
+        a.rgba = (float4*)p->rgba;
+        for (int i = 0; i < 4; ++i) a.level[i] = p->level[i];
+        s = qk_launch(ctx, st, KF_ENCODE, [&] { return launch_encode(a, c.C, c.precision == QUARK_BF16, st); });
+    }
+    if (s != QUARK_OK) {
+        if (fresh) pyramid_free(p);
+        return s;
+    }
+    *out = p;
+    return QUARK_OK;
+}
+
+// -------------------------------------------------------------------------------------------
+// LDM
+// -------------------------------------------------------------------------------------------
+
+static void ldm_free(quark_ldm* l) {
+    quark_ctx* ctx = l->ctx;
+    for (auto& b : l->bufs) qk_free(ctx, b.p, b.bytes);
+    delete l;
+}
+
+extern "C" quark_status quark_release_ldm(quark_ldm* ldm) {
+    if (!ldm) return QUARK_OK;
+    cudaSetDevice(ldm->ctx->device);
+    ldm_free(ldm);
+    return QUARK_OK;
+}
+
+static quark_status ldm_buf(quark_ldm* l, void** p, size_t bytes) {
+    quark_status s = qk_alloc(l->ctx, p, bytes);
+    if (s == QUARK_OK) l->bufs.push_back({*p, bytes});
+    return s;
+}
+
+extern "C" quark_status quark_ldm_create(quark_ctx* ctx, const quark_camera* target, quark_ldm** out) {
+    if (!ctx || !target || !out) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    *out = nullptr;
+    quark_status s = qk_validate_camera(ctx, *target, "target");
+    if (s != QUARK_OK) return s;
+    const quark_config& c = ctx->cfg;
+    for (int j = 0; j < c.n_scales; ++j)
+        if (target->height % c.k[j] || target->width % c.k[j])
+            return qk_fail(ctx, QUARK_EINVAL, "output %dx%d not divisible by k=%d", target->width, target->height, c.k[j]);
+    cudaSetDevice(ctx->device);
+    quark_ldm* l = new quark_ldm();
+    l->ctx = ctx;
+    l->target = *target;
+    const size_t elt = c.precision == QUARK_BF16 ? 2 : 4;
+    size_t vmax = 0, emax = 0, cmax = 0;
+    for (int j = 0; j < c.n_scales; ++j) {
+        size_t e = (size_t)c.L[j] * (target->height / c.k[j]) * (target->width / c.k[j]);
+        emax = std::max(emax, e);
+        vmax = std::max(vmax, e * c.C * elt);
+        if (j > 0 && c.L[j - 1] == 2 * c.L[j])
+            cmax = std::max(cmax, (size_t)c.L[j] * (target->height / c.k[j - 1]) * (target->width / c.k[j - 1]) * c.C * elt);
+    }
+    const int n = c.n_scales - 1;
+    const size_t last_e = (size_t)c.L[n] * (target->height / c.k[n]) * (target->width / c.k[n]);
+    s = ldm_buf(l, &l->vol[0], vmax);
+    if (s == QUARK_OK) s = ldm_buf(l, &l->vol[1], vmax);
+    if (s == QUARK_OK) s = ldm_buf(l, &l->vattn, vmax);
+    if (s == QUARK_OK && cmax) s = ldm_buf(l, &l->collapsed, cmax);
+    if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->colour, emax * 3 * sizeof(float));
+    if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->alpha, emax * sizeof(float));
+    if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->depth, emax * sizeof(float));
+    if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->t_raw, emax * sizeof(float));
+    if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->s_raw, emax * sizeof(float));
+    l->last_e = last_e;
+    if (s != QUARK_OK) {
+        ldm_free(l);
+        return s;
+    }
+    *out = l;
+    return QUARK_OK;
+}
+
+static void step_dims(const quark_ldm* l, int j, int& L, int& H, int& W) {
+    const quark_config& c = l->ctx->cfg;
+    L = c.L[j];
+    H = l->target.height / c.k[j];
+    W = l->target.width / c.k[j];
+}
+
+extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int scale, quark_ldm* ldm,
+                                          void* stream) {
+    if (!ctx || !pyr || !ldm) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
+    const quark_config& c = ctx->cfg;
+    if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);
+    if (scale != 0 && ldm->done != scale - 1)
+        return qk_fail(ctx, QUARK_EINVAL, "step %d needs step %d first (latest done: %d)", scale, scale - 1, ldm->done);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool bf16 = c.precision == QUARK_BF16;
+    const bool last = scale == c.n_scales - 1;
+    int L, H, W;
+    step_dims(ldm, scale, L, H, W);
+    const int k = c.k[scale];
+    quark_status s;
+
+    if (last) {
+        size_t need = ldm->last_e * pyr->V * sizeof(float);
+        if (ldm->beta_bytes < need) {
+            for (auto it = ldm->bufs.begin(); it != ldm->bufs.end(); ++it)
+                if (it->p == ldm->beta) {
+                    qk_free(ctx, it->p, it->bytes);
+                    ldm->bufs.erase(it);
+                    break;
+                }
+            ldm->beta = nullptr;
+            s = ldm_buf(ldm, (void**)&ldm->beta, need);
+            if (s != QUARK_OK) return s;
+            ldm->beta_bytes = need;
+        }
+        ldm->V = pyr->V;
+    }
+
+    // ---- transition ----
+    const void* prev = nullptr;
+    int Hp = 0, Wp = 0;
+    Transition tr = TR_INIT;
+    if (scale > 0) {
+        int Lp;
+        step_dims(ldm, scale - 1, Lp, Hp, Wp);
+        prev = ldm->vol[ldm->cur];
+        if (Lp == 2 * L) {
+            CollapseArgs ca{};
+            ca.in = prev;
+            ca.out = ldm->collapsed;
+            ca.L = L;
+            ca.H = Hp;
+            ca.W = Wp;
+            ca.w = ctx->wdev + ctx->off_collapse[scale];
+            s = qk_launch(ctx, st, KF_COLLAPSE, [&] { return launch_collapse(ca, c.C, bf16, st); });
+            if (s != QUARK_OK) return s;
+            prev = ldm->collapsed;
+        }
+        tr = (c.k[scale - 1] == 2 * k) ? TR_UP2 : TR_SAME;
+    }
+
+    // ---- sample-attend ----
+    AttendArgs aa{};
+    aa.prev = prev;
+    aa.Hp = Hp;
+    aa.Wp = Wp;
+    aa.feat = pyr->level[level_index(k)];
+    aa.fh = pyr->H / k;
+    aa.fw = pyr->W / k;
+    aa.L = L;
+    aa.H = H;
+    aa.W = W;
+    aa.V = pyr->V;
+    aa.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+    aa.w = ctx->wdev + ctx->off_attend[scale];
+    aa.out = ldm->vattn;
+    aa.beta = last ? ldm->beta : nullptr;
+    for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
+    s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
+    if (s != QUARK_OK) return s;
+
+    // ---- conv block + decode ----
+    ConvArgs ca{};
+    ca.in = ldm->vattn;
+    ca.out = ldm->vol[1 - ldm->cur];
+    ca.L = L;
+    ca.H = H;
+    ca.W = W;
+    ca.dp = aa.dp;
+    ca.w = ctx->wdev + ctx->off_conv[scale];
+    ca.colour = ldm->colour;
+    ca.alpha = ldm->alpha;
+    ca.depth = ldm->depth;
+    ca.t_raw = ldm->t_raw;
+    ca.s_raw = ldm->s_raw;
+    s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(ca, c.C, bf16, st); });
+    if (s != QUARK_OK) return s;
+    ldm->cur = 1 - ldm->cur;
+    ldm->done = scale;
+    return QUARK_OK;
+}
+
+extern "C" quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, float* rgba,
+                                         void* stream) {
+    if (!ctx || !ldm || !pyr || !rgba) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    const quark_config& c = ctx->cfg;
+    if (ldm->done != c.n_scales - 1) return qk_fail(ctx, QUARK_EINVAL, "render needs every Update & Fuse step first");
+    if (ldm->V != pyr->V) return qk_fail(ctx, QUARK_EINVAL, "pyramid differs from the one the LDM was solved with");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    quark_ldm* l = const_cast<quark_ldm*>(ldm);
+    const int n = c.n_scales - 1;
+    RenderArgs ra{};
+    ra.t_raw = l->t_raw;
+    ra.s_raw = l->s_raw;
+    ra.beta = l->beta;
+    ra.rgba = (const float4*)pyr->rgba;
+    ra.L = c.L[n];
+    ra.V = pyr->V;
+    ra.Hl = l->target.height / c.k[n];
+    ra.Wl = l->target.width / c.k[n];
+    ra.s = c.k[n];
+    ra.Hout = l->target.height;
+    ra.Wout = l->target.width;
+    ra.Hi = pyr->H;
+    ra.Wi = pyr->W;
+    ra.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+    for (int m = 0; m < pyr->V; ++m) ra.geo.v[m] = qk_view_map(l->target, 1.0, pyr->cams[m], 1.0);
+    const size_t out_bytes = (size_t)ra.Hout * ra.Wout * sizeof(float4);
+    const bool host_out = !is_device_pointer(rgba);
+    if (host_out && l->out_bytes < out_bytes) {
+        for (auto it = l->bufs.begin(); it != l->bufs.end(); ++it)
+            if (it->p == l->out) {
+                qk_free(ctx, it->p, it->bytes);
+                l->bufs.erase(it);
+                break;
+            }
+        l->out = nullptr;
+        quark_status s = ldm_buf(l, &l->out, out_bytes);
+        if (s != QUARK_OK) return s;
+        l->out_bytes = out_bytes;
+    }
+    ra.out = host_out ? (float4*)l->out : (float4*)rgba;
+    quark_status s = qk_launch(ctx, st, KF_RENDER, [&] { return launch_render(ra, st); });
+    if (s != QUARK_OK) return s;
+    if (host_out) QK_CUDA(ctx, cudaMemcpyAsync(rgba, l->out, out_bytes, cudaMemcpyDeviceToHost, st));
+    return QUARK_OK;
+}
+
+extern "C" quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, quark_ldm* ldm, float* rgba,
+                                                void* stream) {
+    if (!ctx) return qk_fail(nullptr, QUARK_EINVAL, "NULL context");
+    for (int j = 0; j < ctx->cfg.n_scales; ++j) {
+        quark_status s = quark_update_fuse(ctx, pyr, j, ldm, stream);
+        if (s != QUARK_OK) return s;
+    }
+    return quark_render_ldm(ctx, ldm, pyr, rgba, stream);
+}
+
+// -------------------------------------------------------------------------------------------
+// Inspection
+// -------------------------------------------------------------------------------------------
+
+extern "C" size_t quark_ldm_field_bytes(const quark_ldm* l, int field) {
+    if (!l || l->done < 0) return 0;
+    int L, H, W;
+    step_dims(l, l->done, L, H, W);
+    const size_t e = (size_t)L * H * W;
+    switch (field) {
+        case QUARK_FIELD_VOLUME:
+        case QUARK_FIELD_VOLUME_ATTN: return e * l->ctx->cfg.C * sizeof(float);
+        case QUARK_FIELD_COLOUR: return e * 3 * sizeof(float);
+        case QUARK_FIELD_ALPHA:
+        case QUARK_FIELD_DEPTH:
+        case QUARK_FIELD_DEPTH_LOGIT:
+        case QUARK_FIELD_DENSITY_LOGIT: return e * sizeof(float);
+        case QUARK_FIELD_BETA_LOGITS: return l->done == l->ctx->cfg.n_scales - 1 ? e * l->V * sizeof(float) : 0;
+        default: return 0;
+    }
+}
+
+extern "C" quark_status quark_ldm_read(quark_ldm* l, int field, void* dst, size_t bytes) {
+    if (!l || !dst) return qk_fail(l ? l->ctx : nullptr, QUARK_EINVAL, "NULL argument");
+    quark_ctx* ctx = l->ctx;
+    size_t need = quark_ldm_field_bytes(l, field);
+    if (need == 0 || need != bytes) return qk_fail(ctx, QUARK_EINVAL, "field %d: %zu bytes expected, %zu given", field, need, bytes);
+    cudaSetDevice(ctx->device);
+    QK_CUDA(ctx, cudaDeviceSynchronize());
+    const void* src = nullptr;
+    switch (field) {
+        case QUARK_FIELD_VOLUME: src = l->vol[l->cur]; break;
+        case QUARK_FIELD_VOLUME_ATTN: src = l->vattn; break;
+        case QUARK_FIELD_COLOUR: src = l->colour; break;
+        case QUARK_FIELD_ALPHA: src = l->alpha; break;
+        case QUARK_FIELD_DEPTH: src = l->depth; break;
+        case QUARK_FIELD_BETA_LOGITS: src = l->beta; break;
+        case QUARK_FIELD_DEPTH_LOGIT: src = l->t_raw; break;
+        case QUARK_FIELD_DENSITY_LOGIT: src = l->s_raw; break;
+    }
+    const bool vol = field == QUARK_FIELD_VOLUME || field == QUARK_FIELD_VOLUME_ATTN;
+    if (vol && ctx->cfg.precision == QUARK_BF16) {
+        const size_t n = bytes / sizeof(float);
+        std::vector<uint16_t> tmp(n);
+        QK_CUDA(ctx, cudaMemcpy(tmp.data(), src, n * 2, cudaMemcpyDeviceToHost));
+        float* f = (float*)dst;
+        for (size_t i = 0; i < n; ++i) {
+            uint32_t u = (uint32_t)tmp[i] << 16;
+            std::memcpy(&f[i], &u, 4);
+        }
+    } else {
+        QK_CUDA(ctx, cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    }
+    return QUARK_OK;
+}

@@ -1,0 +1,90 @@
+// Host-side state behind the opaque handles of quark.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <functional>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "quark.h"
+#include "quark_internal.cuh"
+
+enum KernelFamily { KF_ENCODE = 0, KF_COLLAPSE, KF_ATTEND, KF_CONV, KF_RENDER, KF_COUNT };
+
+struct PendingTiming {
+    KernelFamily fam;
+    cudaEvent_t e0, e1;
+};
+
+struct quark_ctx {
+    quark_config cfg{};
+    int device = 0;
+    std::string last_error;
+    // packed weights (device) and the offsets (floats) of each block
+    float* wdev = nullptr;
+    size_t wbytes = 0;
+    bool weights_loaded = false;
+    size_t off_enc = 0;
+    size_t off_attend[QUARK_MAX_SCALES] = {};
+    size_t off_conv[QUARK_MAX_SCALES] = {};
+    size_t off_collapse[QUARK_MAX_SCALES] = {};
+    // device memory accounting against cfg.hbm_cap_bytes
+    std::mutex mem_mu;
+    size_t bytes = 0;
+    // launch accounting / profiling
+    uint64_t launches = 0;
+    bool profiling = false;
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double fam_ms[KF_COUNT] = {};
+    uint64_t fam_n[KF_COUNT] = {};
+};
+
+struct quark_pyramid {
+    quark_ctx* ctx = nullptr;
+    int V = 0, H = 0, W = 0;
+    std::vector<quark_camera> cams;
+    void* level[4] = {};  // k = 1, 2, 4, 8
+    size_t level_bytes[4] = {};
+    void* rgba = nullptr;  // float4 [V][H][W]
+    size_t rgba_bytes = 0;
+    void* staging = nullptr;  // device copy of host images
+    size_t staging_bytes = 0;
+};
+
+struct DevBuf {
+    void* p;
+    size_t bytes;
+};
+
+struct quark_ldm {
+    quark_ctx* ctx = nullptr;
+    quark_camera target{};
+    std::vector<DevBuf> bufs;
+    void* vol[2] = {};
+    int cur = 0;
+    void* vattn = nullptr;
+    void* collapsed = nullptr;
+    float* colour = nullptr;
+    float* alpha = nullptr;
+    float* depth = nullptr;
+    float* t_raw = nullptr;
+    float* s_raw = nullptr;
+    float* beta = nullptr;
+    size_t beta_bytes = 0;
+    void* out = nullptr;  // device staging of a host render target
+    size_t out_bytes = 0;
+    size_t last_e = 0;
+    int V = 0;
+    int done = -1;  // latest Update & Fuse step completed
+};
+
+quark_status qk_fail(const quark_ctx* ctx, quark_status st, const char* fmt, ...);
+quark_status qk_alloc(quark_ctx* ctx, void** p, size_t bytes);
+void qk_free(quark_ctx* ctx, void* p, size_t bytes);
+quark_status qk_launch(quark_ctx* ctx, cudaStream_t st, KernelFamily fam, const std::function<cudaError_t()>& fn);
+quark_status qk_validate_config(const quark_config* c);
+quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what);
+quark::ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m);

@@ -1,0 +1,144 @@
+// Device helpers shared by the kernels: storage-type vector loads/stores (FP32 or BF16
+// storage, FP32 arithmetic), the depth activation, and the bilinear tap rule.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "quark_internal.cuh"
+
+namespace quark {
+
+// ---- 16-channel vector loads/stores in the storage type --------------------------------------
+
+__device__ __forceinline__ void load16(const float* __restrict__ p, float (&o)[16]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float4 v = __ldg(q + i);
+        o[4 * i + 0] = v.x; o[4 * i + 1] = v.y; o[4 * i + 2] = v.z; o[4 * i + 3] = v.w;
+    }
+}
+
+__device__ __forceinline__ void load16(const __nv_bfloat16* __restrict__ p, float (&o)[16]) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        uint4 v = __ldg(q + i);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 f = __bfloat1622float2(h[j]);
+            o[8 * i + 2 * j] = f.x;
+            o[8 * i + 2 * j + 1] = f.y;
+        }
+    }
+}
+
+// accumulate w * p[0..16) into o
+__device__ __forceinline__ void fma16(const float* __restrict__ p, float w, float (&o)[16]) {
+    float t[16];
+    load16(p, t);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = fmaf(w, t[i], o[i]);
+}
+__device__ __forceinline__ void fma16(const __nv_bfloat16* __restrict__ p, float w, float (&o)[16]) {
+    float t[16];
+    load16(p, t);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = fmaf(w, t[i], o[i]);
+}
+
+__device__ __forceinline__ void store16(float* p, const float (&v)[16]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
+__device__ __forceinline__ void store16(__nv_bfloat16* p, const float (&v)[16]) {
+    uint4 u[2];
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    uint4* q = reinterpret_cast<uint4*>(p);
+    q[0] = u[0];
+    q[1] = u[1];
+}
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ void from_f(float& d, float x) { d = x; }
+__device__ __forceinline__ void from_f(__nv_bfloat16& d, float x) { d = __float2bfloat16_rn(x); }
+
+// acc[0..16) += a * r[0..16) with r 16-byte aligned (shared-memory weight rows)
+__device__ __forceinline__ void fma_row16(const float* r, float a, float (&acc)[16]) {
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float4 w = r4[i];
+        acc[4 * i + 0] = fmaf(a, w.x, acc[4 * i + 0]);
+        acc[4 * i + 1] = fmaf(a, w.y, acc[4 * i + 1]);
+        acc[4 * i + 2] = fmaf(a, w.z, acc[4 * i + 2]);
+        acc[4 * i + 3] = fmaf(a, w.w, acc[4 * i + 3]);
+    }
+}
+
+// ---- elementwise definitions ------------------------------------------------------------------
+
+// Eq. (depth_activation): d = 1 / ((delta + 0.5/L tanh t) (1/near - 1/far) + 1/far),
+// delta = (l - 0.5) / L with l = li + 1.
+__device__ __forceinline__ float depth_from_logit(float t, int li, int L, DepthParams dp) {
+    float delta = (li + 0.5f) / L;
+    return 1.0f / fmaf(delta + 0.5f / L * tanhf(t), dp.span, dp.inv_far);
+}
+__device__ __forceinline__ float depth_anchor(int li, int L, DepthParams dp) {
+    return 1.0f / fmaf((li + 0.5f) / L, dp.span, dp.inv_far);
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// Map target-grid pixel (px, py) at depth d into a view; returns false when the point is
+// at or behind the view's camera plane (z <= 1e-6).
+__device__ __forceinline__ bool reproject(const ViewMap& m, float px, float py, float d, float& u, float& v) {
+    float X = fmaf(d, fmaf(m.A[0], px, fmaf(m.A[1], py, m.A[2])), m.b[0]);
+    float Y = fmaf(d, fmaf(m.A[3], px, fmaf(m.A[4], py, m.A[5])), m.b[1]);
+    float Z = fmaf(d, fmaf(m.A[6], px, fmaf(m.A[7], py, m.A[8])), m.b[2]);
+    if (!(Z > 1e-6f)) return false;
+    float iz = 1.0f / Z;
+    u = X * iz;
+    v = Y * iz;
+    return true;
+}
+
+// Bilinear taps with zero padding at continuous pixel coordinates (u, v) of an h x w map
+// (pixel centres at +0.5).  Returns false when no tap can touch the map (the sample is 0).
+struct Taps {
+    int x0, y0;
+    float fx, fy;
+};
+__device__ __forceinline__ bool bilinear_taps(float u, float v, int h, int w, Taps& t) {
+    float xs = u - 0.5f, ys = v - 0.5f;
+    if (!(xs > -1.0f && xs < (float)w && ys > -1.0f && ys < (float)h)) return false;
+    float x0 = floorf(xs), y0 = floorf(ys);
+    t.fx = xs - x0;
+    t.fy = ys - y0;
+    t.x0 = (int)x0;
+    t.y0 = (int)y0;
+    return true;
+}
+
+// Edge-clamped linear taps of a resize by integer `ratio` (pixel centres aligned):
+// src = (dst + 0.5) / ratio - 0.5.
+__device__ __forceinline__ void resize_taps(int dst, int ratio, int n, int& i0, int& i1, float& w1) {
+    float src = (dst + 0.5f) / ratio - 0.5f;
+    float f = floorf(src);
+    w1 = src - f;
+    int a = (int)f;
+    i0 = min(max(a, 0), n - 1);
+    i1 = min(max(a + 1, 0), n - 1);
+}
+
+}  // namespace quark

@@ -1,0 +1,324 @@
+// Transition and one-to-many attention of an Update & Fuse step.
+//
+// collapse_kernel  Layer Collapse (Sec. 3.2.2): pairs (l = 2j-1, 2j) of the previous step's
+//                  volume -> 0.5 (a + b) + W2^T gelu(W1^T [a; b] + b1) + b2.
+// attend_kernel    the fused sample-attend step: volume entering the step (broadcast v0, or the
+//                  previous volume, bilinearly x2-upsampled on the fly) -> decode depth
+//                  (Eq. depth_activation) -> per view: reproject, bilinear-sample the level-k
+//                  feature map (operator P^T, Sec. 3.1) -> RMSNorm, query projection, online
+//                  softmax over views, weighted sum, output projection, residual (Sec. 3.3).
+//                  On the last step it also writes the blend logits (Sec. 3.2.3).
+//
+// Thread mapping: C/16 threads per LDM element, each owning 16 channels of the query, the
+// sampled features and the head outputs; dot products are finished with shuffles inside the
+// group.  Consecutive elements are consecutive x of one layer row, so a warp's samples land
+// on neighbouring texels of each view.
+#include "device_common.cuh"
+
+namespace quark {
+
+// -------------------------------------------------------------------------------------------
+// Layer collapse
+// -------------------------------------------------------------------------------------------
+
+template <typename T, int C>
+__global__ void __launch_bounds__(128) collapse_kernel(CollapseArgs a) {
+    __shared__ float w[3 * C * C + 2 * C];
+    const CollapseLayout lay{C};
+    for (int i = threadIdx.x; i < lay.total(); i += blockDim.x) w[i] = a.w[i];
+    __syncthreads();
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t n = (size_t)a.L * plane;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const size_t j = e / plane, pix = e % plane;
+    const T* pa = reinterpret_cast<const T*>(a.in) + ((2 * j) * plane + pix) * C;
+    const T* pb = reinterpret_cast<const T*>(a.in) + ((2 * j + 1) * plane + pix) * C;
+    float va[C], vb[C];
+#pragma unroll
+    for (int c0 = 0; c0 < C; c0 += 16) {
+        float t[16];
+        load16(pa + c0, t);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) va[c0 + i] = t[i];
+        load16(pb + c0, t);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) vb[c0 + i] = t[i];
+    }
+    float h[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) h[c] = w[lay.b1() + c];
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const float* r0 = &w[lay.w1() + i * C];
+        const float* r1 = &w[lay.w1() + (C + i) * C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) h[c] = fmaf(va[i], r0[c], fmaf(vb[i], r1[c], h[c]));
+    }
+    float o[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) o[c] = 0.5f * (va[c] + vb[c]) + w[lay.b2() + c];
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        float g = gelu_erf(h[i]);
+        const float* r = &w[lay.w2() + i * C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) o[c] = fmaf(g, r[c], o[c]);
+    }
+    T* po = reinterpret_cast<T*>(a.out) + e * C;
+#pragma unroll
+    for (int c0 = 0; c0 < C; c0 += 16) {
+        float t[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) t[i] = o[c0 + i];
+        store16(po + c0, t);
+    }
+}
+
+cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st) {
+    size_t n = (size_t)a.L * a.H * a.W;
+    unsigned grid = (unsigned)((n + 127) / 128);
+    if (C == 16) {
+        if (bf16) collapse_kernel<__nv_bfloat16, 16><<<grid, 128, 0, st>>>(a);
+        else collapse_kernel<float, 16><<<grid, 128, 0, st>>>(a);
+    } else if (C == 32) {
+        if (bf16) collapse_kernel<__nv_bfloat16, 32><<<grid, 128, 0, st>>>(a);
+        else collapse_kernel<float, 32><<<grid, 128, 0, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------------------------------
+// Sample-attend
+// -------------------------------------------------------------------------------------------
+
+constexpr int ATT_THREADS = 128;
+
+template <typename T, int C, int NH, int TR, bool LAST>
+__global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a) {
+    constexpr int TPE = C / 16;  // threads per element
+    const AttendLayout lay{C, NH};
+    extern __shared__ float4 sw4[];
+    float* sw = reinterpret_cast<float*>(sw4);
+    for (int i = threadIdx.x; i < lay.total(); i += blockDim.x) sw[i] = a.w[i];
+    __syncthreads();
+
+    const int L = a.L, H = a.H, W = a.W;
+    const size_t n = (size_t)L * H * W;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = (int)(gid % TPE);
+    size_t e = gid / TPE;
+    const bool live = e < n;
+    if (!live) e = n - 1;  // keep the group's lanes in the shuffles; no stores
+    const int li = (int)(e / ((size_t)H * W));
+    const int y = (int)((e / W) % H);
+    const int x = (int)(e % W);
+    const int c0 = sub * 16;
+
+    // ---- volume entering the step ----
+    float vin[C];
+    if (TR == TR_INIT) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) vin[c] = sw[lay.v0() + c];
+    } else if (TR == TR_SAME) {
+        const T* p = reinterpret_cast<const T*>(a.prev) + e * C;
+#pragma unroll
+        for (int cc = 0; cc < C; cc += 16) {
+            float t[16];
+            load16(p + cc, t);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vin[cc + i] = t[i];
+        }
+    } else {
+        int y0, y1, x0, x1;
+        float wy, wx;
+        resize_taps(y, 2, a.Hp, y0, y1, wy);
+        resize_taps(x, 2, a.Wp, x0, x1, wx);
+        const T* base = reinterpret_cast<const T*>(a.prev) + (size_t)li * a.Hp * a.Wp * C;
+        const T* p00 = base + ((size_t)y0 * a.Wp + x0) * C;
+        const T* p01 = base + ((size_t)y0 * a.Wp + x1) * C;
+        const T* p10 = base + ((size_t)y1 * a.Wp + x0) * C;
+        const T* p11 = base + ((size_t)y1 * a.Wp + x1) * C;
+#pragma unroll
+        for (int cc = 0; cc < C; cc += 16) {
+            float t00[16], t01[16], t10[16], t11[16];
+            load16(p00 + cc, t00);
+            load16(p01 + cc, t01);
+            load16(p10 + cc, t10);
+            load16(p11 + cc, t11);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                float top = t00[i] + wx * (t01[i] - t00[i]);
+                float bot = t10[i] + wx * (t11[i] - t10[i]);
+                vin[cc + i] = top + wy * (bot - top);
+            }
+        }
+    }
+
+    // ---- depth the views are sampled at ----
+    float d;
+    if (TR == TR_INIT) {
+        d = depth_anchor(li, L, a.dp);
+    } else {
+        float t = sw[lay.bd()];
+#pragma unroll
+        for (int c = 0; c < C; ++c) t = fmaf(vin[c], sw[lay.wd() + c], t);
+        d = depth_from_logit(t, li, L, a.dp);
+    }
+
+    // ---- RMSNorm and query projections ----
+    float ms = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) ms = fmaf(vin[c], vin[c], ms);
+    const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
+    float xn[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) xn[c] = vin[c] * rinv * sw[lay.g() + c];
+    float vres[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float s = 0.f;
+#pragma unroll
+        for (int sb = 0; sb < TPE; ++sb)
+            if (sb == sub) s = vin[sb * 16 + i];
+        vres[i] = s;
+    }
+    float q[NH][16];
+#pragma unroll
+    for (int h = 0; h < NH; ++h)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) q[h][i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            fma_row16(&sw[lay.wq() + k * NH * C + h * C + c0], xn[k], q[h]);
+        }
+    }
+    float qb[16];
+    if constexpr (LAST) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) qb[i] = 0.f;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            fma_row16(&sw[lay.wb() + k * C + c0], xn[k], qb);
+        }
+    }
+
+    // ---- views: sample, online softmax, weighted sum ----
+    const float scale = 1.0f / sqrtf((float)C);
+    const float pxc = x + 0.5f, pyc = y + 0.5f;
+    float mx[NH], l[NH], o[NH][16];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+        mx[h] = -INFINITY;
+        l[h] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[h][i] = 0.f;
+    }
+    const T* feat = reinterpret_cast<const T*>(a.feat);
+    const size_t vstride = (size_t)a.fh * a.fw * C;
+    for (int m = 0; m < a.V; ++m) {
+        float D[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) D[i] = 0.f;
+        float u, v;
+        Taps tp;
+        if (reproject(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp)) {
+            const T* fb = feat + m * vstride + c0;
+            const bool xa = tp.x0 >= 0, xb = tp.x0 + 1 < a.fw, ya = tp.y0 >= 0, yb = tp.y0 + 1 < a.fh;
+            if (ya && xa) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0) * C, (1 - tp.fy) * (1 - tp.fx), D);
+            if (ya && xb) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0 + 1) * C, (1 - tp.fy) * tp.fx, D);
+            if (yb && xa) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0) * C, tp.fy * (1 - tp.fx), D);
+            if (yb && xb) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0 + 1) * C, tp.fy * tp.fx, D);
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) s = fmaf(q[h][i], D[i], s);
+#pragma unroll
+            for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            s *= scale;
+            float mn = fmaxf(mx[h], s);
+            float cs = expf(mx[h] - mn);
+            float p = expf(s - mn);
+            l[h] = fmaf(l[h], cs, p);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[h][i] = fmaf(o[h][i], cs, p * D[i]);
+            mx[h] = mn;
+        }
+        if constexpr (LAST) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) s = fmaf(qb[i], D[i], s);
+#pragma unroll
+            for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (live && sub == 0) a.beta[(((size_t)y * W + x) * L + li) * a.V + m] = s * scale;
+        }
+    }
+
+    // ---- output projection and residual ----
+    float out[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) out[i] = vres[i];
+    const int lane = threadIdx.x & 31;
+    const int gbase = lane & ~(TPE - 1);
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+        const float il = 1.0f / l[h];
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            float ok = o[h][k % 16];
+            if (TPE > 1) ok = __shfl_sync(0xffffffffu, ok, gbase + k / 16);
+            ok *= il;
+            fma_row16(&sw[lay.wo() + (h * C + k) * C + c0], ok, out);
+        }
+    }
+    if (live) store16(reinterpret_cast<T*>(a.out) + e * C + c0, out);
+}
+
+template <typename T, int C, int NH>
+static cudaError_t launch_nh(const AttendArgs& a, Transition tr, bool last, cudaStream_t st) {
+    const AttendLayout lay{C, NH};
+    const size_t smem = (size_t)lay.total() * sizeof(float);
+    const size_t n = (size_t)a.L * a.H * a.W * (C / 16);
+    const unsigned grid = (unsigned)((n + ATT_THREADS - 1) / ATT_THREADS);
+#define QK_LAUNCH(TRV, LASTV)                                                                          \
+    do {                                                                                               \
+        auto k = attend_kernel<T, C, NH, TRV, LASTV>;                                                  \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                \
+        k<<<grid, ATT_THREADS, smem, st>>>(a);                                                         \
+    } while (0)
+    if (tr == TR_INIT) {
+        if (last) QK_LAUNCH(TR_INIT, true); else QK_LAUNCH(TR_INIT, false);
+    } else if (tr == TR_SAME) {
+        if (last) QK_LAUNCH(TR_SAME, true); else QK_LAUNCH(TR_SAME, false);
+    } else {
+        if (last) QK_LAUNCH(TR_UP2, true); else QK_LAUNCH(TR_UP2, false);
+    }
+#undef QK_LAUNCH
+    return cudaGetLastError();
+}
+
+template <typename T, int C>
+static cudaError_t launch_c(const AttendArgs& a, int heads, Transition tr, bool last, cudaStream_t st) {
+    if (heads == 1) return launch_nh<T, C, 1>(a, tr, last, st);
+    if (heads == 2) return launch_nh<T, C, 2>(a, tr, last, st);
+    if (heads == 4) return launch_nh<T, C, 4>(a, tr, last, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
+                          cudaStream_t st) {
+    if (C == 16) return bf16 ? launch_c<__nv_bfloat16, 16>(a, heads, tr, last, st)
+                             : launch_c<float, 16>(a, heads, tr, last, st);
+    if (C == 32) return bf16 ? launch_c<__nv_bfloat16, 32>(a, heads, tr, last, st)
+                             : launch_c<float, 32>(a, heads, tr, last, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace quark

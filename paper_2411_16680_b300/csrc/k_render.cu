@@ -1,0 +1,82 @@
+// Final render (Sec. 3.1 Eq. 1; Sec. 3.2.3 "Upsampling & Activation").  One thread per output
+// pixel: bilinear upsample by s of the raw depth / density / blend logits of the last LDM,
+// activation (Eq. depth_activation, sigmoid, softmax over views), back-projection of every
+// input image onto each layer (zero padding), blend, and the over operator front to back
+// (l = L nearest first): C += T alpha c, T *= (1 - alpha).  Output RGBA with A = 1 - T.
+#include "device_common.cuh"
+
+namespace quark {
+
+constexpr int RD_THREADS = 128;
+
+__device__ __forceinline__ float4 sample_rgba(const float4* __restrict__ img, int h, int w, float u, float v) {
+    Taps t;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!bilinear_taps(u, v, h, w, t)) return r;
+    const bool xa = t.x0 >= 0, xb = t.x0 + 1 < w, ya = t.y0 >= 0, yb = t.y0 + 1 < h;
+    auto acc = [&](int yy, int xx, float wt) {
+        float4 p = __ldg(img + (size_t)yy * w + xx);
+        r.x = fmaf(wt, p.x, r.x);
+        r.y = fmaf(wt, p.y, r.y);
+        r.z = fmaf(wt, p.z, r.z);
+    };
+    if (ya && xa) acc(t.y0, t.x0, (1 - t.fy) * (1 - t.fx));
+    if (ya && xb) acc(t.y0, t.x0 + 1, (1 - t.fy) * t.fx);
+    if (yb && xa) acc(t.y0 + 1, t.x0, t.fy * (1 - t.fx));
+    if (yb && xb) acc(t.y0 + 1, t.x0 + 1, t.fy * t.fx);
+    return r;
+}
+
+__global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)a.Hout * a.Wout) return;
+    const int X = (int)(idx % a.Wout), Y = (int)(idx / a.Wout);
+    const int L = a.L, V = a.V;
+    int y0, y1, x0, x1;
+    float wy, wx;
+    resize_taps(Y, a.s, a.Hl, y0, y1, wy);
+    resize_taps(X, a.s, a.Wl, x0, x1, wx);
+    const size_t q00 = (size_t)y0 * a.Wl + x0, q01 = (size_t)y0 * a.Wl + x1;
+    const size_t q10 = (size_t)y1 * a.Wl + x0, q11 = (size_t)y1 * a.Wl + x1;
+    auto up = [&](const float* f, size_t stride, size_t off) {
+        float top = f[q00 * stride + off] * (1 - wx) + f[q01 * stride + off] * wx;
+        float bot = f[q10 * stride + off] * (1 - wx) + f[q11 * stride + off] * wx;
+        return top * (1 - wy) + bot * wy;
+    };
+    const float pxc = X + 0.5f, pyc = Y + 0.5f;
+    const size_t img_stride = (size_t)a.Hi * a.Wi;
+    float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
+    for (int li = L - 1; li >= 0; --li) {
+        const float d = depth_from_logit(up(a.t_raw, L, li), li, L, a.dp);
+        const float al = sigmoidf_(up(a.s_raw, L, li));
+        const size_t bstride = (size_t)L * V, boff = (size_t)li * V;
+        float bmax = -INFINITY;
+        for (int m = 0; m < V; ++m) bmax = fmaxf(bmax, up(a.beta, bstride, boff + m));
+        float sum = 0.f, lr = 0.f, lg = 0.f, lb = 0.f;
+        for (int m = 0; m < V; ++m) {
+            const float p = expf(up(a.beta, bstride, boff + m) - bmax);
+            sum += p;
+            float u, v;
+            if (reproject(a.geo.v[m], pxc, pyc, d, u, v)) {
+                float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, u, v);
+                lr = fmaf(p, c.x, lr);
+                lg = fmaf(p, c.y, lg);
+                lb = fmaf(p, c.z, lb);
+            }
+        }
+        const float w = T * al / sum;
+        cr = fmaf(w, lr, cr);
+        cg = fmaf(w, lg, cg);
+        cb = fmaf(w, lb, cb);
+        T *= 1.f - al;
+    }
+    a.out[idx] = make_float4(cr, cg, cb, 1.f - T);
+}
+
+cudaError_t launch_render(const RenderArgs& a, cudaStream_t st) {
+    const size_t n = (size_t)a.Hout * a.Wout;
+    render_kernel<<<(unsigned)((n + RD_THREADS - 1) / RD_THREADS), RD_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace quark

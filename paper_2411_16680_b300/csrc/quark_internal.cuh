@@ -1,0 +1,128 @@
+// Internal interfaces between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "quark.h"
+
+namespace quark {
+
+// Plane-induced mapping of one view for a given target grid and view grid:
+// X = d * (A p) + b with p = (x + 0.5, y + 0.5, 1) on the target grid, and
+// (u, v) = (X.x / X.z, X.y / X.z) on the view's grid.  A = K_m R_m R_t^T K_t^-1,
+// b = K_m (t_m - R_m R_t^T t_t); composed on the host in float64, stored as float32.
+struct ViewMap {
+    float A[9];
+    float b[3];
+};
+struct Geometry {
+    ViewMap v[QUARK_MAX_VIEWS];
+};
+
+// Reciprocal-depth parameters of Eq. (depth_activation).
+struct DepthParams {
+    float span;     // 1/near - 1/far
+    float inv_far;  // 1/far
+};
+
+struct EncodeArgs {
+    const float* images;  // [V][H][W][3]
+    int V, H, W;
+    const float* w;       // [27][C] then bias [C]
+    float4* rgba;         // [V][H][W] padded copy of the images
+    void* level[4];       // levels 1, 2, 4, 8 ([V][H/k][W/k][C]); NULL where unused
+};
+
+struct CollapseArgs {
+    const void* in;   // [2L][H][W][C]
+    void* out;        // [L][H][W][C]
+    int L, H, W;
+    const float* w;   // W1 [2C][C], b1 [C], W2 [C][C], b2 [C]
+};
+
+enum Transition { TR_INIT = 0, TR_SAME = 1, TR_UP2 = 2 };
+
+struct AttendArgs {
+    const void* prev;  // [L][Hp][Wp][C] volume entering the step (already collapsed); NULL at step 0
+    int Hp, Wp;
+    const void* feat;  // pyramid level [V][fh][fw][C]
+    int fh, fw;
+    int L, H, W, V;
+    DepthParams dp;
+    const float* w;    // v0 [C], g [C], w_d [C], b_d (padded to C), Wq [C][h*C], Wo [h*C][C], W_beta [C][C]
+    void* out;         // V_attn [L][H][W][C]
+    float* beta;       // [H][W][L][V] blend logits (last step), else NULL
+    Geometry geo;
+};
+
+struct ConvArgs {
+    const void* in;    // V_attn [L][H][W][C]
+    void* out;         // V_out [L][H][W][C]
+    int L, H, W;
+    DepthParams dp;
+    const float* w;    // g [C], W1 [9][C][C], b1 [C], W2 [9][C][C], b2 [C], dec: w_d [C], w_s [C], W_a [C][3], b_a[3], b_d, b_s
+    float* colour;     // [L][H][W][3]
+    float* alpha;      // [L][H][W]
+    float* depth;      // [L][H][W]
+    float* t_raw;      // [H][W][L]
+    float* s_raw;      // [H][W][L]
+};
+
+struct RenderArgs {
+    const float* t_raw;  // [Hl][Wl][L]
+    const float* s_raw;  // [Hl][Wl][L]
+    const float* beta;   // [Hl][Wl][L][V]
+    const float4* rgba;  // [V][Hi][Wi]
+    int L, V, Hl, Wl, s, Hout, Wout, Hi, Wi;
+    DepthParams dp;
+    float4* out;         // [Hout][Wout]
+    Geometry geo;
+};
+
+// Offsets (in floats) of the packed per-step weight blocks.
+struct AttendLayout {
+    int C, h;
+    __host__ __device__ constexpr int v0() const { return 0; }
+    __host__ __device__ constexpr int g() const { return C; }
+    __host__ __device__ constexpr int wd() const { return 2 * C; }
+    __host__ __device__ constexpr int bd() const { return 3 * C; }
+    __host__ __device__ constexpr int wq() const { return 4 * C; }
+    __host__ __device__ constexpr int wo() const { return 4 * C + C * h * C; }
+    __host__ __device__ constexpr int wb() const { return 4 * C + 2 * C * h * C; }
+    __host__ __device__ constexpr int total() const { return 4 * C + 2 * C * h * C + C * C; }
+};
+struct ConvLayout {
+    int C;
+    __host__ __device__ constexpr int g() const { return 0; }
+    __host__ __device__ constexpr int w1() const { return C; }
+    __host__ __device__ constexpr int b1() const { return C + 9 * C * C; }
+    __host__ __device__ constexpr int w2() const { return 2 * C + 9 * C * C; }
+    __host__ __device__ constexpr int b2() const { return 2 * C + 18 * C * C; }
+    __host__ __device__ constexpr int wd() const { return 3 * C + 18 * C * C; }
+    __host__ __device__ constexpr int ws() const { return 4 * C + 18 * C * C; }
+    __host__ __device__ constexpr int wa() const { return 5 * C + 18 * C * C; }
+    __host__ __device__ constexpr int ba() const { return 8 * C + 18 * C * C; }
+    __host__ __device__ constexpr int bd() const { return 8 * C + 18 * C * C + 3; }
+    __host__ __device__ constexpr int bs() const { return 8 * C + 18 * C * C + 4; }
+    __host__ __device__ constexpr int total() const { return 8 * C + 18 * C * C + 8; }
+};
+struct CollapseLayout {
+    int C;
+    __host__ __device__ constexpr int w1() const { return 0; }
+    __host__ __device__ constexpr int b1() const { return 2 * C * C; }
+    __host__ __device__ constexpr int w2() const { return 2 * C * C + C; }
+    __host__ __device__ constexpr int b2() const { return 3 * C * C + C; }
+    __host__ __device__ constexpr int total() const { return 3 * C * C + 2 * C; }
+};
+
+// Launchers (k_*.cu).  Each returns the launch's cudaError_t.
+cudaError_t launch_encode(const EncodeArgs& a, int C, bool bf16, cudaStream_t st);
+cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st);
+cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
+                          cudaStream_t st);
+cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
+cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
+
+}  // namespace quark

@@ -1,0 +1,281 @@
+"""Python binding of libquark.so (include/quark.h).  Argument marshalling only: every step of the
+path runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors (or any object
+with data_ptr()); host buffers are numpy arrays or CPU tensors (pinned for asynchronous copies).
+
+The names mirror the C ABI: Context.encode_pyramid -> quark_encode_pyramid, etc.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libquark.so")
+
+MAX_SCALES = 8
+MAX_VIEWS = 32
+
+OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, ENOTFOUND, EBUSY, EINTERNAL = range(9)
+FP32, BF16 = 0, 1
+FIELD_VOLUME, FIELD_VOLUME_ATTN, FIELD_COLOUR, FIELD_ALPHA, FIELD_DEPTH, FIELD_BETA_LOGITS, \
+    FIELD_DEPTH_LOGIT, FIELD_DENSITY_LOGIT = range(8)
+
+
+class QuarkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"quark status {status}: {msg}")
+        self.status = status
+
+
+class Camera(ct.Structure):
+    _fields_ = [("width", ct.c_int), ("height", ct.c_int), ("fx", ct.c_double), ("fy", ct.c_double),
+                ("cx", ct.c_double), ("cy", ct.c_double), ("R", ct.c_double * 9), ("t", ct.c_double * 3)]
+
+
+class Config(ct.Structure):
+    _fields_ = [("C", ct.c_int), ("heads", ct.c_int), ("n_scales", ct.c_int), ("k", ct.c_int * MAX_SCALES),
+                ("L", ct.c_int * MAX_SCALES), ("near_m", ct.c_float), ("far_m", ct.c_float),
+                ("precision", ct.c_int), ("attn_mode", ct.c_int), ("hbm_cap_bytes", ct.c_size_t)]
+
+
+_FP = ct.POINTER(ct.c_float)
+_PER = ct.POINTER(ct.c_float) * MAX_SCALES
+
+
+class Weights(ct.Structure):
+    _fields_ = [("enc_w", _FP), ("enc_b", _FP), ("v0", _FP), ("attn_g", _PER), ("Wq", _PER), ("Wo", _PER),
+                ("conv_g", _PER), ("conv1_w", _PER), ("conv1_b", _PER), ("conv2_w", _PER), ("conv2_b", _PER),
+                ("col_w1", _PER), ("col_b1", _PER), ("col_w2", _PER), ("col_b2", _PER),
+                ("w_d", _FP), ("b_d", ct.c_float), ("w_sigma", _FP), ("b_sigma", ct.c_float),
+                ("W_a", _FP), ("b_a", _FP), ("W_beta", _FP)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises when it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2411_16680_b300.build`")
+        L = ct.CDLL(LIB_PATH)
+        vp = ct.c_void_p
+        sig = {
+            "quark_create": ([ct.POINTER(Config), ct.c_int, ct.POINTER(vp)], ct.c_int),
+            "quark_destroy": ([vp], ct.c_int),
+            "quark_load_weights": ([vp, ct.POINTER(Weights)], ct.c_int),
+            "quark_encode_pyramid": ([vp, vp, ct.POINTER(Camera), ct.c_int, vp, ct.POINTER(vp)], ct.c_int),
+            "quark_ldm_create": ([vp, ct.POINTER(Camera), ct.POINTER(vp)], ct.c_int),
+            "quark_update_fuse": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
+            "quark_render_ldm": ([vp, vp, vp, vp, vp], ct.c_int),
+            "quark_render_novel_view": ([vp, vp, vp, vp, vp], ct.c_int),
+            "quark_ldm_read": ([vp, ct.c_int, vp, ct.c_size_t], ct.c_int),
+            "quark_ldm_field_bytes": ([vp, ct.c_int], ct.c_size_t),
+            "quark_release_pyramid": ([vp], ct.c_int),
+            "quark_release_ldm": ([vp], ct.c_int),
+            "quark_last_error": ([vp], ct.c_char_p),
+            "quark_launch_count": ([vp], ct.c_uint64),
+            "quark_reset_counters": ([vp], None),
+            "quark_set_profiling": ([vp, ct.c_int], ct.c_int),
+            "quark_kernel_times": ([vp, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64),
+                                    ct.c_int], ct.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    return [n for n in ("quark_create", "quark_destroy", "quark_load_weights", "quark_encode_pyramid",
+                        "quark_ldm_create", "quark_update_fuse", "quark_render_ldm", "quark_render_novel_view",
+                        "quark_ldm_read", "quark_ldm_field_bytes", "quark_release_pyramid", "quark_release_ldm",
+                        "quark_last_error", "quark_launch_count", "quark_reset_counters", "quark_set_profiling",
+                        "quark_kernel_times")]
+
+
+def _check(status: int, ctx=None):
+    if status != OK:
+        msg = lib().quark_last_error(ctx)
+        raise QuarkError(status, msg.decode() if msg else "")
+
+
+def make_camera(cam) -> Camera:
+    c = Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R, np.float64).reshape(9)
+    t = np.asarray(cam.t, np.float64).reshape(3)
+    for i in range(9):
+        c.R[i] = R[i]
+    for i in range(3):
+        c.t[i] = t[i]
+    return c
+
+
+def make_config(cfg, hbm_cap_bytes: int = 0) -> Config:
+    c = Config()
+    c.C, c.heads, c.n_scales = cfg.C, cfg.heads, len(cfg.scales)
+    for j, (k, L) in enumerate(cfg.scales):
+        c.k[j], c.L[j] = k, L
+    c.near_m, c.far_m = cfg.near, cfg.far
+    c.precision = cfg.precision
+    c.attn_mode = cfg.attn_mode
+    c.hbm_cap_bytes = hbm_cap_bytes
+    return c
+
+
+def _ptr(x) -> int:
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Pyramid:
+    def __init__(self, ctx: "Context", handle: ct.c_void_p, V: int):
+        self.ctx, self.handle, self.V = ctx, handle, V
+
+    def release(self):
+        if self.handle:
+            lib().quark_release_pyramid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class LDM:
+    def __init__(self, ctx: "Context", handle: ct.c_void_p):
+        self.ctx, self.handle = ctx, handle
+
+    def field_bytes(self, field: int) -> int:
+        return lib().quark_ldm_field_bytes(self.handle, field)
+
+    def read(self, field: int, shape=None) -> np.ndarray:
+        n = self.field_bytes(field)
+        out = np.empty(n // 4, np.float32)
+        _check(lib().quark_ldm_read(self.handle, field, out.ctypes.data, n), self.ctx.handle)
+        return out if shape is None else out.reshape(shape)
+
+    def release(self):
+        if self.handle:
+            lib().quark_release_ldm(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Context:
+    """quark_ctx: one network configuration and its weights on one device."""
+
+    def __init__(self, cfg, device: int = 0, hbm_cap_bytes: int = 0):
+        self.cfg = cfg
+        self._ccfg = make_config(cfg, hbm_cap_bytes)
+        h = ct.c_void_p()
+        _check(lib().quark_create(ct.byref(self._ccfg), device, ct.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().quark_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().quark_last_error(self.handle).decode()
+
+    def load_weights(self, W: Dict[str, np.ndarray]):
+        keep = {}
+
+        def p(name):
+            a = np.ascontiguousarray(W[name], np.float32)
+            keep[name] = a
+            return a.ctypes.data_as(_FP)
+
+        w = Weights()
+        w.enc_w, w.enc_b, w.v0 = p("enc_w"), p("enc_b"), p("v0")
+        n = len(self.cfg.scales)
+        for j in range(n):
+            w.attn_g[j], w.Wq[j], w.Wo[j] = p(f"attn_g_{j}"), p(f"Wq_{j}"), p(f"Wo_{j}")
+            w.conv_g[j], w.conv1_w[j], w.conv1_b[j] = p(f"conv_g_{j}"), p(f"conv1_w_{j}"), p(f"conv1_b_{j}")
+            w.conv2_w[j], w.conv2_b[j] = p(f"conv2_w_{j}"), p(f"conv2_b_{j}")
+            if f"col_w1_{j}" in W:
+                w.col_w1[j], w.col_b1[j] = p(f"col_w1_{j}"), p(f"col_b1_{j}")
+                w.col_w2[j], w.col_b2[j] = p(f"col_w2_{j}"), p(f"col_b2_{j}")
+        w.w_d, w.w_sigma, w.W_a, w.b_a, w.W_beta = p("w_d"), p("w_sigma"), p("W_a"), p("b_a"), p("W_beta")
+        w.b_d = float(np.asarray(W["b_d"]).reshape(-1)[0])
+        w.b_sigma = float(np.asarray(W["b_sigma"]).reshape(-1)[0])
+        _check(lib().quark_load_weights(self.handle, ct.byref(w)), self.handle)
+
+    def encode_pyramid(self, images, cams: Sequence, stream=None, into: Optional[Pyramid] = None) -> Pyramid:
+        """images: [V, H, W, 3] float32, device tensor or host array/tensor.  `into` re-encodes an
+        existing pyramid in place (same V and resolution) instead of allocating a new one."""
+        V = len(cams)
+        arr = (Camera * V)(*[make_camera(c) for c in cams])
+        h = ct.c_void_p(into.handle.value if into is not None else None)
+        _check(lib().quark_encode_pyramid(self.handle, _ptr(images), arr, V, _stream(stream), ct.byref(h)),
+               self.handle)
+        return into if into is not None else Pyramid(self, h, V)
+
+    def ldm_create(self, target) -> LDM:
+        cam = make_camera(target)
+        h = ct.c_void_p()
+        _check(lib().quark_ldm_create(self.handle, ct.byref(cam), ct.byref(h)), self.handle)
+        return LDM(self, h)
+
+    def update_fuse(self, pyr: Pyramid, scale: int, ldm: LDM, stream=None):
+        _check(lib().quark_update_fuse(self.handle, pyr.handle, scale, ldm.handle, _stream(stream)), self.handle)
+
+    def render_ldm(self, ldm: LDM, pyr: Pyramid, rgba, stream=None):
+        _check(lib().quark_render_ldm(self.handle, ldm.handle, pyr.handle, _ptr(rgba), _stream(stream)), self.handle)
+
+    def render_novel_view(self, pyr: Pyramid, ldm: LDM, rgba, stream=None):
+        _check(lib().quark_render_novel_view(self.handle, pyr.handle, ldm.handle, _ptr(rgba), _stream(stream)),
+               self.handle)
+
+    # ---- accounting ----
+    def launch_count(self) -> int:
+        return int(lib().quark_launch_count(self.handle))
+
+    def reset_counters(self):
+        lib().quark_reset_counters(self.handle)
+
+    def set_profiling(self, on: bool):
+        _check(lib().quark_set_profiling(self.handle, 1 if on else 0), self.handle)
+
+    def kernel_times(self) -> Dict[str, tuple]:
+        cap = 16
+        names = (ct.c_char_p * cap)()
+        ms = (ct.c_double * cap)()
+        n = (ct.c_uint64 * cap)()
+        k = lib().quark_kernel_times(self.handle, names, ms, n, cap)
+        return {names[i].decode(): (int(n[i]), float(ms[i])) for i in range(k)}

@@ -14,6 +14,8 @@ stand in for them.
 from __future__ import annotations
 
 import dataclasses
+import os
+import tempfile
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence, Tuple
 
@@ -124,29 +126,30 @@ def _lattice(rng: np.random.Generator, n: int) -> np.ndarray:
 def value_noise_2d(lat: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
     """Smooth (smoothstep-interpolated) periodic value noise; lat is (n, n, 3) in [0, 1)."""
     n = lat.shape[0]
+    flat = lat.reshape(n * n, 3).astype(np.float32)
     u0 = np.floor(u)
     v0 = np.floor(v)
-    fu = u - u0
-    fv = v - v0
+    fu = (u - u0).astype(np.float32)
+    fv = (v - v0).astype(np.float32)
     fu = fu * fu * (3 - 2 * fu)
     fv = fv * fv * (3 - 2 * fv)
     i0 = u0.astype(np.int64) % n
     j0 = v0.astype(np.int64) % n
     i1 = (i0 + 1) % n
     j1 = (j0 + 1) % n
-    a = lat[j0, i0]
-    b = lat[j0, i1]
-    c = lat[j1, i0]
-    d = lat[j1, i1]
+    a = np.take(flat, j0 * n + i0, axis=0)
+    b = np.take(flat, j0 * n + i1, axis=0)
+    c = np.take(flat, j1 * n + i0, axis=0)
+    d = np.take(flat, j1 * n + i1, axis=0)
     fu = fu[..., None]
     fv = fv[..., None]
-    return (a * (1 - fu) + b * fu) * (1 - fv) + (c * (1 - fu) + d * fu) * fv
+    return (a + (b - a) * fu) * (1 - fv) + (c + (d - c) * fu) * fv
 
 
 def fbm_2d(rng: np.random.Generator, u: np.ndarray, v: np.ndarray, octaves: int,
            lattice_n: int = 64) -> np.ndarray:
     """Sum of `octaves` value-noise octaves (frequency x2, amplitude x0.5), normalised to [0, 1]."""
-    out = np.zeros(u.shape + (3,))
+    out = np.zeros(u.shape + (3,), np.float32)
     amp, tot, freq = 1.0, 0.0, 1.0
     for _ in range(octaves):
         lat = _lattice(rng, lattice_n)
@@ -239,51 +242,88 @@ def scene_raycast(seed: int = 1234, V: int = 8, W: int = 1920, H: int = 1080, f:
             prims.append(("sphere", np.array([px, py, z]), size * 0.7, tex))
     back_tex = rng.integers(0, 2**31)
 
-    images, depths = [], []
-    for cam in cams:
-        o = cam.centre
-        d = _ray_dirs(cam).reshape(-1, 3)
-        best = np.full(d.shape[0], np.inf)
-        col = np.zeros((d.shape[0], 3))
-        # backdrop z = zmax (world); ray param s along d
-        s_back = (zmax - o[2]) / d[:, 2]
-        hit = s_back > 0
-        best[hit] = s_back[hit]
-        P = o + d * best[:, None]
-        col[:] = fbm_2d(np.random.default_rng(back_tex), P[:, 0] / 4.0, P[:, 1] / 4.0, octaves)
-        for pr in prims:
-            if pr[0] == "quad":
-                _, c0, nrm, a1, a2, size, tex = pr
-                den = d @ nrm
-                s = ((c0 - o) @ nrm) / np.where(np.abs(den) < 1e-12, 1e-12, den)
-                P = o + d * s[:, None]
-                lu = (P - c0) @ a1
-                lv = (P - c0) @ a2
-                m = (s > 0) & (s < best) & (np.abs(lu) < size) & (np.abs(lv) < size)
-                if np.any(m):
-                    best[m] = s[m]
-                    col[m] = fbm_2d(np.random.default_rng(tex), lu[m] / size * 4.0, lv[m] / size * 4.0, octaves)
-            else:
-                _, c0, r, tex = pr
-                oc = o - c0
-                b = d @ oc
-                a = np.einsum("ij,ij->i", d, d)
-                cc = oc @ oc - r * r
-                disc = b * b - a * cc
-                ok = disc > 0
-                s = np.full(d.shape[0], np.inf)
-                s[ok] = (-b[ok] - np.sqrt(disc[ok])) / a[ok]
-                m = ok & (s > 0) & (s < best)
-                if np.any(m):
-                    best[m] = s[m]
-                    P = o + d[m] * s[m, None] - c0
-                    lon = np.arctan2(P[:, 0], -P[:, 2])
-                    lat = np.arcsin(np.clip(P[:, 1] / r, -1, 1))
-                    col[m] = fbm_2d(np.random.default_rng(tex), lon * 3.0, lat * 3.0, octaves)
-        images.append(col.reshape(H, W, 3))
-        # the ray direction has unit camera-z, so the ray parameter equals camera depth
-        depths.append(best.reshape(H, W))
-    return Scene(np.stack(images).astype(np.float32), cams, target, np.stack(depths).astype(np.float32))
+    key = None
+    cache_dir = os.environ.get("QUARK_SCENE_CACHE", os.path.join(tempfile.gettempdir(), "quark_scene_cache"))
+    if W * H * V >= 1_000_000:
+        key = os.path.join(cache_dir, f"raycast_{seed}_{V}_{W}x{H}_{f}_{arc}_{radius}_{n_planes}_{n_spheres}_"
+                                      f"{zmin}_{zmax}_{octaves}.npz")
+        if os.path.exists(key):
+            z = np.load(key)
+            return Scene(z["images"], cams, target, z["depth"])
+    args = [(cam, prims, back_tex, zmax, octaves) for cam in cams]
+    if V >= 4 and W * H >= 1_000_000:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=min(V, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_render_view_star, args))
+    else:
+        res = [_render_view(*a) for a in args]
+    images = np.stack([r[0] for r in res]).astype(np.float32)
+    depth = np.stack([r[1] for r in res]).astype(np.float32)
+    if key is not None:
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = key + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, images=images, depth=depth)
+        os.replace(tmp, key)
+    return Scene(images, cams, target, depth)
+
+
+def _render_view(cam: Camera, prims, back_tex, zmax: float, octaves: int):
+    """Nearest hit per pixel (ray parameter = camera depth, since rays have unit camera z),
+    then one texture lookup per pixel from the primitive hit."""
+    H, W = cam.height, cam.width
+    o = cam.centre
+    d = _ray_dirs(cam).reshape(-1, 3)
+    n = d.shape[0]
+    best = np.full(n, np.inf)
+    pid = np.full(n, -1, np.int64)      # -1: backdrop
+    ta = np.zeros(n)                    # texture coordinates of the nearest hit
+    tb = np.zeros(n)
+    s_back = (zmax - o[2]) / d[:, 2]
+    hit = s_back > 0
+    best[hit] = s_back[hit]
+    for i, pr in enumerate(prims):
+        if pr[0] == "quad":
+            _, c0, nrm, a1, a2, size, tex = pr
+            den = d @ nrm
+            s = ((c0 - o) @ nrm) / np.where(np.abs(den) < 1e-12, 1e-12, den)
+            P = o + d * s[:, None] - c0
+            lu = P @ a1
+            lv = P @ a2
+            m = (s > 0) & (s < best) & (np.abs(lu) < size) & (np.abs(lv) < size)
+            best[m] = s[m]
+            pid[m] = i
+            ta[m] = lu[m] / size * 4.0
+            tb[m] = lv[m] / size * 4.0
+        else:
+            _, c0, r, tex = pr
+            oc = o - c0
+            b = d @ oc
+            a = np.einsum("ij,ij->i", d, d)
+            cc = oc @ oc - r * r
+            disc = b * b - a * cc
+            ok = disc > 0
+            s = np.full(n, np.inf)
+            s[ok] = (-b[ok] - np.sqrt(disc[ok])) / a[ok]
+            m = ok & (s > 0) & (s < best)
+            best[m] = s[m]
+            pid[m] = i
+            P = o + d[m] * s[m, None] - c0
+            ta[m] = np.arctan2(P[:, 0], -P[:, 2]) * 3.0
+            tb[m] = np.arcsin(np.clip(P[:, 1] / r, -1, 1)) * 3.0
+    col = np.zeros((n, 3), np.float32)
+    back = pid < 0
+    P = o + d[back] * best[back, None]
+    col[back] = fbm_2d(np.random.default_rng(back_tex), P[:, 0] / 4.0, P[:, 1] / 4.0, octaves)
+    for i, pr in enumerate(prims):
+        m = pid == i
+        if m.any():
+            col[m] = fbm_2d(np.random.default_rng(pr[-1]), ta[m], tb[m], octaves)
+    return col.reshape(H, W, 3), best.reshape(H, W)
+
+
+def _render_view_star(a):
+    return _render_view(*a)
 
 
 def perturb_target(scene: Scene, rng: np.random.Generator, jitter: float) -> Camera:
@@ -326,8 +366,8 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
 def make_weights(cfg: QuarkConfig, seed: int = 5678, std: float = 0.02, sharp: bool = False) -> Dict[str, np.ndarray]:
     """Random-init weights.  Default: every tensor N(0, std) (gains 1 + N(0, std)).
 
-    sharp=True draws fan-in-scaled weights (N(0, 1/fan_in) x gain, with the query and blend
-    projections x4) so that the softmax over views, the blend weights, the depth tanh and
+    sharp=True draws fan-in-scaled weights (N(0, 1/fan_in) x gain: query and blend projections
+    x4, residual-branch outputs x0.4) so that the softmax over views, the blend weights, the depth tanh and
     the gelu are far from their linear regimes."""
     rng = np.random.default_rng(seed)
     out = {}
@@ -346,7 +386,12 @@ def make_weights(cfg: QuarkConfig, seed: int = 5678, std: float = 0.02, sharp: b
                 w = 0.3 * rng.standard_normal(shp)
             else:
                 fan_in = int(np.prod(shp[:-1])) if len(shp) > 1 else shp[0]
-                gain = 4.0 if name.startswith(("Wq", "W_beta")) else (2.0 if name in ("w_d", "w_sigma") else 1.0)
+                if name.startswith(("Wq", "W_beta")):
+                    gain = 4.0
+                elif name.startswith(("Wo_", "conv2_w", "col_w2")):
+                    gain = 0.4  # residual branches scaled down so the volume does not drift
+                else:
+                    gain = 1.0
                 w = gain * rng.standard_normal(shp) / np.sqrt(fan_in)
         out[name] = w.astype(np.float32)
     return out
