@@ -257,6 +257,8 @@ def main():
     ap.add_argument("--form", default="bf16", choices=["bf16", "fp32"], help="headline form for `value`")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sharp", action="store_true", help="sharp random weights instead of N(0, 0.02)")
+    ap.add_argument("--size", default="1920x1080", help="WxH of views and output (profiling runs use a smaller case)")
+    ap.add_argument("--forms", default="fp32,bf16", help="forms to time (comma separated)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -266,8 +268,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     peaks = load_peaks()
 
-    base_cfg = synth.config_1080p()
-    scene = synth.scene_1080p()
+    sw, sh = (int(v) for v in args.size.lower().split("x"))
+    workload = WORKLOAD if (sw, sh) == (1920, 1080) else WORKLOAD.replace("1080p", f"{sw}x{sh}").replace(
+        "1920x1080", f"{sw}x{sh}")
+    base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh)
+    scene = synth.scene_1080p(W=sw, H=sh)
     V = len(scene.cams)
     img_h, img_w = scene.images.shape[1:3]
 
@@ -288,7 +293,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / fps, 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded ray-cast scene; random-init weights)",
-                "config": {"workload": WORKLOAD, "form": "oracle", "l2": "inputs larger than L2"},
+                "config": {"workload": workload, "form": "oracle", "l2": "inputs larger than L2"},
                 "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": blas_threads(),
                                  "kind": "oracle", "sample": desc},
                 "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0,
@@ -304,7 +309,7 @@ def main():
 
     forms = {}
     results = {}
-    for form in ("fp32", "bf16"):
+    for form in [f.strip() for f in args.forms.split(",") if f.strip()]:
         cfg = base_cfg.replace(precision=synth.PREC_FP32 if form == "fp32" else synth.PREC_BF16)
         W = synth.make_weights(cfg, sharp=args.sharp)
         res = run_form(cfg, W, scene, args.steps, args.warmup, rank, world, dev, peaks)
@@ -320,7 +325,8 @@ def main():
     if rank == 0:
         import numpy as np
         from oracle import quark_oracle as O
-        rects = [(0, 4, 0, 4), (538, 542, 958, 962), (1076, 1080, 1916, 1920)]
+        Ho, Wo = base_cfg.out_h, base_cfg.out_w
+        rects = [(0, 4, 0, 4), (Ho // 2 - 2, Ho // 2 + 2, Wo // 2 - 2, Wo // 2 + 2), (Ho - 4, Ho, Wo - 4, Wo)]
         W = synth.make_weights(base_cfg, sharp=args.sharp)
         refs = [O.forward(base_cfg, W, scene, r)[0] for r in rects]
         for form, (cfg, res) in results.items():
@@ -334,7 +340,7 @@ def main():
             forms[form]["max_abs_vs_oracle"] = float(f"{max(errs):.3g}")
             forms[form]["psnr_db_vs_oracle"] = round(10 * np.log10(1 / mse), 1) if mse > 0 else None
 
-    head = args.form
+    head = args.form if args.form in results else next(iter(results))
     cfg, res = results[head]
     f = forms[head]
     cpu = None
@@ -349,7 +355,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32",
             "data": "synthetic (seeded ray-cast scene of 20 textured primitives; random-init weights N(0,0.02))",
-            "config": {"workload": WORKLOAD, "form": head, "parallelism": f"replicas x{world}",
+            "config": {"workload": workload, "form": head, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (2.8 GB pyramid per frame), no flush"},
             "latency_ms": {"p50": f["p50_ms"], "p99": f["p99_ms"]},
             "forms": forms,
