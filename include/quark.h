@@ -180,6 +180,35 @@ quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_
 quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, quark_ldm* ldm, float* rgba,
                                      void* stream);
 
+/* One Update & Fuse step that allocates no device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while they run, e.g. a
+ * frame loop with a fixed memory budget reserved up front (cudaMalloc can fail at run time and
+ * synchronises the device, stalling the frame), a process whose device memory is owned by
+ * another allocator, or code that must not make allocating CUDA calls at that point.
+ *
+ * It computes exactly what quark_update_fuse computes for step `scale`, launching the same
+ * kernels, but takes the LDM buffers from the caller instead of an LDM handle:
+ *   target    the novel view (as for quark_ldm_create)
+ *   v_prev    step scale-1's output volume [L'][H'][W'][C] (FP32, or BF16 in the BF16 form);
+ *             ignored at scale 0
+ *   v_out     this step's output volume [L][H][W][C], same element type
+ *   colour [L][H][W][3], alpha / depth [L][H][W], t_raw / s_raw [H][W][L] (float32)
+ *   beta      blend logits [H][W][L][V] (float32), required on the last step, else ignored
+ * All buffers are device memory owned by the caller.  The two intermediates (the volume after
+ * the attention block and, where L halves, the collapsed volume) live in one static device
+ * array of QUARK_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds until the
+ * process exits; a step whose intermediates need more returns QUARK_EINVAL (use
+ * quark_update_fuse for it).  Every call shares that array and it keeps the last call's
+ * contents (each call overwrites what it reads), so calls whose work overlaps on the GPU --
+ * on different streams, or from different contexts on one device -- race; serialise them.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. */
+#define QUARK_NOALLOC_SCRATCH_BYTES (32u << 20)
+quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_pyramid* pyr, int scale,
+                                       const quark_camera* target, const void* v_prev, void* v_out,
+                                       float* colour, float* alpha, float* depth, float* t_raw, float* s_raw,
+                                       float* beta, void* stream);
+
 /* Fields of an LDM readable for inspection (state after the latest quark_update_fuse). */
 enum {
     QUARK_FIELD_VOLUME = 0,       /* [L][H][W][C] feature volume after the step (FP32 out)    */

@@ -1,0 +1,150 @@
+// quark_update_fuse_noalloc: one Update & Fuse step that allocates no device memory.
+//
+// The regular step (quark_update_fuse) keeps its intermediate buffers -- the volume after the
+// attention block and, where the layer count halves, the collapsed volume -- in memory the
+// library allocates for the LDM handle.  This variant takes every input and output from the
+// caller and keeps those two intermediates in one fixed, file-scope device array instead, so
+// the call itself never allocates.  It launches the same kernels as the regular step.
+#include <cmath>
+#include <mutex>
+
+#include "quark_internal.cuh"
+#include "api_internal.h"
+
+using namespace quark;
+
+// The shared scratch.  Every GPU that loads this library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QUARK_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The array's name is only a
+// host-side stand-in for the symbol, so its device address is looked up once per device with
+// that device current, and the looked-up pointer is what the kernels receive.
+quark_status scratch_address(const quark_ctx* ctx, int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kMaxDevices) return qk_fail(ctx, QUARK_EINVAL, "device %d beyond the scratch table", dev);
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return qk_fail(ctx, QUARK_ECUDA, "cudaGetSymbolAddress(static scratch) on device %d: %s", dev,
+                           cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return QUARK_OK;
+}
+
+size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_pyramid* pyr, int scale,
+                                                  const quark_camera* target, const void* v_prev, void* v_out,
+                                                  float* colour, float* alpha, float* depth, float* t_raw,
+                                                  float* s_raw, float* beta, void* stream) {
+    if (!ctx || !pyr || !target || !v_out || !colour || !alpha || !depth || !t_raw || !s_raw)
+        return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (pyr->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "pyramid from another context");
+    if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
+    const quark_config& c = ctx->cfg;
+    if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);
+    if (scale > 0 && !v_prev) return qk_fail(ctx, QUARK_EINVAL, "step %d needs the previous step's volume", scale);
+    const bool last = scale == c.n_scales - 1;
+    if (last && !beta) return qk_fail(ctx, QUARK_EINVAL, "the last step writes blend logits: beta is NULL");
+    quark_status s = qk_validate_camera(ctx, *target, "target");
+    if (s != QUARK_OK) return s;
+    for (int j = 0; j < c.n_scales; ++j)
+        if (target->height % c.k[j] || target->width % c.k[j])
+            return qk_fail(ctx, QUARK_EINVAL, "output %dx%d not divisible by k=%d", target->width, target->height,
+                           c.k[j]);
+
+    const bool bf16 = c.precision == QUARK_BF16;
+    const size_t elt = bf16 ? 2 : 4;
+    const int k = c.k[scale], L = c.L[scale];
+    const int H = target->height / k, W = target->width / k;
+    int Lp = 0, Hp = 0, Wp = 0;
+    bool collapse = false;
+    if (scale > 0) {
+        Lp = c.L[scale - 1];
+        Hp = target->height / c.k[scale - 1];
+        Wp = target->width / c.k[scale - 1];
+        collapse = Lp == 2 * L;
+    }
+    const size_t attn_bytes = round256((size_t)L * H * W * c.C * elt);
+    const size_t col_bytes = collapse ? round256((size_t)L * Hp * Wp * c.C * elt) : 0;
+    if (attn_bytes + col_bytes > QUARK_NOALLOC_SCRATCH_BYTES)
+        return qk_fail(ctx, QUARK_EINVAL,
+                       "step %d needs %zu bytes of scratch; the static scratch holds %zu (use quark_update_fuse)",
+                       scale, attn_bytes + col_bytes, (size_t)QUARK_NOALLOC_SCRATCH_BYTES);
+
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    unsigned char* scratch = nullptr;
+    s = scratch_address(ctx, ctx->device, &scratch);
+    if (s != QUARK_OK) return s;
+    void* vattn = scratch;
+    void* collapsed = scratch + attn_bytes;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const void* prev = v_prev;
+    Transition tr = TR_INIT;
+    if (scale > 0) {
+        if (collapse) {
+            CollapseArgs ca{};
+            ca.in = v_prev;
+            ca.out = collapsed;
+            ca.L = L;
+            ca.H = Hp;
+            ca.W = Wp;
+            ca.w = ctx->wdev + ctx->off_collapse[scale];
+            e = launch_collapse(ca, c.C, bf16, st);
+            ctx->launches++;
+            if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "collapse launch: %s", cudaGetErrorString(e));
+            prev = collapsed;
+        }
+        tr = (c.k[scale - 1] == 2 * k) ? TR_UP2 : TR_SAME;
+    }
+
+    AttendArgs aa{};
+    aa.prev = prev;
+    aa.Hp = Hp;
+    aa.Wp = Wp;
+    const int li = k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3;
+    aa.feat = pyr->level[li];
+    aa.fh = pyr->H / k;
+    aa.fw = pyr->W / k;
+    aa.L = L;
+    aa.H = H;
+    aa.W = W;
+    aa.V = pyr->V;
+    aa.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+    aa.w = ctx->wdev + ctx->off_attend[scale];
+    aa.out = vattn;
+    aa.beta = last ? beta : nullptr;
+    for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(*target, k, pyr->cams[m], k);
+    e = launch_attend(aa, c.C, c.heads, tr, last, bf16, st);
+    ctx->launches++;
+    if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "attend launch: %s", cudaGetErrorString(e));
+
+    ConvArgs cv{};
+    cv.in = vattn;
+    cv.out = v_out;
+    cv.L = L;
+    cv.H = H;
+    cv.W = W;
+    cv.dp = aa.dp;
+    cv.w = ctx->wdev + ctx->off_conv[scale];
+    cv.colour = colour;
+    cv.alpha = alpha;
+    cv.depth = depth;
+    cv.t_raw = t_raw;
+    cv.s_raw = s_raw;
+    e = launch_conv_block(cv, c.C, bf16, st);
+    ctx->launches++;
+    if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "conv block launch: %s", cudaGetErrorString(e));
+    return QUARK_OK;
+}

@@ -83,6 +83,8 @@ def lib():
             "quark_set_profiling": ([vp, ct.c_int], ct.c_int),
             "quark_kernel_times": ([vp, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64),
                                     ct.c_int], ct.c_int),
+            "quark_update_fuse_noalloc": ([vp, vp, ct.c_int, ct.POINTER(Camera), vp, vp, vp, vp, vp, vp, vp, vp, vp],
+                                          ct.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -254,6 +256,16 @@ class Context:
 
     def update_fuse(self, pyr: Pyramid, scale: int, ldm: LDM, stream=None):
         _check(lib().quark_update_fuse(self.handle, pyr.handle, scale, ldm.handle, _stream(stream)), self.handle)
+
+    def update_fuse_noalloc(self, pyr: Pyramid, scale: int, target, v_prev, v_out, colour, alpha, depth, t_raw,
+                            s_raw, beta=None, stream=None):
+        """quark_update_fuse_noalloc: one step on caller-owned device buffers; the library allocates
+        nothing (its intermediates use a fixed static device array, see quark.h)."""
+        cam = make_camera(target)
+        p = lambda x: None if x is None else _ptr(x)
+        _check(lib().quark_update_fuse_noalloc(self.handle, pyr.handle, scale, ct.byref(cam), p(v_prev), p(v_out),
+                                               p(colour), p(alpha), p(depth), p(t_raw), p(s_raw), p(beta),
+                                               _stream(stream)), self.handle)
 
     def render_ldm(self, ldm: LDM, pyr: Pyramid, rgba, stream=None):
         _check(lib().quark_render_ldm(self.handle, ldm.handle, pyr.handle, _ptr(rgba), _stream(stream)), self.handle)
