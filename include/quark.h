@@ -233,6 +233,11 @@ quark_status quark_release_ldm(quark_ldm* ldm);
 /* Last error message of a context (or of the calling thread when ctx is NULL). */
 const char* quark_last_error(const quark_ctx* ctx);
 
+/* Synchronise the context's device and report device-side failures: QUARK_ETIMEDOUT if a
+ * kernel's bounded wait (on tensor-core completion) ran out since the last check, in which case
+ * that launch's outputs are invalid; the error word is then cleared. */
+quark_status quark_check_device(quark_ctx* ctx);
+
 /* Kernel accounting.  quark_launch_count returns the number of kernels this context has
  * launched since creation or the last reset.  With profiling on, every launch is bracketed
  * by CUDA events on its own stream and quark_kernel_times (which synchronises) returns, per

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -210,6 +211,9 @@ extern "C" quark_status quark_destroy(quark_ctx* ctx) {
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     qk_free(ctx, ctx->wdev, ctx->wbytes);
+    qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
+    qk_free(ctx, ctx->wat, ctx->wat_bytes);
+    qk_free(ctx, ctx->dev_err, sizeof(int));
     delete ctx;
     return QUARK_OK;
 }
@@ -217,6 +221,24 @@ extern "C" quark_status quark_destroy(quark_ctx* ctx) {
 // -------------------------------------------------------------------------------------------
 // Weights: packed into one device blob per context
 // -------------------------------------------------------------------------------------------
+
+// float -> bf16 bits, round to nearest even (weights are finite)
+static uint16_t to_bf16_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// 3x3 conv weights [dy][dx][ci][co] (fp32) -> per tap a K-major tcgen05 B operand (N = co rows,
+// K = ci): element (co, ci) at (ci / 8) * C * 8 + co * 8 + ci % 8 (bf16 elements).
+static void pack_conv_weights_bf16(const float* w, int C, uint16_t* dst) {
+    for (int tap = 0; tap < 9; ++tap)
+        for (int ci = 0; ci < C; ++ci)
+            for (int co = 0; co < C; ++co)
+                dst[(size_t)tap * C * C + (ci / 8) * C * 8 + co * 8 + ci % 8] =
+                    to_bf16_bits(w[((size_t)tap * C + ci) * C + co]);
+}
 
 extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* w) {
     if (!ctx || !w) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
@@ -303,7 +325,64 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     quark_status s = qk_alloc(ctx, (void**)&ctx->wdev, ctx->wbytes);
     if (s != QUARK_OK) return s;
     QK_CUDA(ctx, cudaMemcpy(ctx->wdev, blob.data(), ctx->wbytes, cudaMemcpyHostToDevice));
+    if (c.precision == QUARK_BF16) {
+        ctx->wtc_step_bytes = 2 * 9 * (size_t)C * C * sizeof(uint16_t);
+        std::vector<uint16_t> tc(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
+        for (int j = 0; j < c.n_scales; ++j) {
+            uint16_t* d = tc.data() + (size_t)j * 2 * 9 * C * C;
+            pack_conv_weights_bf16(w->conv1_w[j], C, d);
+            pack_conv_weights_bf16(w->conv2_w[j], C, d + 9 * (size_t)C * C);
+        }
+        // attention: B_q rows n < hC from Wq[k][n], rows hC.. from W_beta[k][n - hC] (K = C);
+        // B_o rows n < C from Wo[k][n] (K = hC); element (n, k) at (k / 8) * N * 8 + n * 8 + k % 8
+        const int NQ = h * C + C;
+        ctx->wat_step_bytes = ((size_t)NQ * C + (size_t)C * h * C) * sizeof(uint16_t);
+        std::vector<uint16_t> at(ctx->wat_step_bytes / sizeof(uint16_t) * c.n_scales);
+        for (int j = 0; j < c.n_scales; ++j) {
+            uint16_t* bq = at.data() + (size_t)j * (ctx->wat_step_bytes / sizeof(uint16_t));
+            uint16_t* bo = bq + (size_t)NQ * C;
+            for (int n = 0; n < NQ; ++n)
+                for (int k = 0; k < C; ++k) {
+                    float v = n < h * C ? w->Wq[j][(size_t)k * h * C + n] : w->W_beta[(size_t)k * C + (n - h * C)];
+                    bq[(size_t)(k / 8) * NQ * 8 + n * 8 + k % 8] = to_bf16_bits(v);
+                }
+            for (int n = 0; n < C; ++n)
+                for (int k = 0; k < h * C; ++k)
+                    bo[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->Wo[j][(size_t)k * C + n]);
+        }
+        qk_free(ctx, ctx->wat, ctx->wat_bytes);
+        ctx->wat = nullptr;
+        ctx->wat_bytes = at.size() * sizeof(uint16_t);
+        s = qk_alloc(ctx, &ctx->wat, ctx->wat_bytes);
+        if (s != QUARK_OK) return s;
+        QK_CUDA(ctx, cudaMemcpy(ctx->wat, at.data(), ctx->wat_bytes, cudaMemcpyHostToDevice));
+        qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
+        ctx->wtc = nullptr;
+        ctx->wtc_bytes = tc.size() * sizeof(uint16_t);
+        s = qk_alloc(ctx, &ctx->wtc, ctx->wtc_bytes);
+        if (s != QUARK_OK) return s;
+        QK_CUDA(ctx, cudaMemcpy(ctx->wtc, tc.data(), ctx->wtc_bytes, cudaMemcpyHostToDevice));
+    }
+    if (!ctx->dev_err) {
+        s = qk_alloc(ctx, (void**)&ctx->dev_err, sizeof(int));
+        if (s != QUARK_OK) return s;
+        QK_CUDA(ctx, cudaMemset(ctx->dev_err, 0, sizeof(int)));
+    }
     ctx->weights_loaded = true;
+    return QUARK_OK;
+}
+
+extern "C" quark_status quark_check_device(quark_ctx* ctx) {
+    if (!ctx) return qk_fail(nullptr, QUARK_EINVAL, "NULL context");
+    cudaSetDevice(ctx->device);
+    QK_CUDA(ctx, cudaDeviceSynchronize());
+    if (!ctx->dev_err) return QUARK_OK;
+    int e = 0;
+    QK_CUDA(ctx, cudaMemcpy(&e, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        QK_CUDA(ctx, cudaMemset(ctx->dev_err, 0, sizeof(int)));
+        return qk_fail(ctx, QUARK_ETIMEDOUT, "a kernel's bounded wait ran out (code %d); its outputs are invalid", e);
+    }
     return QUARK_OK;
 }
 
@@ -607,6 +686,8 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
     aa.w = ctx->wdev + ctx->off_attend[scale];
     aa.out = ldm->vattn;
     aa.beta = last ? ldm->beta : nullptr;
+    aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
+    aa.err = ctx->dev_err;
     for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
     s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
     if (s != QUARK_OK) return s;
@@ -625,6 +706,8 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
     ca.depth = ldm->depth;
     ca.t_raw = ldm->t_raw;
     ca.s_raw = ldm->s_raw;
+    ca.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
+    ca.err = ctx->dev_err;
     s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(ca, c.C, bf16, st); });
     if (s != QUARK_OK) return s;
     ldm->cur = 1 - ldm->cur;

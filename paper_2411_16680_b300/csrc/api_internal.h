@@ -30,6 +30,16 @@ struct quark_ctx {
     size_t off_attend[QUARK_MAX_SCALES] = {};
     size_t off_conv[QUARK_MAX_SCALES] = {};
     size_t off_collapse[QUARK_MAX_SCALES] = {};
+    // BF16 form: conv weights packed as tcgen05 B operands, per step W1 then W2
+    void* wtc = nullptr;
+    size_t wtc_bytes = 0;
+    size_t wtc_step_bytes = 0;
+    // BF16 form: [Wq | W_beta] and W^O packed as tcgen05 B operands, per step
+    void* wat = nullptr;
+    size_t wat_bytes = 0;
+    size_t wat_step_bytes = 0;
+    // device error word written by kernels whose bounded waits run out
+    int* dev_err = nullptr;
     // device memory accounting against cfg.hbm_cap_bytes
     std::mutex mem_mu;
     size_t bytes = 0;

@@ -105,16 +105,20 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a)
     for (int i = threadIdx.x; i < lay.total(); i += blockDim.x) sw[i] = a.w[i];
     __syncthreads();
 
+    // Block b covers pixels [(b / L) * EPB, + EPB) of layer b % L: the layer varies fastest, so
+    // the blocks resident at one time sample every layer of the same pixels and each texel of the
+    // feature level is fetched from DRAM about once per step rather than once per layer.
+    constexpr int EPB = ATT_THREADS / TPE;
     const int L = a.L, H = a.H, W = a.W;
-    const size_t n = (size_t)L * H * W;
-    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int sub = (int)(gid % TPE);
-    size_t e = gid / TPE;
-    const bool live = e < n;
-    if (!live) e = n - 1;  // keep the group's lanes in the shuffles; no stores
-    const int li = (int)(e / ((size_t)H * W));
-    const int y = (int)((e / W) % H);
-    const int x = (int)(e % W);
+    const size_t plane = (size_t)H * W;
+    const int li = (int)(blockIdx.x % L);
+    const int sub = (int)(threadIdx.x % TPE);
+    size_t pix = (size_t)(blockIdx.x / L) * EPB + threadIdx.x / TPE;
+    const bool live = pix < plane;
+    if (!live) pix = plane - 1;  // keep the group's lanes in the shuffles; no stores
+    const size_t e = (size_t)li * plane + pix;
+    const int y = (int)(pix / W);
+    const int x = (int)(pix % W);
     const int c0 = sub * 16;
 
     // ---- volume entering the step ----
@@ -284,8 +288,9 @@ template <typename T, int C, int NH>
 static cudaError_t launch_nh(const AttendArgs& a, Transition tr, bool last, cudaStream_t st) {
     const AttendLayout lay{C, NH};
     const size_t smem = (size_t)lay.total() * sizeof(float);
-    const size_t n = (size_t)a.L * a.H * a.W * (C / 16);
-    const unsigned grid = (unsigned)((n + ATT_THREADS - 1) / ATT_THREADS);
+    constexpr int EPB = ATT_THREADS / (C / 16);
+    const size_t plane = (size_t)a.H * a.W;
+    const unsigned grid = (unsigned)(((plane + EPB - 1) / EPB) * a.L);
 #define QK_LAUNCH(TRV, LASTV)                                                                          \
     do {                                                                                               \
         auto k = attend_kernel<T, C, NH, TRV, LASTV>;                                                  \
@@ -312,12 +317,12 @@ static cudaError_t launch_c(const AttendArgs& a, int heads, Transition tr, bool 
     return cudaErrorInvalidValue;
 }
 
+// FP32 form: this SIMT kernel.  BF16 form: projections on tcgen05 (k_attend_tc.cu).
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                           cudaStream_t st) {
-    if (C == 16) return bf16 ? launch_c<__nv_bfloat16, 16>(a, heads, tr, last, st)
-                             : launch_c<float, 16>(a, heads, tr, last, st);
-    if (C == 32) return bf16 ? launch_c<__nv_bfloat16, 32>(a, heads, tr, last, st)
-                             : launch_c<float, 32>(a, heads, tr, last, st);
+    if (bf16) return launch_attend_tc(a, C, heads, tr, last, st);
+    if (C == 16) return launch_c<float, 16>(a, heads, tr, last, st);
+    if (C == 32) return launch_c<float, 32>(a, heads, tr, last, st);
     return cudaErrorInvalidValue;
 }
 

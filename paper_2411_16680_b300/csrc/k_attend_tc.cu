@@ -1,0 +1,381 @@
+// Fused sample-attend step of the BF16 form with the dense contractions on tcgen05 tensor cores
+// (Sec. 3.3: MultiHead(N(V), D) = concat_i softmax(N(V) W_i^q D^T / sqrt(C)) D  W^O, plus the
+// blend-logit query N(V) W^beta of the last step, Sec. 3.2.3).
+//
+// A CTA owns 128 LDM elements: a 16 x 8 pixel tile of one layer plane (M = 128), so that the
+// bilinear taps of vertically and horizontally neighbouring elements hit the same L1 lines.  The
+// layer is the fastest-varying grid index: the CTAs resident at one time cover every layer of a
+// band of tiles, so each texel of the (larger than L2) feature level is fetched from DRAM about
+// once per step rather than once per layer.
+//   1. Volume entering the step (v0, or the previous volume, x2-upsampled on the fly), decoded
+//      depth, RMSNorm -> X (BF16) in shared memory as a K-major tcgen05 A operand.
+//   2. One MMA chain Q = X [Wq | W^beta] (N = hC (+C), K = C) into TMEM; copied to shared memory.
+//   3. Per element, two threads (16 channels each) reproject into every view, bilinearly sample
+//      the BF16 level-k features, and run the online softmax over views (FP32), exactly as the
+//      SIMT kernel; the last step also writes the blend logits.
+//   4. The head outputs O (BF16) go back to shared memory as an A operand; one MMA chain
+//      O W^O (N = C, K = hC) into TMEM; residual add in FP32; V_attn stored as BF16.
+// Completion of each MMA chain is signalled through an mbarrier; every wait is bounded.
+#include "device_common.cuh"
+#include "umma.cuh"
+
+namespace quark {
+
+constexpr int AT_M = 128;
+constexpr int AT_TW = 16, AT_TH = 8;  // pixel tile of the 128 elements
+constexpr uint64_t AT_WAIT_NS = 1000000000ull;
+
+template <int C, int NH>
+struct AtSmem {
+    static constexpr int NQ = NH * C + C;        // query columns incl. the blend query
+    static constexpr int QS = NQ + 4;            // padded fp32 row stride of the Q copy
+    static constexpr int x_off = 0;                               // A: 128 x C bf16
+    static constexpr int o_off = x_off + AT_M * C * 2;            // A: 128 x hC bf16
+    static constexpr int wq_off = o_off + AT_M * NH * C * 2;      // B: NQ x C bf16
+    static constexpr int wo_off = wq_off + NQ * C * 2;            // B: C x hC bf16
+    static constexpr int q_off = wo_off + C * NH * C * 2;         // fp32 128 x QS (Q copy, then output copy)
+    static constexpr int misc_off = q_off + AT_M * QS * 4;        // v0, g, w_d, b_d
+    static constexpr int beta_off = misc_off + 4 * C * 4;         // fp32 128 x QUARK_MAX_VIEWS blend logits
+    static constexpr int bar_off = beta_off + AT_M * QUARK_MAX_VIEWS * 4;
+    static constexpr int total = bar_off + 16;
+    static constexpr int tmem_cols = NQ <= 32 ? 32 : NQ <= 64 ? 64 : NQ <= 128 ? 128 : 256;
+};
+
+template <int C, int NH, int TR, bool LAST>
+__global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
+    constexpr int TPE = C / 16;
+    constexpr int NT = AT_M * TPE;
+    using S = AtSmem<C, NH>;
+    constexpr int NQ_USED = LAST ? S::NQ : NH * C;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t* s_x = sm + S::x_off;
+    uint8_t* s_o = sm + S::o_off;
+    uint8_t* s_wq = sm + S::wq_off;
+    uint8_t* s_wo = sm + S::wo_off;
+    float* s_q = reinterpret_cast<float*>(sm + S::q_off);
+    float* misc = reinterpret_cast<float*>(sm + S::misc_off);
+    float* s_beta = reinterpret_cast<float*>(sm + S::beta_off);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::bar_off);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::bar_off + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = a.L, H = a.H, W = a.W;
+    const int li = blockIdx.x;
+    const int e = tid / TPE, sub = tid % TPE, c0 = sub * 16;
+    const int x = blockIdx.y * AT_TW + e % AT_TW, y = blockIdx.z * AT_TH + e / AT_TW;
+    const bool live = x < W && y < H;
+    const int xc = min(x, W - 1), yc = min(y, H - 1);
+
+    // ---- weights: packed BF16 B operands, FP32 misc ----
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.wtc);
+        uint4* dq = reinterpret_cast<uint4*>(s_wq);
+        constexpr int nq = S::NQ * C * 2 / 16, no = C * NH * C * 2 / 16;
+        for (int i = tid; i < nq + no; i += NT) dq[i] = __ldg(src + i);  // wq then wo, contiguous
+    }
+    for (int i = tid; i < 4 * C; i += NT) misc[i] = a.w[i];  // v0 [C], g [C], w_d [C], b_d (padded)
+
+    // ---- volume entering the step, depth, RMSNorm ----
+    __syncthreads();
+    float vin[C];
+    if (TR == TR_INIT) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) vin[c] = misc[c];
+    } else if (TR == TR_SAME) {
+        const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(a.prev) +
+                                 (((size_t)li * H + yc) * W + xc) * C;
+#pragma unroll
+        for (int cc = 0; cc < C; cc += 16) {
+            float t[16];
+            load16(p + cc, t);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vin[cc + i] = t[i];
+        }
+    } else {
+        int ya, yb, xa, xb;
+        float wy, wx;
+        resize_taps(yc, 2, a.Hp, ya, yb, wy);
+        resize_taps(xc, 2, a.Wp, xa, xb, wx);
+        const __nv_bfloat16* base = reinterpret_cast<const __nv_bfloat16*>(a.prev) + (size_t)li * a.Hp * a.Wp * C;
+        const __nv_bfloat16* p00 = base + ((size_t)ya * a.Wp + xa) * C;
+        const __nv_bfloat16* p01 = base + ((size_t)ya * a.Wp + xb) * C;
+        const __nv_bfloat16* p10 = base + ((size_t)yb * a.Wp + xa) * C;
+        const __nv_bfloat16* p11 = base + ((size_t)yb * a.Wp + xb) * C;
+#pragma unroll
+        for (int cc = 0; cc < C; cc += 16) {
+            float t00[16], t01[16], t10[16], t11[16];
+            load16(p00 + cc, t00);
+            load16(p01 + cc, t01);
+            load16(p10 + cc, t10);
+            load16(p11 + cc, t11);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                float top = t00[i] + wx * (t01[i] - t00[i]);
+                float bot = t10[i] + wx * (t11[i] - t10[i]);
+                vin[cc + i] = top + wy * (bot - top);
+            }
+        }
+    }
+    float d;
+    if (TR == TR_INIT) {
+        d = depth_anchor(li, L, a.dp);
+    } else {
+        float t = misc[3 * C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) t = fmaf(vin[c], misc[2 * C + c], t);
+        d = depth_from_logit(t, li, L, a.dp);
+    }
+    float ms = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) ms = fmaf(vin[c], vin[c], ms);
+    const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
+    float vres[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float s = 0.f;
+#pragma unroll
+        for (int sb = 0; sb < TPE; ++sb)
+            if (sb == sub) s = vin[sb * 16 + i];
+        vres[i] = s;
+    }
+    {
+        // this thread's 16 channels of X = N(V_in): two 8-channel groups, K-major A layout
+        // (group g of row m at g * 128 * 16 + m * 16)
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            uint4 u;
+            __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = 8 * g + 2 * j;
+                hh[j] = __floats2bfloat162_rn(vres[i] * rinv * misc[C + c0 + i], vres[i + 1] * rinv * misc[C + c0 + i + 1]);
+            }
+            *reinterpret_cast<uint4*>(s_x + ((size_t)(c0 / 8 + g) * AT_M + e) * 16) = u;
+        }
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, S::tmem_cols);
+    if (tid == 0) umma::mbar_init(mbar, 1);
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // ---- Q = X [Wq | W^beta] ----
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma::idesc_bf16_f32(AT_M, NQ_USED);
+        const uint32_t a0 = umma::smem_u32(s_x), b0 = umma::smem_u32(s_wq);
+        constexpr uint32_t LBO_A = AT_M * 16, LBO_B = S::NQ * 16;
+#pragma unroll
+        for (int kk = 0; kk < C / 16; ++kk)
+            umma::mma_bf16(tmem, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128), umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128),
+                           idesc, kk > 0);
+        umma::commit(mbar);
+    }
+    bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, AT_WAIT_NS));
+    uint32_t failed_phase = 0;
+    umma::fence_after_sync();
+    if (!failed) {
+        // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16
+        const int q = warp & 3, grp = warp >> 2;
+        for (int ch = grp; ch < NQ_USED / 16; ch += TPE) {
+            float v[16];
+            umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+            float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    if (!failed) {
+        float qv[NH][16];
+        float qb[16];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + h * C + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 t = src[i];
+                qv[h][4 * i] = t.x; qv[h][4 * i + 1] = t.y; qv[h][4 * i + 2] = t.z; qv[h][4 * i + 3] = t.w;
+            }
+        }
+        if constexpr (LAST) {
+            const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 t = src[i];
+                qb[4 * i] = t.x; qb[4 * i + 1] = t.y; qb[4 * i + 2] = t.z; qb[4 * i + 3] = t.w;
+            }
+        }
+
+        // ---- views: sample, online softmax, weighted sum (FP32) ----
+        const float scale = 1.0f / sqrtf((float)C);
+        const float pxc = xc + 0.5f, pyc = yc + 0.5f;
+        float mx[NH], l[NH], o[NH][16];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            mx[h] = -INFINITY;
+            l[h] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[h][i] = 0.f;
+        }
+        const __nv_bfloat16* feat = reinterpret_cast<const __nv_bfloat16*>(a.feat);
+        const size_t vstride = (size_t)a.fh * a.fw * C;
+        for (int m = 0; m < a.V; ++m) {
+            float D[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) D[i] = 0.f;
+            float u, v;
+            Taps tp;
+            if (reproject(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp)) {
+                const __nv_bfloat16* fb = feat + m * vstride + c0;
+                const bool xa = tp.x0 >= 0, xb = tp.x0 + 1 < a.fw, ya = tp.y0 >= 0, yb = tp.y0 + 1 < a.fh;
+                if (ya && xa) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0) * C, (1 - tp.fy) * (1 - tp.fx), D);
+                if (ya && xb) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0 + 1) * C, (1 - tp.fy) * tp.fx, D);
+                if (yb && xa) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0) * C, tp.fy * (1 - tp.fx), D);
+                if (yb && xb) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0 + 1) * C, tp.fy * tp.fx, D);
+            }
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+                float s = 0.f;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) s = fmaf(qv[h][i], D[i], s);
+#pragma unroll
+                for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                s *= scale;
+                const float mn = fmaxf(mx[h], s);
+                const float cs = expf(mx[h] - mn);
+                const float p = expf(s - mn);
+                l[h] = fmaf(l[h], cs, p);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[h][i] = fmaf(o[h][i], cs, p * D[i]);
+                mx[h] = mn;
+            }
+            if constexpr (LAST) {
+                float s = 0.f;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) s = fmaf(qb[i], D[i], s);
+#pragma unroll
+                for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (sub == 0) s_beta[e * QUARK_MAX_VIEWS + m] = s * scale;
+            }
+        }
+        // head outputs -> BF16 A operand (K = h * C + channel)
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const float il = 1.0f / l[h];
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint4 u;
+                __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    hh[j] = __floats2bfloat162_rn(o[h][8 * g + 2 * j] * il, o[h][8 * g + 2 * j + 1] * il);
+                *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = u;
+            }
+        }
+    }
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    if (!failed) {
+        // ---- O W^O into TMEM columns [0, C) ----
+        if (tid == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16_f32(AT_M, C);
+            const uint32_t a0 = umma::smem_u32(s_o), b0 = umma::smem_u32(s_wo);
+            constexpr uint32_t LBO_A = AT_M * 16, LBO_B = C * 16;
+#pragma unroll
+            for (int kk = 0; kk < NH * C / 16; ++kk)
+                umma::mma_bf16(tmem, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128),
+                               umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128), idesc, kk > 0);
+            umma::commit(mbar);
+        }
+        failed = __syncthreads_or(!umma::mbar_wait(mbar, 1, AT_WAIT_NS));
+        failed_phase = 1;
+        umma::fence_after_sync();
+        if (!failed) {
+            const int q = warp & 3, grp = warp >> 2;
+            for (int ch = grp; ch < C / 16; ch += TPE) {
+                float v[16];
+                umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+                float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (!failed && live) {
+            float out[16];
+            const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 t = src[i];
+                out[4 * i] = vres[4 * i] + t.x;
+                out[4 * i + 1] = vres[4 * i + 1] + t.y;
+                out[4 * i + 2] = vres[4 * i + 2] + t.z;
+                out[4 * i + 3] = vres[4 * i + 3] + t.w;
+            }
+            store16(reinterpret_cast<__nv_bfloat16*>(a.out) + (((size_t)li * H + y) * W + x) * C + c0, out);
+        }
+        if constexpr (LAST) {
+            // blend logits of the element, contiguous [m] in the [H][W][L][V] layout
+            if (!failed && live)
+                for (int m = sub; m < a.V; m += TPE)
+                    a.beta[(((size_t)y * W + x) * L + li) * a.V + m] = s_beta[e * QUARK_MAX_VIEWS + m];
+        }
+    }
+    if (failed && tid == 0) atomicExch(a.err, 3 + (int)failed_phase);
+    if (failed) umma::mbar_wait(mbar, failed_phase, AT_WAIT_NS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(tmem, S::tmem_cols);
+}
+
+template <int C, int NH>
+static cudaError_t launch_tc_nh(const AttendArgs& a, Transition tr, bool last, cudaStream_t st) {
+    using S = AtSmem<C, NH>;
+    const size_t smem = S::total;
+    dim3 grid(a.L, (a.W + AT_TW - 1) / AT_TW, (a.H + AT_TH - 1) / AT_TH);
+    const int threads = AT_M * (C / 16);
+#define QK_TC_LAUNCH(TRV, LASTV)                                                                       \
+    do {                                                                                               \
+        auto k = attend_tc_kernel<C, NH, TRV, LASTV>;                                                  \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                \
+        k<<<grid, threads, smem, st>>>(a);                                                             \
+    } while (0)
+    if (tr == TR_INIT) {
+        if (last) QK_TC_LAUNCH(TR_INIT, true); else QK_TC_LAUNCH(TR_INIT, false);
+    } else if (tr == TR_SAME) {
+        if (last) QK_TC_LAUNCH(TR_SAME, true); else QK_TC_LAUNCH(TR_SAME, false);
+    } else {
+        if (last) QK_TC_LAUNCH(TR_UP2, true); else QK_TC_LAUNCH(TR_UP2, false);
+    }
+#undef QK_TC_LAUNCH
+    return cudaGetLastError();
+}
+
+template <int C>
+static cudaError_t launch_tc_c(const AttendArgs& a, int heads, Transition tr, bool last, cudaStream_t st) {
+    if (heads == 1) return launch_tc_nh<C, 1>(a, tr, last, st);
+    if (heads == 2) return launch_tc_nh<C, 2>(a, tr, last, st);
+    if (heads == 4) return launch_tc_nh<C, 4>(a, tr, last, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st) {
+    if (!a.wtc || !a.err) return cudaErrorInvalidValue;
+    if (C == 16) return launch_tc_c<16>(a, heads, tr, last, st);
+    if (C == 32) return launch_tc_c<32>(a, heads, tr, last, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace quark

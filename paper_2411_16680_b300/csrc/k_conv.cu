@@ -187,9 +187,11 @@ static cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// FP32 form: this SIMT kernel.  BF16 form: the tcgen05 kernel (k_conv_tc.cu).
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st) {
-    if (C == 16) return bf16 ? launch_t<__nv_bfloat16, 16>(a, st) : launch_t<float, 16>(a, st);
-    if (C == 32) return bf16 ? launch_t<__nv_bfloat16, 32>(a, st) : launch_t<float, 32>(a, st);
+    if (bf16) return launch_conv_block_tc(a, C, st);
+    if (C == 16) return launch_t<float, 16>(a, st);
+    if (C == 32) return launch_t<float, 32>(a, st);
     return cudaErrorInvalidValue;
 }
 

@@ -125,6 +125,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     aa.w = ctx->wdev + ctx->off_attend[scale];
     aa.out = vattn;
     aa.beta = last ? beta : nullptr;
+    aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
+    aa.err = ctx->dev_err;
     for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(*target, k, pyr->cams[m], k);
     e = launch_attend(aa, c.C, c.heads, tr, last, bf16, st);
     ctx->launches++;
@@ -143,6 +145,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     cv.depth = depth;
     cv.t_raw = t_raw;
     cv.s_raw = s_raw;
+    cv.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
+    cv.err = ctx->dev_err;
     e = launch_conv_block(cv, c.C, bf16, st);
     ctx->launches++;
     if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "conv block launch: %s", cudaGetErrorString(e));

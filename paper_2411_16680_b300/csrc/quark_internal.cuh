@@ -54,6 +54,8 @@ struct AttendArgs {
     const float* w;    // v0 [C], g [C], w_d [C], b_d (padded to C), Wq [C][h*C], Wo [h*C][C], W_beta [C][C]
     void* out;         // V_attn [L][H][W][C]
     float* beta;       // [H][W][L][V] blend logits (last step), else NULL
+    const void* wtc;   // BF16 form: [Wq | W_beta] and W^O packed as tcgen05 B operands
+    int* err;          // device error word (bounded waits)
     Geometry geo;
 };
 
@@ -68,6 +70,8 @@ struct ConvArgs {
     float* depth;      // [L][H][W]
     float* t_raw;      // [H][W][L]
     float* s_raw;      // [H][W][L]
+    const void* wtc;   // BF16 form: W1 then W2 packed as tcgen05 B operands (see pack_conv_weights_bf16)
+    int* err;          // device error word: set when a bounded wait inside the kernel runs out
 };
 
 struct RenderArgs {
@@ -123,6 +127,8 @@ cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                           cudaStream_t st);
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
+cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st);
+cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
 
 }  // namespace quark

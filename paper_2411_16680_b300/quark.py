@@ -83,6 +83,7 @@ def lib():
             "quark_set_profiling": ([vp, ct.c_int], ct.c_int),
             "quark_kernel_times": ([vp, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64),
                                     ct.c_int], ct.c_int),
+            "quark_check_device": ([vp], ct.c_int),
             "quark_update_fuse_noalloc": ([vp, vp, ct.c_int, ct.POINTER(Camera), vp, vp, vp, vp, vp, vp, vp, vp, vp],
                                           ct.c_int),
         }
@@ -273,6 +274,10 @@ class Context:
     def render_novel_view(self, pyr: Pyramid, ldm: LDM, rgba, stream=None):
         _check(lib().quark_render_novel_view(self.handle, pyr.handle, ldm.handle, _ptr(rgba), _stream(stream)),
                self.handle)
+
+    def check_device(self):
+        """Synchronise and raise if a kernel's bounded device-side wait ran out."""
+        _check(lib().quark_check_device(self.handle), self.handle)
 
     # ---- accounting ----
     def launch_count(self) -> int:
