@@ -233,6 +233,70 @@ quark_status quark_release_ldm(quark_ldm* ldm);
 /* Last error message of a context (or of the calling thread when ctx is NULL). */
 const char* quark_last_error(const quark_ctx* ctx);
 
+/* ---- Serving (spec form 5; the paper serves one novel view per frame, Sec. 1) ----------
+ * A server owns the context while it runs: one scheduler thread makes every launch.  Time steps
+ * (sets of posed input images) are encoded once and kept resident; requests name a time step,
+ * a target camera (whose width x height is the output resolution) and how many of the time
+ * step's views to use (the first n_views).  Requests queue FIFO and are admitted as soon as a
+ * slot (its own CUDA stream) is free and the request's device footprint fits under
+ * hbm_cap_bytes next to the resident pyramids; admitted requests run concurrently.  A result is
+ * identical whether the request ran alone or among others. */
+typedef struct quark_server quark_server;
+
+typedef struct {
+    int n_slots;           /* requests in flight on the device at once, 1..64 */
+    int queue_capacity;    /* pending requests beyond which submit returns QUARK_EBUSY */
+    size_t hbm_cap_bytes;  /* admission cap: resident pyramids + in-flight LDMs (0 = none) */
+} quark_serve_config;
+
+typedef struct {
+    int timestep;          /* resident time step (quark_serve_set_timestep) */
+    quark_camera target;   /* novel view; width x height = output resolution */
+    int n_views;           /* use the first n_views views of the time step */
+    float* rgba;           /* [height][width][4] float32 output: device memory or host memory
+                              (pinned); owned by the caller, valid until the result is polled */
+    uint64_t user_tag;
+} quark_request;
+
+typedef struct {
+    quark_status status;   /* QUARK_OK, or why the request failed (QUARK_EINVAL when cancelled) */
+    int cancelled;
+    uint64_t user_tag;
+    double queue_ms;       /* submit -> admission */
+    double gpu_ms;         /* admission -> completion seen by the scheduler */
+    double total_ms;       /* submit -> completion */
+} quark_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled, rejected;
+    int in_flight, queued;
+    double p50_ms, p99_ms, mean_ms;  /* submit -> completion of completed requests */
+    double fps;                      /* completed requests per second since start */
+    size_t hbm_in_use, hbm_high_water;
+} quark_stats;
+
+/* Start the scheduler thread.  The context's weights must be loaded. */
+quark_status quark_serve_start(quark_ctx* ctx, const quark_serve_config* cfg, quark_server** out);
+/* Encode (or re-encode) time step `timestep` from V posed images (as quark_encode_pyramid) and
+ * keep it resident.  Synchronous.  QUARK_EBUSY while requests for that step are queued/running. */
+quark_status quark_serve_set_timestep(quark_server* srv, int timestep, const float* images,
+                                      const quark_camera* cams, int V);
+/* Queue a request (thread-safe).  QUARK_EINVAL: bad camera / view count / NULL output;
+ * QUARK_ENOTFOUND: time step not resident; QUARK_ENOMEM: footprint can never fit the cap;
+ * QUARK_EBUSY: queue full. */
+quark_status quark_serve_submit(quark_server* srv, const quark_request* req, uint64_t* ticket);
+/* Wait up to timeout_us for a ticket (0: do not wait).  QUARK_OK consumes the ticket and fills
+ * *out; QUARK_EAGAIN (timeout_us == 0) / QUARK_ETIMEDOUT if not done; QUARK_ENOTFOUND if the
+ * ticket is unknown or already consumed. */
+quark_status quark_serve_poll(quark_server* srv, uint64_t ticket, int timeout_us, quark_result* out);
+/* Cancel a request that has not been admitted (QUARK_EBUSY once it runs). */
+quark_status quark_serve_cancel(quark_server* srv, uint64_t ticket);
+/* Hold (1) or resume (0) admissions; queued requests wait while held. */
+quark_status quark_serve_pause(quark_server* srv, int paused);
+quark_status quark_serve_stats(quark_server* srv, quark_stats* out);
+/* Cancel queued requests, wait for running ones, stop the thread, free the resident pyramids. */
+quark_status quark_serve_stop(quark_server* srv);
+
 /* Synchronise the context's device and report device-side failures: QUARK_ETIMEDOUT if a
  * kernel's bounded wait (on tensor-core completion) ran out since the last check, in which case
  * that launch's outputs are invalid; the error word is then cleared. */

@@ -547,9 +547,14 @@ extern "C" quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images
 
 static void ldm_free(quark_ldm* l) {
     quark_ctx* ctx = l->ctx;
-    for (auto& b : l->bufs) qk_free(ctx, b.p, b.bytes);
+    for (auto& b : l->bufs) {
+        if (l->async) cudaFreeAsync(b.p, l->stream);
+        else qk_free(ctx, b.p, b.bytes);
+    }
     delete l;
 }
+
+void qk_ldm_free(quark_ldm* l) { ldm_free(l); }
 
 extern "C" quark_status quark_release_ldm(quark_ldm* ldm) {
     if (!ldm) return QUARK_OK;
@@ -559,12 +564,47 @@ extern "C" quark_status quark_release_ldm(quark_ldm* ldm) {
 }
 
 static quark_status ldm_buf(quark_ldm* l, void** p, size_t bytes) {
-    quark_status s = qk_alloc(l->ctx, p, bytes);
+    quark_status s;
+    if (l->async) {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync(p, bytes, l->stream);
+        s = e == cudaSuccess ? QUARK_OK
+                             : qk_fail(l->ctx, QUARK_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+        if (e != cudaSuccess) cudaGetLastError();
+    } else {
+        s = qk_alloc(l->ctx, p, bytes);
+    }
     if (s == QUARK_OK) l->bufs.push_back({*p, bytes});
     return s;
 }
 
+// Bytes an LDM for `target` holds (three volumes, collapse buffer, decoded attributes, blend
+// logits for V views, and a host-output staging buffer when host_out).
+size_t qk_ldm_bytes(const quark_config& c, int width, int height, int V, bool host_out) {
+    const size_t elt = c.precision == QUARK_BF16 ? 2 : 4;
+    size_t vmax = 0, emax = 0, cmax = 0;
+    for (int j = 0; j < c.n_scales; ++j) {
+        size_t e = (size_t)c.L[j] * (height / c.k[j]) * (width / c.k[j]);
+        emax = std::max(emax, e);
+        vmax = std::max(vmax, e * c.C * elt);
+        if (j > 0 && c.L[j - 1] == 2 * c.L[j])
+            cmax = std::max(cmax, (size_t)c.L[j] * (height / c.k[j - 1]) * (width / c.k[j - 1]) * c.C * elt);
+    }
+    const int n = c.n_scales - 1;
+    const size_t last_e = (size_t)c.L[n] * (height / c.k[n]) * (width / c.k[n]);
+    return 3 * vmax + cmax + emax * 7 * sizeof(float) + last_e * V * sizeof(float) +
+           (host_out ? (size_t)width * height * 16 : 0);
+}
+
 extern "C" quark_status quark_ldm_create(quark_ctx* ctx, const quark_camera* target, quark_ldm** out) {
+    return qk_ldm_create(ctx, target, 0, nullptr, out);
+}
+
+// LDM for `target`.  With a non-NULL `async_stream` every buffer comes from the stream-ordered
+// allocator on that stream (no device-wide synchronisation) and the blend logits are sized for
+// V_beta views up front.
+quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_beta, cudaStream_t async_stream,
+                           quark_ldm** out) {
     if (!ctx || !target || !out) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     *out = nullptr;
     quark_status s = qk_validate_camera(ctx, *target, "target");
@@ -577,6 +617,8 @@ extern "C" quark_status quark_ldm_create(quark_ctx* ctx, const quark_camera* tar
     quark_ldm* l = new quark_ldm();
     l->ctx = ctx;
     l->target = *target;
+    l->async = async_stream != nullptr;
+    l->stream = async_stream;
     const size_t elt = c.precision == QUARK_BF16 ? 2 : 4;
     size_t vmax = 0, emax = 0, cmax = 0;
     for (int j = 0; j < c.n_scales; ++j) {
@@ -598,6 +640,10 @@ extern "C" quark_status quark_ldm_create(quark_ctx* ctx, const quark_camera* tar
     if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->t_raw, emax * sizeof(float));
     if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->s_raw, emax * sizeof(float));
     l->last_e = last_e;
+    if (s == QUARK_OK && V_beta > 0) {
+        s = ldm_buf(l, (void**)&l->beta, last_e * V_beta * sizeof(float));
+        l->beta_bytes = last_e * V_beta * sizeof(float);
+    }
     if (s != QUARK_OK) {
         ldm_free(l);
         return s;
@@ -615,14 +661,22 @@ static void step_dims(const quark_ldm* l, int j, int& L, int& H, int& W) {
 
 extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int scale, quark_ldm* ldm,
                                           void* stream) {
+    if (!pyr) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    return qk_update_fuse(ctx, pyr, pyr->V, scale, ldm, (cudaStream_t)stream);
+}
+
+// One Update & Fuse step using the first V_use views of the pyramid.
+quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use, int scale, quark_ldm* ldm,
+                            cudaStream_t stream) {
     if (!ctx || !pyr || !ldm) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (V_use < 1 || V_use > pyr->V) return qk_fail(ctx, QUARK_EINVAL, "view count %d outside 1..%d", V_use, pyr->V);
     if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
     const quark_config& c = ctx->cfg;
     if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);
     if (scale != 0 && ldm->done != scale - 1)
         return qk_fail(ctx, QUARK_EINVAL, "step %d needs step %d first (latest done: %d)", scale, scale - 1, ldm->done);
     cudaSetDevice(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t st = stream;
     const bool bf16 = c.precision == QUARK_BF16;
     const bool last = scale == c.n_scales - 1;
     int L, H, W;
@@ -631,7 +685,7 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
     quark_status s;
 
     if (last) {
-        size_t need = ldm->last_e * pyr->V * sizeof(float);
+        size_t need = ldm->last_e * V_use * sizeof(float);
         if (ldm->beta_bytes < need) {
             for (auto it = ldm->bufs.begin(); it != ldm->bufs.end(); ++it)
                 if (it->p == ldm->beta) {
@@ -644,7 +698,7 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
             if (s != QUARK_OK) return s;
             ldm->beta_bytes = need;
         }
-        ldm->V = pyr->V;
+        ldm->V = V_use;
     }
 
     // ---- transition ----
@@ -681,14 +735,14 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
     aa.L = L;
     aa.H = H;
     aa.W = W;
-    aa.V = pyr->V;
+    aa.V = V_use;
     aa.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
     aa.w = ctx->wdev + ctx->off_attend[scale];
     aa.out = ldm->vattn;
     aa.beta = last ? ldm->beta : nullptr;
     aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
     aa.err = ctx->dev_err;
-    for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
+    for (int m = 0; m < V_use; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
     s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
     if (s != QUARK_OK) return s;
 
@@ -717,12 +771,20 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
 
 extern "C" quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, float* rgba,
                                          void* stream) {
+    if (!ldm || !pyr) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    return qk_render(ctx, ldm, pyr, ldm->V, rgba, is_device_pointer(rgba) ? 0 : 1, (cudaStream_t)stream);
+}
+
+// Final render from the first V_use views; host_out: rgba is host memory (copied out on the stream).
+quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, int V_use, float* rgba,
+                       int host_out, cudaStream_t stream) {
     if (!ctx || !ldm || !pyr || !rgba) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     const quark_config& c = ctx->cfg;
     if (ldm->done != c.n_scales - 1) return qk_fail(ctx, QUARK_EINVAL, "render needs every Update & Fuse step first");
-    if (ldm->V != pyr->V) return qk_fail(ctx, QUARK_EINVAL, "pyramid differs from the one the LDM was solved with");
+    if (ldm->V != V_use || V_use > pyr->V)
+        return qk_fail(ctx, QUARK_EINVAL, "render uses %d views; the LDM was solved with %d", V_use, ldm->V);
     cudaSetDevice(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t st = stream;
     quark_ldm* l = const_cast<quark_ldm*>(ldm);
     const int n = c.n_scales - 1;
     RenderArgs ra{};
@@ -731,7 +793,7 @@ extern "C" quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, c
     ra.beta = l->beta;
     ra.rgba = (const float4*)pyr->rgba;
     ra.L = c.L[n];
-    ra.V = pyr->V;
+    ra.V = V_use;
     ra.Hl = l->target.height / c.k[n];
     ra.Wl = l->target.width / c.k[n];
     ra.s = c.k[n];
@@ -740,9 +802,8 @@ extern "C" quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, c
     ra.Hi = pyr->H;
     ra.Wi = pyr->W;
     ra.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
-    for (int m = 0; m < pyr->V; ++m) ra.geo.v[m] = qk_view_map(l->target, 1.0, pyr->cams[m], 1.0);
+    for (int m = 0; m < V_use; ++m) ra.geo.v[m] = qk_view_map(l->target, 1.0, pyr->cams[m], 1.0);
     const size_t out_bytes = (size_t)ra.Hout * ra.Wout * sizeof(float4);
-    const bool host_out = !is_device_pointer(rgba);
     if (host_out && l->out_bytes < out_bytes) {
         for (auto it = l->bufs.begin(); it != l->bufs.end(); ++it)
             if (it->p == l->out) {

@@ -89,6 +89,8 @@ struct quark_ldm {
     size_t last_e = 0;
     int V = 0;
     int done = -1;  // latest Update & Fuse step completed
+    bool async = false;            // buffers from the stream-ordered allocator on `stream`
+    cudaStream_t stream = nullptr;
 };
 
 quark_status qk_fail(const quark_ctx* ctx, quark_status st, const char* fmt, ...);
@@ -98,3 +100,13 @@ quark_status qk_launch(quark_ctx* ctx, cudaStream_t st, KernelFamily fam, const 
 quark_status qk_validate_config(const quark_config* c);
 quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what);
 quark::ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m);
+size_t qk_ldm_bytes(const quark_config& c, int width, int height, int V, bool host_out);
+quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_beta, cudaStream_t async_stream,
+                           quark_ldm** out);
+void qk_ldm_free(quark_ldm* l);
+quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use, int scale, quark_ldm* ldm,
+                            cudaStream_t stream);
+quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, int V_use, float* rgba,
+                       int host_out, cudaStream_t stream);
+quark_status qk_encode_pyramid_sync(quark_ctx* ctx, const float* images, const quark_camera* cams, int V,
+                                    quark_pyramid** out);

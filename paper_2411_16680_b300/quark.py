@@ -53,6 +53,27 @@ class Weights(ct.Structure):
                 ("W_a", _FP), ("b_a", _FP), ("W_beta", _FP)]
 
 
+class ServeConfig(ct.Structure):
+    _fields_ = [("n_slots", ct.c_int), ("queue_capacity", ct.c_int), ("hbm_cap_bytes", ct.c_size_t)]
+
+
+class Request(ct.Structure):
+    _fields_ = [("timestep", ct.c_int), ("target", Camera), ("n_views", ct.c_int), ("rgba", ct.c_void_p),
+                ("user_tag", ct.c_uint64)]
+
+
+class Result(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("cancelled", ct.c_int), ("user_tag", ct.c_uint64), ("queue_ms", ct.c_double),
+                ("gpu_ms", ct.c_double), ("total_ms", ct.c_double)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("submitted", ct.c_uint64), ("completed", ct.c_uint64), ("failed", ct.c_uint64),
+                ("cancelled", ct.c_uint64), ("rejected", ct.c_uint64), ("in_flight", ct.c_int), ("queued", ct.c_int),
+                ("p50_ms", ct.c_double), ("p99_ms", ct.c_double), ("mean_ms", ct.c_double), ("fps", ct.c_double),
+                ("hbm_in_use", ct.c_size_t), ("hbm_high_water", ct.c_size_t)]
+
+
 _lib = None
 
 
@@ -84,6 +105,14 @@ def lib():
             "quark_kernel_times": ([vp, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64),
                                     ct.c_int], ct.c_int),
             "quark_check_device": ([vp], ct.c_int),
+            "quark_serve_start": ([vp, ct.POINTER(ServeConfig), ct.POINTER(vp)], ct.c_int),
+            "quark_serve_set_timestep": ([vp, ct.c_int, vp, ct.POINTER(Camera), ct.c_int], ct.c_int),
+            "quark_serve_submit": ([vp, ct.POINTER(Request), ct.POINTER(ct.c_uint64)], ct.c_int),
+            "quark_serve_poll": ([vp, ct.c_uint64, ct.c_int, ct.POINTER(Result)], ct.c_int),
+            "quark_serve_cancel": ([vp, ct.c_uint64], ct.c_int),
+            "quark_serve_pause": ([vp, ct.c_int], ct.c_int),
+            "quark_serve_stats": ([vp, ct.POINTER(Stats)], ct.c_int),
+            "quark_serve_stop": ([vp], ct.c_int),
             "quark_update_fuse_noalloc": ([vp, vp, ct.c_int, ct.POINTER(Camera), vp, vp, vp, vp, vp, vp, vp, vp, vp],
                                           ct.c_int),
         }
@@ -296,3 +325,56 @@ class Context:
         n = (ct.c_uint64 * cap)()
         k = lib().quark_kernel_times(self.handle, names, ms, n, cap)
         return {names[i].decode(): (int(n[i]), float(ms[i])) for i in range(k)}
+
+
+class Server:
+    """quark_server: continuous-batching request loop over resident time steps (see quark.h)."""
+
+    def __init__(self, ctx: Context, n_slots: int = 8, queue_capacity: int = 1024, hbm_cap_bytes: int = 0):
+        self.ctx = ctx
+        cfg = ServeConfig(n_slots, queue_capacity, hbm_cap_bytes)
+        h = ct.c_void_p()
+        _check(lib().quark_serve_start(ctx.handle, ct.byref(cfg), ct.byref(h)), ctx.handle)
+        self.handle = h
+
+    def set_timestep(self, timestep: int, images, cams: Sequence):
+        V = len(cams)
+        arr = (Camera * V)(*[make_camera(c) for c in cams])
+        _check(lib().quark_serve_set_timestep(self.handle, timestep, _ptr(images), arr, V), self.ctx.handle)
+
+    def submit(self, timestep: int, target, n_views: int, rgba, user_tag: int = 0) -> int:
+        req = Request(timestep, make_camera(target), n_views, _ptr(rgba), user_tag)
+        t = ct.c_uint64()
+        _check(lib().quark_serve_submit(self.handle, ct.byref(req), ct.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0) -> Optional[Result]:
+        """The ticket's result, or None if not done within timeout_us (EAGAIN / ETIMEDOUT)."""
+        r = Result()
+        st = lib().quark_serve_poll(self.handle, ticket, timeout_us, ct.byref(r))
+        if st in (EAGAIN, ETIMEDOUT):
+            return None
+        _check(st)
+        return r
+
+    def cancel(self, ticket: int):
+        _check(lib().quark_serve_cancel(self.handle, ticket))
+
+    def pause(self, paused: bool):
+        _check(lib().quark_serve_pause(self.handle, 1 if paused else 0))
+
+    def stats(self) -> Stats:
+        st = Stats()
+        _check(lib().quark_serve_stats(self.handle, ct.byref(st)))
+        return st
+
+    def stop(self):
+        if getattr(self, "handle", None):
+            lib().quark_serve_stop(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
