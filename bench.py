@@ -248,6 +248,106 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     return r
 
 
+def run_serve(args):
+    """Serving workload: Poisson arrivals (mean `rate`/s, seed 42) for `duration` s after `serve_warmup`
+    s; output resolution uniform over {1280x720, 1920x1080, 3840x2160}; V uniform over {4, 8, 12, 16}
+    (the first V of 16 resident views); time step uniform over 4 resident 16-view 1080p steps;
+    pose = arc midpoint + U(-0.2, 0.2) m per axis; BF16 form; admission capped at 150 GB."""
+    import dataclasses
+    import threading
+    import numpy as np
+    import torch
+    from paper_2411_16680_b300 import quark
+
+    cfg = synth.config_1080p().replace(precision=synth.PREC_BF16)
+    W = synth.make_weights(cfg, sharp=args.sharp)
+    base = synth.scene_raycast(seed=1234, V=16, W=1920, H=1080, f=1400.0)
+    ctx = quark.Context(cfg)
+    ctx.load_weights(W)
+    srv = quark.Server(ctx, n_slots=args.slots, queue_capacity=args.queue, hbm_cap_bytes=150 << 30)
+    for t in range(4):
+        imgs = np.clip(base.images * (1.0 - 0.03 * t) + 0.02 * t, 0.0, 1.0).astype(np.float32)
+        srv.set_timestep(t, torch.tensor(imgs, device="cuda"), base.cams)
+    rng = np.random.default_rng(42)
+    res = [(1280, 720), (1920, 1080), (3840, 2160)]
+    total = args.serve_warmup + args.duration
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, int(total * args.rate * 1.5) + 10))
+    arrivals = arrivals[arrivals < total]
+    reqs = []
+    for a in arrivals:
+        w, h = res[rng.integers(0, 3)]
+        V = int(rng.choice([4, 8, 12, 16]))
+        ts = int(rng.integers(0, 4))
+        c = base.target.centre + rng.uniform(-0.2, 0.2, 3)
+        tgt = dataclasses.replace(base.target, width=w, height=h, fx=base.target.fx * w / 1920,
+                                  fy=base.target.fy * h / 1080, cx=w / 2, cy=h / 2, t=-base.target.R @ c)
+        reqs.append((float(a), ts, tgt, V, (w, h)))
+    pools = {r: [] for r in res}
+    lock = threading.Lock()
+    inflight = []
+    done = []
+    rejected = [0, 0]
+    stop = threading.Event()
+
+    def buf(r):
+        with lock:
+            if pools[r]:
+                return pools[r].pop()
+        return torch.empty(r[1], r[0], 4, device="cuda")
+
+    def completer():
+        while not stop.is_set() or inflight:
+            with lock:
+                item = inflight.pop(0) if inflight else None
+            if item is None:
+                time.sleep(0.0005)
+                continue
+            tk, t_arr, r, b = item
+            out = srv.poll(tk, timeout_us=60_000_000)
+            with lock:
+                pools[r].append(b)
+            if out is not None and out.status == 0:
+                done.append((t_arr, out.total_ms, out.queue_ms))
+
+    th = threading.Thread(target=completer)
+    th.start()
+    t0 = time.perf_counter()
+    for a, ts, tgt, V, r in reqs:
+        dt = a - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        b = buf(r)
+        try:
+            tk = srv.submit(ts, tgt, V, b)
+        except quark.QuarkError:
+            rejected[0 if a < args.serve_warmup else 1] += 1
+            with lock:
+                pools[r].append(b)
+            continue
+        with lock:
+            inflight.append((tk, a, r, b))
+    stop.set()
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.stop()
+    win = [d for d in done if d[0] >= args.serve_warmup]
+    lat = sorted(d[1] for d in win)
+    n_off = sum(1 for r in reqs if r[0] >= args.serve_warmup)
+    pct = lambda p: round(lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))], 2) if lat else None
+    line = {"metric": "serving: novel views/s on a Poisson request stream (mixed 720p/1080p/4K, V 4-16), p50/p99",
+            "value": round(len(win) / args.duration, 2), "unit": "requests/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic (seeded ray-cast scene; random-init weights)",
+            "config": {"workload": "serving", "offered_rate_per_s": args.rate, "duration_s": args.duration,
+                       "warmup_s": args.serve_warmup, "slots": args.slots, "queue_capacity": args.queue,
+                       "hbm_cap_gb": 150, "time_steps": 4, "views_resident": 16},
+            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99)},
+            "offered": n_off, "completed": len(win), "rejected_queue_full": rejected[1],
+            "hbm_high_water_gb": round(st.hbm_high_water / 2**30, 1), "wall_s": round(wall, 1)}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,10 +359,18 @@ def main():
     ap.add_argument("--sharp", action="store_true", help="sharp random weights instead of N(0, 0.02)")
     ap.add_argument("--size", default="1920x1080", help="WxH of views and output (profiling runs use a smaller case)")
     ap.add_argument("--forms", default="fp32,bf16", help="forms to time (comma separated)")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--rate", type=float, default=120.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--serve-warmup", type=float, default=5.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--queue", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
 
+    if args.serve:
+        return run_serve(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

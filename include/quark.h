@@ -227,6 +227,10 @@ enum {
 quark_status quark_ldm_read(quark_ldm* ldm, int field, void* dst, size_t bytes);
 size_t quark_ldm_field_bytes(const quark_ldm* ldm, int field);
 
+/* Copy pyramid level k ([V][H/k][W/k][C], the precision form's element type) to dst (host or
+ * device; synchronous).  `bytes` must equal the level's size. */
+quark_status quark_pyramid_read(const quark_pyramid* pyr, int k, void* dst, size_t bytes);
+
 quark_status quark_release_pyramid(quark_pyramid* pyr);
 quark_status quark_release_ldm(quark_ldm* ldm);
 
@@ -296,6 +300,52 @@ quark_status quark_serve_pause(quark_server* srv, int paused);
 quark_status quark_serve_stats(quark_server* srv, quark_stats* out);
 /* Cancel queued requests, wait for running ones, stop the thread, free the resident pyramids. */
 quark_status quark_serve_stop(quark_server* srv);
+
+/* ---- Differentiation (spec form 3; the paper trains with differentiable rendering,
+ * Sec. 3.1 and Sec. 3.4) -------------------------------------------------------------------------
+ * The differentiable stage is the last Update & Fuse step and the final render, as a function
+ * of the volume entering the step (V_in), the step's pyramid level (F) and the step's weights.
+ * FP32 form only.  The backward pass is hand written: the over operator's reverse scan, the
+ * blend softmax, the image sampling and its coordinates, the decode, the conv block, and the
+ * one-to-many attention with its sampling (feature gradient scattered into F with atomics,
+ * coordinate gradient through the decoded depth).  The sampled features are recomputed in the
+ * backward pass, not stored by the forward. */
+
+/* Volume entering step `scale` (collapse and x2 upsample of step scale-1's output), written to
+ * v_in [L][H][W][C] (device, float32).  Needs steps 0..scale-1 done on `ldm`. */
+quark_status quark_step_input(quark_ctx* ctx, quark_ldm* ldm, int scale, float* v_in, void* stream);
+
+/* Forward of the stage: last step from v_in [L][H][W][C] with level features feat [V][h][w][C]
+ * (device float32, e.g. a copy of the pyramid's level), then the render into rgba [H][W][4]
+ * (device).  `pyr` provides the cameras and the images the render samples. */
+quark_status quark_stage_forward(quark_ctx* ctx, const quark_pyramid* pyr, const float* feat, const float* v_in,
+                                 quark_ldm* ldm, float* rgba, void* stream);
+
+/* Weight gradients of the stage (device float32, caller-owned, every field overwritten); shapes
+ * as in quark_weights for the last step. */
+typedef struct {
+    float* attn_g;   /* [C] */
+    float* Wq;       /* [C][h C] */
+    float* Wo;       /* [h C][C] */
+    float* W_beta;   /* [C][C] */
+    float* conv_g;   /* [C] */
+    float* conv1_w;  /* [3][3][C][C] */
+    float* conv1_b;  /* [C] */
+    float* conv2_w;  /* [3][3][C][C] */
+    float* conv2_b;  /* [C] */
+    float* w_d;      /* [C] */
+    float* b_d;      /* [1] */
+    float* w_sigma;  /* [C] */
+    float* b_sigma;  /* [1] */
+} quark_stage_grads;
+
+/* Backward of the stage after quark_stage_forward on the same ldm / v_in / feat: from
+ * dl_drgb [H][W][3] (gradient of the loss w.r.t. the output RGB) writes dv_in [L][H][W][C],
+ * dfeat [V][h][w][C] and the weight gradients.  The feature gradient is accumulated with
+ * atomics, so its last bits depend on scheduling; every other output is deterministic. */
+quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid* pyr, const float* feat, const float* v_in,
+                                  quark_ldm* ldm, const float* dl_drgb, float* dv_in, float* dfeat,
+                                  const quark_stage_grads* grads, void* stream);
 
 /* Synchronise the context's device and report device-side failures: QUARK_ETIMEDOUT if a
  * kernel's bounded wait (on tensor-core completion) ran out since the last check, in which case

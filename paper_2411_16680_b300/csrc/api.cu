@@ -78,7 +78,7 @@ void qk_free(quark_ctx* ctx, void* p, size_t bytes) {
 // Launch accounting
 // -------------------------------------------------------------------------------------------
 
-static const char* kFamilyNames[KF_COUNT] = {"encode", "collapse", "attend", "conv_block", "render"};
+static const char* kFamilyNames[KF_COUNT] = {"encode", "collapse", "attend", "conv_block", "render", "backward"};
 
 static cudaEvent_t get_event(quark_ctx* ctx) {
     if (!ctx->event_pool.empty()) {
@@ -214,6 +214,7 @@ extern "C" quark_status quark_destroy(quark_ctx* ctx) {
     qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
     qk_free(ctx, ctx->wat, ctx->wat_bytes);
     qk_free(ctx, ctx->dev_err, sizeof(int));
+    qk_free(ctx, ctx->bwd_ws, ctx->bwd_ws_bytes);
     delete ctx;
     return QUARK_OK;
 }
@@ -468,6 +469,20 @@ extern "C" quark_status quark_release_pyramid(quark_pyramid* pyr) {
 
 static int level_index(int k) { return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3; }
 
+extern "C" quark_status quark_pyramid_read(const quark_pyramid* pyr, int k, void* dst, size_t bytes) {
+    if (!pyr || !dst) return qk_fail(nullptr, QUARK_EINVAL, "NULL argument");
+    if (k != 1 && k != 2 && k != 4 && k != 8) return qk_fail(pyr->ctx, QUARK_EINVAL, "k must be 1, 2, 4 or 8");
+    const int li = level_index(k);
+    if (!pyr->level[li]) return qk_fail(pyr->ctx, QUARK_EINVAL, "level %d is not part of this pyramid", k);
+    if (bytes != pyr->level_bytes[li])
+        return qk_fail(pyr->ctx, QUARK_EINVAL, "level %d holds %zu bytes, %zu given", k, pyr->level_bytes[li], bytes);
+    cudaSetDevice(pyr->ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(dst, pyr->level[li], bytes, cudaMemcpyDefault);
+    if (e != cudaSuccess) return qk_fail(pyr->ctx, QUARK_ECUDA, "level copy: %s", cudaGetErrorString(e));
+    return QUARK_OK;
+}
+
 extern "C" quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images, const quark_camera* cams, int V,
                                              void* stream, quark_pyramid** out) {
     if (!ctx || !images || !cams || !out) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
@@ -667,13 +682,13 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
 
 // One Update & Fuse step using the first V_use views of the pyramid.
 quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use, int scale, quark_ldm* ldm,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, const void* prev_override, const void* feat_override) {
     if (!ctx || !pyr || !ldm) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     if (V_use < 1 || V_use > pyr->V) return qk_fail(ctx, QUARK_EINVAL, "view count %d outside 1..%d", V_use, pyr->V);
     if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
     const quark_config& c = ctx->cfg;
     if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);
-    if (scale != 0 && ldm->done != scale - 1)
+    if (scale != 0 && ldm->done != scale - 1 && !prev_override)
         return qk_fail(ctx, QUARK_EINVAL, "step %d needs step %d first (latest done: %d)", scale, scale - 1, ldm->done);
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream;
@@ -705,7 +720,12 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     const void* prev = nullptr;
     int Hp = 0, Wp = 0;
     Transition tr = TR_INIT;
-    if (scale > 0) {
+    if (prev_override) {
+        prev = prev_override;  // the volume entering the step, given on the step's own grid
+        Hp = H;
+        Wp = W;
+        tr = TR_SAME;
+    } else if (scale > 0) {
         int Lp;
         step_dims(ldm, scale - 1, Lp, Hp, Wp);
         prev = ldm->vol[ldm->cur];
@@ -729,7 +749,7 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     aa.prev = prev;
     aa.Hp = Hp;
     aa.Wp = Wp;
-    aa.feat = pyr->level[level_index(k)];
+    aa.feat = feat_override ? feat_override : pyr->level[level_index(k)];
     aa.fh = pyr->H / k;
     aa.fw = pyr->W / k;
     aa.L = L;

@@ -11,7 +11,7 @@
 #include "quark.h"
 #include "quark_internal.cuh"
 
-enum KernelFamily { KF_ENCODE = 0, KF_COLLAPSE, KF_ATTEND, KF_CONV, KF_RENDER, KF_COUNT };
+enum KernelFamily { KF_ENCODE = 0, KF_COLLAPSE, KF_ATTEND, KF_CONV, KF_RENDER, KF_BACKWARD, KF_COUNT };
 
 struct PendingTiming {
     KernelFamily fam;
@@ -50,6 +50,9 @@ struct quark_ctx {
     std::vector<cudaEvent_t> event_pool;
     double fam_ms[KF_COUNT] = {};
     uint64_t fam_n[KF_COUNT] = {};
+    // differentiable stage: backward workspace (grown on demand)
+    void* bwd_ws = nullptr;
+    size_t bwd_ws_bytes = 0;
 };
 
 struct quark_pyramid {
@@ -105,7 +108,8 @@ quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_bet
                            quark_ldm** out);
 void qk_ldm_free(quark_ldm* l);
 quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use, int scale, quark_ldm* ldm,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const void* prev_override = nullptr,
+                            const void* feat_override = nullptr);
 quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, int V_use, float* rgba,
                        int host_out, cudaStream_t stream);
 quark_status qk_encode_pyramid_sync(quark_ctx* ctx, const float* images, const quark_camera* cams, int V,

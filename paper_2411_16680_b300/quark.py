@@ -74,6 +74,14 @@ class Stats(ct.Structure):
                 ("hbm_in_use", ct.c_size_t), ("hbm_high_water", ct.c_size_t)]
 
 
+STAGE_GRAD_FIELDS = ("attn_g", "Wq", "Wo", "W_beta", "conv_g", "conv1_w", "conv1_b", "conv2_w", "conv2_b", "w_d",
+                     "b_d", "w_sigma", "b_sigma")
+
+
+class StageGrads(ct.Structure):
+    _fields_ = [(n, ct.c_void_p) for n in STAGE_GRAD_FIELDS]
+
+
 _lib = None
 
 
@@ -105,6 +113,10 @@ def lib():
             "quark_kernel_times": ([vp, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64),
                                     ct.c_int], ct.c_int),
             "quark_check_device": ([vp], ct.c_int),
+            "quark_pyramid_read": ([vp, ct.c_int, vp, ct.c_size_t], ct.c_int),
+            "quark_step_input": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
+            "quark_stage_forward": ([vp, vp, vp, vp, vp, vp, vp], ct.c_int),
+            "quark_stage_backward": ([vp, vp, vp, vp, vp, vp, vp, vp, ct.POINTER(StageGrads), vp], ct.c_int),
             "quark_serve_start": ([vp, ct.POINTER(ServeConfig), ct.POINTER(vp)], ct.c_int),
             "quark_serve_set_timestep": ([vp, ct.c_int, vp, ct.POINTER(Camera), ct.c_int], ct.c_int),
             "quark_serve_submit": ([vp, ct.POINTER(Request), ct.POINTER(ct.c_uint64)], ct.c_int),
@@ -183,6 +195,11 @@ def _stream(stream) -> Optional[int]:
 class Pyramid:
     def __init__(self, ctx: "Context", handle: ct.c_void_p, V: int):
         self.ctx, self.handle, self.V = ctx, handle, V
+
+    def read_level(self, k: int, dst):
+        """Copy level k into dst (a tensor or array of exactly the level's size)."""
+        n = dst.numel() * dst.element_size() if hasattr(dst, "numel") else dst.nbytes
+        _check(lib().quark_pyramid_read(self.handle, k, _ptr(dst), n), self.ctx.handle)
 
     def release(self):
         if self.handle:
@@ -303,6 +320,19 @@ class Context:
     def render_novel_view(self, pyr: Pyramid, ldm: LDM, rgba, stream=None):
         _check(lib().quark_render_novel_view(self.handle, pyr.handle, ldm.handle, _ptr(rgba), _stream(stream)),
                self.handle)
+
+    # ---- differentiable stage (FP32): last Update & Fuse step + render ----
+    def step_input(self, ldm: LDM, scale: int, v_in, stream=None):
+        _check(lib().quark_step_input(self.handle, ldm.handle, scale, _ptr(v_in), _stream(stream)), self.handle)
+
+    def stage_forward(self, pyr: Pyramid, feat, v_in, ldm: LDM, rgba, stream=None):
+        _check(lib().quark_stage_forward(self.handle, pyr.handle, _ptr(feat), _ptr(v_in), ldm.handle, _ptr(rgba),
+                                         _stream(stream)), self.handle)
+
+    def stage_backward(self, pyr: Pyramid, feat, v_in, ldm: LDM, dl_drgb, dv_in, dfeat, grads: Dict, stream=None):
+        g = StageGrads(*[_ptr(grads[n]) for n in STAGE_GRAD_FIELDS])
+        _check(lib().quark_stage_backward(self.handle, pyr.handle, _ptr(feat), _ptr(v_in), ldm.handle, _ptr(dl_drgb),
+                                          _ptr(dv_in), _ptr(dfeat), ct.byref(g), _stream(stream)), self.handle)
 
     def check_device(self):
         """Synchronise and raise if a kernel's bounded device-side wait ran out."""
