@@ -218,6 +218,24 @@ def run_form(cfg, W, scene, steps, warmup, rank, world, dev, peaks):
     }
 
 
+def measured_traffic(fam, cfg, bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json), scaled from the
+    captured launch by its measured DRAM-to-algorithmic byte ratio; None when no capture covers this
+    kernel or its source changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        rec = json.load(fh).get(fam)
+    if not rec or rec.get("form") != ("bf16" if cfg.precision == 1 else "fp32"):
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        return None
+    return int(rec["dram_bytes_per_algorithmic_byte"] * bytes_per_launch)
+
+
 def roofline(cfg, V, img_h, img_w, res, peaks):
     work = accounting.per_view_work(cfg, V, img_h, img_w)
     steps_done = None
@@ -240,7 +258,7 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
              "peak_source": f"{peaks['source']} copy bandwidth"}
     r["frac"] = round(r["achieved"] / r["peak"], 4)
     r["kernel"] = fam
-    r["traffic"] = None
+    r["traffic"] = measured_traffic(fam, cfg, bytes_per_launch)
     r["algorithmic_bytes_per_launch"] = int(bytes_per_launch)
     r["algorithmic_flops_per_launch"] = int(flops_per_launch)
     r["avg_launch_ms"] = round(per_launch_ms, 4)

@@ -25,19 +25,23 @@ constexpr int AT_M = 128;
 constexpr int AT_TW = 16, AT_TH = 8;  // pixel tile of the 128 elements
 constexpr uint64_t AT_WAIT_NS = 1000000000ull;
 
-template <int C, int NH>
+// Shared memory of one CTA.  Only the query columns in use are copied (the blend query exists
+// on the last step only) and the blend logits are staged for the V views present, so that the
+// rest of the SM's unified L1 stays free to cache the sampled texels.
+template <int C, int NH, bool LAST>
 struct AtSmem {
-    static constexpr int NQ = NH * C + C;        // query columns incl. the blend query
-    static constexpr int QS = NQ + 4;            // padded fp32 row stride of the Q copy
+    static constexpr int NQ = NH * C + C;        // packed query columns incl. the blend query
+    static constexpr int NQ_USED = LAST ? NQ : NH * C;
+    static constexpr int QS = NQ_USED + 4;       // padded fp32 row stride of the Q copy
     static constexpr int x_off = 0;                               // A: 128 x C bf16
     static constexpr int o_off = x_off + AT_M * C * 2;            // A: 128 x hC bf16
     static constexpr int wq_off = o_off + AT_M * NH * C * 2;      // B: NQ x C bf16
     static constexpr int wo_off = wq_off + NQ * C * 2;            // B: C x hC bf16
     static constexpr int q_off = wo_off + C * NH * C * 2;         // fp32 128 x QS (Q copy, then output copy)
     static constexpr int misc_off = q_off + AT_M * QS * 4;        // v0, g, w_d, b_d
-    static constexpr int beta_off = misc_off + 4 * C * 4;         // fp32 128 x QUARK_MAX_VIEWS blend logits
-    static constexpr int bar_off = beta_off + AT_M * QUARK_MAX_VIEWS * 4;
-    static constexpr int total = bar_off + 16;
+    static constexpr int bar_off = misc_off + 4 * C * 4;
+    static constexpr int beta_off = bar_off + 16;                 // fp32 128 x V blend logits (last step)
+    static int total(int V) { return beta_off + (LAST ? AT_M * V * 4 : 0); }
     static constexpr int tmem_cols = NQ <= 32 ? 32 : NQ <= 64 ? 64 : NQ <= 128 ? 128 : 256;
 };
 
@@ -45,8 +49,8 @@ template <int C, int NH, int TR, bool LAST>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;
     constexpr int NT = AT_M * TPE;
-    using S = AtSmem<C, NH>;
-    constexpr int NQ_USED = LAST ? S::NQ : NH * C;
+    using S = AtSmem<C, NH, LAST>;
+    constexpr int NQ_USED = S::NQ_USED;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_x = sm + S::x_off;
     uint8_t* s_o = sm + S::o_off;
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 for (int i = 0; i < 16; ++i) s = fmaf(qb[i], D[i], s);
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                if (sub == 0) s_beta[e * QUARK_MAX_VIEWS + m] = s * scale;
+                if (sub == 0) s_beta[e * a.V + m] = s * scale;
             }
         }
         // head outputs -> BF16 A operand (K = h * C + channel)
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             // blend logits of the element, contiguous [m] in the [H][W][L][V] layout
             if (!failed && live)
                 for (int m = sub; m < a.V; m += TPE)
-                    a.beta[(((size_t)y * W + x) * L + li) * a.V + m] = s_beta[e * QUARK_MAX_VIEWS + m];
+                    a.beta[(((size_t)y * W + x) * L + li) * a.V + m] = s_beta[e * a.V + m];
         }
     }
     if (failed && tid == 0) atomicExch(a.err, 3 + (int)failed_phase);
@@ -341,12 +345,11 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 
 template <int C, int NH>
 static cudaError_t launch_tc_nh(const AttendArgs& a, Transition tr, bool last, cudaStream_t st) {
-    using S = AtSmem<C, NH>;
-    const size_t smem = S::total;
     dim3 grid(a.L, (a.W + AT_TW - 1) / AT_TW, (a.H + AT_TH - 1) / AT_TH);
     const int threads = AT_M * (C / 16);
 #define QK_TC_LAUNCH(TRV, LASTV)                                                                       \
     do {                                                                                               \
+        const size_t smem = AtSmem<C, NH, LASTV>::total(a.V);                                          \
         auto k = attend_tc_kernel<C, NH, TRV, LASTV>;                                                  \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                \

@@ -3,7 +3,8 @@
 // attributes (Sec. 3.2.2, Sec. 3.2.3 Eq. depth_activation).  BF16 operands, FP32 accumulation in
 // TMEM; normalisation, gelu, residual and decode in FP32 registers.
 //
-// Implicit GEMM.  A CTA owns an output tile of TC_R rows x 126 columns of one layer plane.  Each
+// Implicit GEMM.  A CTA owns an output tile of TC_R rows x 126 columns of one layer plane; two
+// CTAs share an SM, so one CTA's tile loads overlap the other's MMAs and epilogues.  Each
 // tile row is one M = 128 MMA block (pixels), N = C (output channels), K = 9 taps x C input
 // channels.  The normalised input tile (TC_R + 4 rows x 130 columns) is stored channel-group
 // major -- pixel p, channel c at (c / 8) * NPIX * 16 + p * 16 + (c % 8) * 2 -- so the A operand of
@@ -19,7 +20,7 @@
 
 namespace quark {
 
-constexpr int TC_R = 8;
+constexpr int TC_R = 4;  // output rows per tile: two CTAs fit on an SM
 constexpr int TC_M = 128;
 constexpr int TC_OUT_W = TC_M - 2;
 constexpr int TC_IN_W = TC_M + 2;
@@ -33,15 +34,18 @@ struct TcSmem {
     static constexpr int G = C / 8;
     static constexpr int NPIX_IN = TC_IN_H * TC_IN_W + 8;
     static constexpr int NPIX_MID = TC_MID_H * TC_M + 8;
+    // the mid tile reuses the input tile's memory: conv1 has finished reading it when the
+    // first epilogue writes gelu(conv1)
     static constexpr int in_off = 0;
-    static constexpr int mid_off = in_off + G * NPIX_IN * 16;
-    static constexpr int w1_off = mid_off + G * NPIX_MID * 16;
+    static constexpr int mid_off = 0;
+    static_assert(NPIX_MID <= NPIX_IN, "mid tile must fit in the input tile");
+    static constexpr int w1_off = in_off + G * NPIX_IN * 16;
     static constexpr int w2_off = w1_off + 9 * C * C * 2;
     static constexpr int misc_off = w2_off + 9 * C * C * 2;
     static constexpr int misc_n = 8 * C + 8;
     static constexpr int bar_off = misc_off + misc_n * 4;
     static constexpr int total = bar_off + 16;
-    static_assert(total <= 232448, "shared memory budget");
+    static_assert(2 * (total + 1024) <= 233472, "two CTAs per SM");
 };
 
 template <int C>
@@ -66,8 +70,10 @@ __device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[C]) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const ConvArgs a) {
     using S = TcSmem<C>;
+    constexpr uint32_t TMEM_COLS = TC_MID_H * C <= 128 ? 128 : 256;  // conv1 accumulators, per CTA
+    static_assert(TC_MID_H * C <= 256, "TMEM budget of two CTAs");
     const ConvLayout lay{C};
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_in = sm + S::in_off;
@@ -112,30 +118,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     __syncthreads();
 
     // ---- normalised input tile: rows y0-2 .. y0+TC_R+1, columns x0-2 .. x0+127 ----
-    for (int p = tid; p < TC_IN_H * TC_IN_W; p += TC_THREADS) {
-        const int gy = y0 - 2 + p / TC_IN_W, gx = x0 - 2 + p % TC_IN_W;
-        float v[C];
+    // two pixels per thread per iteration: both pixels' loads are in flight before either is used
+    constexpr int NPIX = TC_IN_H * TC_IN_W;
+    for (int p0 = tid; p0 < NPIX; p0 += 2 * TC_THREADS) {
+        uint4 raw[2][C / 8];
+        bool in[2];
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const __nv_bfloat16* src = vin + ((size_t)gy * W + gx) * C;
+        for (int u = 0; u < 2; ++u) {
+            const int p = p0 + u * TC_THREADS;
+            const int gy = y0 - 2 + p / TC_IN_W, gx = x0 - 2 + p % TC_IN_W;
+            in[u] = p < NPIX && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const uint4* src = reinterpret_cast<const uint4*>(vin + ((size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0)) * C);
 #pragma unroll
-            for (int c0 = 0; c0 < C; c0 += 16) {
-                float t[16];
-                load16(src + c0, t);
+            for (int g = 0; g < C / 8; ++g) raw[u][g] = in[u] ? __ldg(src + g) : make_uint4(0, 0, 0, 0);
+        }
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[c0 + i] = t[i];
+        for (int u = 0; u < 2; ++u) {
+            const int p = p0 + u * TC_THREADS;
+            if (p >= NPIX) break;
+            float v[C];
+#pragma unroll
+            for (int g = 0; g < C / 8; ++g) {
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw[u][g]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 f = __bfloat1622float2(h[j]);
+                    v[8 * g + 2 * j] = f.x;
+                    v[8 * g + 2 * j + 1] = f.y;
+                }
             }
             float ms = 0.f;
 #pragma unroll
             for (int c = 0; c < C; ++c) ms = fmaf(v[c], v[c], ms);
-            const float r = 1.0f / sqrtf(ms / C + 1e-6f);
+            const float r = in[u] ? 1.0f / sqrtf(ms / C + 1e-6f) : 0.f;
 #pragma unroll
             for (int c = 0; c < C; ++c) v[c] = v[c] * r * misc[c];
+            store_pixel_bf16<C>(s_in, S::NPIX_IN, p, v);
         }
-        store_pixel_bf16<C>(s_in, S::NPIX_IN, p, v);
     }
-    if (warp == 0) umma::tmem_alloc(tslot, 512);
+    if (warp == 0) umma::tmem_alloc(tslot, TMEM_COLS);
     if (tid == 0) umma::mbar_init(mbar, 1);
     umma::fence_smem_to_async();
     umma::fence_before_sync();
@@ -255,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 0) umma::tmem_dealloc(tmem, 512);
+    if (warp == 0) umma::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 template <int C>

@@ -1,8 +1,9 @@
 // Final render (Sec. 3.1 Eq. 1; Sec. 3.2.3 "Upsampling & Activation").  One thread per output
-// pixel: bilinear upsample by s of the raw depth / density / blend logits of the last LDM,
-// activation (Eq. depth_activation, sigmoid, softmax over views), back-projection of every
-// input image onto each layer (zero padding), blend, and the over operator front to back
-// (l = L nearest first): C += T alpha c, T *= (1 - alpha).  Output RGBA with A = 1 - T.
+// pixel: bilinear upsample by s of the raw depth / density / blend logits of the last LDM (a
+// direct read when s = 1), activation (Eq. depth_activation, sigmoid, softmax over views in one
+// online pass), back-projection of every input image onto each layer (zero padding), blend, and
+// the over operator front to back (l = L nearest first): C += T alpha c, T *= (1 - alpha).
+// Output RGBA with A = 1 - T.
 #include "device_common.cuh"
 
 namespace quark {
@@ -27,48 +28,81 @@ __device__ __forceinline__ float4 sample_rgba(const float4* __restrict__ img, in
     return r;
 }
 
+// One layer's contribution: blend-weighted colour of the V views with an online softmax over the
+// views (running maximum, rescaled sums), so the logits are read once.
+template <typename LogitFn>
+__device__ __forceinline__ void blend_layer(const RenderArgs& a, LogitFn logit, float pxc, float pyc, float d,
+                                            float& cr, float& cg, float& cb) {
+    const size_t img_stride = (size_t)a.Hi * a.Wi;
+    float mx = -INFINITY, sum = 0.f, lr = 0.f, lg = 0.f, lb = 0.f;
+    for (int m = 0; m < a.V; ++m) {
+        const float b = logit(m);
+        const float mn = fmaxf(mx, b);
+        const float sc = expf(mx - mn), p = expf(b - mn);
+        sum = fmaf(sum, sc, p);
+        lr *= sc;
+        lg *= sc;
+        lb *= sc;
+        float u, v;
+        if (reproject(a.geo.v[m], pxc, pyc, d, u, v)) {
+            const float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, u, v);
+            lr = fmaf(p, c.x, lr);
+            lg = fmaf(p, c.y, lg);
+            lb = fmaf(p, c.z, lb);
+        }
+        mx = mn;
+    }
+    const float is = 1.0f / sum;
+    cr = lr * is;
+    cg = lg * is;
+    cb = lb * is;
+}
+
 __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)a.Hout * a.Wout) return;
     const int X = (int)(idx % a.Wout), Y = (int)(idx / a.Wout);
     const int L = a.L, V = a.V;
-    int y0, y1, x0, x1;
-    float wy, wx;
-    resize_taps(Y, a.s, a.Hl, y0, y1, wy);
-    resize_taps(X, a.s, a.Wl, x0, x1, wx);
-    const size_t q00 = (size_t)y0 * a.Wl + x0, q01 = (size_t)y0 * a.Wl + x1;
-    const size_t q10 = (size_t)y1 * a.Wl + x0, q11 = (size_t)y1 * a.Wl + x1;
-    auto up = [&](const float* f, size_t stride, size_t off) {
-        float top = f[q00 * stride + off] * (1 - wx) + f[q01 * stride + off] * wx;
-        float bot = f[q10 * stride + off] * (1 - wx) + f[q11 * stride + off] * wx;
-        return top * (1 - wy) + bot * wy;
-    };
     const float pxc = X + 0.5f, pyc = Y + 0.5f;
-    const size_t img_stride = (size_t)a.Hi * a.Wi;
     float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
-    for (int li = L - 1; li >= 0; --li) {
-        const float d = depth_from_logit(up(a.t_raw, L, li), li, L, a.dp);
-        const float al = sigmoidf_(up(a.s_raw, L, li));
-        const size_t bstride = (size_t)L * V, boff = (size_t)li * V;
-        float bmax = -INFINITY;
-        for (int m = 0; m < V; ++m) bmax = fmaxf(bmax, up(a.beta, bstride, boff + m));
-        float sum = 0.f, lr = 0.f, lg = 0.f, lb = 0.f;
-        for (int m = 0; m < V; ++m) {
-            const float p = expf(up(a.beta, bstride, boff + m) - bmax);
-            sum += p;
-            float u, v;
-            if (reproject(a.geo.v[m], pxc, pyc, d, u, v)) {
-                float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, u, v);
-                lr = fmaf(p, c.x, lr);
-                lg = fmaf(p, c.y, lg);
-                lb = fmaf(p, c.z, lb);
-            }
+    if (a.s == 1) {
+        // the LDM grid is the output grid: the upsample is the identity
+        for (int li = L - 1; li >= 0; --li) {
+            const float d = depth_from_logit(a.t_raw[idx * L + li], li, L, a.dp);
+            const float al = sigmoidf_(a.s_raw[idx * L + li]);
+            const float* bl = a.beta + (idx * L + li) * V;
+            float r, g, b;
+            blend_layer(a, [&](int m) { return __ldg(bl + m); }, pxc, pyc, d, r, g, b);
+            const float w = T * al;
+            cr = fmaf(w, r, cr);
+            cg = fmaf(w, g, cg);
+            cb = fmaf(w, b, cb);
+            T *= 1.f - al;
         }
-        const float w = T * al / sum;
-        cr = fmaf(w, lr, cr);
-        cg = fmaf(w, lg, cg);
-        cb = fmaf(w, lb, cb);
-        T *= 1.f - al;
+    } else {
+        int y0, y1, x0, x1;
+        float wy, wx;
+        resize_taps(Y, a.s, a.Hl, y0, y1, wy);
+        resize_taps(X, a.s, a.Wl, x0, x1, wx);
+        const size_t q00 = (size_t)y0 * a.Wl + x0, q01 = (size_t)y0 * a.Wl + x1;
+        const size_t q10 = (size_t)y1 * a.Wl + x0, q11 = (size_t)y1 * a.Wl + x1;
+        auto up = [&](const float* f, size_t stride, size_t off) {
+            float top = f[q00 * stride + off] * (1 - wx) + f[q01 * stride + off] * wx;
+            float bot = f[q10 * stride + off] * (1 - wx) + f[q11 * stride + off] * wx;
+            return top * (1 - wy) + bot * wy;
+        };
+        for (int li = L - 1; li >= 0; --li) {
+            const float d = depth_from_logit(up(a.t_raw, L, li), li, L, a.dp);
+            const float al = sigmoidf_(up(a.s_raw, L, li));
+            const size_t bstride = (size_t)L * V, boff = (size_t)li * V;
+            float r, g, b;
+            blend_layer(a, [&](int m) { return up(a.beta, bstride, boff + m); }, pxc, pyc, d, r, g, b);
+            const float w = T * al;
+            cr = fmaf(w, r, cr);
+            cg = fmaf(w, g, cg);
+            cb = fmaf(w, b, cb);
+            T *= 1.f - al;
+        }
     }
     a.out[idx] = make_float4(cr, cg, cb, 1.f - T);
 }
