@@ -45,6 +45,7 @@ struct AtSmem {
     static constexpr int tmem_cols = NQ <= 32 ? 32 : NQ <= 64 ? 64 : NQ <= 128 ? 128 : 256;
 };
 
+
 template <int C, int NH, int TR, bool LAST>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;
@@ -80,68 +81,48 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     for (int i = tid; i < 4 * C; i += NT) misc[i] = a.w[i];  // v0 [C], g [C], w_d [C], b_d (padded)
 
     // ---- volume entering the step, depth, RMSNorm ----
+    // Each thread of an element's group holds its own 16 channels (vres); the depth logit and the
+    // mean square are partial sums over those channels, completed with shuffles in the group.
     __syncthreads();
-    float vin[C];
+    float vres[16];
     if (TR == TR_INIT) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) vin[c] = misc[c];
+        for (int i = 0; i < 16; ++i) vres[i] = misc[c0 + i];
     } else if (TR == TR_SAME) {
-        const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(a.prev) +
-                                 (((size_t)li * H + yc) * W + xc) * C;
-#pragma unroll
-        for (int cc = 0; cc < C; cc += 16) {
-            float t[16];
-            load16(p + cc, t);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) vin[cc + i] = t[i];
-        }
+        load16(reinterpret_cast<const __nv_bfloat16*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0, vres);
     } else {
         int ya, yb, xa, xb;
         float wy, wx;
         resize_taps(yc, 2, a.Hp, ya, yb, wy);
         resize_taps(xc, 2, a.Wp, xa, xb, wx);
-        const __nv_bfloat16* base = reinterpret_cast<const __nv_bfloat16*>(a.prev) + (size_t)li * a.Hp * a.Wp * C;
-        const __nv_bfloat16* p00 = base + ((size_t)ya * a.Wp + xa) * C;
-        const __nv_bfloat16* p01 = base + ((size_t)ya * a.Wp + xb) * C;
-        const __nv_bfloat16* p10 = base + ((size_t)yb * a.Wp + xa) * C;
-        const __nv_bfloat16* p11 = base + ((size_t)yb * a.Wp + xb) * C;
+        const __nv_bfloat16* base =
+            reinterpret_cast<const __nv_bfloat16*>(a.prev) + (size_t)li * a.Hp * a.Wp * C + c0;
+        float t00[16], t01[16], t10[16], t11[16];
+        load16(base + ((size_t)ya * a.Wp + xa) * C, t00);
+        load16(base + ((size_t)ya * a.Wp + xb) * C, t01);
+        load16(base + ((size_t)yb * a.Wp + xa) * C, t10);
+        load16(base + ((size_t)yb * a.Wp + xb) * C, t11);
 #pragma unroll
-        for (int cc = 0; cc < C; cc += 16) {
-            float t00[16], t01[16], t10[16], t11[16];
-            load16(p00 + cc, t00);
-            load16(p01 + cc, t01);
-            load16(p10 + cc, t10);
-            load16(p11 + cc, t11);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float top = t00[i] + wx * (t01[i] - t00[i]);
-                float bot = t10[i] + wx * (t11[i] - t10[i]);
-                vin[cc + i] = top + wy * (bot - top);
-            }
+        for (int i = 0; i < 16; ++i) {
+            const float top = t00[i] + wx * (t01[i] - t00[i]);
+            const float bot = t10[i] + wx * (t11[i] - t10[i]);
+            vres[i] = top + wy * (bot - top);
         }
     }
-    float d;
-    if (TR == TR_INIT) {
-        d = depth_anchor(li, L, a.dp);
-    } else {
-        float t = misc[3 * C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) t = fmaf(vin[c], misc[2 * C + c], t);
-        d = depth_from_logit(t, li, L, a.dp);
-    }
-    float ms = 0.f;
-#pragma unroll
-    for (int c = 0; c < C; ++c) ms = fmaf(vin[c], vin[c], ms);
-    const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
-    float vres[16];
+    float tpart = 0.f, ms = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        float s = 0.f;
-#pragma unroll
-        for (int sb = 0; sb < TPE; ++sb)
-            if (sb == sub) s = vin[sb * 16 + i];
-        vres[i] = s;
+        tpart = fmaf(vres[i], misc[2 * C + c0 + i], tpart);
+        ms = fmaf(vres[i], vres[i], ms);
     }
+#pragma unroll
+    for (int off = 1; off < TPE; off <<= 1) {
+        tpart += __shfl_xor_sync(0xffffffffu, tpart, off);
+        ms += __shfl_xor_sync(0xffffffffu, ms, off);
+    }
+    const float d = TR == TR_INIT ? depth_anchor(li, L, a.dp)
+                                  : depth_from_logit(misc[3 * C] + tpart, li, L, a.dp);
+    const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
     {
         // this thread's 16 channels of X = N(V_in): two 8-channel groups, K-major A layout
         // (group g of row m at g * 128 * 16 + m * 16)
@@ -196,7 +177,6 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 
     if (!failed) {
         float qv[NH][16];
-        float qb[16];
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
             const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + h * C + c0);
@@ -206,14 +186,8 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 qv[h][4 * i] = t.x; qv[h][4 * i + 1] = t.y; qv[h][4 * i + 2] = t.z; qv[h][4 * i + 3] = t.w;
             }
         }
-        if constexpr (LAST) {
-            const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float4 t = src[i];
-                qb[4 * i] = t.x; qb[4 * i + 1] = t.y; qb[4 * i + 2] = t.z; qb[4 * i + 3] = t.w;
-            }
-        }
+        // the blend query stays in shared memory (read once per view) to keep registers for the loop
+        const float4* qb4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
 
         // ---- views: sample, online softmax, weighted sum (FP32) ----
         const float scale = 1.0f / sqrtf((float)C);
@@ -235,12 +209,13 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             float u, v;
             Taps tp;
             if (reproject(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp)) {
-                const __nv_bfloat16* fb = feat + m * vstride + c0;
+                const int rowC = a.fw * C;
+                const __nv_bfloat16* t00 = feat + m * vstride + ((size_t)tp.y0 * a.fw + tp.x0) * C + c0;
                 const bool xa = tp.x0 >= 0, xb = tp.x0 + 1 < a.fw, ya = tp.y0 >= 0, yb = tp.y0 + 1 < a.fh;
-                if (ya && xa) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0) * C, (1 - tp.fy) * (1 - tp.fx), D);
-                if (ya && xb) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0 + 1) * C, (1 - tp.fy) * tp.fx, D);
-                if (yb && xa) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0) * C, tp.fy * (1 - tp.fx), D);
-                if (yb && xb) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0 + 1) * C, tp.fy * tp.fx, D);
+                if (ya && xa) fma16(t00, (1 - tp.fy) * (1 - tp.fx), D);
+                if (ya && xb) fma16(t00 + C, (1 - tp.fy) * tp.fx, D);
+                if (yb && xa) fma16(t00 + rowC, tp.fy * (1 - tp.fx), D);
+                if (yb && xb) fma16(t00 + rowC + C, tp.fy * tp.fx, D);
             }
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
@@ -250,18 +225,25 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
                 s *= scale;
-                const float mn = fmaxf(mx[h], s);
-                const float cs = expf(mx[h] - mn);
-                const float p = expf(s - mn);
-                l[h] = fmaf(l[h], cs, p);
+                if (s > mx[h]) {  // the running maximum moves: rescale (rare after the first views)
+                    const float cs = expf(mx[h] - s);
+                    l[h] *= cs;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) o[h][i] = fmaf(o[h][i], cs, p * D[i]);
-                mx[h] = mn;
+                    for (int i = 0; i < 16; ++i) o[h][i] *= cs;
+                    mx[h] = s;
+                }
+                const float p = expf(s - mx[h]);
+                l[h] += p;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[h][i] = fmaf(p, D[i], o[h][i]);
             }
             if constexpr (LAST) {
                 float s = 0.f;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) s = fmaf(qb[i], D[i], s);
+                for (int i = 0; i < 4; ++i) {
+                    const float4 q4 = qb4[i];
+                    s = fmaf(q4.x, D[4 * i], fmaf(q4.y, D[4 * i + 1], fmaf(q4.z, D[4 * i + 2], fmaf(q4.w, D[4 * i + 3], s))));
+                }
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
                 if (sub == 0) s_beta[e * a.V + m] = s * scale;
