@@ -46,6 +46,31 @@ struct AtSmem {
 };
 
 
+
+// Packed FP32x2 arithmetic (sm_100 family): two channels per instruction.
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t x) {
+    return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+}
+__device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    const float2 w2 = make_float2(w, w);
+    D[0] = __ffma2_rn(bf2_to_f2(a.x), w2, D[0]);
+    D[1] = __ffma2_rn(bf2_to_f2(a.y), w2, D[1]);
+    D[2] = __ffma2_rn(bf2_to_f2(a.z), w2, D[2]);
+    D[3] = __ffma2_rn(bf2_to_f2(a.w), w2, D[3]);
+    D[4] = __ffma2_rn(bf2_to_f2(b.x), w2, D[4]);
+    D[5] = __ffma2_rn(bf2_to_f2(b.y), w2, D[5]);
+    D[6] = __ffma2_rn(bf2_to_f2(b.z), w2, D[6]);
+    D[7] = __ffma2_rn(bf2_to_f2(b.w), w2, D[7]);
+}
+__device__ __forceinline__ float dot16(const float2 (&a)[8], const float2 (&b)[8]) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc = __ffma2_rn(a[j], b[j], acc);
+    return acc.x + acc.y;
+}
+
 template <int C, int NH, int TR, bool LAST>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;
@@ -176,14 +201,15 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     umma::fence_after_sync();
 
     if (!failed) {
-        float qv[NH][16];
+        float2 qv[NH][8];
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
             const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + h * C + c0);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                float4 t = src[i];
-                qv[h][4 * i] = t.x; qv[h][4 * i + 1] = t.y; qv[h][4 * i + 2] = t.z; qv[h][4 * i + 3] = t.w;
+                const float4 t = src[i];
+                qv[h][2 * i] = make_float2(t.x, t.y);
+                qv[h][2 * i + 1] = make_float2(t.z, t.w);
             }
         }
         // the blend query stays in shared memory (read once per view) to keep registers for the loop
@@ -192,58 +218,61 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // ---- views: sample, online softmax, weighted sum (FP32) ----
         const float scale = 1.0f / sqrtf((float)C);
         const float pxc = xc + 0.5f, pyc = yc + 0.5f;
-        float mx[NH], l[NH], o[NH][16];
+        float mx[NH], l[NH];
+        float2 o[NH][8];
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
             mx[h] = -INFINITY;
             l[h] = 0.f;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[h][i] = 0.f;
+            for (int j = 0; j < 8; ++j) o[h][j] = make_float2(0.f, 0.f);
         }
         const __nv_bfloat16* feat = reinterpret_cast<const __nv_bfloat16*>(a.feat);
         const size_t vstride = (size_t)a.fh * a.fw * C;
         for (int m = 0; m < a.V; ++m) {
-            float D[16];
+            float2 D[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) D[i] = 0.f;
+            for (int j = 0; j < 8; ++j) D[j] = make_float2(0.f, 0.f);
             float u, v;
             Taps tp;
             if (reproject(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp)) {
                 const int rowC = a.fw * C;
                 const __nv_bfloat16* t00 = feat + m * vstride + ((size_t)tp.y0 * a.fw + tp.x0) * C + c0;
                 const bool xa = tp.x0 >= 0, xb = tp.x0 + 1 < a.fw, ya = tp.y0 >= 0, yb = tp.y0 + 1 < a.fh;
-                if (ya && xa) fma16(t00, (1 - tp.fy) * (1 - tp.fx), D);
-                if (ya && xb) fma16(t00 + C, (1 - tp.fy) * tp.fx, D);
-                if (yb && xa) fma16(t00 + rowC, tp.fy * (1 - tp.fx), D);
-                if (yb && xb) fma16(t00 + rowC + C, tp.fy * tp.fx, D);
+                if (ya && xa) fma_taps16(t00, (1 - tp.fy) * (1 - tp.fx), D);
+                if (ya && xb) fma_taps16(t00 + C, (1 - tp.fy) * tp.fx, D);
+                if (yb && xa) fma_taps16(t00 + rowC, tp.fy * (1 - tp.fx), D);
+                if (yb && xb) fma_taps16(t00 + rowC + C, tp.fy * tp.fx, D);
             }
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
-                float s = 0.f;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) s = fmaf(qv[h][i], D[i], s);
+                float s = dot16(qv[h], D);
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
                 s *= scale;
                 if (s > mx[h]) {  // the running maximum moves: rescale (rare after the first views)
                     const float cs = expf(mx[h] - s);
+                    const float2 cs2 = make_float2(cs, cs);
                     l[h] *= cs;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) o[h][i] *= cs;
+                    for (int j = 0; j < 8; ++j) o[h][j] = __fmul2_rn(o[h][j], cs2);
                     mx[h] = s;
                 }
                 const float p = expf(s - mx[h]);
+                const float2 p2 = make_float2(p, p);
                 l[h] += p;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) o[h][i] = fmaf(p, D[i], o[h][i]);
+                for (int j = 0; j < 8; ++j) o[h][j] = __ffma2_rn(p2, D[j], o[h][j]);
             }
             if constexpr (LAST) {
-                float s = 0.f;
+                float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const float4 q4 = qb4[i];
-                    s = fmaf(q4.x, D[4 * i], fmaf(q4.y, D[4 * i + 1], fmaf(q4.z, D[4 * i + 2], fmaf(q4.w, D[4 * i + 3], s))));
+                    acc = __ffma2_rn(make_float2(q4.x, q4.y), D[2 * i], acc);
+                    acc = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], acc);
                 }
+                float s = acc.x + acc.y;
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
                 if (sub == 0) s_beta[e * a.V + m] = s * scale;
@@ -259,7 +288,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    hh[j] = __floats2bfloat162_rn(o[h][8 * g + 2 * j] * il, o[h][8 * g + 2 * j + 1] * il);
+                    hh[j] = __floats2bfloat162_rn(o[h][4 * g + j].x * il, o[h][4 * g + j].y * il);
                 *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = u;
             }
         }
