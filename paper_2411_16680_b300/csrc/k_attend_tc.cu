@@ -51,6 +51,19 @@ struct AtSmem {
 __device__ __forceinline__ float2 bf2_to_f2(uint32_t x) {
     return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
 }
+__device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    const float2 w2 = make_float2(w, w);
+    D[0] = __fmul2_rn(bf2_to_f2(a.x), w2);
+    D[1] = __fmul2_rn(bf2_to_f2(a.y), w2);
+    D[2] = __fmul2_rn(bf2_to_f2(a.z), w2);
+    D[3] = __fmul2_rn(bf2_to_f2(a.w), w2);
+    D[4] = __fmul2_rn(bf2_to_f2(b.x), w2);
+    D[5] = __fmul2_rn(bf2_to_f2(b.y), w2);
+    D[6] = __fmul2_rn(bf2_to_f2(b.z), w2);
+    D[7] = __fmul2_rn(bf2_to_f2(b.w), w2);
+}
 __device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
     const uint4* q = reinterpret_cast<const uint4*>(p);
     const uint4 a = __ldg(q), b = __ldg(q + 1);
@@ -64,13 +77,30 @@ __device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, floa
     D[6] = __ffma2_rn(bf2_to_f2(b.z), w2, D[6]);
     D[7] = __ffma2_rn(bf2_to_f2(b.w), w2, D[7]);
 }
-__device__ __forceinline__ float dot16(const float2 (&a)[8], const float2 (&b)[8]) {
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc = __ffma2_rn(a[j], b[j], acc);
-    return acc.x + acc.y;
+// 2^x and 1/x on the special-function unit (PTX ex2.approx / rcp.approx, flush-to-zero).  The
+// softmax below works in log2 units, so that each weight is one ex2.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
-
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// Sec. 3.2.2 reprojection of the target pixel centre (px, py) at depth d into one view
+// (X = d A p + b, then the perspective divide), with the divide as one reciprocal.
+__device__ __forceinline__ bool reproject_rcp(const ViewMap& m, float px, float py, float d, float& u, float& v) {
+    const float X = fmaf(d, fmaf(m.A[0], px, fmaf(m.A[1], py, m.A[2])), m.b[0]);
+    const float Y = fmaf(d, fmaf(m.A[3], px, fmaf(m.A[4], py, m.A[5])), m.b[1]);
+    const float Z = fmaf(d, fmaf(m.A[6], px, fmaf(m.A[7], py, m.A[8])), m.b[2]);
+    if (!(Z > 1e-6f)) return false;
+    const float iz = rcp_approx(Z);
+    u = X * iz;
+    v = Y * iz;
+    return true;
+}
 template <int C, int NH, int TR, bool LAST>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;
@@ -188,12 +218,16 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     if (!failed) {
         // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16
         const int q = warp & 3, grp = warp >> 2;
+        // the 1/sqrt(C) of the logits is folded into the queries here, and for the attention heads
+        // also log2(e), so that the softmax below runs on ex2
+        const float qscale = rsqrtf((float)C);
         for (int ch = grp; ch < NQ_USED / 16; ch += TPE) {
             float v[16];
             umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+            const float f = ch * 16 < NH * C ? qscale * 1.4426950408889634f : qscale;
             float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i] * f, v[4 * i + 1] * f, v[4 * i + 2] * f, v[4 * i + 3] * f);
         }
     }
     umma::fence_before_sync();
@@ -201,22 +235,12 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     umma::fence_after_sync();
 
     if (!failed) {
-        float2 qv[NH][8];
-#pragma unroll
-        for (int h = 0; h < NH; ++h) {
-            const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + h * C + c0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 t = src[i];
-                qv[h][2 * i] = make_float2(t.x, t.y);
-                qv[h][2 * i + 1] = make_float2(t.z, t.w);
-            }
-        }
+        // the queries stay in shared memory (read once per view) to keep registers for the gathers
+        const float4* qh4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + c0);
         // the blend query stays in shared memory (read once per view) to keep registers for the loop
         const float4* qb4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
 
-        // ---- views: sample, online softmax, weighted sum (FP32) ----
-        const float scale = 1.0f / sqrtf((float)C);
+        // ---- views: sample, online softmax (log2 units), weighted sum (FP32) ----
         const float pxc = xc + 0.5f, pyc = yc + 0.5f;
         float mx[NH], l[NH];
         float2 o[NH][8];
@@ -227,38 +251,52 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) o[h][j] = make_float2(0.f, 0.f);
         }
-        const __nv_bfloat16* feat = reinterpret_cast<const __nv_bfloat16*>(a.feat);
-        const size_t vstride = (size_t)a.fh * a.fw * C;
-        for (int m = 0; m < a.V; ++m) {
-            float2 D[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) D[j] = make_float2(0.f, 0.f);
+        const __nv_bfloat16* feat_m = reinterpret_cast<const __nv_bfloat16*>(a.feat) + c0;
+        const int vstride = a.fh * a.fw * C;  // < 2^31 for every accepted level size
+        const int rowC = a.fw * C;
+        for (int m = 0; m < a.V; ++m, feat_m += vstride) {
+            // The four taps are always fetched, from indices clamped into the map, with the weight of
+            // a tap outside the map (or of a sample behind the camera) set to zero: no branch, so the
+            // eight loads of the view are in flight together.
             float u, v;
-            Taps tp;
-            if (reproject(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp)) {
-                const int rowC = a.fw * C;
-                const __nv_bfloat16* t00 = feat + m * vstride + ((size_t)tp.y0 * a.fw + tp.x0) * C + c0;
-                const bool xa = tp.x0 >= 0, xb = tp.x0 + 1 < a.fw, ya = tp.y0 >= 0, yb = tp.y0 + 1 < a.fh;
-                if (ya && xa) fma_taps16(t00, (1 - tp.fy) * (1 - tp.fx), D);
-                if (ya && xb) fma_taps16(t00 + C, (1 - tp.fy) * tp.fx, D);
-                if (yb && xa) fma_taps16(t00 + rowC, tp.fy * (1 - tp.fx), D);
-                if (yb && xb) fma_taps16(t00 + rowC + C, tp.fy * tp.fx, D);
-            }
+            Taps tp{0, 0, 0.f, 0.f};
+            const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp);
+            const bool xa = ok && tp.x0 >= 0, xb = ok && tp.x0 + 1 < a.fw;
+            const bool ya = ok && tp.y0 >= 0, yb = ok && tp.y0 + 1 < a.fh;
+            const int cx0 = max(tp.x0, 0) * C, cx1 = min(tp.x0 + 1, a.fw - 1) * C;
+            const __nv_bfloat16* r0 = feat_m + max(tp.y0, 0) * rowC;
+            const __nv_bfloat16* r1 = feat_m + min(tp.y0 + 1, a.fh - 1) * rowC;
+            const float gy0 = ya ? 1 - tp.fy : 0.f, gy1 = yb ? tp.fy : 0.f;
+            const float gx0 = xa ? 1 - tp.fx : 0.f, gx1 = xb ? tp.fx : 0.f;
+            float2 D[8];
+            mul_taps16(r0 + cx0, gy0 * gx0, D);
+            fma_taps16(r0 + cx1, gy0 * gx1, D);
+            fma_taps16(r1 + cx0, gy1 * gx0, D);
+            fma_taps16(r1 + cx1, gy1 * gx1, D);
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
-                float s = dot16(qv[h], D);
+                float s;
+                {
+                    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 q4 = qh4[h * C / 4 + i];
+                        acc0 = __ffma2_rn(make_float2(q4.x, q4.y), D[2 * i], acc0);
+                        acc1 = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], acc1);
+                    }
+                    s = (acc0.x + acc1.x) + (acc0.y + acc1.y);
+                }
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                s *= scale;
                 if (s > mx[h]) {  // the running maximum moves: rescale (rare after the first views)
-                    const float cs = expf(mx[h] - s);
+                    const float cs = ex2_approx(mx[h] - s);
                     const float2 cs2 = make_float2(cs, cs);
                     l[h] *= cs;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) o[h][j] = __fmul2_rn(o[h][j], cs2);
                     mx[h] = s;
                 }
-                const float p = expf(s - mx[h]);
+                const float p = ex2_approx(s - mx[h]);
                 const float2 p2 = make_float2(p, p);
                 l[h] += p;
 #pragma unroll
@@ -275,7 +313,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 float s = acc.x + acc.y;
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                if (sub == 0) s_beta[e * a.V + m] = s * scale;
+                if (sub == 0) s_beta[e * a.V + m] = s;
             }
         }
         // head outputs -> BF16 A operand (K = h * C + channel)
@@ -337,13 +375,21 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 out[4 * i + 2] = vres[4 * i + 2] + t.z;
                 out[4 * i + 3] = vres[4 * i + 3] + t.w;
             }
-            store16(reinterpret_cast<__nv_bfloat16*>(a.out) + (((size_t)li * H + y) * W + x) * C + c0, out);
+            {
+                uint4 u[2];
+                __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) hh[j] = __floats2bfloat162_rn(out[2 * j], out[2 * j + 1]);
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + (((size_t)li * H + y) * W + x) * C + c0);
+                __stcs(dst, u[0]);  // streaming: V_attn is read back only by the next kernel
+                __stcs(dst + 1, u[1]);
+            }
         }
         if constexpr (LAST) {
             // blend logits of the element, contiguous [m] in the [H][W][L][V] layout
             if (!failed && live)
                 for (int m = sub; m < a.V; m += TPE)
-                    a.beta[(((size_t)y * W + x) * L + li) * a.V + m] = s_beta[e * a.V + m];
+                    __stcs(a.beta + (((size_t)y * W + x) * L + li) * a.V + m, s_beta[e * a.V + m]);
         }
     }
     if (failed && tid == 0) atomicExch(a.err, 3 + (int)failed_phase);
