@@ -130,6 +130,23 @@ __device__ __forceinline__ bool bilinear_taps(float u, float v, int h, int w, Ta
     return true;
 }
 
+// The same four taps as in-map texel indices (row-major, h x w) and weights.  A tap outside the map,
+// or every tap of a sample that cannot touch it (ok false, or no tap inside), keeps an in-map index
+// and gets weight zero, so the four fetches need no branch and can be in flight together.
+struct Taps4 {
+    int i00, i01, i10, i11;
+    float w00, w01, w10, w11;
+};
+__device__ __forceinline__ Taps4 bilinear_taps4(bool ok, float u, float v, int h, int w) {
+    Taps t{0, 0, 0.f, 0.f};
+    ok = ok && bilinear_taps(u, v, h, w, t);
+    const float gx0 = ok && t.x0 >= 0 ? 1 - t.fx : 0.f, gx1 = ok && t.x0 + 1 < w ? t.fx : 0.f;
+    const float gy0 = ok && t.y0 >= 0 ? 1 - t.fy : 0.f, gy1 = ok && t.y0 + 1 < h ? t.fy : 0.f;
+    const int cx0 = max(t.x0, 0), cx1 = min(t.x0 + 1, w - 1);
+    const int ry0 = max(t.y0, 0) * w, ry1 = min(t.y0 + 1, h - 1) * w;
+    return Taps4{ry0 + cx0, ry0 + cx1, ry1 + cx0, ry1 + cx1, gy0 * gx0, gy0 * gx1, gy1 * gx0, gy1 * gx1};
+}
+
 // Edge-clamped linear taps of a resize by integer `ratio` (pixel centres aligned):
 // src = (dst + 0.5) / ratio - 0.5.
 __device__ __forceinline__ void resize_taps(int dst, int ratio, int n, int& i0, int& i1, float& w1) {

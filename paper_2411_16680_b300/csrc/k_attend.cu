@@ -229,15 +229,13 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a)
 #pragma unroll
         for (int i = 0; i < 16; ++i) D[i] = 0.f;
         float u, v;
-        Taps tp;
-        if (reproject(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp)) {
-            const T* fb = feat + m * vstride + c0;
-            const bool xa = tp.x0 >= 0, xb = tp.x0 + 1 < a.fw, ya = tp.y0 >= 0, yb = tp.y0 + 1 < a.fh;
-            if (ya && xa) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0) * C, (1 - tp.fy) * (1 - tp.fx), D);
-            if (ya && xb) fma16(fb + ((size_t)tp.y0 * a.fw + tp.x0 + 1) * C, (1 - tp.fy) * tp.fx, D);
-            if (yb && xa) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0) * C, tp.fy * (1 - tp.fx), D);
-            if (yb && xb) fma16(fb + ((size_t)(tp.y0 + 1) * a.fw + tp.x0 + 1) * C, tp.fy * tp.fx, D);
-        }
+        const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
+        const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
+        const T* fb = feat + m * vstride + c0;
+        fma16(fb + (size_t)tp.i00 * C, tp.w00, D);
+        fma16(fb + (size_t)tp.i01 * C, tp.w01, D);
+        fma16(fb + (size_t)tp.i10 * C, tp.w10, D);
+        fma16(fb + (size_t)tp.i11 * C, tp.w11, D);
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
             float s = 0.f;

@@ -253,26 +253,17 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         }
         const __nv_bfloat16* feat_m = reinterpret_cast<const __nv_bfloat16*>(a.feat) + c0;
         const int vstride = a.fh * a.fw * C;  // < 2^31 for every accepted level size
-        const int rowC = a.fw * C;
         for (int m = 0; m < a.V; ++m, feat_m += vstride) {
-            // The four taps are always fetched, from indices clamped into the map, with the weight of
-            // a tap outside the map (or of a sample behind the camera) set to zero: no branch, so the
-            // eight loads of the view are in flight together.
-            float u, v;
-            Taps tp{0, 0, 0.f, 0.f};
-            const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v) && bilinear_taps(u, v, a.fh, a.fw, tp);
-            const bool xa = ok && tp.x0 >= 0, xb = ok && tp.x0 + 1 < a.fw;
-            const bool ya = ok && tp.y0 >= 0, yb = ok && tp.y0 + 1 < a.fh;
-            const int cx0 = max(tp.x0, 0) * C, cx1 = min(tp.x0 + 1, a.fw - 1) * C;
-            const __nv_bfloat16* r0 = feat_m + max(tp.y0, 0) * rowC;
-            const __nv_bfloat16* r1 = feat_m + min(tp.y0 + 1, a.fh - 1) * rowC;
-            const float gy0 = ya ? 1 - tp.fy : 0.f, gy1 = yb ? tp.fy : 0.f;
-            const float gx0 = xa ? 1 - tp.fx : 0.f, gx1 = xb ? tp.fx : 0.f;
+            // the four taps are always fetched (clamped into the map, weight zero outside it): no
+            // branch, so the eight loads of the view are in flight together
+            float u = 0.f, v = 0.f;
+            const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
+            const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
             float2 D[8];
-            mul_taps16(r0 + cx0, gy0 * gx0, D);
-            fma_taps16(r0 + cx1, gy0 * gx1, D);
-            fma_taps16(r1 + cx0, gy1 * gx0, D);
-            fma_taps16(r1 + cx1, gy1 * gx1, D);
+            mul_taps16(feat_m + tp.i00 * C, tp.w00, D);
+            fma_taps16(feat_m + tp.i01 * C, tp.w01, D);
+            fma_taps16(feat_m + tp.i10 * C, tp.w10, D);
+            fma_taps16(feat_m + tp.i11 * C, tp.w11, D);
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
                 float s;

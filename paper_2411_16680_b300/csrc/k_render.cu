@@ -10,21 +10,15 @@ namespace quark {
 
 constexpr int RD_THREADS = 128;
 
-__device__ __forceinline__ float4 sample_rgba(const float4* __restrict__ img, int h, int w, float u, float v) {
-    Taps t;
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!bilinear_taps(u, v, h, w, t)) return r;
-    const bool xa = t.x0 >= 0, xb = t.x0 + 1 < w, ya = t.y0 >= 0, yb = t.y0 + 1 < h;
-    auto acc = [&](int yy, int xx, float wt) {
-        float4 p = __ldg(img + (size_t)yy * w + xx);
-        r.x = fmaf(wt, p.x, r.x);
-        r.y = fmaf(wt, p.y, r.y);
-        r.z = fmaf(wt, p.z, r.z);
-    };
-    if (ya && xa) acc(t.y0, t.x0, (1 - t.fy) * (1 - t.fx));
-    if (ya && xb) acc(t.y0, t.x0 + 1, (1 - t.fy) * t.fx);
-    if (yb && xa) acc(t.y0 + 1, t.x0, t.fy * (1 - t.fx));
-    if (yb && xb) acc(t.y0 + 1, t.x0 + 1, t.fy * t.fx);
+__device__ __forceinline__ float4 sample_rgba(const float4* __restrict__ img, int h, int w, bool ok, float u, float v) {
+    const Taps4 t = bilinear_taps4(ok, u, v, h, w);
+    const float4 p00 = __ldg(img + t.i00), p01 = __ldg(img + t.i01);
+    const float4 p10 = __ldg(img + t.i10), p11 = __ldg(img + t.i11);
+    float4 r;
+    r.x = fmaf(t.w11, p11.x, fmaf(t.w10, p10.x, fmaf(t.w01, p01.x, t.w00 * p00.x)));
+    r.y = fmaf(t.w11, p11.y, fmaf(t.w10, p10.y, fmaf(t.w01, p01.y, t.w00 * p00.y)));
+    r.z = fmaf(t.w11, p11.z, fmaf(t.w10, p10.z, fmaf(t.w01, p01.z, t.w00 * p00.z)));
+    r.w = 0.f;
     return r;
 }
 
@@ -43,13 +37,12 @@ __device__ __forceinline__ void blend_layer(const RenderArgs& a, LogitFn logit, 
         lr *= sc;
         lg *= sc;
         lb *= sc;
-        float u, v;
-        if (reproject(a.geo.v[m], pxc, pyc, d, u, v)) {
-            const float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, u, v);
-            lr = fmaf(p, c.x, lr);
-            lg = fmaf(p, c.y, lg);
-            lb = fmaf(p, c.z, lb);
-        }
+        float u = 0.f, v = 0.f;
+        const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
+        const float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, ok, u, v);
+        lr = fmaf(p, c.x, lr);
+        lg = fmaf(p, c.y, lg);
+        lb = fmaf(p, c.z, lb);
         mx = mn;
     }
     const float is = 1.0f / sum;
