@@ -336,8 +336,11 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         }
         // attention: B_q rows n < hC from Wq[k][n], rows hC.. from W_beta[k][n - hC] (K = C);
         // B_o rows n < C from Wo[k][n] (K = hC); element (n, k) at (k / 8) * N * 8 + n * 8 + k % 8
+        // layer collapse of the step (when it has one), after B_o: B_1 rows n < C from col_w1[k][n]
+        // (K = 2C), then B_2 from col_w2[k][n] (K = C), same element order
         const int NQ = h * C + C;
-        ctx->wat_step_bytes = ((size_t)NQ * C + (size_t)C * h * C) * sizeof(uint16_t);
+        const size_t att_elems = (size_t)NQ * C + (size_t)C * h * C;
+        ctx->wat_step_bytes = (att_elems + 3 * (size_t)C * C) * sizeof(uint16_t);
         std::vector<uint16_t> at(ctx->wat_step_bytes / sizeof(uint16_t) * c.n_scales);
         for (int j = 0; j < c.n_scales; ++j) {
             uint16_t* bq = at.data() + (size_t)j * (ctx->wat_step_bytes / sizeof(uint16_t));
@@ -350,6 +353,16 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             for (int n = 0; n < C; ++n)
                 for (int k = 0; k < h * C; ++k)
                     bo[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->Wo[j][(size_t)k * C + n]);
+            if (ctx->off_collapse[j] != (size_t)-1) {
+                uint16_t* b1 = bq + att_elems;
+                uint16_t* b2 = b1 + 2 * (size_t)C * C;
+                for (int n = 0; n < C; ++n) {
+                    for (int k = 0; k < 2 * C; ++k)
+                        b1[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->col_w1[j][(size_t)k * C + n]);
+                    for (int k = 0; k < C; ++k)
+                        b2[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->col_w2[j][(size_t)k * C + n]);
+                }
+            }
         }
         qk_free(ctx, ctx->wat, ctx->wat_bytes);
         ctx->wat = nullptr;
@@ -737,6 +750,11 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
             ca.H = Hp;
             ca.W = Wp;
             ca.w = ctx->wdev + ctx->off_collapse[scale];
+            if (ctx->wat) {
+                const size_t att_bytes = ((size_t)(c.heads * c.C + c.C) * c.C + (size_t)c.C * c.heads * c.C) * 2;
+                ca.wtc = (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes + att_bytes;
+            }
+            ca.err = ctx->dev_err;
             s = qk_launch(ctx, st, KF_COLLAPSE, [&] { return launch_collapse(ca, c.C, bf16, st); });
             if (s != QUARK_OK) return s;
             prev = ldm->collapsed;

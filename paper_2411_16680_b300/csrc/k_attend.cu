@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(128) collapse_kernel(CollapseArgs a) {
     }
 }
 
+// FP32 form: this SIMT kernel.  BF16 form: both MLP layers on tcgen05 (k_collapse_tc.cu).
 cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st) {
+    if (bf16) return launch_collapse_tc(a, C, st);
     size_t n = (size_t)a.L * a.H * a.W;
     unsigned grid = (unsigned)((n + 127) / 128);
     if (C == 16) {

@@ -1,0 +1,195 @@
+// Layer Collapse of the BF16 form on tcgen05 tensor cores (Sec. 3.2.2): each pair (l = 2j-1, 2j)
+// of the previous step's volume becomes 0.5 (a + b) + gelu([a; b] W1 + b1) W2 + b2.
+//
+// A CTA owns 128 pixels of one layer pair (M = 128, one element per thread):
+//   1. a and b (BF16) are copied as they are into shared memory as the K-major A operand
+//      X = [a | b] (K = 2C); 0.5 (a + b) is kept in FP32 registers.
+//   2. X W1 (N = C) into TMEM; + b1, erf-GELU, BF16 -> shared memory as the A operand G (K = C).
+//   3. G W2 (N = C) into the next TMEM columns; + b2 + 0.5 (a + b); stored as BF16.
+// Each MMA chain signals an mbarrier through tcgen05.commit; every wait is bounded.
+#include "device_common.cuh"
+#include "umma.cuh"
+
+namespace quark {
+
+constexpr int CL_M = 128;
+constexpr uint64_t CL_WAIT_NS = 1000000000ull;
+
+template <int C>
+struct ClSmem {
+    static constexpr int x_off = 0;                        // A: 128 x 2C bf16
+    static constexpr int g_off = x_off + CL_M * 2 * C * 2;  // A: 128 x C bf16
+    static constexpr int w1_off = g_off + CL_M * C * 2;     // B: C x 2C bf16
+    static constexpr int w2_off = w1_off + 2 * C * C * 2;   // B: C x C bf16
+    static constexpr int b_off = w2_off + C * C * 2;        // b1 [C], b2 [C] fp32
+    static constexpr int bar_off = b_off + 2 * C * 4;
+    static constexpr int total = bar_off + 16;
+    static constexpr uint32_t tmem_cols = 2 * C;  // X W1 in [0, C), G W2 in [C, 2C)
+};
+
+// 16 consecutive TMEM columns of this warp's lanes
+__device__ __forceinline__ void tmem_row16(uint32_t tmem, int warp, int col, float (&v)[16]) {
+    umma::ld_32x32b_x16(tmem + ((uint32_t)(warp * 32) << 16) + col, v);
+}
+
+template <int C>
+__global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a) {
+    using S = ClSmem<C>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t* s_x = sm + S::x_off;
+    uint8_t* s_g = sm + S::g_off;
+    float* s_b = reinterpret_cast<float*>(sm + S::b_off);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::bar_off);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::bar_off + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t plane = (size_t)a.H * a.W;
+    const size_t pix = (size_t)blockIdx.x * CL_M + tid;
+    const bool live = pix < plane;
+    const size_t pixc = live ? pix : plane - 1;
+    const int j = blockIdx.y;
+
+    // weights: packed BF16 B operands (W1 then W2, contiguous), FP32 biases
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.wtc);
+        uint4* dst = reinterpret_cast<uint4*>(sm + S::w1_off);
+        constexpr int n16 = 3 * C * C * 2 / 16;
+        for (int i = tid; i < n16; i += CL_M) dst[i] = __ldg(src + i);
+        const CollapseLayout lay{C};
+        for (int i = tid; i < C; i += CL_M) {
+            s_b[i] = a.w[lay.b1() + i];
+            s_b[C + i] = a.w[lay.b2() + i];
+        }
+    }
+    // X row of this element: channel group g (8 bf16) of row m at g * 128 * 16 + m * 16
+    float avg[C];
+    {
+        const uint4* pa = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
+                                                         ((size_t)(2 * j) * plane + pixc) * C);
+        const uint4* pb = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
+                                                         ((size_t)(2 * j + 1) * plane + pixc) * C);
+#pragma unroll
+        for (int g = 0; g < C / 8; ++g) {
+            const uint4 ua = __ldg(pa + g), ub = __ldg(pb + g);
+            *reinterpret_cast<uint4*>(s_x + ((size_t)g * CL_M + tid) * 16) = ua;
+            *reinterpret_cast<uint4*>(s_x + ((size_t)(C / 8 + g) * CL_M + tid) * 16) = ub;
+            const __nv_bfloat162* ha = reinterpret_cast<const __nv_bfloat162*>(&ua);
+            const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&ub);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 fa = __bfloat1622float2(ha[i]), fb = __bfloat1622float2(hb[i]);
+                avg[8 * g + 2 * i] = 0.5f * (fa.x + fb.x);
+                avg[8 * g + 2 * i + 1] = 0.5f * (fa.y + fb.y);
+            }
+        }
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, S::tmem_cols);
+    if (tid == 0) umma::mbar_init(mbar, 1);
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // ---- H = X W1 ----
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma::idesc_bf16_f32(CL_M, C);
+        const uint32_t a0 = umma::smem_u32(s_x), b0 = umma::smem_u32(sm + S::w1_off);
+        constexpr uint32_t LBO_A = CL_M * 16, LBO_B = C * 16;
+#pragma unroll
+        for (int kk = 0; kk < 2 * C / 16; ++kk)
+            umma::mma_bf16(tmem, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128), umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128),
+                           idesc, kk > 0);
+        umma::commit(mbar);
+    }
+    bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, CL_WAIT_NS));
+    uint32_t failed_phase = 0;
+    umma::fence_after_sync();
+    if (!failed) {
+        // G = gelu(H + b1) -> BF16 A operand (K = C)
+#pragma unroll
+        for (int ch = 0; ch < C / 16; ++ch) {
+            float hv[16];
+            tmem_row16(tmem, warp, ch * 16, hv);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint4 u;
+                __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = ch * 16 + 8 * g + 2 * i;
+                    hh[i] = __floats2bfloat162_rn(gelu_erf(hv[8 * g + 2 * i] + s_b[c]),
+                                                  gelu_erf(hv[8 * g + 2 * i + 1] + s_b[c + 1]));
+                }
+                *reinterpret_cast<uint4*>(s_g + ((size_t)(2 * ch + g) * CL_M + tid) * 16) = u;
+            }
+        }
+    }
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    if (!failed) {
+        // ---- G W2 into TMEM columns [C, 2C) ----
+        if (tid == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16_f32(CL_M, C);
+            const uint32_t a0 = umma::smem_u32(s_g), b0 = umma::smem_u32(sm + S::w2_off);
+            constexpr uint32_t LBO_A = CL_M * 16, LBO_B = C * 16;
+#pragma unroll
+            for (int kk = 0; kk < C / 16; ++kk)
+                umma::mma_bf16(tmem + C, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128),
+                               umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128), idesc, kk > 0);
+            umma::commit(mbar);
+        }
+        failed = __syncthreads_or(!umma::mbar_wait(mbar, 1, CL_WAIT_NS));
+        failed_phase = 1;
+        umma::fence_after_sync();
+        if (!failed) {
+            uint4* po = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + ((size_t)j * plane + pixc) * C);
+#pragma unroll
+            for (int ch = 0; ch < C / 16; ++ch) {
+                float ov[16];
+                tmem_row16(tmem, warp, C + ch * 16, ov);
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    uint4 u;
+                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int c = ch * 16 + 8 * g + 2 * i;
+                        hh[i] = __floats2bfloat162_rn(avg[c] + s_b[C + c] + ov[8 * g + 2 * i],
+                                                      avg[c + 1] + s_b[C + c + 1] + ov[8 * g + 2 * i + 1]);
+                    }
+                    if (live) po[2 * ch + g] = u;
+                }
+            }
+        }
+    }
+    if (failed && tid == 0) atomicExch(a.err, 5 + (int)failed_phase);
+    if (failed) umma::mbar_wait(mbar, failed_phase, CL_WAIT_NS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(tmem, S::tmem_cols);
+}
+
+cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st) {
+    if (!a.wtc || !a.err) return cudaErrorInvalidValue;
+    const size_t plane = (size_t)a.H * a.W;
+    const dim3 grid((unsigned)((plane + CL_M - 1) / CL_M), (unsigned)a.L);
+#define QK_CL_LAUNCH(CV)                                                                               \
+    do {                                                                                               \
+        auto k = collapse_tc_kernel<CV>;                                                               \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ClSmem<CV>::total); \
+        if (e != cudaSuccess) return e;                                                                \
+        k<<<grid, CL_M, ClSmem<CV>::total, st>>>(a);                                                   \
+    } while (0)
+    if (C == 16) QK_CL_LAUNCH(16);
+    else if (C == 32) QK_CL_LAUNCH(32);
+    else return cudaErrorInvalidValue;
+#undef QK_CL_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace quark

@@ -1,112 +1,158 @@
 // Encode Input Images (Sec. 3.2.1): F_1 = conv3x3(I) (3 -> C, zero pad, bias, no activation),
-// F_2k = 2x2 mean pool of F_k.  One CTA per 8x8 pixel tile of one view: the conv output of the
-// tile stays in shared memory and is pooled to levels 2, 4 and 8 there, so level 1 is never
-// read back from HBM.  Also writes the RGBA-padded copy of the images used by the render.
+// F_2k = 2x2 mean pool of F_k.  One CTA per 16x16 pixel tile of one view.  A thread owns a 2x2
+// pixel quad and 16 of the C channels, so level 2 is its own quad mean; levels 4 and 8 are means
+// of neighbouring quads, taken with warp shuffles (a warp covers 8 x 4 quads = 16 x 8 pixels).
+// Level 1 is never read back from HBM.  Also writes the RGBA-padded copy of the images used by
+// the render.  The conv runs on packed FP32x2 arithmetic, two channels per instruction.
 #include "device_common.cuh"
 
 namespace quark {
 
-constexpr int ENC_T = 8;  // tile edge (pixels); the largest pyramid factor is 8
+constexpr int ENC_T = 16;  // tile edge (pixels)
+constexpr int ENC_P = ENC_T + 2;
 
-template <typename T, int C>
-__device__ __forceinline__ void store_level(void* base, int v, int hk, int wk, int Y, int X, int c, float val) {
-    T* p = reinterpret_cast<T*>(base);
-    from_f(p[(((size_t)v * hk + Y) * wk + X) * C + c], val);
+// 16 channels of one texel of a level at p (T = float or bf16)
+__device__ __forceinline__ void store16x2(float* p, const float2 (&v)[8]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+}
+__device__ __forceinline__ void store16x2(__nv_bfloat16* p, const float2 (&v)[8]) {
+    uint4 u[2];
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[j].x, v[j].y);
+    uint4* q = reinterpret_cast<uint4*>(p);
+    q[0] = u[0];
+    q[1] = u[1];
+}
+
+// 2x2 mean of the 16-channel texels held by this lane and its partners at lane ^ dx and ^ dy
+__device__ __forceinline__ void quad_mean(float2 (&t)[8], int dx, int dy) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float2 s = t[j];
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, dx);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, dx);
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, dy);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, dy);
+        t[j] = make_float2(0.25f * s.x, 0.25f * s.y);
+    }
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(64) encode_kernel(EncodeArgs a) {
-    __shared__ float patch[ENC_T + 2][ENC_T + 2][3];
-    __shared__ float w[28 * C];
-    __shared__ float f1[ENC_T * ENC_T][C + 1];
-    __shared__ float f2[16][C + 1];
-    __shared__ float f4[4][C + 1];
+__global__ void __launch_bounds__(64 * (C / 16)) encode_kernel(EncodeArgs a) {
+    constexpr int NT = 64 * (C / 16);
+    __shared__ float patch[ENC_P][ENC_P][3];
+    __shared__ __align__(16) float w[28 * C];  // [tap = (dy * 3 + dx) * 3 + ci][C], then bias [C]
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int v = blockIdx.z;
     const int X0 = blockIdx.x * ENC_T, Y0 = blockIdx.y * ENC_T;
     const int H = a.H, W = a.W;
 
-    for (int i = tid; i < 28 * C; i += 64) w[i] = a.w[i];
-    for (int i = tid; i < (ENC_T + 2) * (ENC_T + 2) * 3; i += 64) {
-        int c = i % 3, px = (i / 3) % (ENC_T + 2), py = i / (3 * (ENC_T + 2));
-        int gy = Y0 - 1 + py, gx = X0 - 1 + px;
+    for (int i = tid; i < 28 * C; i += NT) w[i] = a.w[i];
+    const float* img = a.images + (size_t)v * H * W * 3;
+    for (int i = tid; i < ENC_P * ENC_P * 3; i += NT) {
+        const int c = i % 3, px = (i / 3) % ENC_P, py = i / (3 * ENC_P);
+        const int gy = Y0 - 1 + py, gx = X0 - 1 + px;
         float val = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) val = a.images[(((size_t)v * H + gy) * W + gx) * 3 + c];
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) val = img[((size_t)gy * W + gx) * 3 + c];
         patch[py][px][c] = val;
     }
     __syncthreads();
 
-    const int px = tid % ENC_T, py = tid / ENC_T;
-    const int X = X0 + px, Y = Y0 + py;
-    const bool inside = (X < W) && (Y < H);
-    float acc[C];
+    // RGBA copy of the tile
+    for (int i = tid; i < ENC_T * ENC_T; i += NT) {
+        const int px = i % ENC_T, py = i / ENC_T, X = X0 + px, Y = Y0 + py;
+        if (X < W && Y < H)
+            a.rgba[((size_t)v * H + Y) * W + X] =
+                make_float4(patch[py + 1][px + 1][0], patch[py + 1][px + 1][1], patch[py + 1][px + 1][2], 0.f);
+    }
+
+    // quad (qx, qy) of the 8 x 8 quads of the tile; warp w % 4 holds quad rows 4 (w % 4) .. + 3
+    const int cg = tid / 64, c0 = cg * 16;
+    const int qx = lane & 7, qy = ((tid & 63) >> 5) * 4 + (lane >> 3);
+    const int px0 = 2 * qx, py0 = 2 * qy;
+
+    float2 acc[4][8];
+    {
+        const float4* b4 = reinterpret_cast<const float4*>(&w[27 * C + c0]);
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = w[27 * C + c];
+        for (int i = 0; i < 4; ++i) {
+            const float4 b = b4[i];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                acc[p][2 * i] = make_float2(b.x, b.y);
+                acc[p][2 * i + 1] = make_float2(b.z, b.w);
+            }
+        }
+    }
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
             for (int ci = 0; ci < 3; ++ci) {
-                float x = patch[py + dy][px + dx][ci];
-                const float* wr = &w[((dy * 3 + dx) * 3 + ci) * C];
+                const float4* w4 = reinterpret_cast<const float4*>(&w[((dy * 3 + dx) * 3 + ci) * C + c0]);
+                float2 wr[8];
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[c] = fmaf(x, wr[c], acc[c]);
+                for (int i = 0; i < 4; ++i) {
+                    const float4 t = w4[i];
+                    wr[2 * i] = make_float2(t.x, t.y);
+                    wr[2 * i + 1] = make_float2(t.z, t.w);
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float x = patch[py0 + (p >> 1) + dy][px0 + (p & 1) + dx][ci];
+                    const float2 x2 = make_float2(x, x);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[p][j] = __ffma2_rn(x2, wr[j], acc[p][j]);
+                }
             }
-    if (inside) {
-        a.rgba[((size_t)v * H + Y) * W + X] =
-            make_float4(patch[py + 1][px + 1][0], patch[py + 1][px + 1][1], patch[py + 1][px + 1][2], 0.f);
-        if (a.level[0]) {
-            T* p = reinterpret_cast<T*>(a.level[0]) + (((size_t)v * H + Y) * W + X) * C;
-#pragma unroll
-            for (int c0 = 0; c0 < C; c0 += 16) {
-                float t[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) t[i] = acc[c0 + i];
-                store16(p + c0, t);
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) f1[tid][c] = acc[c];
-    __syncthreads();
 
-    // 2x2 mean-pool chain; image sizes are divisible by every level used, so a level-k texel
-    // inside the image always has its whole k x k block inside this tile.
-    for (int i = tid; i < 16 * C; i += 64) {
-        int c = i % C, t = i / C, ty = t / 4, tx = t % 4;
-        float s = f1[(2 * ty) * ENC_T + 2 * tx][c] + f1[(2 * ty) * ENC_T + 2 * tx + 1][c] +
-                  f1[(2 * ty + 1) * ENC_T + 2 * tx][c] + f1[(2 * ty + 1) * ENC_T + 2 * tx + 1][c];
-        s *= 0.25f;
-        f2[t][c] = s;
-        int Yk = Y0 / 2 + ty, Xk = X0 / 2 + tx;
-        if (a.level[1] && Yk < H / 2 && Xk < W / 2) store_level<T, C>(a.level[1], v, H / 2, W / 2, Yk, Xk, c, s);
-    }
-    __syncthreads();
-    for (int i = tid; i < 4 * C; i += 64) {
-        int c = i % C, t = i / C, ty = t / 2, tx = t % 2;
-        float s = f2[(2 * ty) * 4 + 2 * tx][c] + f2[(2 * ty) * 4 + 2 * tx + 1][c] + f2[(2 * ty + 1) * 4 + 2 * tx][c] +
-                  f2[(2 * ty + 1) * 4 + 2 * tx + 1][c];
-        s *= 0.25f;
-        f4[t][c] = s;
-        int Yk = Y0 / 4 + ty, Xk = X0 / 4 + tx;
-        if (a.level[2] && Yk < H / 4 && Xk < W / 4) store_level<T, C>(a.level[2], v, H / 4, W / 4, Yk, Xk, c, s);
-    }
-    __syncthreads();
-    if (a.level[3]) {
-        for (int c = tid; c < C; c += 64) {
-            float s = 0.25f * (f4[0][c] + f4[1][c] + f4[2][c] + f4[3][c]);
-            int Yk = Y0 / 8, Xk = X0 / 8;
-            if (Yk < H / 8 && Xk < W / 8) store_level<T, C>(a.level[3], v, H / 8, W / 8, Yk, Xk, c, s);
+    // level 1: the four pixels of the quad
+    if (a.level[0]) {
+        T* l1 = reinterpret_cast<T*>(a.level[0]) + (size_t)v * H * W * C + c0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int X = X0 + px0 + (p & 1), Y = Y0 + py0 + (p >> 1);
+            if (X < W && Y < H) store16x2(l1 + ((size_t)Y * W + X) * C, acc[p]);
         }
+    }
+    // level 2: the quad mean
+    float2 t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float2 s01 = make_float2(acc[0][j].x + acc[1][j].x, acc[0][j].y + acc[1][j].y);
+        const float2 s23 = make_float2(acc[2][j].x + acc[3][j].x, acc[2][j].y + acc[3][j].y);
+        t[j] = make_float2(0.25f * (s01.x + s23.x), 0.25f * (s01.y + s23.y));
+    }
+    {
+        const int H2 = H / 2, W2 = W / 2, X = X0 / 2 + qx, Y = Y0 / 2 + qy;
+        if (a.level[1] && X < W2 && Y < H2)
+            store16x2(reinterpret_cast<T*>(a.level[1]) + (((size_t)v * H2 + Y) * W2 + X) * C + c0, t);
+    }
+    // level 4: quads (qx ^ 1, qy ^ 1) are lanes ^ 1 and ^ 8
+    quad_mean(t, 1, 8);
+    {
+        const int H4 = H / 4, W4 = W / 4, X = X0 / 4 + qx / 2, Y = Y0 / 4 + qy / 2;
+        if (a.level[2] && !(qx & 1) && !(qy & 1) && X < W4 && Y < H4)
+            store16x2(reinterpret_cast<T*>(a.level[2]) + (((size_t)v * H4 + Y) * W4 + X) * C + c0, t);
+    }
+    // level 8: level-4 texels at lanes ^ 2 and ^ 16
+    quad_mean(t, 2, 16);
+    {
+        const int H8 = H / 8, W8 = W / 8, X = X0 / 8 + qx / 4, Y = Y0 / 8 + qy / 4;
+        if (a.level[3] && !(qx & 3) && !(qy & 3) && X < W8 && Y < H8)
+            store16x2(reinterpret_cast<T*>(a.level[3]) + (((size_t)v * H8 + Y) * W8 + X) * C + c0, t);
     }
 }
 
 template <typename T, int C>
 static cudaError_t launch_t(const EncodeArgs& a, cudaStream_t st) {
     dim3 grid((a.W + ENC_T - 1) / ENC_T, (a.H + ENC_T - 1) / ENC_T, a.V);
-    encode_kernel<T, C><<<grid, 64, 0, st>>>(a);
+    encode_kernel<T, C><<<grid, 64 * (C / 16), 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ struct CollapseArgs {
     void* out;        // [L][H][W][C]
     int L, H, W;
     const float* w;   // W1 [2C][C], b1 [C], W2 [C][C], b2 [C]
+    const void* wtc;  // BF16 form: packed B operands of W1 (C x 2C) then W2 (C x C); else NULL
+    int* err;         // BF16 form: set when a bounded wait of the tensor-core kernel runs out
 };
 
 enum Transition { TR_INIT = 0, TR_SAME = 1, TR_UP2 = 2 };
@@ -124,6 +126,7 @@ struct CollapseLayout {
 // Launchers (k_*.cu).  Each returns the launch's cudaError_t.
 cudaError_t launch_encode(const EncodeArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st);
+cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st);
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                           cudaStream_t st);
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
