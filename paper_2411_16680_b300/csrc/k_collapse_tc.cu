@@ -4,7 +4,8 @@
 // A CTA owns 128 pixels of one layer pair (M = 128, one element per thread):
 //   1. a and b (BF16) are copied as they are into shared memory as the K-major A operand
 //      X = [a | b] (K = 2C); 0.5 (a + b) is kept in FP32 registers.
-//   2. X W1 (N = C) into TMEM; + b1, erf-GELU, BF16 -> shared memory as the A operand G (K = C).
+//   2. X W1 (N = C) into TMEM; + b1, GELU (polynomial erf form), BF16 -> shared memory as the
+//      A operand G (K = C).
 //   3. G W2 (N = C) into the next TMEM columns; + b2 + 0.5 (a + b); stored as BF16.
 // Each MMA chain signals an mbarrier through tcgen05.commit; every wait is bounded.
 #include "device_common.cuh"
@@ -118,8 +119,8 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int c = ch * 16 + 8 * g + 2 * i;
-                    hh[i] = __floats2bfloat162_rn(gelu_erf(hv[8 * g + 2 * i] + s_b[c]),
-                                                  gelu_erf(hv[8 * g + 2 * i + 1] + s_b[c + 1]));
+                    const float2 ge = gelu_poly2(make_float2(hv[8 * g + 2 * i] + s_b[c], hv[8 * g + 2 * i + 1] + s_b[c + 1]));
+                    hh[i] = __floats2bfloat162_rn(ge.x, ge.y);
                 }
                 *reinterpret_cast<uint4*>(s_g + ((size_t)(2 * ch + g) * CL_M + tid) * 16) = u;
             }

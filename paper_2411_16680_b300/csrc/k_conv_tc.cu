@@ -199,7 +199,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
             const int gy = y0 - 1 + r, gx = x0 - 1 + col;
             const bool inside = gy >= 0 && gy < H && gx >= 0 && gx < W;
 #pragma unroll
-            for (int c = 0; c < C; ++c) v[c] = inside ? gelu_erf(v[c] + misc[C + c]) : 0.f;
+            for (int c = 0; c < C; c += 2) {
+                const float2 g = gelu_poly2(__fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(misc[C + c], misc[C + c + 1])));
+                v[c] = inside ? g.x : 0.f;
+                v[c + 1] = inside ? g.y : 0.f;
+            }
             store_pixel_bf16<C>(s_mid, S::NPIX_MID, r * TC_M + col, v);
         }
         umma::fence_smem_to_async();
