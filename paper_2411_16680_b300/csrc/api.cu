@@ -750,10 +750,7 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
             ca.H = Hp;
             ca.W = Wp;
             ca.w = ctx->wdev + ctx->off_collapse[scale];
-            if (ctx->wat) {
-                const size_t att_bytes = ((size_t)(c.heads * c.C + c.C) * c.C + (size_t)c.C * c.heads * c.C) * 2;
-                ca.wtc = (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes + att_bytes;
-            }
+            ca.wtc = qk_collapse_wtc(ctx, scale);
             ca.err = ctx->dev_err;
             s = qk_launch(ctx, st, KF_COLLAPSE, [&] { return launch_collapse(ca, c.C, bf16, st); });
             if (s != QUARK_OK) return s;
@@ -793,18 +790,45 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     ca.W = W;
     ca.dp = aa.dp;
     ca.w = ctx->wdev + ctx->off_conv[scale];
-    ca.colour = ldm->colour;
-    ca.alpha = ldm->alpha;
-    ca.depth = ldm->depth;
-    ca.t_raw = ldm->t_raw;
-    ca.s_raw = ldm->s_raw;
+    // the raw depth / density logits are written here for the step that is rendered; every other
+    // decoded attribute is produced on demand (qk_decode) when it is read
+    ca.t_raw = last ? ldm->t_raw : nullptr;
+    ca.s_raw = last ? ldm->s_raw : nullptr;
     ca.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
     ca.err = ctx->dev_err;
     s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(ca, c.C, bf16, st); });
     if (s != QUARK_OK) return s;
     ldm->cur = 1 - ldm->cur;
     ldm->done = scale;
+    ldm->decoded = -1;
     return QUARK_OK;
+}
+
+// Decoded attributes (colour, alpha, depth, raw logits) of step `scale` from its stored volume.
+quark_status qk_decode(quark_ctx* ctx, int scale, const void* vol, int L, int H, int W, float* colour, float* alpha,
+                       float* depth, float* t_raw, float* s_raw, cudaStream_t st) {
+    const quark_config& c = ctx->cfg;
+    DecodeArgs da{};
+    da.vol = vol;
+    da.L = L;
+    da.H = H;
+    da.W = W;
+    da.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+    da.w = ctx->wdev + ctx->off_conv[scale];
+    da.colour = colour;
+    da.alpha = alpha;
+    da.depth = depth;
+    da.t_raw = t_raw;
+    da.s_raw = s_raw;
+    return qk_launch(ctx, st, KF_CONV, [&] { return launch_decode(da, c.C, c.precision == QUARK_BF16, st); });
+}
+
+// Packed BF16 collapse weights of step `scale` (after the step's attention packs), or NULL.
+const void* qk_collapse_wtc(const quark_ctx* ctx, int scale) {
+    if (!ctx->wat) return nullptr;
+    const quark_config& c = ctx->cfg;
+    const size_t att_bytes = ((size_t)(c.heads * c.C + c.C) * c.C + (size_t)c.C * c.heads * c.C) * 2;
+    return (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes + att_bytes;
 }
 
 extern "C" quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, float* rgba,
@@ -900,6 +924,17 @@ extern "C" quark_status quark_ldm_read(quark_ldm* l, int field, void* dst, size_
     if (need == 0 || need != bytes) return qk_fail(ctx, QUARK_EINVAL, "field %d: %zu bytes expected, %zu given", field, need, bytes);
     cudaSetDevice(ctx->device);
     QK_CUDA(ctx, cudaDeviceSynchronize());
+    const bool decoded_field = field == QUARK_FIELD_COLOUR || field == QUARK_FIELD_ALPHA || field == QUARK_FIELD_DEPTH ||
+                               field == QUARK_FIELD_DEPTH_LOGIT || field == QUARK_FIELD_DENSITY_LOGIT;
+    if (decoded_field && l->decoded != l->done) {
+        int L, H, W;
+        step_dims(l, l->done, L, H, W);
+        quark_status s = qk_decode(ctx, l->done, l->vol[l->cur], L, H, W, l->colour, l->alpha, l->depth, l->t_raw,
+                                   l->s_raw, nullptr);
+        if (s != QUARK_OK) return s;
+        QK_CUDA(ctx, cudaDeviceSynchronize());
+        l->decoded = l->done;
+    }
     const void* src = nullptr;
     switch (field) {
         case QUARK_FIELD_VOLUME: src = l->vol[l->cur]; break;

@@ -91,7 +91,8 @@ struct quark_ldm {
     size_t out_bytes = 0;
     size_t last_e = 0;
     int V = 0;
-    int done = -1;  // latest Update & Fuse step completed
+    int done = -1;     // latest Update & Fuse step completed
+    int decoded = -1;  // step whose decoded attributes (colour, alpha, depth, logits) are current
     bool async = false;            // buffers from the stream-ordered allocator on `stream`
     cudaStream_t stream = nullptr;
 };
@@ -110,6 +111,9 @@ void qk_ldm_free(quark_ldm* l);
 quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use, int scale, quark_ldm* ldm,
                             cudaStream_t stream, const void* prev_override = nullptr,
                             const void* feat_override = nullptr);
+quark_status qk_decode(quark_ctx* ctx, int scale, const void* vol, int L, int H, int W, float* colour, float* alpha,
+                       float* depth, float* t_raw, float* s_raw, cudaStream_t st);
+const void* qk_collapse_wtc(const quark_ctx* ctx, int scale);
 quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, int V_use, float* rgba,
                        int host_out, cudaStream_t stream);
 quark_status qk_encode_pyramid_sync(quark_ctx* ctx, const float* images, const quark_camera* cams, int V,

@@ -1,8 +1,8 @@
 // Residual conv block of the fusion block (Sec. 3.3): V' = V + Conv2(gelu(Conv1(N(V)))), 3x3
-// convolutions per layer plane (zero padding), N = RMSNorm, followed by the decode of the LDM
-// attributes (Sec. 3.2.2 "Decoding"; Sec. 3.2.3 Eq. depth_activation):
-//   colour = sigmoid(V W_a + b_a), alpha = sigmoid(V w_sigma + b_sigma), depth from t = V w_d + b_d,
-//   plus the raw logits t and V w_sigma + b_sigma in pixel-major [H][W][L] order for the render.
+// convolutions per layer plane (zero padding), N = RMSNorm.  When asked (the last step, whose
+// LDM is rendered), it also writes the raw depth and density logits t = V' w_d + b_d and
+// V' w_sigma + b_sigma (Sec. 3.2.2 "Decoding") in pixel-major [H][W][L] order; the other decoded
+// attributes are produced on demand by k_decode.cu.
 //
 // FP32 SIMT form.  One CTA per 16x8 output tile of one layer plane: the normalised input tile
 // with a 2-pixel halo and the gelu(Conv1) tile with a 1-pixel halo stay in shared memory, so
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     float* sin = sm + S::in_off;
     float* smid = sm + S::mid_off;
     float* sw = sm + S::w_off;
-    float* misc = sm + S::misc_off;  // g, b1, b2, w_d, w_s, W_a (3C), b_a (3), b_d, b_s
+    float* misc = sm + S::misc_off;  // g, b1, b2, w_d, w_s, (unused 3C + 3), b_d, b_s
 
     const int tid = threadIdx.x;
     const int H = a.H, W = a.W, L = a.L;
@@ -51,11 +51,7 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
         misc[2 * C + i] = a.w[lay.b2() + i];
         misc[3 * C + i] = a.w[lay.wd() + i];
         misc[4 * C + i] = a.w[lay.ws() + i];
-        misc[5 * C + 3 * i + 0] = a.w[lay.wa() + 3 * i + 0];
-        misc[5 * C + 3 * i + 1] = a.w[lay.wa() + 3 * i + 1];
-        misc[5 * C + 3 * i + 2] = a.w[lay.wa() + 3 * i + 2];
     }
-    if (tid < 3) misc[8 * C + tid] = a.w[lay.ba() + tid];
     if (tid == 3) misc[8 * C + 3] = a.w[lay.bd()];
     if (tid == 4) misc[8 * C + 4] = a.w[lay.bs()];
     {
@@ -149,7 +145,6 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     const T* res = vin + pix * C;
     T* out = reinterpret_cast<T*>(a.out) + ((size_t)li * plane + pix) * C;
     float t = misc[8 * C + 3], s = misc[8 * C + 4];
-    float rgb[3] = {misc[8 * C], misc[8 * C + 1], misc[8 * C + 2]};
 #pragma unroll
     for (int c0 = 0; c0 < C; c0 += 16) {
         float r[16], o[16];
@@ -160,20 +155,13 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
             o[i] = r[i] + acc[c0 / 16][i];
             t = fmaf(o[i], misc[3 * C + c], t);
             s = fmaf(o[i], misc[4 * C + c], s);
-            rgb[0] = fmaf(o[i], misc[5 * C + 3 * c + 0], rgb[0]);
-            rgb[1] = fmaf(o[i], misc[5 * C + 3 * c + 1], rgb[1]);
-            rgb[2] = fmaf(o[i], misc[5 * C + 3 * c + 2], rgb[2]);
         }
         store16(out + c0, o);
     }
-    const size_t el = (size_t)li * plane + pix;
-    a.colour[3 * el + 0] = sigmoidf_(rgb[0]);
-    a.colour[3 * el + 1] = sigmoidf_(rgb[1]);
-    a.colour[3 * el + 2] = sigmoidf_(rgb[2]);
-    a.alpha[el] = sigmoidf_(s);
-    a.depth[el] = depth_from_logit(t, li, L, a.dp);
-    a.t_raw[pix * L + li] = t;
-    a.s_raw[pix * L + li] = s;
+    if (a.t_raw) {
+        a.t_raw[pix * L + li] = t;
+        a.s_raw[pix * L + li] = s;
+    }
 }
 
 template <typename T, int C>

@@ -1,7 +1,7 @@
 // Residual conv block on 5th-generation tensor cores (BF16 form): V' = V + Conv2(gelu(Conv1(N(V))))
-// with 3x3 convolutions per layer plane (Sec. 3.3), followed by the decode of the LDM
-// attributes (Sec. 3.2.2, Sec. 3.2.3 Eq. depth_activation).  BF16 operands, FP32 accumulation in
-// TMEM; normalisation, gelu, residual and decode in FP32 registers.
+// with 3x3 convolutions per layer plane (Sec. 3.3); when asked (the last step), also the raw
+// depth and density logits of V' as stored in BF16 (Sec. 3.2.2 "Decoding").  BF16 operands, FP32
+// accumulation in TMEM; normalisation, gelu and residual in FP32 registers.
 //
 // Implicit GEMM.  A CTA owns an output tile of TC_R rows x 126 columns of one layer plane; two
 // CTAs share an SM, so one CTA's tile loads overlap the other's MMAs and epilogues.  Each
@@ -98,11 +98,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
         misc[2 * C + i] = a.w[lay.b2() + i];
         misc[3 * C + i] = a.w[lay.wd() + i];
         misc[4 * C + i] = a.w[lay.ws() + i];
-        misc[5 * C + 3 * i + 0] = a.w[lay.wa() + 3 * i + 0];
-        misc[5 * C + 3 * i + 1] = a.w[lay.wa() + 3 * i + 1];
-        misc[5 * C + 3 * i + 2] = a.w[lay.wa() + 3 * i + 2];
     }
-    if (tid < 3) misc[8 * C + tid] = a.w[lay.ba() + tid];
     if (tid == 3) misc[8 * C + 3] = a.w[lay.bd()];
     if (tid == 4) misc[8 * C + 4] = a.w[lay.bs()];
     {
@@ -243,31 +239,30 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
                 const size_t pix = (size_t)gy * W + gx;
                 const size_t el = (size_t)li * plane + pix;
                 float t = misc[8 * C + 3], s = misc[8 * C + 4];
-                float rgb[3] = {misc[8 * C], misc[8 * C + 1], misc[8 * C + 2]};
-                __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.out) + el * C;
+                uint4* out = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + el * C);
 #pragma unroll
                 for (int c0 = 0; c0 < C; c0 += 16) {
-                    float rr[16], o[16];
+                    float rr[16];
                     load16(vin + pix * C + c0, rr);
+                    uint4 u[2];
+                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int c = c0 + i;
-                        o[i] = rr[i] + v[c] + misc[2 * C + c];
-                        t = fmaf(o[i], misc[3 * C + c], t);
-                        s = fmaf(o[i], misc[4 * C + c], s);
-                        rgb[0] = fmaf(o[i], misc[5 * C + 3 * c + 0], rgb[0]);
-                        rgb[1] = fmaf(o[i], misc[5 * C + 3 * c + 1], rgb[1]);
-                        rgb[2] = fmaf(o[i], misc[5 * C + 3 * c + 2], rgb[2]);
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = c0 + 2 * j;
+                        hh[j] = __floats2bfloat162_rn(rr[2 * j] + v[c] + misc[2 * C + c],
+                                                      rr[2 * j + 1] + v[c + 1] + misc[2 * C + c + 1]);
+                        // the logits from V' as stored, as the on-demand decode computes them
+                        const float2 o = __bfloat1622float2(hh[j]);
+                        t = fmaf(o.y, misc[3 * C + c + 1], fmaf(o.x, misc[3 * C + c], t));
+                        s = fmaf(o.y, misc[4 * C + c + 1], fmaf(o.x, misc[4 * C + c], s));
                     }
-                    store16(out + c0, o);
+                    out[c0 / 8] = u[0];
+                    out[c0 / 8 + 1] = u[1];
                 }
-                a.colour[3 * el + 0] = sigmoidf_(rgb[0]);
-                a.colour[3 * el + 1] = sigmoidf_(rgb[1]);
-                a.colour[3 * el + 2] = sigmoidf_(rgb[2]);
-                a.alpha[el] = sigmoidf_(s);
-                a.depth[el] = depth_from_logit(t, li, L, a.dp);
-                a.t_raw[pix * L + li] = t;
-                a.s_raw[pix * L + li] = s;
+                if (a.t_raw) {
+                    a.t_raw[pix * L + li] = t;
+                    a.s_raw[pix * L + li] = s;
+                }
             }
         } else if (tid == 0) {
             atomicExch(a.err, 2);

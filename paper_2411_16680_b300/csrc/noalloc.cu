@@ -4,7 +4,8 @@
 // attention block and, where the layer count halves, the collapsed volume -- in memory the
 // library allocates for the LDM handle.  This variant takes every input and output from the
 // caller and keeps those two intermediates in one fixed, file-scope device array instead, so
-// the call itself never allocates.  It launches the same kernels as the regular step.
+// the call itself never allocates.  It launches the same kernels as the regular step, and the
+// attribute decode that the regular step runs when its decoded attributes are read.
 #include <cmath>
 #include <mutex>
 
@@ -101,6 +102,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
             ca.H = Hp;
             ca.W = Wp;
             ca.w = ctx->wdev + ctx->off_collapse[scale];
+            ca.wtc = qk_collapse_wtc(ctx, scale);
+            ca.err = ctx->dev_err;
             e = launch_collapse(ca, c.C, bf16, st);
             ctx->launches++;
             if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "collapse launch: %s", cudaGetErrorString(e));
@@ -140,15 +143,11 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     cv.W = W;
     cv.dp = aa.dp;
     cv.w = ctx->wdev + ctx->off_conv[scale];
-    cv.colour = colour;
-    cv.alpha = alpha;
-    cv.depth = depth;
-    cv.t_raw = t_raw;
-    cv.s_raw = s_raw;
     cv.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
     cv.err = ctx->dev_err;
     e = launch_conv_block(cv, c.C, bf16, st);
     ctx->launches++;
     if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "conv block launch: %s", cudaGetErrorString(e));
-    return QUARK_OK;
+    // the decoded attributes, from the volume just written (the regular step makes them on demand)
+    return qk_decode(ctx, scale, v_out, L, H, W, colour, alpha, depth, t_raw, s_raw, st);
 }

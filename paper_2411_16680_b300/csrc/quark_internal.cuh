@@ -67,13 +67,23 @@ struct ConvArgs {
     int L, H, W;
     DepthParams dp;
     const float* w;    // g [C], W1 [9][C][C], b1 [C], W2 [9][C][C], b2 [C], dec: w_d [C], w_s [C], W_a [C][3], b_a[3], b_d, b_s
+    float* t_raw;      // [H][W][L] raw depth logits, or NULL (not written)
+    float* s_raw;      // [H][W][L] raw density logits, or NULL (not written)
+    const void* wtc;   // BF16 form: W1 then W2 packed as tcgen05 B operands (see pack_conv_weights_bf16)
+    int* err;          // device error word: set when a bounded wait inside the kernel runs out
+};
+
+// Decode of the LDM attributes from a stored volume (Sec. 3.2.2 "Decoding", Eq. depth_activation).
+struct DecodeArgs {
+    const void* vol;   // V [L][H][W][C] as stored (FP32 or BF16)
+    int L, H, W;
+    DepthParams dp;
+    const float* w;    // the step's conv-block weights (ConvLayout: w_d, w_s, W_a, b_a, b_d, b_s)
     float* colour;     // [L][H][W][3]
     float* alpha;      // [L][H][W]
     float* depth;      // [L][H][W]
     float* t_raw;      // [H][W][L]
     float* s_raw;      // [H][W][L]
-    const void* wtc;   // BF16 form: W1 then W2 packed as tcgen05 B operands (see pack_conv_weights_bf16)
-    int* err;          // device error word: set when a bounded wait inside the kernel runs out
 };
 
 struct RenderArgs {
@@ -131,6 +141,7 @@ cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, 
                           cudaStream_t st);
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st);
+cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
 
