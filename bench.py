@@ -377,6 +377,7 @@ def main():
     ap.add_argument("--sharp", action="store_true", help="sharp random weights instead of N(0, 0.02)")
     ap.add_argument("--size", default="1920x1080", help="WxH of views and output (profiling runs use a smaller case)")
     ap.add_argument("--forms", default="fp32,bf16", help="forms to time (comma separated)")
+    ap.add_argument("--views", type=int, default=8, help="input views used (1..8; profiling of per-view cost)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=120.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -397,8 +398,14 @@ def main():
     sw, sh = (int(v) for v in args.size.lower().split("x"))
     workload = WORKLOAD if (sw, sh) == (1920, 1080) else WORKLOAD.replace("1080p", f"{sw}x{sh}").replace(
         "1920x1080", f"{sw}x{sh}")
+    if args.views != 8:
+        workload = workload.replace("V=8 views", f"V={args.views} views")
     base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh)
     scene = synth.scene_1080p(W=sw, H=sh)
+    if not 1 <= args.views <= len(scene.cams):
+        ap.error(f"--views must be in 1..{len(scene.cams)}")
+    if args.views < len(scene.cams):
+        scene = synth.Scene(scene.images[:args.views], scene.cams[:args.views], scene.target)
     V = len(scene.cams)
     img_h, img_w = scene.images.shape[1:3]
 
@@ -472,7 +479,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cfg64 = base_cfg.replace(precision=synth.PREC_FP32)
-        fps_cpu, secs, desc = oracle_sample(cfg64, synth.make_weights(cfg64, sharp=args.sharp), scene, rows=2)
+        fps_cpu, secs, desc = oracle_sample(cfg64, synth.make_weights(cfg64, sharp=args.sharp), scene, rows=6)
         cpu = {"value": round(fps_cpu, 6), "unit": "frames/s", "cores": blas_threads(), "kind": "oracle",
                "sample": desc, "seconds": round(secs, 1)}
     if rank == 0:
