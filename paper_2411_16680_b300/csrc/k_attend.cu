@@ -98,6 +98,29 @@ cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_
 
 constexpr int ATT_THREADS = 128;
 
+// acc[j] += x * (w[2j], w[2j+1]) for 16 weights at w (shared memory): packed FP32x2
+__device__ __forceinline__ void fma_row16_x2(const float* w, float x, float2 (&acc)[8]) {
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    const float2 x2 = make_float2(x, x);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 t = w4[i];
+        acc[2 * i] = __ffma2_rn(x2, make_float2(t.x, t.y), acc[2 * i]);
+        acc[2 * i + 1] = __ffma2_rn(x2, make_float2(t.z, t.w), acc[2 * i + 1]);
+    }
+}
+// D[j] += w * texel[2j .. 2j+1] for 16 FP32 channels at p (global memory)
+__device__ __forceinline__ void fma_tap16_x2(const float* p, float w, float2 (&D)[8]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float2 w2 = make_float2(w, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 t = __ldg(q + i);
+        D[2 * i] = __ffma2_rn(make_float2(t.x, t.y), w2, D[2 * i]);
+        D[2 * i + 1] = __ffma2_rn(make_float2(t.z, t.w), w2, D[2 * i + 1]);
+    }
+}
+
 template <typename T, int C, int NH, int TR, bool LAST>
 __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;  // threads per element
@@ -191,73 +214,78 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a)
             if (sb == sub) s = vin[sb * 16 + i];
         vres[i] = s;
     }
-    float q[NH][16];
+    float2 q[NH][8];
 #pragma unroll
     for (int h = 0; h < NH; ++h)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) q[h][i] = 0.f;
+        for (int j = 0; j < 8; ++j) q[h][j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
 #pragma unroll
-        for (int h = 0; h < NH; ++h) {
-            fma_row16(&sw[lay.wq() + k * NH * C + h * C + c0], xn[k], q[h]);
-        }
+        for (int h = 0; h < NH; ++h) fma_row16_x2(&sw[lay.wq() + k * NH * C + h * C + c0], xn[k], q[h]);
     }
-    float qb[16];
+    float2 qb[8];
     if constexpr (LAST) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) qb[i] = 0.f;
+        for (int j = 0; j < 8; ++j) qb[j] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            fma_row16(&sw[lay.wb() + k * C + c0], xn[k], qb);
-        }
+        for (int k = 0; k < C; ++k) fma_row16_x2(&sw[lay.wb() + k * C + c0], xn[k], qb);
     }
 
-    // ---- views: sample, online softmax, weighted sum ----
-    const float scale = 1.0f / sqrtf((float)C);
+    // ---- views: sample, online softmax (log2 units, lazy rescale), weighted sum ----
+    const float lscale = 1.4426950408889634f / sqrtf((float)C), scale = 1.0f / sqrtf((float)C);
     const float pxc = x + 0.5f, pyc = y + 0.5f;
-    float mx[NH], l[NH], o[NH][16];
+    float mx[NH], l[NH];
+    float2 o[NH][8];
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
         mx[h] = -INFINITY;
         l[h] = 0.f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) o[h][i] = 0.f;
+        for (int j = 0; j < 8; ++j) o[h][j] = make_float2(0.f, 0.f);
     }
     const T* feat = reinterpret_cast<const T*>(a.feat);
     const size_t vstride = (size_t)a.fh * a.fw * C;
     for (int m = 0; m < a.V; ++m) {
-        float D[16];
+        float2 D[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) D[i] = 0.f;
+        for (int j = 0; j < 8; ++j) D[j] = make_float2(0.f, 0.f);
         float u, v;
         const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
         const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
         const T* fb = feat + m * vstride + c0;
-        fma16(fb + (size_t)tp.i00 * C, tp.w00, D);
-        fma16(fb + (size_t)tp.i01 * C, tp.w01, D);
-        fma16(fb + (size_t)tp.i10 * C, tp.w10, D);
-        fma16(fb + (size_t)tp.i11 * C, tp.w11, D);
+        fma_tap16_x2(fb + (size_t)tp.i00 * C, tp.w00, D);
+        fma_tap16_x2(fb + (size_t)tp.i01 * C, tp.w01, D);
+        fma_tap16_x2(fb + (size_t)tp.i10 * C, tp.w10, D);
+        fma_tap16_x2(fb + (size_t)tp.i11 * C, tp.w11, D);
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
-            float s = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) s = fmaf(q[h][i], D[i], s);
+            for (int j = 0; j < 8; ++j) acc = __ffma2_rn(q[h][j], D[j], acc);
+            float s = acc.x + acc.y;
 #pragma unroll
             for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            s *= scale;
-            float mn = fmaxf(mx[h], s);
-            float cs = expf(mx[h] - mn);
-            float p = expf(s - mn);
-            l[h] = fmaf(l[h], cs, p);
+            s *= lscale;
+            if (s > mx[h]) {  // the running maximum moves: rescale
+                const float cs = exp2f(mx[h] - s);
+                const float2 cs2 = make_float2(cs, cs);
+                l[h] *= cs;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[h][i] = fmaf(o[h][i], cs, p * D[i]);
-            mx[h] = mn;
+                for (int j = 0; j < 8; ++j) o[h][j] = __fmul2_rn(o[h][j], cs2);
+                mx[h] = s;
+            }
+            const float p = exp2f(s - mx[h]);
+            const float2 p2 = make_float2(p, p);
+            l[h] += p;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[h][j] = __ffma2_rn(p2, D[j], o[h][j]);
         }
         if constexpr (LAST) {
-            float s = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) s = fmaf(qb[i], D[i], s);
+            for (int j = 0; j < 8; ++j) acc = __ffma2_rn(qb[j], D[j], acc);
+            float s = acc.x + acc.y;
 #pragma unroll
             for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
             if (live && sub == 0) a.beta[(((size_t)y * W + x) * L + li) * a.V + m] = s * scale;
@@ -265,9 +293,9 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a)
     }
 
     // ---- output projection and residual ----
-    float out[16];
+    float2 out2[8];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) out[i] = vres[i];
+    for (int j = 0; j < 8; ++j) out2[j] = make_float2(vres[2 * j], vres[2 * j + 1]);
     const int lane = threadIdx.x & 31;
     const int gbase = lane & ~(TPE - 1);
 #pragma unroll
@@ -275,11 +303,17 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a)
         const float il = 1.0f / l[h];
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            float ok = o[h][k % 16];
+            const float2 pr = o[h][(k % 16) / 2];
+            float ok = (k & 1) ? pr.y : pr.x;
             if (TPE > 1) ok = __shfl_sync(0xffffffffu, ok, gbase + k / 16);
-            ok *= il;
-            fma_row16(&sw[lay.wo() + (h * C + k) * C + c0], ok, out);
+            fma_row16_x2(&sw[lay.wo() + (h * C + k) * C + c0], ok * il, out2);
         }
+    }
+    float out[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        out[2 * j] = out2[j].x;
+        out[2 * j + 1] = out2[j].y;
     }
     if (live) store16(reinterpret_cast<T*>(a.out) + e * C + c0, out);
 }

@@ -27,6 +27,19 @@ struct ConvSmem {
     static constexpr int total = misc_off + 8 * C + 8;
 };
 
+// acc[j] += x * (w[2j], w[2j+1]) over a row of C weights: packed FP32x2, two channels per FMA
+template <int C>
+__device__ __forceinline__ void fma_row_x2(const float* w, float x, float2 (&acc)[C / 2]) {
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    const float2 x2 = make_float2(x, x);
+#pragma unroll
+    for (int i = 0; i < C / 4; ++i) {
+        const float4 t = w4[i];
+        acc[2 * i] = __ffma2_rn(x2, make_float2(t.x, t.y), acc[2 * i]);
+        acc[2 * i + 1] = __ffma2_rn(x2, make_float2(t.z, t.w), acc[2 * i + 1]);
+    }
+}
+
 template <typename T, int C>
 __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a) {
     using S = ConvSmem<C>;
@@ -94,22 +107,21 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
         const int gy = Y0 - 1 + my, gx = X0 - 1 + mx;
         float* dst = smid + p * P;
         if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            float acc[C / 16][16];
+            float2 acc[C / 2];
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c / 16][c % 16] = misc[C + c];
+            for (int j = 0; j < C / 2; ++j) acc[j] = make_float2(misc[C + 2 * j], misc[C + 2 * j + 1]);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const float* src = sin + ((my + tap / 3) * CV_IW + mx + tap % 3) * P;
                 const float* wt = sw + tap * C * C;
 #pragma unroll 4
-                for (int ci = 0; ci < C; ++ci) {
-                    const float x = src[ci];
-#pragma unroll
-                    for (int c0 = 0; c0 < C; c0 += 16) fma_row16(wt + ci * C + c0, x, acc[c0 / 16]);
-                }
+                for (int ci = 0; ci < C; ++ci) fma_row_x2<C>(wt + ci * C, src[ci], acc);
             }
 #pragma unroll
-            for (int c = 0; c < C; ++c) dst[c] = gelu_erf(acc[c / 16][c % 16]);
+            for (int j = 0; j < C / 2; ++j) {
+                dst[2 * j] = gelu_erf(acc[j].x);
+                dst[2 * j + 1] = gelu_erf(acc[j].y);
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) dst[c] = 0.f;
@@ -127,19 +139,15 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     const int oy = tid / CV_TW, ox = tid % CV_TW;
     const int gy = Y0 + oy, gx = X0 + ox;
     if (gy >= H || gx >= W) return;
-    float acc[C / 16][16];
+    float2 acc[C / 2];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c / 16][c % 16] = misc[2 * C + c];
+    for (int j = 0; j < C / 2; ++j) acc[j] = make_float2(misc[2 * C + 2 * j], misc[2 * C + 2 * j + 1]);
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
         const float* src = smid + ((oy + tap / 3) * CV_MW + ox + tap % 3) * P;
         const float* wt = sw + tap * C * C;
 #pragma unroll 4
-        for (int ci = 0; ci < C; ++ci) {
-            const float x = src[ci];
-#pragma unroll
-            for (int c0 = 0; c0 < C; c0 += 16) fma_row16(wt + ci * C + c0, x, acc[c0 / 16]);
-        }
+        for (int ci = 0; ci < C; ++ci) fma_row_x2<C>(wt + ci * C, src[ci], acc);
     }
     const size_t pix = (size_t)gy * W + gx;
     const T* res = vin + pix * C;
@@ -152,7 +160,7 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int c = c0 + i;
-            o[i] = r[i] + acc[c0 / 16][i];
+            o[i] = r[i] + (i & 1 ? acc[c / 2].y : acc[c / 2].x);
             t = fmaf(o[i], misc[3 * C + c], t);
             s = fmaf(o[i], misc[4 * C + c], s);
         }
