@@ -126,7 +126,7 @@ def oracle_sample(cfg, W, scene, rows: int = 2):
     y0 = cfg.out_h // 2 - rows // 2
     rect = (y0, y0 + rows, 0, cfg.out_w)
     t0 = time.perf_counter()
-    O.forward(cfg, W, scene, rect)
+    O.forward(cfg, W, scene, rect, mode=cfg.attn_mode)
     dt = time.perf_counter() - t0
     fps = (rows / cfg.out_h) / dt
     desc = (f"oracle (float64 numpy) on output rows {rect[0]}-{rect[1] - 1} x all {cfg.out_w} columns of the "
@@ -240,7 +240,8 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     work = accounting.per_view_work(cfg, V, img_h, img_w)
     steps_done = None
     fam, (n, ms) = max(res["ktimes"].items(), key=lambda kv: kv[1][1])
-    steps_done = n / max(work[fam]["launches"], 1)
+    # frames timed: the render runs once per frame
+    steps_done = res["ktimes"].get("render", (n, 0))[0] / max(work["render"]["launches"], 1)
     per_launch_ms = ms / n
     w = work[fam]
     bytes_per_launch = w["bytes"] / w["launches"]
@@ -378,6 +379,8 @@ def main():
     ap.add_argument("--size", default="1920x1080", help="WxH of views and output (profiling runs use a smaller case)")
     ap.add_argument("--forms", default="fp32,bf16", help="forms to time (comma separated)")
     ap.add_argument("--views", type=int, default=8, help="input views used (1..8; profiling of per-view cost)")
+    ap.add_argument("--attn", default="one_to_many", choices=["one_to_many", "standard"],
+                    help="attention of the fusion blocks (standard: K/V projections, the comparison mode)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=120.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -400,7 +403,10 @@ def main():
         "1920x1080", f"{sw}x{sh}")
     if args.views != 8:
         workload = workload.replace("V=8 views", f"V={args.views} views")
-    base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh)
+    attn_mode = synth.ATTN_STANDARD if args.attn == "standard" else synth.ATTN_ONE_TO_MANY
+    if attn_mode == synth.ATTN_STANDARD:
+        workload += ", standard attention"
+    base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh, attn_mode=attn_mode)
     scene = synth.scene_1080p(W=sw, H=sh)
     if not 1 <= args.views <= len(scene.cams):
         ap.error(f"--views must be in 1..{len(scene.cams)}")
@@ -461,7 +467,7 @@ def main():
         Ho, Wo = base_cfg.out_h, base_cfg.out_w
         rects = [(0, 4, 0, 4), (Ho // 2 - 2, Ho // 2 + 2, Wo // 2 - 2, Wo // 2 + 2), (Ho - 4, Ho, Wo - 4, Wo)]
         W = synth.make_weights(base_cfg, sharp=args.sharp)
-        refs = [O.forward(base_cfg, W, scene, r)[0] for r in rects]
+        refs = [O.forward(base_cfg, W, scene, r, mode=base_cfg.attn_mode)[0] for r in rects]
         for form, (cfg, res) in results.items():
             errs, sq, n = [], 0.0, 0
             for r, ref in zip(rects, refs):

@@ -48,7 +48,8 @@ typedef enum {
 #define QUARK_MAX_VIEWS 32
 
 enum { QUARK_FP32 = 0, QUARK_BF16 = 1 };             /* storage / tensor-core precision form */
-enum { QUARK_ATTN_ONE_TO_MANY = 0 };                  /* Sec. 3.3 "Optimized Attention" */
+enum { QUARK_ATTN_ONE_TO_MANY = 0,                    /* Sec. 3.3 "Optimized Attention" */
+       QUARK_ATTN_STANDARD = 1 };                     /* Sec. 3.3 Eq. MultiHead with K/V projections */
 
 /* Pinhole camera (Sec. 3.1: camera parameters theta).  R row-major, world->camera. */
 typedef struct {
@@ -59,8 +60,9 @@ typedef struct {
 } quark_camera;
 
 /* Network shape (Sec. 3.2; tables "Model description for Quark / Quark+").
- *   C          channels of features, pyramid and feature volume: 16, 32 or 64
- *   heads      one-to-many attention heads h: 1, 2 or 4 (per-head width C, appendix A)
+ *   C          channels of features, pyramid and feature volume: 16 or 32
+ *   heads      attention heads h: 1, 2 or 4 (one-to-many: per-head width C, appendix A;
+ *              standard: per-head width C/h)
  *   n_scales   number of Update & Fuse steps, 1..8
  *   k[j], L[j] pyramid factor and LDM layer count of step j, coarse to fine.  k in {1,2,4,8};
  *              k[j-1]/k[j] in {1,2} (x2 spatial upsample); L[j-1]/L[j] in {1,2} (layer
@@ -69,6 +71,13 @@ typedef struct {
  *   precision  QUARK_FP32 (all storage and arithmetic FP32) or QUARK_BF16 (pyramid and
  *              feature volume stored in BF16, contractions on tensor cores with FP32
  *              accumulation; geometry, softmax and transmittance stay FP32)
+ *   attn_mode  QUARK_ATTN_ONE_TO_MANY (the paper's optimized attention: no K/V projections)
+ *              or QUARK_ATTN_STANDARD (textbook multi-head cross attention, Sec. 3.3 Eq.
+ *              MultiHead: keys and values are the sampled features times W^k and W^val, here
+ *              projected once per pyramid texel -- exact, since bilinear sampling is linear and
+ *              the projections have no bias -- and sampled from the projected maps).  The
+ *              standard mode runs on SIMT kernels in both precisions and needs the *_std
+ *              weights; quark_update_fuse_noalloc accepts one-to-many only.
  *   hbm_cap_bytes  cap on this context's device allocations (0 = no cap)              */
 typedef struct {
     int C, heads, n_scales;
@@ -116,6 +125,11 @@ typedef struct {
     const float* W_a;
     const float* b_a;
     const float* W_beta;
+    /* attn_mode QUARK_ATTN_STANDARD only (else may be NULL), per step j: [C][C] each */
+    const float* Wq_std[QUARK_MAX_SCALES];
+    const float* Wk_std[QUARK_MAX_SCALES];
+    const float* Wv_std[QUARK_MAX_SCALES];
+    const float* Wo_std[QUARK_MAX_SCALES];
 } quark_weights;
 
 typedef struct quark_ctx quark_ctx;

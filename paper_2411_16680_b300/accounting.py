@@ -38,10 +38,20 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
                 c["bytes"] += (Lp + L) * Hp * Wp * C * elt
                 c["flops"] += 2 * 3 * C * C * L * Hp * Wp
                 c["launches"] += 1
-        a["bytes"] += vin + V * (img_h // k) * (img_w // k) * C * elt + E * C * elt + (E * V * 4 if last else 0)
-        macs = 2 * h * C * C + 2 * V * h * C + 4 * V * C + (C * C + V * C if last else 0)
-        a["flops"] += 2 * macs * E
-        a["launches"] += 1
+        texels = V * (img_h // k) * (img_w // k)
+        if getattr(cfg, "attn_mode", 0) == 1:
+            # standard: keys / values (and the features on the last step) projected once per texel
+            # (written, then read by the sampling), per element q = x W^q, q_i . k_i and p v_i per
+            # view and head, W^O
+            nc = (3 if last else 2) * C
+            a["bytes"] += vin + texels * C * elt + 2 * texels * nc * elt + E * C * elt + (E * V * 4 if last else 0)
+            a["flops"] += 2 * (texels * 2 * C * C + E * (2 * C * C + 2 * V * C + (C * C + V * C if last else 0)))
+            a["launches"] += 2
+        else:
+            a["bytes"] += vin + texels * C * elt + E * C * elt + (E * V * 4 if last else 0)
+            macs = 2 * h * C * C + 2 * V * h * C + 4 * V * C + (C * C + V * C if last else 0)
+            a["flops"] += 2 * macs * E
+            a["launches"] += 1
         cb = out["conv_block"]
         cb["bytes"] += 2 * E * C * elt + E * 7 * 4
         cb["flops"] += 2 * (18 * C * C + 5 * C) * E

@@ -179,7 +179,10 @@ quark_status qk_validate_config(const quark_config* c) {
         return qk_fail(nullptr, QUARK_EINVAL, "need 0 < near < far < inf");
     if (c->precision != QUARK_FP32 && c->precision != QUARK_BF16)
         return qk_fail(nullptr, QUARK_EINVAL, "unknown precision %d", c->precision);
-    if (c->attn_mode != QUARK_ATTN_ONE_TO_MANY) return qk_fail(nullptr, QUARK_EINVAL, "unknown attention mode");
+    if (c->attn_mode != QUARK_ATTN_ONE_TO_MANY && c->attn_mode != QUARK_ATTN_STANDARD)
+        return qk_fail(nullptr, QUARK_EINVAL, "unknown attention mode %d", c->attn_mode);
+    if (c->attn_mode == QUARK_ATTN_STANDARD && c->C % c->heads)
+        return qk_fail(nullptr, QUARK_EINVAL, "standard attention needs C divisible by heads");
     return QUARK_OK;
 }
 
@@ -305,6 +308,23 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         blob.push_back(0.f);
         if (blob.size() - ctx->off_conv[j] != (size_t)cl.total()) return qk_fail(ctx, QUARK_EINTERNAL, "conv layout");
         pad4();
+        ctx->off_std[j] = (size_t)-1;
+        if (c.attn_mode == QUARK_ATTN_STANDARD) {
+            if (!need(w->Wq_std[j], "Wq_std") || !need(w->Wk_std[j], "Wk_std") || !need(w->Wv_std[j], "Wv_std") ||
+                !need(w->Wo_std[j], "Wo_std"))
+                return QUARK_EINVAL;
+            // StdLayout: W^q, W^O, then rows k of [W^k | W^val]
+            ctx->off_std[j] = blob.size();
+            put(w->Wq_std[j], (size_t)C * C);
+            put(w->Wo_std[j], (size_t)C * C);
+            for (int k = 0; k < C; ++k) {
+                for (int n = 0; n < C; ++n) blob.push_back(w->Wk_std[j][(size_t)k * C + n]);
+                for (int n = 0; n < C; ++n) blob.push_back(w->Wv_std[j][(size_t)k * C + n]);
+            }
+            if (blob.size() - ctx->off_std[j] != (size_t)StdLayout{C}.total())
+                return qk_fail(ctx, QUARK_EINTERNAL, "standard attention layout");
+            pad4();
+        }
         ctx->off_collapse[j] = (size_t)-1;
         if (j > 0 && c.L[j - 1] == 2 * c.L[j]) {
             if (!need(w->col_w1[j], "col_w1") || !need(w->col_b1[j], "col_b1") || !need(w->col_w2[j], "col_w2") ||
@@ -591,6 +611,11 @@ extern "C" quark_status quark_release_ldm(quark_ldm* ldm) {
     return QUARK_OK;
 }
 
+static quark_status ldm_buf(quark_ldm* l, void** p, size_t bytes);
+
+// A scratch buffer of the LDM that grows on demand (the superseded one is freed with the LDM).
+quark_status qk_ldm_scratch(quark_ldm* l, void** p, size_t bytes) { return ldm_buf(l, p, bytes); }
+
 static quark_status ldm_buf(quark_ldm* l, void** p, size_t bytes) {
     quark_status s;
     if (l->async) {
@@ -778,7 +803,26 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
     aa.err = ctx->dev_err;
     for (int m = 0; m < V_use; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
-    s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
+    if (c.attn_mode == QUARK_ATTN_STANDARD) {
+        // keys and values (and on the last step the features) projected in image space, then sampled
+        const size_t texels = (size_t)V_use * aa.fh * aa.fw;
+        const size_t need = texels * (size_t)(last ? 3 : 2) * c.C * (bf16 ? 2 : 4);
+        if (ldm->kv_bytes < need) {
+            s = qk_ldm_scratch(ldm, &ldm->kv, need);
+            if (s != QUARK_OK) return s;
+            ldm->kv_bytes = need;
+        }
+        const float* wkv = ctx->wdev + ctx->off_std[scale] + StdLayout{c.C}.wkv();
+        const void* level = aa.feat;
+        s = qk_launch(ctx, st, KF_ATTEND,
+                      [&] { return launch_kv_project(level, texels, c.C, wkv, ldm->kv, last, bf16, st); });
+        if (s != QUARK_OK) return s;
+        aa.feat = ldm->kv;
+        aa.w_std = ctx->wdev + ctx->off_std[scale];
+        s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend_std(aa, c.C, c.heads, tr, last, bf16, st); });
+    } else {
+        s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
+    }
     if (s != QUARK_OK) return s;
 
     // ---- conv block + decode ----

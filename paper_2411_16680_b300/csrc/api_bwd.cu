@@ -17,6 +17,8 @@ using namespace quark;
 static quark_status check_stage(quark_ctx* ctx, const quark_pyramid* pyr, const quark_ldm* ldm) {
     if (!ctx || !pyr || !ldm) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     if (ctx->cfg.precision != QUARK_FP32) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage is FP32 only");
+    if (ctx->cfg.attn_mode != QUARK_ATTN_ONE_TO_MANY)
+        return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage covers one-to-many attention");
     if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     return QUARK_OK;
@@ -26,6 +28,7 @@ extern "C" quark_status quark_step_input(quark_ctx* ctx, quark_ldm* ldm, int sca
     if (!ctx || !ldm || !v_in) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     const quark_config& c = ctx->cfg;
     if (c.precision != QUARK_FP32) return qk_fail(ctx, QUARK_EINVAL, "FP32 form only");
+    if (c.attn_mode != QUARK_ATTN_ONE_TO_MANY) return qk_fail(ctx, QUARK_EINVAL, "one-to-many attention only");
     if (scale < 1 || scale >= c.n_scales || ldm->done != scale - 1)
         return qk_fail(ctx, QUARK_EINVAL, "step %d's input needs step %d done (latest: %d)", scale, scale - 1, ldm->done);
     cudaSetDevice(ctx->device);

@@ -30,6 +30,7 @@ struct quark_ctx {
     size_t off_attend[QUARK_MAX_SCALES] = {};
     size_t off_conv[QUARK_MAX_SCALES] = {};
     size_t off_collapse[QUARK_MAX_SCALES] = {};
+    size_t off_std[QUARK_MAX_SCALES] = {};  // standard attention weights (StdLayout), or (size_t)-1
     // BF16 form: conv weights packed as tcgen05 B operands, per step W1 then W2
     void* wtc = nullptr;
     size_t wtc_bytes = 0;
@@ -87,6 +88,8 @@ struct quark_ldm {
     float* s_raw = nullptr;
     float* beta = nullptr;
     size_t beta_bytes = 0;
+    void* kv = nullptr;  // standard attention: the projected keys / values of the step's level
+    size_t kv_bytes = 0;
     void* out = nullptr;  // device staging of a host render target
     size_t out_bytes = 0;
     size_t last_e = 0;
@@ -111,6 +114,7 @@ void qk_ldm_free(quark_ldm* l);
 quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use, int scale, quark_ldm* ldm,
                             cudaStream_t stream, const void* prev_override = nullptr,
                             const void* feat_override = nullptr);
+quark_status qk_ldm_scratch(quark_ldm* l, void** p, size_t bytes);
 quark_status qk_decode(quark_ctx* ctx, int scale, const void* vol, int L, int H, int W, float* colour, float* alpha,
                        float* depth, float* t_raw, float* s_raw, cudaStream_t st);
 const void* qk_collapse_wtc(const quark_ctx* ctx, int scale);

@@ -50,6 +50,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     if (!ctx || !pyr || !target || !v_out || !colour || !alpha || !depth || !t_raw || !s_raw)
         return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     if (pyr->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "pyramid from another context");
+    if (ctx->cfg.attn_mode != QUARK_ATTN_ONE_TO_MANY)
+        return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs one-to-many attention only (use quark_update_fuse)");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     const quark_config& c = ctx->cfg;
     if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);

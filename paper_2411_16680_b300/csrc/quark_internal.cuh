@@ -58,6 +58,7 @@ struct AttendArgs {
     float* beta;       // [H][W][L][V] blend logits (last step), else NULL
     const void* wtc;   // BF16 form: [Wq | W_beta] and W^O packed as tcgen05 B operands
     int* err;          // device error word (bounded waits)
+    const float* w_std;  // standard mode: StdLayout (W^q, W^O); else NULL
     Geometry geo;
 };
 
@@ -109,6 +110,14 @@ struct AttendLayout {
     __host__ __device__ constexpr int wb() const { return 4 * C + 2 * C * h * C; }
     __host__ __device__ constexpr int total() const { return 4 * C + 2 * C * h * C + C * C; }
 };
+// Standard-mode weights of one step: W^q [C][C], W^O [C][C], then [W^k | W^val] [C][2C].
+struct StdLayout {
+    int C;
+    __host__ __device__ constexpr int wq() const { return 0; }
+    __host__ __device__ constexpr int wo() const { return C * C; }
+    __host__ __device__ constexpr int wkv() const { return 2 * C * C; }
+    __host__ __device__ constexpr int total() const { return 4 * C * C; }
+};
 struct ConvLayout {
     int C;
     __host__ __device__ constexpr int g() const { return 0; }
@@ -143,6 +152,10 @@ cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t 
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st);
 cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st);
+cudaError_t launch_kv_project(const void* feat, size_t texels, int C, const float* wkv, void* out, bool with_f, bool bf16,
+                              cudaStream_t st);
+cudaError_t launch_attend_std(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
+                              cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
 
 }  // namespace quark

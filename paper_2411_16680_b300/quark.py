@@ -50,7 +50,8 @@ class Weights(ct.Structure):
                 ("conv_g", _PER), ("conv1_w", _PER), ("conv1_b", _PER), ("conv2_w", _PER), ("conv2_b", _PER),
                 ("col_w1", _PER), ("col_b1", _PER), ("col_w2", _PER), ("col_b2", _PER),
                 ("w_d", _FP), ("b_d", ct.c_float), ("w_sigma", _FP), ("b_sigma", ct.c_float),
-                ("W_a", _FP), ("b_a", _FP), ("W_beta", _FP)]
+                ("W_a", _FP), ("b_a", _FP), ("W_beta", _FP),
+                ("Wq_std", _PER), ("Wk_std", _PER), ("Wv_std", _PER), ("Wo_std", _PER)]
 
 
 class ServeConfig(ct.Structure):
@@ -280,6 +281,9 @@ class Context:
             if f"col_w1_{j}" in W:
                 w.col_w1[j], w.col_b1[j] = p(f"col_w1_{j}"), p(f"col_b1_{j}")
                 w.col_w2[j], w.col_b2[j] = p(f"col_w2_{j}"), p(f"col_b2_{j}")
+            if f"Wq_std_{j}" in W:
+                w.Wq_std[j], w.Wk_std[j] = p(f"Wq_std_{j}"), p(f"Wk_std_{j}")
+                w.Wv_std[j], w.Wo_std[j] = p(f"Wv_std_{j}"), p(f"Wo_std_{j}")
         w.w_d, w.w_sigma, w.W_a, w.b_a, w.W_beta = p("w_d"), p("w_sigma"), p("W_a"), p("b_a"), p("W_beta")
         w.b_d = float(np.asarray(W["b_d"]).reshape(-1)[0])
         w.b_sigma = float(np.asarray(W["b_sigma"]).reshape(-1)[0])
