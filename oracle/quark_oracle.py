@@ -448,6 +448,27 @@ def render_rect(cfg, scene, last: StepResult, out_rect: Rect, return_layers: boo
     return rgba
 
 
+def render_depth_rect(cfg, last: StepResult, out_rect: Rect):
+    """Depth map of the novel view on out_rect (Sec. 3.1: the optional output, the decoded depth
+    over-composited instead of the blended input views).  The raw depth and density logits of the
+    last LDM are upsampled and activated exactly as for the colour render; then, front (l = L) to
+    back, D += T alpha_l d_l and T *= 1 - alpha_l, with 0 behind the last layer.  Reading: the
+    over-composite itself, not normalised by the accumulated alpha."""
+    k, L = cfg.scales[-1]
+    Hl, Wl = cfg.out_h // k, cfg.out_w // k
+    t_up = resize_rect(last.t[..., None], last.rect_out, Hl, Wl, k, out_rect)[..., 0]
+    s_up = resize_rect(last.s[..., None], last.rect_out, Hl, Wl, k, out_rect)[..., 0]
+    ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
+    d = depth_activation(t_up, ell, L, cfg.near, cfg.far)
+    alpha = sigmoid(s_up)
+    D = np.zeros(d.shape[1:])
+    T = np.ones(d.shape[1:])
+    for li in range(L - 1, -1, -1):
+        D += T * alpha[li] * d[li]
+        T = T * (1.0 - alpha[li])
+    return D
+
+
 def over_back_to_front(col, alpha):
     """Over operator applied back to front (l = 1 first), as the paper states it (Sec. 3.1)."""
     rgb = np.zeros(col.shape[1:])

@@ -345,6 +345,34 @@ def test_render_two_layer_closed_form_and_order():
     assert col.min() >= 0 and col.max() <= 1
 
 
+def test_depth_map_closed_forms():
+    """Sec. 3.1 optional depth output: over-compositing the decoded depth.  One opaque nearest
+    layer gives its depth; a transparent LDM gives 0; two layers give a_L d_L + (1 - a_L) a_{L-1}
+    d_{L-1}, the same as the back-to-front over operator applied to depth as a colour; t = 0
+    puts every layer at its anchor depth (Eq. depth_activation)."""
+    cfg = synth.config_small()
+    L, h, w = 4, 24, 32
+    rect = (0, 48, 0, 64)
+    s = np.full((L, 1, 1), -60.0)
+    s[L - 1] = 60.0
+    D = O.render_depth_rect(cfg, _fake_last(L, h, w, 2, 0.0, s, 0.0), rect)
+    anchors = O.depth_activation(np.zeros(L), np.arange(1, L + 1), L, cfg.near, cfg.far)
+    np.testing.assert_allclose(D, anchors[L - 1], rtol=1e-12)
+    np.testing.assert_allclose(O.render_depth_rect(cfg, _fake_last(L, h, w, 2, 0.0, -80.0, 0.0), rect), 0.0,
+                               atol=1e-30)
+    cfg2 = cfg.replace(scales=[(2, 2)])
+    rng = np.random.default_rng(3)
+    t = rng.standard_normal((2, 24, 32))
+    s2 = rng.standard_normal((2, 24, 32))
+    last = _fake_last(2, 24, 32, 2, t, s2, 0.0)
+    D = O.render_depth_rect(cfg2, last, rect)
+    _, _, alpha, d, _ = O.render_rect(cfg2, synth.scene_small(), last, rect, True)
+    np.testing.assert_allclose(D, alpha[1] * d[1] + (1 - alpha[1]) * alpha[0] * d[0], rtol=1e-12)
+    np.testing.assert_allclose(D, O.over_back_to_front(d[..., None], alpha)[..., 0], rtol=1e-12)
+    # the depth map lies between 0 and the farthest layer depth
+    assert D.min() >= 0 and D.max() <= d.max()
+
+
 def test_render_identical_views_identity_geometry():
     # every view is the target camera with the same image: each layer's colour is the image
     sc = synth.scene_small()
