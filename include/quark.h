@@ -45,7 +45,7 @@ typedef enum {
 } quark_status;
 
 #define QUARK_MAX_SCALES 8
-#define QUARK_MAX_VIEWS 32
+#define QUARK_MAX_VIEWS 64
 
 enum { QUARK_FP32 = 0, QUARK_BF16 = 1 };             /* storage / tensor-core precision form */
 enum { QUARK_ATTN_ONE_TO_MANY = 0,                    /* Sec. 3.3 "Optimized Attention" */
@@ -153,7 +153,7 @@ quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* w);
  *   images  [V][H][W][3] float32 in [0, 1]; device memory, or host memory (pinned for an
  *           asynchronous copy), which is then copied in on `stream`
  *   cams    V host cameras; all views share one resolution W x H, divisible by every k
- *   V       1..32
+ *   V       1..64
  * If *out is NULL on entry, a new pyramid is allocated ([V][H/k][W/k][C] per level, FP32 or
  * BF16 by the precision form) and returned in *out; free it with quark_release_pyramid.  If
  * *out holds a pyramid of this context with the same V and resolution, it is re-encoded in
@@ -189,6 +189,14 @@ quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int sca
  *         memory, or host memory (copied out on `stream`; synchronise before reading). */
 quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, float* rgba,
                               void* stream);
+
+/* Depth map of the novel view (Sec. 3.1: "a depth map can optionally be produced by
+ * over-compositing the decoded depth instead of the blended input views"): the last LDM's raw
+ * depth and density logits are upsampled and activated as for quark_render_ldm, and, front to
+ * back, D += T alpha_l d_l, T *= 1 - alpha_l (0 behind the last layer; not normalised by the
+ * accumulated alpha).  depth: [target height][target width] float, device or host memory (a
+ * host target is copied out on the stream).  Needs every Update & Fuse step run (EINVAL). */
+quark_status quark_render_depth(quark_ctx* ctx, const quark_ldm* ldm, float* depth, void* stream);
 
 /* Convenience: every Update & Fuse step then the render, for one novel view. */
 quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, quark_ldm* ldm, float* rgba,

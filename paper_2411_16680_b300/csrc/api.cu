@@ -929,6 +929,51 @@ quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid
     return QUARK_OK;
 }
 
+extern "C" quark_status quark_render_depth(quark_ctx* ctx, const quark_ldm* ldm, float* depth, void* stream) {
+    if (!ctx || !ldm || !depth) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "LDM from another context");
+    const quark_config& c = ctx->cfg;
+    if (ldm->done != c.n_scales - 1) return qk_fail(ctx, QUARK_EINVAL, "the depth map needs every Update & Fuse step first");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    quark_ldm* l = const_cast<quark_ldm*>(ldm);
+    const int n = c.n_scales - 1;
+    RenderArgs ra{};
+    ra.t_raw = l->t_raw;
+    ra.s_raw = l->s_raw;
+    ra.L = c.L[n];
+    ra.Hl = l->target.height / c.k[n];
+    ra.Wl = l->target.width / c.k[n];
+    ra.s = c.k[n];
+    ra.Hout = l->target.height;
+    ra.Wout = l->target.width;
+    ra.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+    const bool host_out = !is_device_pointer(depth);
+    const size_t bytes = (size_t)ra.Hout * ra.Wout * sizeof(float);
+    float* dst = depth;
+    if (host_out) {
+        // the render's host-output staging buffer (RGBA-sized, so large enough)
+        const size_t need = (size_t)ra.Hout * ra.Wout * sizeof(float4);
+        if (l->out_bytes < need) {
+            for (auto it = l->bufs.begin(); it != l->bufs.end(); ++it)
+                if (it->p == l->out) {
+                    qk_free(ctx, it->p, it->bytes);
+                    l->bufs.erase(it);
+                    break;
+                }
+            l->out = nullptr;
+            quark_status s = ldm_buf(l, &l->out, need);
+            if (s != QUARK_OK) return s;
+            l->out_bytes = need;
+        }
+        dst = (float*)l->out;
+    }
+    quark_status s = qk_launch(ctx, st, KF_RENDER, [&] { return launch_render_depth(ra, dst, st); });
+    if (s != QUARK_OK) return s;
+    if (host_out) QK_CUDA(ctx, cudaMemcpyAsync(depth, dst, bytes, cudaMemcpyDeviceToHost, st));
+    return QUARK_OK;
+}
+
 extern "C" quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, quark_ldm* ldm, float* rgba,
                                                 void* stream) {
     if (!ctx) return qk_fail(nullptr, QUARK_EINVAL, "NULL context");

@@ -100,6 +100,50 @@ __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) 
     a.out[idx] = make_float4(cr, cg, cb, 1.f - T);
 }
 
+// Depth map (Sec. 3.1, the optional output): the decoded depth over-composited instead of the
+// blended input views, D += T alpha_l d_l front to back, 0 behind the last layer.  The raw logits
+// are upsampled and activated as in render_kernel.
+__global__ void __launch_bounds__(RD_THREADS) render_depth_kernel(const RenderArgs a, float* __restrict__ depth) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)a.Hout * a.Wout) return;
+    const int X = (int)(idx % a.Wout), Y = (int)(idx / a.Wout);
+    const int L = a.L;
+    float D = 0.f, T = 1.f;
+    if (a.s == 1) {
+        for (int li = L - 1; li >= 0; --li) {
+            const float d = depth_from_logit(a.t_raw[idx * L + li], li, L, a.dp);
+            const float al = sigmoidf_(a.s_raw[idx * L + li]);
+            D = fmaf(T * al, d, D);
+            T *= 1.f - al;
+        }
+    } else {
+        int y0, y1, x0, x1;
+        float wy, wx;
+        resize_taps(Y, a.s, a.Hl, y0, y1, wy);
+        resize_taps(X, a.s, a.Wl, x0, x1, wx);
+        const size_t q00 = (size_t)y0 * a.Wl + x0, q01 = (size_t)y0 * a.Wl + x1;
+        const size_t q10 = (size_t)y1 * a.Wl + x0, q11 = (size_t)y1 * a.Wl + x1;
+        auto up = [&](const float* f, int li) {
+            const float top = f[q00 * L + li] * (1 - wx) + f[q01 * L + li] * wx;
+            const float bot = f[q10 * L + li] * (1 - wx) + f[q11 * L + li] * wx;
+            return top * (1 - wy) + bot * wy;
+        };
+        for (int li = L - 1; li >= 0; --li) {
+            const float d = depth_from_logit(up(a.t_raw, li), li, L, a.dp);
+            const float al = sigmoidf_(up(a.s_raw, li));
+            D = fmaf(T * al, d, D);
+            T *= 1.f - al;
+        }
+    }
+    depth[idx] = D;
+}
+
+cudaError_t launch_render_depth(const RenderArgs& a, float* depth, cudaStream_t st) {
+    const size_t n = (size_t)a.Hout * a.Wout;
+    render_depth_kernel<<<(unsigned)((n + RD_THREADS - 1) / RD_THREADS), RD_THREADS, 0, st>>>(a, depth);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st) {
     const size_t n = (size_t)a.Hout * a.Wout;
     render_kernel<<<(unsigned)((n + RD_THREADS - 1) / RD_THREADS), RD_THREADS, 0, st>>>(a);

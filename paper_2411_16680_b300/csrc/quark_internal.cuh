@@ -157,5 +157,6 @@ cudaError_t launch_kv_project(const void* feat, size_t texels, int C, const floa
 cudaError_t launch_attend_std(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                               cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
+cudaError_t launch_render_depth(const RenderArgs& a, float* depth, cudaStream_t st);
 
 }  // namespace quark

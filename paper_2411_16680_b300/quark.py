@@ -16,7 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libquark.so")
 
 MAX_SCALES = 8
-MAX_VIEWS = 32
+MAX_VIEWS = 64
 
 OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, ENOTFOUND, EBUSY, EINTERNAL = range(9)
 FP32, BF16 = 0, 1
@@ -103,6 +103,7 @@ def lib():
             "quark_update_fuse": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
             "quark_render_ldm": ([vp, vp, vp, vp, vp], ct.c_int),
             "quark_render_novel_view": ([vp, vp, vp, vp, vp], ct.c_int),
+            "quark_render_depth": ([vp, vp, vp, vp], ct.c_int),
             "quark_ldm_read": ([vp, ct.c_int, vp, ct.c_size_t], ct.c_int),
             "quark_ldm_field_bytes": ([vp, ct.c_int], ct.c_size_t),
             "quark_release_pyramid": ([vp], ct.c_int),
@@ -140,6 +141,7 @@ def lib():
 def exported_symbols() -> List[str]:
     return [n for n in ("quark_create", "quark_destroy", "quark_load_weights", "quark_encode_pyramid",
                         "quark_ldm_create", "quark_update_fuse", "quark_render_ldm", "quark_render_novel_view",
+                        "quark_render_depth",
                         "quark_ldm_read", "quark_ldm_field_bytes", "quark_release_pyramid", "quark_release_ldm",
                         "quark_last_error", "quark_launch_count", "quark_reset_counters", "quark_set_profiling",
                         "quark_kernel_times")]
@@ -320,6 +322,10 @@ class Context:
 
     def render_ldm(self, ldm: LDM, pyr: Pyramid, rgba, stream=None):
         _check(lib().quark_render_ldm(self.handle, ldm.handle, pyr.handle, _ptr(rgba), _stream(stream)), self.handle)
+
+    def render_depth(self, ldm: LDM, depth, stream=None):
+        """Depth map [H_out, W_out] of the solved LDM (device tensor or host array)."""
+        _check(lib().quark_render_depth(self.handle, ldm.handle, _ptr(depth), _stream(stream)), self.handle)
 
     def render_novel_view(self, pyr: Pyramid, ldm: LDM, rgba, stream=None):
         _check(lib().quark_render_novel_view(self.handle, pyr.handle, ldm.handle, _ptr(rgba), _stream(stream)),
