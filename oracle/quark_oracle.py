@@ -211,12 +211,64 @@ def encode_level(image, enc_w, enc_b, k):
     return encode_box(image, enc_w, enc_b, k, (0, H // k, 0, W // k))
 
 
+# ---------------------------------------------------------------------------------------------
+# Ray directional encoding (Sec. 3.2.1)
+# ---------------------------------------------------------------------------------------------
+
+RAY_OCTAVES = 8
+
+
+def ray_difference(cam_m, cam_t, k0, near, far):
+    """For the pixel centres of view m on its k0-times coarser grid: the ray's intersections with
+    the near and far planes of the LDM frustum (target-camera depth `near` and `far`), each taken
+    to the target's normalised image plane (x / z, y / z), and their difference, far minus near.
+    [h0, w0, 2].  Zero for a ray through the target camera's centre (a target ray)."""
+    h0, w0 = cam_m.height // k0, cam_m.width // k0
+    ys, xs = np.meshgrid(np.arange(h0) + 0.5, np.arange(w0) + 0.5, indexing="ij")
+    p = np.stack([xs, ys, np.ones_like(xs)], -1)
+    d_w = (p @ np.linalg.inv(scaled_K(cam_m, k0)).T) @ cam_m.R  # ray direction, world
+    c_w = -cam_m.R.T @ cam_m.t                                  # view m's centre, world
+    A = cam_t.R @ c_w + cam_t.t                                 # ray in target coordinates: A + lam B
+    B = d_w @ cam_t.R.T
+    Bz = B[..., 2]
+    Bz = np.where(np.abs(Bz) < 1e-300, 1e-300, Bz)
+    planes = []
+    for z in (near, far):
+        lam = (z - A[2]) / Bz
+        X = A + lam[..., None] * B  # X.z == z
+        planes.append(X[..., :2] / z)
+    return planes[1] - planes[0]
+
+
+def ray_encoding(diff):
+    """tanh of the difference vector, then a sinusoidal encoding with 8 octaves: feature
+    4 i + 2 j + {0, 1} = {sin, cos}(2^i pi tanh(diff_j)), i = 0..7, j = x, y.  [..., 32]."""
+    e = np.tanh(diff)
+    feats = []
+    for i in range(RAY_OCTAVES):
+        for j in range(2):
+            a = (2.0 ** i) * math.pi * e[..., j]
+            feats += [np.sin(a), np.cos(a)]
+    return np.stack(feats, -1)
+
+
+def ray_gamma(cam_m, cam_t, k0, k, near, far, W_ray, box):
+    """gamma_k of view m on `box` (y0, y1, x0, x1) of level k: the encoding computed once on the
+    coarse grid k0, bilinearly upsampled by k0 / k (pixel centres aligned, edge clamp) and
+    projected to C channels by the level's own matrix W_ray [32][C]."""
+    coarse = ray_encoding(ray_difference(cam_m, cam_t, k0, near, far))
+    h0, w0 = coarse.shape[:2]
+    up = resize_rect(coarse, (0, h0, 0, w0), h0, w0, k0 // k, box)
+    return up @ W_ray
+
+
 class LevelFetch:
     """Texel fetch from level k of view m with zero padding; evaluates the encoder lazily on
     the bounding box of the texels asked for (all fetches are declared first by `need`)."""
 
-    def __init__(self, image, enc_w, enc_b, k):
+    def __init__(self, image, enc_w, enc_b, k, gamma=None):
         self.image, self.enc_w, self.enc_b, self.k = image, enc_w, enc_b, k
+        self.gamma = gamma  # optional: box -> ray directional encoding added to the features
         self.h, self.w = image.shape[0] // k, image.shape[1] // k
         self.box = None
         self.data = None
@@ -232,6 +284,8 @@ class LevelFetch:
         box = (int(ys[inside].min()), int(ys[inside].max()) + 1, int(xs[inside].min()), int(xs[inside].max()) + 1)
         self.box = box
         self.data = encode_box(self.image, self.enc_w, self.enc_b, self.k, box)
+        if self.gamma is not None:
+            self.data = self.data + self.gamma(box)
 
     def __call__(self, iy, ix):
         inside = (iy >= 0) & (iy < self.h) & (ix >= 0) & (ix < self.w)
@@ -513,8 +567,20 @@ def plan_rects(cfg, out_rect: Rect):
 
 
 def make_fetchers(cfg, scene, W):
+    """Level-k texel fetchers of every view; with the ray directional encoding on, the fetched
+    update features are F_k + gamma_k (reading: the encoding is added to the image features; the
+    encoding is computed at the coarsest level the network uses)."""
+    k0 = max(cfg.levels())
+    ray = getattr(cfg, "ray_encoding", 0)
+
+    def gamma(m, k):
+        if not ray:
+            return None
+        Wr = np.asarray(W[f"W_ray_{k}"], np.float64)
+        return lambda box: ray_gamma(scene.cams[m], scene.target, k0, k, cfg.near, cfg.far, Wr, box)
+
     return {k: [LevelFetch(scene.images[m], np.asarray(W["enc_w"], np.float64),
-                           np.asarray(W["enc_b"], np.float64), k) for m in range(len(scene.cams))]
+                           np.asarray(W["enc_b"], np.float64), k, gamma(m, k)) for m in range(len(scene.cams))]
             for k in cfg.levels()}
 
 

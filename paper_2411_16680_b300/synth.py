@@ -51,6 +51,7 @@ class QuarkConfig:
     out_w: int = 64
     attn_mode: int = ATTN_ONE_TO_MANY
     precision: int = PREC_FP32
+    ray_encoding: int = 0  # 1: add the ray directional encoding gamma_k to the sampled features
 
     @property
     def n_scales(self) -> int:
@@ -347,6 +348,7 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
                  Wq_std_j, Wk_std_j, Wv_std_j, Wo_std_j (C, C)         standard cross-attention mode
     w_d (C,), b_d (1,), w_sigma (C,), b_sigma (1,), W_a (C, 3), b_a (3,)   LDM decoders
     W_beta (C, C): blend-weight query projection of the final block (Sec. 3.2.3)
+    W_ray_k (32, C) per pyramid level k used: projection of the ray directional encoding (Sec. 3.2.1)
     """
     C, h = cfg.C, cfg.heads
     s = {"enc_w": (3, 3, 3, C), "enc_b": (C,), "v0": (C,)}
@@ -360,6 +362,8 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
         })
     s.update({"w_d": (C,), "b_d": (1,), "w_sigma": (C,), "b_sigma": (1,), "W_a": (C, 3), "b_a": (3,),
               "W_beta": (C, C)})
+    for k in cfg.levels():
+        s[f"W_ray_{k}"] = (32, C)
     return s
 
 

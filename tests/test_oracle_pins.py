@@ -495,3 +495,103 @@ def test_pipeline_matches_independent_library_formulation(case):
     ours, _ = O.forward(cfg, W, sc)
     ref = torch_pipeline.forward(cfg, W, sc)
     np.testing.assert_allclose(ours, ref, atol=1e-10)
+
+
+# --------------------------------------------------------------------------------------------
+# Ray directional encoding (Sec. 3.2.1)
+# --------------------------------------------------------------------------------------------
+
+def _ray_AB(cam_m, cam_t, k0):
+    """Independent setup: view m's centre and its pixel-centre rays in target coordinates."""
+    h0, w0 = cam_m.height // k0, cam_m.width // k0
+    K0 = np.array(cam_m.K, np.float64).copy()
+    K0[:2] /= k0
+    centre = np.linalg.solve(cam_m.R, -cam_m.t)  # R c + t = 0
+    out_A = cam_t.R @ centre + cam_t.t
+    B = np.zeros((h0, w0, 3))
+    for y in range(h0):
+        for x in range(w0):
+            d_cam = np.linalg.solve(K0, np.array([x + 0.5, y + 0.5, 1.0]))
+            B[y, x] = cam_t.R @ np.linalg.solve(cam_m.R, d_cam)
+    return out_A, B
+
+
+def test_ray_difference_closed_form():
+    """far - near in the target's normalised image plane equals (1/eta - 1/f) (A_z B_xy / B_z -
+    A_xy) for the ray A + lam B in target coordinates (eliminate lam at z = eta and z = f)."""
+    sc = synth.scene_raycast(V=3, W=64, H=48, f=50, arc=0.6)
+    near, far = 1.5, 40.0
+    for m in range(3):
+        A, B = _ray_AB(sc.cams[m], sc.target, 4)
+        ref = (1 / near - 1 / far) * (A[2] * B[..., :2] / B[..., 2:3] - A[:2])
+        np.testing.assert_allclose(O.ray_difference(sc.cams[m], sc.target, 4, near, far), ref, atol=1e-12)
+
+
+def test_ray_difference_zero_through_target_centre():
+    """A view whose centre is the target camera's centre (any rotation and focal length): every
+    ray is a target ray, so the encoding's input vanishes (the paper's first property)."""
+    sc = synth.scene_raycast(V=2, W=64, H=48, f=50, arc=0.3)
+    tgt = sc.target
+    centre = np.linalg.solve(tgt.R, -tgt.t)
+    view = synth.make_camera(64, 48, 37.0, tuple(centre), target=tuple(centre + np.array([0.3, -0.2, 1.0])))
+    np.testing.assert_allclose(O.ray_difference(view, tgt, 2, 1.0, 30.0), 0.0, atol=1e-12)
+    assert np.abs(O.ray_difference(sc.cams[0], tgt, 2, 1.0, 30.0)).max() > 1e-3
+
+
+def test_ray_encoding_octaves_and_saturation():
+    rng = np.random.default_rng(4)
+    diff = rng.standard_normal((5, 7, 2))
+    pe = O.ray_encoding(diff)
+    assert pe.shape == (5, 7, 32)
+    s, c = pe[..., 0::2], pe[..., 1::2]
+    np.testing.assert_allclose(s ** 2 + c ** 2, 1.0, atol=1e-14)
+    # octave i + 1 is the double angle of octave i: sin 2a = 2 sin a cos a, cos 2a = cos^2 a - sin^2 a
+    for i in range(7):
+        for j in range(2):
+            a, b = 4 * i + 2 * j, 4 * (i + 1) + 2 * j
+            np.testing.assert_allclose(pe[..., b], 2 * pe[..., a] * pe[..., a + 1], atol=1e-13)
+            np.testing.assert_allclose(pe[..., b + 1], pe[..., a + 1] ** 2 - pe[..., a] ** 2, atol=1e-13)
+    # octave 0 is sin / cos of pi tanh(diff)
+    np.testing.assert_allclose(pe[..., 0], np.sin(np.pi * np.tanh(diff[..., 0])), atol=1e-15)
+    # zero difference: sin 0 = 0, cos 0 = 1; a huge one saturates tanh at +-1: sin(2^i pi) = 0
+    np.testing.assert_allclose(O.ray_encoding(np.zeros(2)), np.tile([0.0, 1.0], 16), atol=0)
+    np.testing.assert_allclose(O.ray_encoding(np.array([1e9, -1e9]))[0::2], 0.0, atol=1e-12)
+
+
+def test_ray_gamma_is_upsampled_projection():
+    """gamma_k = bilinear upsample (pixel centres aligned, edge clamp) of the coarse encoding,
+    projected; checked against a separable np.interp upsample."""
+    sc = synth.scene_raycast(V=2, W=64, H=48, f=50, arc=0.3)
+    rng = np.random.default_rng(8)
+    Wr = rng.standard_normal((32, 5))
+    k0, k = 8, 2
+    r = k0 // k
+    coarse = O.ray_encoding(O.ray_difference(sc.cams[1], sc.target, k0, 1.0, 30.0)) @ Wr  # [6, 8, 5]
+    h0, w0 = coarse.shape[:2]
+    H, Wd = 48 // k, 64 // k
+    sy = np.clip((np.arange(H) + 0.5) / r - 0.5, 0, h0 - 1)
+    sx = np.clip((np.arange(Wd) + 0.5) / r - 0.5, 0, w0 - 1)
+    rows = np.stack([np.stack([np.interp(sy, np.arange(h0), coarse[:, x, c]) for c in range(5)], -1)
+                     for x in range(w0)], 1)                      # [H, w0, 5]
+    ref = np.stack([np.stack([np.interp(sx, np.arange(w0), rows[y, :, c]) for c in range(5)], -1)
+                    for y in range(H)], 0)                        # [H, Wd, 5]
+    got = O.ray_gamma(sc.cams[1], sc.target, k0, k, 1.0, 30.0, Wr, (0, H, 0, Wd))
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+    # at the coarse level itself the upsample is the identity
+    np.testing.assert_allclose(O.ray_gamma(sc.cams[1], sc.target, k0, k0, 1.0, 30.0, Wr, (0, h0, 0, w0)), coarse,
+                               atol=1e-14)
+
+
+def test_ray_encoding_off_or_zero_weights_leaves_the_pipeline():
+    """With W_ray = 0 the encoding adds nothing: the pipeline equals the one without it; with the
+    seeded weights it changes the output."""
+    cfg = synth.QuarkConfig(C=8, heads=2, scales=[(4, 4), (2, 2)], near=1, far=20, out_h=48, out_w=64,
+                            ray_encoding=1)
+    W = synth.make_weights(cfg, sharp=True)
+    sc = synth.scene_raycast(V=3, W=64, H=48, f=50, arc=0.3)
+    base, _ = O.forward(cfg.replace(ray_encoding=0), W, sc)
+    W0 = dict(W)
+    for k in cfg.levels():
+        W0[f"W_ray_{k}"] = np.zeros_like(W[f"W_ray_{k}"])
+    np.testing.assert_allclose(O.forward(cfg, W0, sc)[0], base, atol=1e-14)
+    assert np.abs(O.forward(cfg, W, sc)[0] - base).max() > 1e-3
