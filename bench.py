@@ -403,6 +403,7 @@ def main():
     ap.add_argument("--size", default="1920x1080", help="WxH of views and output (profiling runs use a smaller case)")
     ap.add_argument("--forms", default="fp32,bf16", help="forms to time (comma separated)")
     ap.add_argument("--views", type=int, default=8, help="input views used (1..64; the view sweep and the per-view cost split)")
+    ap.add_argument("--ray", action="store_true", help="add the ray directional encoding (Sec. 3.2.1) to the features")
     ap.add_argument("--attn", default="one_to_many", choices=["one_to_many", "standard"],
                     help="attention of the fusion blocks (standard: K/V projections, the comparison mode)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
@@ -430,7 +431,9 @@ def main():
     attn_mode = synth.ATTN_STANDARD if args.attn == "standard" else synth.ATTN_ONE_TO_MANY
     if attn_mode == synth.ATTN_STANDARD:
         workload += ", standard attention"
-    base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh, attn_mode=attn_mode)
+    if args.ray:
+        workload += ", ray directional encoding"
+    base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh, attn_mode=attn_mode, ray_encoding=int(args.ray))
     if not 1 <= args.views <= 64:
         ap.error("--views must be in 1..64")
     scene = synth.scene_1080p(W=sw, H=sh, V=max(8, args.views))

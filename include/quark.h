@@ -78,6 +78,13 @@ typedef struct {
  *              the projections have no bias -- and sampled from the projected maps).  The
  *              standard mode runs on SIMT kernels in both precisions and needs the *_std
  *              weights; quark_update_fuse_noalloc accepts one-to-many only.
+ *   ray_encoding  1: the ray directional encoding gamma_k of Sec. 3.2.1 is added to each view's
+ *              level-k features before they are sampled -- per input pixel, the difference of
+ *              its ray's intersections with the near and far planes of the target (LDM)
+ *              frustum in the target's normalised image plane, tanh, 8 octaves of sinusoids
+ *              (32 values) on the coarsest level, bilinearly upsampled to level k and projected
+ *              to C channels by W_ray of that level.  Needs the W_ray weights; not with
+ *              quark_update_fuse_noalloc nor the differentiable stage.  0: off.
  *   hbm_cap_bytes  cap on this context's device allocations (0 = no cap)              */
 typedef struct {
     int C, heads, n_scales;
@@ -86,6 +93,7 @@ typedef struct {
     float near_m, far_m;
     int precision;
     int attn_mode;
+    int ray_encoding;
     size_t hbm_cap_bytes;
 } quark_config;
 
@@ -130,6 +138,9 @@ typedef struct {
     const float* Wk_std[QUARK_MAX_SCALES];
     const float* Wv_std[QUARK_MAX_SCALES];
     const float* Wo_std[QUARK_MAX_SCALES];
+    /* ray_encoding only (else may be NULL): [32][C] projection of the encoding for pyramid level
+     * k = 1, 2, 4, 8 (index 0..3), for every level some step uses */
+    const float* W_ray[4];
 } quark_weights;
 
 typedef struct quark_ctx quark_ctx;

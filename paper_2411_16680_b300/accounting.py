@@ -39,6 +39,12 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
                 c["flops"] += 2 * 3 * C * C * L * Hp * Wp
                 c["launches"] += 1
         texels = V * (img_h // k) * (img_w // k)
+        if getattr(cfg, "ray_encoding", 0):
+            # gamma_k: the level read and written once more (the coarse encoding is negligible)
+            k0 = max(cfg.levels())
+            out["attend"]["bytes"] += 2 * texels * C * elt
+            out["attend"]["flops"] += 2 * V * (img_h // k0) * (img_w // k0) * 32 * C + 2 * 4 * texels * C
+            out["attend"]["launches"] += 2
         if getattr(cfg, "attn_mode", 0) == 1:
             # standard: keys / values (and the features on the last step) projected once per texel
             # (written, then read by the sampling), per element q = x W^q, q_i . k_i and p v_i per

@@ -181,6 +181,7 @@ quark_status qk_validate_config(const quark_config* c) {
         return qk_fail(nullptr, QUARK_EINVAL, "unknown precision %d", c->precision);
     if (c->attn_mode != QUARK_ATTN_ONE_TO_MANY && c->attn_mode != QUARK_ATTN_STANDARD)
         return qk_fail(nullptr, QUARK_EINVAL, "unknown attention mode %d", c->attn_mode);
+    if (c->ray_encoding != 0 && c->ray_encoding != 1) return qk_fail(nullptr, QUARK_EINVAL, "ray_encoding must be 0 or 1");
     if (c->attn_mode == QUARK_ATTN_STANDARD && c->C % c->heads)
         return qk_fail(nullptr, QUARK_EINVAL, "standard attention needs C divisible by heads");
     return QUARK_OK;
@@ -243,6 +244,8 @@ static void pack_conv_weights_bf16(const float* w, int C, uint16_t* dst) {
                 dst[(size_t)tap * C * C + (ci / 8) * C * 8 + co * 8 + ci % 8] =
                     to_bf16_bits(w[((size_t)tap * C + ci) * C + co]);
 }
+
+static int level_index(int k) { return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3; }
 
 extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* w) {
     if (!ctx || !w) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
@@ -335,6 +338,17 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             put(w->col_b1[j], C);
             put(w->col_w2[j], (size_t)C * C);
             put(w->col_b2[j], C);
+            pad4();
+        }
+    }
+    for (int i = 0; i < 4; ++i) ctx->off_ray[i] = (size_t)-1;
+    if (c.ray_encoding) {
+        for (int j = 0; j < c.n_scales; ++j) {
+            const int li = level_index(c.k[j]);
+            if (ctx->off_ray[li] != (size_t)-1) continue;
+            if (!need(w->W_ray[li], "W_ray")) return QUARK_EINVAL;
+            ctx->off_ray[li] = blob.size();
+            put(w->W_ray[li], 32 * (size_t)C);
             pad4();
         }
     }
@@ -443,6 +457,29 @@ quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, con
 }
 
 // A = K_m R_m R_t^T K_t^-1 and b = K_m (t_m - R_m R_t^T t_t), both grids scaled by 1/k.
+// Ray of view pixel (x + 0.5, y + 0.5) on the view's k0-coarser grid in target-camera coordinates:
+// direction A p with A = R_t R_m^T K_{m,k0}^-1, origin b = R_t c_m + t_t (c_m = -R_m^T t_m).
+ViewMap qk_ray_map(const quark_camera& tgt, const quark_camera& view, double k0) {
+    const double Kinv[9] = {k0 / view.fx, 0, -view.cx / view.fx, 0, k0 / view.fy, -view.cy / view.fy, 0, 0, 1};
+    double Rrel[9] = {0}, A[9] = {0}, cm[3] = {0}, b[3] = {0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int q = 0; q < 3; ++q) Rrel[3 * i + j] += tgt.R[3 * i + q] * view.R[3 * j + q];  // R_t R_m^T
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int q = 0; q < 3; ++q) A[3 * i + j] += Rrel[3 * i + q] * Kinv[3 * q + j];
+    for (int i = 0; i < 3; ++i)
+        for (int q = 0; q < 3; ++q) cm[i] -= view.R[3 * q + i] * view.t[q];  // -R_m^T t_m
+    for (int i = 0; i < 3; ++i) {
+        b[i] = tgt.t[i];
+        for (int q = 0; q < 3; ++q) b[i] += tgt.R[3 * i + q] * cm[q];
+    }
+    ViewMap m;
+    for (int i = 0; i < 9; ++i) m.A[i] = (float)A[i];
+    for (int i = 0; i < 3; ++i) m.b[i] = (float)b[i];
+    return m;
+}
+
 ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m) {
     double Kt_inv[9] = {k_t / tgt.fx, 0, -tgt.cx / tgt.fx, 0, k_t / tgt.fy, -tgt.cy / tgt.fy, 0, 0, 1};
     double Km[9] = {view.fx / k_m, 0, view.cx / k_m, 0, view.fy / k_m, view.cy / k_m, 0, 0, 1};
@@ -500,7 +537,6 @@ extern "C" quark_status quark_release_pyramid(quark_pyramid* pyr) {
     return QUARK_OK;
 }
 
-static int level_index(int k) { return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3; }
 
 extern "C" quark_status quark_pyramid_read(const quark_pyramid* pyr, int k, void* dst, size_t bytes) {
     if (!pyr || !dst) return qk_fail(nullptr, QUARK_EINVAL, "NULL argument");
@@ -803,6 +839,41 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
     aa.err = ctx->dev_err;
     for (int m = 0; m < V_use; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
+    if (c.ray_encoding) {
+        // gamma_k (Sec. 3.2.1) added to this level of the first V_use views, into LDM scratch
+        int k0 = 1;
+        for (int j = 0; j < c.n_scales; ++j) k0 = std::max(k0, c.k[j]);
+        RayArgs ra{};
+        ra.V = V_use;
+        ra.C = c.C;
+        ra.h0 = pyr->H / k0;
+        ra.w0 = pyr->W / k0;
+        ra.h = aa.fh;
+        ra.w = aa.fw;
+        ra.ratio = k0 / k;
+        ra.span = (float)(1.0 / c.near_m - 1.0 / c.far_m);
+        ra.w_ray = ctx->wdev + ctx->off_ray[level_index(k)];
+        for (int m = 0; m < V_use; ++m) ra.geo.v[m] = qk_ray_map(ldm->target, pyr->cams[m], k0);
+        const size_t gbytes = (size_t)V_use * ra.h0 * ra.w0 * c.C * sizeof(float);
+        const size_t fbytes = (size_t)V_use * ra.h * ra.w * c.C * (bf16 ? 2 : 4);
+        if (ldm->ray_g_bytes < gbytes) {
+            s = qk_ldm_scratch(ldm, (void**)&ldm->ray_g, gbytes);
+            if (s != QUARK_OK) return s;
+            ldm->ray_g_bytes = gbytes;
+        }
+        if (ldm->ray_feat_bytes < fbytes) {
+            s = qk_ldm_scratch(ldm, &ldm->ray_feat, fbytes);
+            if (s != QUARK_OK) return s;
+            ldm->ray_feat_bytes = fbytes;
+        }
+        ra.g = ldm->ray_g;
+        const void* level = aa.feat;
+        s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_ray_coarse(ra, st); });
+        if (s == QUARK_OK)
+            s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_ray_add(ra, level, ldm->ray_feat, bf16, st); });
+        if (s != QUARK_OK) return s;
+        aa.feat = ldm->ray_feat;
+    }
     if (c.attn_mode == QUARK_ATTN_STANDARD) {
         // keys and values (and on the last step the features) projected in image space, then sampled
         const size_t texels = (size_t)V_use * aa.fh * aa.fw;

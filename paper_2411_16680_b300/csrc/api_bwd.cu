@@ -19,6 +19,7 @@ static quark_status check_stage(quark_ctx* ctx, const quark_pyramid* pyr, const 
     if (ctx->cfg.precision != QUARK_FP32) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage is FP32 only");
     if (ctx->cfg.attn_mode != QUARK_ATTN_ONE_TO_MANY)
         return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage covers one-to-many attention");
+    if (ctx->cfg.ray_encoding) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage runs without the ray encoding");
     if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     return QUARK_OK;
@@ -29,6 +30,7 @@ extern "C" quark_status quark_step_input(quark_ctx* ctx, quark_ldm* ldm, int sca
     const quark_config& c = ctx->cfg;
     if (c.precision != QUARK_FP32) return qk_fail(ctx, QUARK_EINVAL, "FP32 form only");
     if (c.attn_mode != QUARK_ATTN_ONE_TO_MANY) return qk_fail(ctx, QUARK_EINVAL, "one-to-many attention only");
+    if (c.ray_encoding) return qk_fail(ctx, QUARK_EINVAL, "no ray encoding in the differentiable stage");
     if (scale < 1 || scale >= c.n_scales || ldm->done != scale - 1)
         return qk_fail(ctx, QUARK_EINVAL, "step %d's input needs step %d done (latest: %d)", scale, scale - 1, ldm->done);
     cudaSetDevice(ctx->device);

@@ -31,6 +31,7 @@ struct quark_ctx {
     size_t off_conv[QUARK_MAX_SCALES] = {};
     size_t off_collapse[QUARK_MAX_SCALES] = {};
     size_t off_std[QUARK_MAX_SCALES] = {};  // standard attention weights (StdLayout), or (size_t)-1
+    size_t off_ray[4] = {};                   // ray encoding projection per level index, or (size_t)-1
     // BF16 form: conv weights packed as tcgen05 B operands, per step W1 then W2
     void* wtc = nullptr;
     size_t wtc_bytes = 0;
@@ -90,6 +91,10 @@ struct quark_ldm {
     size_t beta_bytes = 0;
     void* kv = nullptr;  // standard attention: the projected keys / values of the step's level
     size_t kv_bytes = 0;
+    float* ray_g = nullptr;  // ray encoding: the projected coarse encoding of the step's level
+    size_t ray_g_bytes = 0;
+    void* ray_feat = nullptr;  // ray encoding: the step's level plus gamma_k
+    size_t ray_feat_bytes = 0;
     void* out = nullptr;  // device staging of a host render target
     size_t out_bytes = 0;
     size_t last_e = 0;
@@ -107,6 +112,7 @@ quark_status qk_launch(quark_ctx* ctx, cudaStream_t st, KernelFamily fam, const 
 quark_status qk_validate_config(const quark_config* c);
 quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what);
 quark::ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m);
+quark::ViewMap qk_ray_map(const quark_camera& tgt, const quark_camera& view, double k0);
 size_t qk_ldm_bytes(const quark_config& c, int width, int height, int V, bool host_out);
 quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_beta, cudaStream_t async_stream,
                            quark_ldm** out);

@@ -52,6 +52,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     if (pyr->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "pyramid from another context");
     if (ctx->cfg.attn_mode != QUARK_ATTN_ONE_TO_MANY)
         return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs one-to-many attention only (use quark_update_fuse)");
+    if (ctx->cfg.ray_encoding)
+        return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs without the ray encoding (use quark_update_fuse)");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     const quark_config& c = ctx->cfg;
     if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);

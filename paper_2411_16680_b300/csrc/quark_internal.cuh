@@ -87,6 +87,17 @@ struct DecodeArgs {
     float* s_raw;      // [H][W][L]
 };
 
+// Ray directional encoding of one step's pyramid level (Sec. 3.2.1).
+struct RayArgs {
+    int V, C;
+    int h0, w0;          // the coarsest level's grid (factor k0)
+    int h, w, ratio;     // this level's grid and k0 / k
+    float span;          // 1/near - 1/far
+    const float* w_ray;  // [32][C] projection of this level
+    float* g;            // [V][h0][w0][C] projected coarse encoding
+    Geometry geo;        // per view: A = R_t R_m^T K_{m,k0}^-1 (ray direction map), b = centre (target coords)
+};
+
 struct RenderArgs {
     const float* t_raw;  // [Hl][Wl][L]
     const float* s_raw;  // [Hl][Wl][L]
@@ -157,6 +168,8 @@ cudaError_t launch_kv_project(const void* feat, size_t texels, int C, const floa
 cudaError_t launch_attend_std(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                               cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
+cudaError_t launch_ray_coarse(const RayArgs& a, cudaStream_t st);
+cudaError_t launch_ray_add(const RayArgs& a, const void* feat, void* out, bool bf16, cudaStream_t st);
 cudaError_t launch_render_depth(const RenderArgs& a, float* depth, cudaStream_t st);
 
 }  // namespace quark

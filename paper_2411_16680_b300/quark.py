@@ -38,7 +38,8 @@ class Camera(ct.Structure):
 class Config(ct.Structure):
     _fields_ = [("C", ct.c_int), ("heads", ct.c_int), ("n_scales", ct.c_int), ("k", ct.c_int * MAX_SCALES),
                 ("L", ct.c_int * MAX_SCALES), ("near_m", ct.c_float), ("far_m", ct.c_float),
-                ("precision", ct.c_int), ("attn_mode", ct.c_int), ("hbm_cap_bytes", ct.c_size_t)]
+                ("precision", ct.c_int), ("attn_mode", ct.c_int), ("ray_encoding", ct.c_int),
+                ("hbm_cap_bytes", ct.c_size_t)]
 
 
 _FP = ct.POINTER(ct.c_float)
@@ -51,7 +52,8 @@ class Weights(ct.Structure):
                 ("col_w1", _PER), ("col_b1", _PER), ("col_w2", _PER), ("col_b2", _PER),
                 ("w_d", _FP), ("b_d", ct.c_float), ("w_sigma", _FP), ("b_sigma", ct.c_float),
                 ("W_a", _FP), ("b_a", _FP), ("W_beta", _FP),
-                ("Wq_std", _PER), ("Wk_std", _PER), ("Wv_std", _PER), ("Wo_std", _PER)]
+                ("Wq_std", _PER), ("Wk_std", _PER), ("Wv_std", _PER), ("Wo_std", _PER),
+                ("W_ray", _FP * 4)]
 
 
 class ServeConfig(ct.Structure):
@@ -174,6 +176,7 @@ def make_config(cfg, hbm_cap_bytes: int = 0) -> Config:
     c.near_m, c.far_m = cfg.near, cfg.far
     c.precision = cfg.precision
     c.attn_mode = cfg.attn_mode
+    c.ray_encoding = getattr(cfg, "ray_encoding", 0)
     c.hbm_cap_bytes = hbm_cap_bytes
     return c
 
@@ -287,6 +290,9 @@ class Context:
                 w.Wq_std[j], w.Wk_std[j] = p(f"Wq_std_{j}"), p(f"Wk_std_{j}")
                 w.Wv_std[j], w.Wo_std[j] = p(f"Wv_std_{j}"), p(f"Wo_std_{j}")
         w.w_d, w.w_sigma, w.W_a, w.b_a, w.W_beta = p("w_d"), p("w_sigma"), p("W_a"), p("b_a"), p("W_beta")
+        for i, k in enumerate((1, 2, 4, 8)):
+            if f"W_ray_{k}" in W:
+                w.W_ray[i] = p(f"W_ray_{k}")
         w.b_d = float(np.asarray(W["b_d"]).reshape(-1)[0])
         w.b_sigma = float(np.asarray(W["b_sigma"]).reshape(-1)[0])
         _check(lib().quark_load_weights(self.handle, ct.byref(w)), self.handle)
