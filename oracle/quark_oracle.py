@@ -394,8 +394,10 @@ class StepResult:
 def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
                      rect_attn: Rect, rect_out: Rect, last: bool, mode: int = 0) -> StepResult:
     f64 = lambda a: np.asarray(a, np.float64)
-    k, L = cfg.scales[j]
-    H, Wd = cfg.out_h // k, cfg.out_w // k
+    k, L = cfg.scales[j]          # pyramid level of the views, layers
+    f = cfg.f_of(j)               # LDM grid factor relative to the output
+    _, H, Wd = cfg.ldm_shape(j)
+    heads = cfg.heads_of(j)
     C = cfg.C
     ys = np.arange(rect_attn[0], rect_attn[1])[:, None]
     xs = np.arange(rect_attn[2], rect_attn[3])[None, :]
@@ -407,32 +409,44 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
         V_in = np.broadcast_to(f64(W["v0"]), (L, h, w, C)).copy()
         d = np.broadcast_to(1.0 / ((ell - 0.5) / L * (1 / cfg.near - 1 / cfg.far) + 1 / cfg.far), (L, h, w)).copy()
     else:
-        kp, Lp = cfg.scales[j - 1]
+        Lp, Hp, Wp = cfg.ldm_shape(j - 1)
         Vp, rp = prev.V_out, prev.rect_out
         if Lp == 2 * L:
             Vp = layer_collapse(Vp, f64(W[f"col_w1_{j}"]), f64(W[f"col_b1_{j}"]),
                                 f64(W[f"col_w2_{j}"]), f64(W[f"col_b2_{j}"]))
         else:
             assert Lp == L
-        ratio = kp // k
-        V_in = resize_rect(Vp, rp, cfg.out_h // kp, cfg.out_w // kp, ratio, rect_attn)
-        t_in = V_in @ f64(W["w_d"]) + f64(W["b_d"])[0]
-        d = depth_activation(t_in, ell, L, cfg.near, cfg.far)
+        ratio = int(round(cfg.f_of(j - 1) / f))
+        V_in = resize_rect(Vp, rp, Hp, Wp, ratio, rect_attn)
+        if cfg.reuse_of(j) or heads == 0:
+            # the depths of the latest scale that sampled (same grid and layers): reused for the
+            # sampling, or carried through a block without attention
+            assert ratio == 1 and Lp == L
+            oy, ox = rect_attn[0] - prev.rect_attn[0], rect_attn[2] - prev.rect_attn[2]
+            d = prev.depth_used[:, oy:oy + h, ox:ox + w]
+        else:
+            t_in = V_in @ f64(W["w_d"]) + f64(W["b_d"])[0]
+            d = depth_activation(t_in, ell, L, cfg.near, cfg.far)
 
-    # ---- back-project the views' level-k features at the current depths ----
-    Delta = sample_views(fetchers[k], scene.cams, scene.target, k, k, d, ys, xs)  # [L,h,w,V,C]
-
-    # ---- fusion block: one-to-many attention ----
-    x = rmsnorm(V_in, f64(W[f"attn_g_{j}"]))
-    if mode == 0:
-        upd, _ = one_to_many_attention(x, Delta, f64(W[f"Wq_{j}"]), f64(W[f"Wo_{j}"]), cfg.heads)
+    if heads == 0:
+        # a fusion block without attention (its residual CNN block only)
+        Delta, x, V_attn = None, None, V_in
     else:
-        upd = standard_attention(x, Delta, f64(W[f"Wq_std_{j}"]), f64(W[f"Wk_std_{j}"]),
-                                 f64(W[f"Wv_std_{j}"]), f64(W[f"Wo_std_{j}"]), cfg.heads)
-    V_attn = V_in + upd
+        # ---- back-project the views' level-k features at the current depths ----
+        Delta = sample_views(fetchers[k], scene.cams, scene.target, f, k, d, ys, xs)  # [L,h,w,V,C]
+
+        # ---- fusion block: one-to-many attention ----
+        x = rmsnorm(V_in, f64(W[f"attn_g_{j}"]))
+        if mode == 0:
+            upd, _ = one_to_many_attention(x, Delta, f64(W[f"Wq_{j}"]), f64(W[f"Wo_{j}"]), heads)
+        else:
+            upd = standard_attention(x, Delta, f64(W[f"Wq_std_{j}"]), f64(W[f"Wk_std_{j}"]),
+                                     f64(W[f"Wv_std_{j}"]), f64(W[f"Wo_std_{j}"]), heads)
+        V_attn = V_in + upd
 
     beta = None
     if last:
+        assert heads > 0, "the blend logits come from the last block's attention"
         qb = x @ f64(W["W_beta"])
         beta = np.einsum("...c,...mc->...m", qb, Delta) / math.sqrt(C)
 
@@ -459,9 +473,8 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
 
 def render_rect(cfg, scene, last: StepResult, out_rect: Rect, return_layers: bool = False):
     """RGBA of the novel view on out_rect (full output resolution)."""
-    k, L = cfg.scales[-1]
-    Hl, Wl = cfg.out_h // k, cfg.out_w // k
-    s = k
+    L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
+    s = cfg.upsample_s
     rect_beta = last.rect_attn
     ob = (last.rect_out[0] - rect_beta[0], last.rect_out[2] - rect_beta[2])
     hb, wb = last.V_out.shape[1], last.V_out.shape[2]
@@ -508,10 +521,10 @@ def render_depth_rect(cfg, last: StepResult, out_rect: Rect):
     last LDM are upsampled and activated exactly as for the colour render; then, front (l = L) to
     back, D += T alpha_l d_l and T *= 1 - alpha_l, with 0 behind the last layer.  Reading: the
     over-composite itself, not normalised by the accumulated alpha."""
-    k, L = cfg.scales[-1]
-    Hl, Wl = cfg.out_h // k, cfg.out_w // k
-    t_up = resize_rect(last.t[..., None], last.rect_out, Hl, Wl, k, out_rect)[..., 0]
-    s_up = resize_rect(last.s[..., None], last.rect_out, Hl, Wl, k, out_rect)[..., 0]
+    L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
+    s = cfg.upsample_s
+    t_up = resize_rect(last.t[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
+    s_up = resize_rect(last.s[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
     ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
     d = depth_activation(t_up, ell, L, cfg.near, cfg.far)
     alpha = sigmoid(s_up)
@@ -540,24 +553,22 @@ def over_back_to_front(col, alpha):
 def plan_rects(cfg, out_rect: Rect):
     """Windows each scale must compute so that out_rect of the final render is exact."""
     n = cfg.n_scales
-    k, L = cfg.scales[-1]
-    Hl, Wl = cfg.out_h // k, cfg.out_w // k
+    _, Hl, Wl = cfg.ldm_shape(n - 1)
+    s = cfg.upsample_s
     ys = np.arange(out_rect[0], out_rect[1])
     xs = np.arange(out_rect[2], out_rect[3])
-    y0, y1, _ = resize_taps(ys, k, Hl)
-    x0, x1, _ = resize_taps(xs, k, Wl)
+    y0, y1, _ = resize_taps(ys, s, Hl)
+    x0, x1, _ = resize_taps(xs, s, Wl)
     need = (int(y0.min()), int(y1.max()) + 1, int(x0.min()), int(x1.max()) + 1)
     rect_out = [None] * n
     rect_attn = [None] * n
     for j in range(n - 1, -1, -1):
-        kj, _ = cfg.scales[j]
-        H, W = cfg.out_h // kj, cfg.out_w // kj
+        _, H, W = cfg.ldm_shape(j)
         rect_out[j] = need
         rect_attn[j] = grow(need, 2, H, W)
         if j > 0:
-            kp, _ = cfg.scales[j - 1]
-            ratio = kp // kj
-            Hp, Wp = cfg.out_h // kp, cfg.out_w // kp
+            ratio = int(round(cfg.f_of(j - 1) / cfg.f_of(j)))
+            _, Hp, Wp = cfg.ldm_shape(j - 1)
             ys = np.arange(rect_attn[j][0], rect_attn[j][1])
             xs = np.arange(rect_attn[j][2], rect_attn[j][3])
             a0, a1, _ = resize_taps(ys, ratio, Hp)

@@ -36,10 +36,19 @@ PREC_BF16 = 1
 class QuarkConfig:
     """Shape of one Quark network instance.
 
-    scales: list of (k, L) from coarse to fine.  Scale j uses pyramid level k_j and an LDM
-    of L_j layers on a grid of (out_h / k_j, out_w / k_j) pixels.  Consecutive scales have
-    k_{j-1} / k_j in {1, 2} and L_{j-1} / L_j in {1, 2} (layer collapse, Sec. 3.2).
-    The final render upsamples the last scale by s = k_last (Sec. 3.2.3, factor s).
+    scales: list of (k, L) from coarse to fine.  Scale j uses pyramid level k_j (relative to
+    the input views) and an LDM of L_j layers on a grid of (out_h / f_j, out_w / f_j) pixels,
+    f_j = k_j unless ldm_f gives it.  Consecutive scales have f_{j-1} / f_j and k_{j-1} / k_j in
+    {1, 2} and L_{j-1} / L_j in {1, 2} (layer collapse, Sec. 3.2).  The final render upsamples
+    the last scale by s = f_last (Sec. 3.2.3, factor s).
+
+    Per-scale options of the full model schedule (the paper's model tables), None = defaults:
+      scale_heads  attention heads of each scale's fusion block; 0 = a block with no attention
+                   (the second residual CNN block of an "A, C, C" group)
+      ldm_f        LDM grid factor of each scale relative to the output (e.g. 30, 15, 7.5, 3.75)
+      reuse_depth  1 = the scale samples the views at the depths of the latest scale that
+                   sampled (one set of update features Delta per Update & Fuse step, fused by
+                   several blocks)
     """
 
     C: int = 16
@@ -52,18 +61,33 @@ class QuarkConfig:
     attn_mode: int = ATTN_ONE_TO_MANY
     precision: int = PREC_FP32
     ray_encoding: int = 0  # 1: add the ray directional encoding gamma_k to the sampled features
+    scale_heads: Optional[List[int]] = None
+    ldm_f: Optional[List[float]] = None
+    reuse_depth: Optional[List[int]] = None
 
     @property
     def n_scales(self) -> int:
         return len(self.scales)
 
+    def heads_of(self, j: int) -> int:
+        return self.heads if self.scale_heads is None else int(self.scale_heads[j])
+
+    def f_of(self, j: int) -> float:
+        return float(self.scales[j][0]) if self.ldm_f is None else float(self.ldm_f[j])
+
+    def reuse_of(self, j: int) -> int:
+        return 0 if self.reuse_depth is None else int(self.reuse_depth[j])
+
     @property
-    def upsample_s(self) -> int:
-        return self.scales[-1][0]
+    def upsample_s(self) -> float:
+        return self.f_of(self.n_scales - 1)
 
     def ldm_shape(self, j: int) -> Tuple[int, int, int]:
-        k, L = self.scales[j]
-        return L, self.out_h // k, self.out_w // k
+        L = self.scales[j][1]
+        f = self.f_of(j)
+        H, W = int(round(self.out_h / f)), int(round(self.out_w / f))
+        assert abs(H * f - self.out_h) < 1e-6 and abs(W * f - self.out_w) < 1e-6, "output not divisible by f"
+        return L, H, W
 
     def levels(self) -> List[int]:
         return sorted({k for k, _ in self.scales})
@@ -350,16 +374,19 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
     W_beta (C, C): blend-weight query projection of the final block (Sec. 3.2.3)
     W_ray_k (32, C) per pyramid level k used: projection of the ray directional encoding (Sec. 3.2.1)
     """
-    C, h = cfg.C, cfg.heads
+    C = cfg.C
     s = {"enc_w": (3, 3, 3, C), "enc_b": (C,), "v0": (C,)}
     for j in range(cfg.n_scales):
+        h = cfg.heads_of(j)
+        if h > 0:
+            s.update({f"attn_g_{j}": (C,), f"Wq_{j}": (C, h * C), f"Wo_{j}": (h * C, C)})
         s.update({
-            f"attn_g_{j}": (C,), f"Wq_{j}": (C, h * C), f"Wo_{j}": (h * C, C),
             f"conv_g_{j}": (C,), f"conv1_w_{j}": (3, 3, C, C), f"conv1_b_{j}": (C,),
             f"conv2_w_{j}": (3, 3, C, C), f"conv2_b_{j}": (C,),
             f"col_w1_{j}": (2 * C, C), f"col_b1_{j}": (C,), f"col_w2_{j}": (C, C), f"col_b2_{j}": (C,),
-            f"Wq_std_{j}": (C, C), f"Wk_std_{j}": (C, C), f"Wv_std_{j}": (C, C), f"Wo_std_{j}": (C, C),
         })
+        if h > 0:
+            s.update({f"Wq_std_{j}": (C, C), f"Wk_std_{j}": (C, C), f"Wv_std_{j}": (C, C), f"Wo_std_{j}": (C, C)})
     s.update({"w_d": (C,), "b_d": (1,), "w_sigma": (C,), "b_sigma": (1,), "W_a": (C, 3), "b_a": (3,),
               "W_beta": (C, C)})
     for k in cfg.levels():

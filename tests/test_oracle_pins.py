@@ -595,3 +595,78 @@ def test_ray_encoding_off_or_zero_weights_leaves_the_pipeline():
         W0[f"W_ray_{k}"] = np.zeros_like(W[f"W_ray_{k}"])
     np.testing.assert_allclose(O.forward(cfg, W0, sc)[0], base, atol=1e-14)
     assert np.abs(O.forward(cfg, W, sc)[0] - base).max() > 1e-3
+
+
+# --------------------------------------------------------------------------------------------
+# Model schedules: per-scale heads, blocks without attention, one Delta per step, grid factors
+# --------------------------------------------------------------------------------------------
+
+def _schedule_cfg(**kw):
+    # views 48 x 80 (levels 1, 2, 4, 8); output 45 x 120; LDM factors 15, 7.5, 3.75
+    base = dict(C=8, heads=2, scales=[(8, 4), (8, 4), (8, 4), (4, 4), (4, 4), (2, 2), (2, 2)], near=1.0, far=30.0,
+                out_h=45, out_w=120, ldm_f=[15, 15, 15, 7.5, 7.5, 3.75, 3.75],
+                scale_heads=[4, 0, 4, 4, 0, 2, 1], reuse_depth=[0, 0, 1, 0, 0, 0, 1])
+    base.update(kw)
+    return synth.QuarkConfig(**base)
+
+
+def _schedule_scene():
+    sc = synth.scene_raycast(V=3, W=80, H=48, f=60, arc=0.3)
+    tgt = sc.target
+    target = synth.Camera(120, 45, tgt.fx * 1.5, tgt.fx * 1.5, 60.0, 22.5, tgt.R, tgt.t)
+    return synth.Scene(sc.images, sc.cams, target)
+
+
+def test_schedule_grids_and_weights():
+    cfg = _schedule_cfg()
+    assert [cfg.ldm_shape(j) for j in range(cfg.n_scales)] == [(4, 3, 8)] * 3 + [(4, 6, 16)] * 2 + [(2, 12, 32)] * 2
+    assert cfg.upsample_s == 3.75
+    W = synth.make_weights(cfg)
+    assert "Wq_1" not in W and "Wq_4" not in W and W["Wq_0"].shape == (8, 32) and W["Wq_6"].shape == (8, 8)
+
+
+def test_schedule_one_delta_per_step_and_blocks_without_attention():
+    """A block without attention leaves V_attn = V_in and carries the depths; a reusing block
+    samples exactly the Delta of the step's first block (same depths, same features)."""
+    cfg = _schedule_cfg()
+    W = synth.make_weights(cfg, sharp=True)
+    sc = _schedule_scene()
+    _, steps = O.forward(cfg, W, sc)
+    assert steps[1].Delta is None
+    np.testing.assert_array_equal(steps[1].V_attn, steps[1].V_in)
+    r0, r1 = steps[0].rect_attn, steps[1].rect_attn
+    h1, w1 = steps[1].depth_used.shape[1:]
+    np.testing.assert_array_equal(steps[1].depth_used,
+                                  steps[0].depth_used[:, r1[0] - r0[0]:r1[0] - r0[0] + h1, r1[2] - r0[2]:r1[2] - r0[2] + w1])
+    # scale 2 reuses: its Delta equals the one a fresh sampling at scale 0's depths gives
+    cfg_fresh = _schedule_cfg(reuse_depth=[0] * 7)
+    _, fresh = O.forward(cfg_fresh, W, sc)
+    assert not np.allclose(steps[2].Delta, fresh[2].Delta)  # the refined volume moved the depths
+    d0 = steps[0].depth_used
+    r2 = steps[2].rect_attn
+    oy, ox = r2[0] - r0[0], r2[2] - r0[2]
+    h2, w2 = steps[2].depth_used.shape[1:]
+    np.testing.assert_array_equal(steps[2].depth_used, d0[:, oy:oy + h2, ox:ox + w2])
+
+
+def test_schedule_with_default_options_is_the_plain_pipeline():
+    """Explicit per-scale options equal to the defaults reproduce the default pipeline bit for bit."""
+    cfg = synth.QuarkConfig(C=8, heads=2, scales=[(4, 8), (2, 4), (2, 2), (1, 2)], near=1, far=50, out_h=48,
+                            out_w=64)
+    W = synth.make_weights(cfg, sharp=True)
+    sc = synth.scene_raycast(V=3, W=64, H=48, f=50, arc=0.3)
+    a, _ = O.forward(cfg, W, sc)
+    cfg2 = cfg.replace(scale_heads=[2] * 4, ldm_f=[4, 2, 2, 1], reuse_depth=[0] * 4)
+    b, _ = O.forward(cfg2, W, sc)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_schedule_fractional_grid_render_is_windowed_exactly():
+    """Windows of the output through a 3.75x final upsample equal the full frame."""
+    cfg = _schedule_cfg()
+    W = synth.make_weights(cfg, sharp=True)
+    sc = _schedule_scene()
+    full, _ = O.forward(cfg, W, sc)
+    for rect in [(0, 7, 0, 11), (20, 33, 50, 77), (44, 45, 0, 120)]:
+        part, _ = O.forward(cfg, W, sc, rect)
+        np.testing.assert_allclose(part, full[rect[0]:rect[1], rect[2]:rect[3]], atol=1e-13)
