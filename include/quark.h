@@ -44,7 +44,7 @@ typedef enum {
     QUARK_EINTERNAL = 8
 } quark_status;
 
-#define QUARK_MAX_SCALES 8
+#define QUARK_MAX_SCALES 32
 #define QUARK_MAX_VIEWS 64
 
 enum { QUARK_FP32 = 0, QUARK_BF16 = 1 };             /* storage / tensor-core precision form */
@@ -63,10 +63,12 @@ typedef struct {
  *   C          channels of features, pyramid and feature volume: 16 or 32
  *   heads      attention heads h: 1, 2 or 4 (one-to-many: per-head width C, appendix A;
  *              standard: per-head width C/h)
- *   n_scales   number of Update & Fuse steps, 1..8
+ *   n_scales   number of fusion steps j, 1..32 (one per fusion block of the model tables)
  *   k[j], L[j] pyramid factor and LDM layer count of step j, coarse to fine.  k in {1,2,4,8};
- *              k[j-1]/k[j] in {1,2} (x2 spatial upsample); L[j-1]/L[j] in {1,2} (layer
- *              collapse, Sec. 3.2.2); L <= 64.  The final render upsamples by s = k[n-1].
+ *              k[j-1]/k[j] in {1,2}; L[j-1]/L[j] in {1,2} (layer collapse, Sec. 3.2.2);
+ *              L <= 64.  Step j's LDM grid is (target height / f_j, target width / f_j) with
+ *              f_j = ldm_f[j], or k[j] where ldm_f[j] is 0; f[j-1]/f[j] in {1,2} (x2 spatial
+ *              upsample).  The final render upsamples by s = f of the last step (e.g. 3.75).
  *   near_m, far_m  near and far planes eta and f of Eq. (depth_activation), 0 < near < far
  *   precision  QUARK_FP32 (all storage and arithmetic FP32) or QUARK_BF16 (pyramid and
  *              feature volume stored in BF16, contractions on tensor cores with FP32
@@ -85,7 +87,19 @@ typedef struct {
  *              (32 values) on the coarsest level, bilinearly upsampled to level k and projected
  *              to C channels by W_ray of that level.  Needs the W_ray weights; not with
  *              quark_update_fuse_noalloc nor the differentiable stage.  0: off.
- *   hbm_cap_bytes  cap on this context's device allocations (0 = no cap)              */
+ *   hbm_cap_bytes  cap on this context's device allocations (0 = no cap)
+ * Full model schedule (Sec. 3.2; tables "Model description for Quark / Quark+": an Update &
+ * Fuse step back-projects its update features once and runs several fusion blocks, each an
+ * attention block A_h followed by residual CNN blocks C).  Each fusion step j here is one
+ * A_h + C pair or one further C; zero-filled arrays give the uniform schedule above.
+ *   scale_heads[j]  0: `heads`; 1, 2 or 4: this step's heads; -1: a block without attention
+ *              (the conv block only: same grid and layers as step j-1, j > 0)
+ *   ldm_f[j]   LDM grid factor relative to the target (0: k[j]); the target's width and height
+ *              must be multiples of it (e.g. 30, 15, 7.5, 3.75 for 1920 x 1080)
+ *   reuse_depth[j]  1: sample the views at the depths the latest sampling step used instead of
+ *              the depths decoded from this step's input (one set of update features per Update
+ *              & Fuse step); needs the same grid and layers back to that step.  0: decode.
+ * quark_update_fuse_noalloc and the differentiable stage take the uniform schedule only.     */
 typedef struct {
     int C, heads, n_scales;
     int k[QUARK_MAX_SCALES];
@@ -94,6 +108,9 @@ typedef struct {
     int precision;
     int attn_mode;
     int ray_encoding;
+    int scale_heads[QUARK_MAX_SCALES];
+    float ldm_f[QUARK_MAX_SCALES];
+    int reuse_depth[QUARK_MAX_SCALES];
     size_t hbm_cap_bytes;
 } quark_config;
 
@@ -101,8 +118,9 @@ typedef struct {
  * quark_load_weights; the caller keeps ownership.  Shapes for C channels and h heads:
  *   enc_w [3][3][3][C] (dy, dx, c_in, c_out), enc_b [C]   encoder conv (Sec. 3.2.1)
  *   v0 [C]                                              learned initial feature (Sec. 3.2.2)
- *   per step j:
+ *   per step j (h = that step's heads):
  *     attn_g[j] [C], Wq[j] [C][h*C], Wo[j] [h*C][C]      RMSNorm gain, one-to-many attention
+ *                                                       (NULL for a block without attention)
  *     conv_g[j] [C], conv1_w[j], conv2_w[j] [3][3][C][C], conv1_b[j], conv2_b[j] [C]
  *                                                       residual conv block (Sec. 3.3)
  *     col_w1[j] [2C][C], col_b1[j] [C], col_w2[j] [C][C], col_b2[j] [C]
@@ -176,15 +194,16 @@ quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images, const qua
 
 /* Allocate an LDM (feature volume, decoded attributes and blend logits for every step)
  * in the frustum of the novel view `target` (Sec. 3.1).  target->width/height is the
- * output resolution and must be divisible by every k. */
+ * output resolution and must be divisible by every step's grid factor f. */
 quark_status quark_ldm_create(quark_ctx* ctx, const quark_camera* target, quark_ldm** out);
 
 /* One Update & Fuse step (Sec. 3.2.2, Fig. "Update & Fuse Step"; Sec. 3.3), step `scale`
  * (steps run in order 0..n_scales-1 on one LDM):
  *   transition   step 0: broadcast v0, layers flat at the depth anchors; step j > 0: layer
- *                collapse when L halves, then x2 bilinear upsample when k halves
- *   back-project decode depth (Eq. depth_activation), unproject each LDM pixel x layer,
- *                reproject into every view, bilinearly sample its level-k features (zero pad)
+ *                collapse when L halves, then x2 bilinear upsample when f halves
+ *   back-project decode depth (Eq. depth_activation; or the reused depths), unproject each LDM
+ *                pixel x layer, reproject into every view, bilinearly sample its level-k
+ *                features (zero pad); skipped with the attention by a block without attention
  *   fusion block V += MultiHead(N(V), Delta) (one-to-many, Sec. 3.3), then
  *                V += Conv(gelu(Conv(N(V)))) (3x3 per layer plane)
  *   decode       colour = sigmoid(V W_a + b_a), alpha = sigmoid(V w_sigma + b_sigma),

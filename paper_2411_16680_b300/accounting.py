@@ -12,7 +12,7 @@ from typing import Dict
 
 
 def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, float]]:
-    C, h = cfg.C, cfg.heads
+    C = cfg.C
     elt = 2 if cfg.precision == 1 else 4
     out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "launches": 0}
                                         for k in ("encode", "collapse", "attend", "conv_block", "render")}
@@ -24,21 +24,32 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
     e["flops"] += 2 * 27 * C * V * img_h * img_w
     e["launches"] += 1
     for j, (k, L) in enumerate(cfg.scales):
-        H, W = cfg.out_h // k, cfg.out_w // k
+        _, H, W = cfg.ldm_shape(j)
         E = L * H * W
+        h = cfg.heads_of(j)
         last = j == cfg.n_scales - 1
         a = out["attend"]
         vin = 0
         if j > 0:
-            kp, Lp = cfg.scales[j - 1]
-            Hp, Wp = cfg.out_h // kp, cfg.out_w // kp
+            Lp, Hp, Wp = cfg.ldm_shape(j - 1)
             vin = L * Hp * Wp * C * elt
             if Lp == 2 * L:
                 c = out["collapse"]
                 c["bytes"] += (Lp + L) * Hp * Wp * C * elt
                 c["flops"] += 2 * 3 * C * C * L * Hp * Wp
                 c["launches"] += 1
+        cb = out["conv_block"]
+        cb["bytes"] += 2 * E * C * elt + (2 * E * 4 if last else 0)  # V in and out; raw logits of the last step
+        cb["flops"] += 2 * (18 * C * C + 5 * C) * E
+        cb["launches"] += 1
+        if h == 0:
+            continue  # a block without attention: its conv block only
         texels = V * (img_h // k) * (img_w // k)
+        # the sampled depths: read by a block that reuses them, written for the next sampling block
+        # when that one reuses them
+        nxt = next((i for i in range(j + 1, cfg.n_scales) if cfg.heads_of(i)), None)
+        writes = nxt is not None and cfg.reuse_of(nxt) and not cfg.reuse_of(j)
+        a["bytes"] += E * 4 * (int(bool(cfg.reuse_of(j))) + int(bool(writes)))
         if getattr(cfg, "ray_encoding", 0):
             # gamma_k: the level read and written once more (the coarse encoding is negligible)
             k0 = max(cfg.levels())
@@ -58,12 +69,7 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
             macs = 2 * h * C * C + 2 * V * h * C + 4 * V * C + (C * C + V * C if last else 0)
             a["flops"] += 2 * macs * E
             a["launches"] += 1
-        cb = out["conv_block"]
-        cb["bytes"] += 2 * E * C * elt + E * 7 * 4
-        cb["flops"] += 2 * (18 * C * C + 5 * C) * E
-        cb["launches"] += 1
-    k, L = cfg.scales[-1]
-    Hl, Wl = cfg.out_h // k, cfg.out_w // k
+    L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
     r = out["render"]
     r["bytes"] += L * Hl * Wl * (2 + V) * 4 + V * img_h * img_w * 16 + cfg.out_h * cfg.out_w * 16
     r["flops"] += 2 * cfg.out_h * cfg.out_w * L * V * 16

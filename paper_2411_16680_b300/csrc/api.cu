@@ -1,5 +1,6 @@
 // C ABI of the library (include/quark.h): contexts, validation, weight packing, handles and
 // the per-step launch sequence.  Host code only; the compute is in the k_*.cu kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -158,6 +159,29 @@ extern "C" int quark_kernel_times(quark_ctx* ctx, const char** names, double* ms
 
 static bool is_pow2_factor(int k) { return k == 1 || k == 2 || k == 4 || k == 8; }
 
+int qk_heads(const quark_config& c, int j) {
+    const int h = c.scale_heads[j];
+    return h == 0 ? c.heads : h < 0 ? 0 : h;
+}
+
+double qk_f(const quark_config& c, int j) { return c.ldm_f[j] > 0.f ? (double)c.ldm_f[j] : (double)c.k[j]; }
+
+bool qk_uniform(const quark_config& c) {
+    for (int j = 0; j < QUARK_MAX_SCALES; ++j)
+        if (c.scale_heads[j] != 0 || c.ldm_f[j] != 0.f || c.reuse_depth[j] != 0) return false;
+    return true;
+}
+
+bool qk_grid(const quark_config& c, int j, int width, int height, int& H, int& W) {
+    const double f = qk_f(c, j);
+    H = (int)std::lround(height / f);
+    W = (int)std::lround(width / f);
+    return H >= 1 && W >= 1 && std::fabs(H * f - height) < 1e-3 && std::fabs(W * f - width) < 1e-3;
+}
+
+// a == 2 b (x2 upsample) or a == b, for grid factors given as float
+static bool same_f(double a, double b) { return std::fabs(a - b) <= 1e-6 * b; }
+
 quark_status qk_validate_config(const quark_config* c) {
     if (!c) return qk_fail(nullptr, QUARK_EINVAL, "NULL config");
     if (c->C != 16 && c->C != 32) return qk_fail(nullptr, QUARK_EINVAL, "C must be 16 or 32 (got %d)", c->C);
@@ -165,16 +189,44 @@ quark_status qk_validate_config(const quark_config* c) {
         return qk_fail(nullptr, QUARK_EINVAL, "heads must be 1, 2 or 4 (got %d)", c->heads);
     if (c->n_scales < 1 || c->n_scales > QUARK_MAX_SCALES)
         return qk_fail(nullptr, QUARK_EINVAL, "n_scales must be 1..%d", QUARK_MAX_SCALES);
+    for (int j = 0; j < QUARK_MAX_SCALES; ++j) {
+        const int h = c->scale_heads[j];
+        if (h != 0 && h != -1 && h != 1 && h != 2 && h != 4)
+            return qk_fail(nullptr, QUARK_EINVAL, "scale_heads[%d] must be 0, -1, 1, 2 or 4 (got %d)", j, h);
+        if (!(c->ldm_f[j] >= 0.f) || !std::isfinite(c->ldm_f[j]))
+            return qk_fail(nullptr, QUARK_EINVAL, "ldm_f[%d] must be finite and >= 0", j);
+        if (c->reuse_depth[j] != 0 && c->reuse_depth[j] != 1)
+            return qk_fail(nullptr, QUARK_EINVAL, "reuse_depth[%d] must be 0 or 1", j);
+        if (j >= c->n_scales && (h != 0 || c->ldm_f[j] != 0.f || c->reuse_depth[j] != 0))
+            return qk_fail(nullptr, QUARK_EINVAL, "schedule fields set beyond n_scales (step %d)", j);
+    }
+    int sampled = -1;  // latest step that sampled the views
     for (int j = 0; j < c->n_scales; ++j) {
         if (!is_pow2_factor(c->k[j])) return qk_fail(nullptr, QUARK_EINVAL, "k[%d] must be 1, 2, 4 or 8", j);
         if (c->L[j] < 1 || c->L[j] > 64) return qk_fail(nullptr, QUARK_EINVAL, "L[%d] must be 1..64", j);
+        const int h = qk_heads(*c, j);
         if (j > 0) {
             if (c->k[j - 1] != c->k[j] && c->k[j - 1] != 2 * c->k[j])
                 return qk_fail(nullptr, QUARK_EINVAL, "k[%d]/k[%d] must be 1 or 2", j - 1, j);
             if (c->L[j - 1] != c->L[j] && c->L[j - 1] != 2 * c->L[j])
                 return qk_fail(nullptr, QUARK_EINVAL, "L[%d]/L[%d] must be 1 or 2", j - 1, j);
+            const double fp = qk_f(*c, j - 1), f = qk_f(*c, j);
+            if (!same_f(fp, f) && !same_f(fp, 2 * f))
+                return qk_fail(nullptr, QUARK_EINVAL, "grid factor ratio f[%d]/f[%d] must be 1 or 2", j - 1, j);
+            if ((h == 0 || c->reuse_depth[j]) && (!same_f(fp, f) || c->L[j - 1] != c->L[j]))
+                return qk_fail(nullptr, QUARK_EINVAL,
+                               "step %d (no attention or reused depths) needs the grid and layers of step %d", j, j - 1);
+        } else if (h == 0 || c->reuse_depth[0]) {
+            return qk_fail(nullptr, QUARK_EINVAL, "step 0 must attend and decode its depths");
         }
+        if (c->reuse_depth[j] && sampled < 0)
+            return qk_fail(nullptr, QUARK_EINVAL, "step %d reuses depths but no step sampled before it", j);
+        if (h > 0) sampled = j;
+        if (c->attn_mode == QUARK_ATTN_STANDARD && h > 0 && c->C % h)
+            return qk_fail(nullptr, QUARK_EINVAL, "standard attention needs C divisible by heads (step %d)", j);
     }
+    if (qk_heads(*c, c->n_scales - 1) == 0)
+        return qk_fail(nullptr, QUARK_EINVAL, "the last step must attend (its attention gives the blend logits)");
     if (!(c->near_m > 0.f) || !(c->far_m > c->near_m) || !std::isfinite(c->far_m))
         return qk_fail(nullptr, QUARK_EINVAL, "need 0 < near < far < inf");
     if (c->precision != QUARK_FP32 && c->precision != QUARK_BF16)
@@ -182,8 +234,6 @@ quark_status qk_validate_config(const quark_config* c) {
     if (c->attn_mode != QUARK_ATTN_ONE_TO_MANY && c->attn_mode != QUARK_ATTN_STANDARD)
         return qk_fail(nullptr, QUARK_EINVAL, "unknown attention mode %d", c->attn_mode);
     if (c->ray_encoding != 0 && c->ray_encoding != 1) return qk_fail(nullptr, QUARK_EINVAL, "ray_encoding must be 0 or 1");
-    if (c->attn_mode == QUARK_ATTN_STANDARD && c->C % c->heads)
-        return qk_fail(nullptr, QUARK_EINVAL, "standard attention needs C divisible by heads");
     return QUARK_OK;
 }
 
@@ -251,7 +301,7 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     if (!ctx || !w) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     cudaSetDevice(ctx->device);
     const quark_config& c = ctx->cfg;
-    const int C = c.C, h = c.heads;
+    const int C = c.C;
     auto need = [&](const void* p, const char* name) -> bool {
         if (!p) {
             qk_fail(ctx, QUARK_EINVAL, "weight %s is NULL", name);
@@ -275,23 +325,28 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     put(w->enc_b, C);
     pad4();
     for (int j = 0; j < c.n_scales; ++j) {
-        if (!need(w->attn_g[j], "attn_g") || !need(w->Wq[j], "Wq") || !need(w->Wo[j], "Wo") ||
-            !need(w->conv_g[j], "conv_g") || !need(w->conv1_w[j], "conv1_w") || !need(w->conv1_b[j], "conv1_b") ||
+        const int h = qk_heads(c, j);
+        if (!need(w->conv_g[j], "conv_g") || !need(w->conv1_w[j], "conv1_w") || !need(w->conv1_b[j], "conv1_b") ||
             !need(w->conv2_w[j], "conv2_w") || !need(w->conv2_b[j], "conv2_b"))
             return QUARK_EINVAL;
-        // attend block: v0, g, w_d, b_d (padded to C), Wq, Wo, W_beta
-        const AttendLayout al{C, h};
-        ctx->off_attend[j] = blob.size();
-        put(w->v0, C);
-        put(w->attn_g[j], C);
-        put(w->w_d, C);
-        blob.push_back(w->b_d);
-        for (int i = 1; i < C; ++i) blob.push_back(0.f);
-        put(w->Wq[j], (size_t)C * h * C);
-        put(w->Wo[j], (size_t)h * C * C);
-        put(w->W_beta, (size_t)C * C);
-        if (blob.size() - ctx->off_attend[j] != (size_t)al.total()) return qk_fail(ctx, QUARK_EINTERNAL, "attend layout");
-        pad4();
+        ctx->off_attend[j] = (size_t)-1;
+        if (h > 0) {
+            if (!need(w->attn_g[j], "attn_g") || !need(w->Wq[j], "Wq") || !need(w->Wo[j], "Wo")) return QUARK_EINVAL;
+            // attend block: v0, g, w_d, b_d (padded to C), Wq, Wo, W_beta
+            const AttendLayout al{C, h};
+            ctx->off_attend[j] = blob.size();
+            put(w->v0, C);
+            put(w->attn_g[j], C);
+            put(w->w_d, C);
+            blob.push_back(w->b_d);
+            for (int i = 1; i < C; ++i) blob.push_back(0.f);
+            put(w->Wq[j], (size_t)C * h * C);
+            put(w->Wo[j], (size_t)h * C * C);
+            put(w->W_beta, (size_t)C * C);
+            if (blob.size() - ctx->off_attend[j] != (size_t)al.total())
+                return qk_fail(ctx, QUARK_EINTERNAL, "attend layout");
+            pad4();
+        }
         // conv block: g, W1, b1, W2, b2, w_d, w_s, W_a, b_a, b_d, b_s (+3 pad)
         const ConvLayout cl{C};
         ctx->off_conv[j] = blob.size();
@@ -312,7 +367,7 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         if (blob.size() - ctx->off_conv[j] != (size_t)cl.total()) return qk_fail(ctx, QUARK_EINTERNAL, "conv layout");
         pad4();
         ctx->off_std[j] = (size_t)-1;
-        if (c.attn_mode == QUARK_ATTN_STANDARD) {
+        if (c.attn_mode == QUARK_ATTN_STANDARD && h > 0) {
             if (!need(w->Wq_std[j], "Wq_std") || !need(w->Wk_std[j], "Wk_std") || !need(w->Wv_std[j], "Wv_std") ||
                 !need(w->Wo_std[j], "Wo_std"))
                 return QUARK_EINVAL;
@@ -345,7 +400,7 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     if (c.ray_encoding) {
         for (int j = 0; j < c.n_scales; ++j) {
             const int li = level_index(c.k[j]);
-            if (ctx->off_ray[li] != (size_t)-1) continue;
+            if (qk_heads(c, j) == 0 || ctx->off_ray[li] != (size_t)-1) continue;
             if (!need(w->W_ray[li], "W_ray")) return QUARK_EINVAL;
             ctx->off_ray[li] = blob.size();
             put(w->W_ray[li], 32 * (size_t)C);
@@ -371,22 +426,31 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         // attention: B_q rows n < hC from Wq[k][n], rows hC.. from W_beta[k][n - hC] (K = C);
         // B_o rows n < C from Wo[k][n] (K = hC); element (n, k) at (k / 8) * N * 8 + n * 8 + k % 8
         // layer collapse of the step (when it has one), after B_o: B_1 rows n < C from col_w1[k][n]
-        // (K = 2C), then B_2 from col_w2[k][n] (K = C), same element order
-        const int NQ = h * C + C;
-        const size_t att_elems = (size_t)NQ * C + (size_t)C * h * C;
-        ctx->wat_step_bytes = (att_elems + 3 * (size_t)C * C) * sizeof(uint16_t);
-        std::vector<uint16_t> at(ctx->wat_step_bytes / sizeof(uint16_t) * c.n_scales);
+        // (K = 2C), then B_2 from col_w2[k][n] (K = C), same element order.  Every step's block
+        // is a multiple of 16 bytes (C is 16 or 32).
+        size_t total = 0;
         for (int j = 0; j < c.n_scales; ++j) {
-            uint16_t* bq = at.data() + (size_t)j * (ctx->wat_step_bytes / sizeof(uint16_t));
+            const int h = qk_heads(c, j);
+            ctx->off_wat[j] = total;
+            total += (h > 0 ? (size_t)(h * C + C) * C + (size_t)C * h * C : 0) +
+                     (ctx->off_collapse[j] != (size_t)-1 ? 3 * (size_t)C * C : 0);
+        }
+        std::vector<uint16_t> at(std::max<size_t>(total, 8));
+        for (int j = 0; j < c.n_scales; ++j) {
+            const int h = qk_heads(c, j), NQ = h * C + C;
+            uint16_t* bq = at.data() + ctx->off_wat[j];
             uint16_t* bo = bq + (size_t)NQ * C;
-            for (int n = 0; n < NQ; ++n)
-                for (int k = 0; k < C; ++k) {
-                    float v = n < h * C ? w->Wq[j][(size_t)k * h * C + n] : w->W_beta[(size_t)k * C + (n - h * C)];
-                    bq[(size_t)(k / 8) * NQ * 8 + n * 8 + k % 8] = to_bf16_bits(v);
-                }
-            for (int n = 0; n < C; ++n)
-                for (int k = 0; k < h * C; ++k)
-                    bo[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->Wo[j][(size_t)k * C + n]);
+            const size_t att_elems = h > 0 ? (size_t)NQ * C + (size_t)C * h * C : 0;
+            if (h > 0) {
+                for (int n = 0; n < NQ; ++n)
+                    for (int k = 0; k < C; ++k) {
+                        float v = n < h * C ? w->Wq[j][(size_t)k * h * C + n] : w->W_beta[(size_t)k * C + (n - h * C)];
+                        bq[(size_t)(k / 8) * NQ * 8 + n * 8 + k % 8] = to_bf16_bits(v);
+                    }
+                for (int n = 0; n < C; ++n)
+                    for (int k = 0; k < h * C; ++k)
+                        bo[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->Wo[j][(size_t)k * C + n]);
+            }
             if (ctx->off_collapse[j] != (size_t)-1) {
                 uint16_t* b1 = bq + att_elems;
                 uint16_t* b2 = b1 + 2 * (size_t)C * C;
@@ -398,6 +462,7 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
                 }
             }
         }
+        for (int j = 0; j < c.n_scales; ++j) ctx->off_wat[j] *= sizeof(uint16_t);
         qk_free(ctx, ctx->wat, ctx->wat_bytes);
         ctx->wat = nullptr;
         ctx->wat_bytes = at.size() * sizeof(uint16_t);
@@ -667,21 +732,37 @@ static quark_status ldm_buf(quark_ldm* l, void** p, size_t bytes) {
     return s;
 }
 
-// Bytes an LDM for `target` holds (three volumes, collapse buffer, decoded attributes, blend
-// logits for V views, and a host-output staging buffer when host_out).
-size_t qk_ldm_bytes(const quark_config& c, int width, int height, int V, bool host_out) {
+// Buffer sizes of an LDM for a width x height target: the largest volume, collapse input and
+// element count over the steps, the last step's element count, and whether a step reuses depths.
+struct LdmSizes {
+    size_t vmax = 0, cmax = 0, emax = 0, last_e = 0;
+    bool reuse = false;
+};
+static LdmSizes ldm_sizes(const quark_config& c, int width, int height) {
     const size_t elt = c.precision == QUARK_BF16 ? 2 : 4;
-    size_t vmax = 0, emax = 0, cmax = 0;
+    LdmSizes z;
     for (int j = 0; j < c.n_scales; ++j) {
-        size_t e = (size_t)c.L[j] * (height / c.k[j]) * (width / c.k[j]);
-        emax = std::max(emax, e);
-        vmax = std::max(vmax, e * c.C * elt);
-        if (j > 0 && c.L[j - 1] == 2 * c.L[j])
-            cmax = std::max(cmax, (size_t)c.L[j] * (height / c.k[j - 1]) * (width / c.k[j - 1]) * c.C * elt);
+        int H, W;
+        qk_grid(c, j, width, height, H, W);
+        const size_t e = (size_t)c.L[j] * H * W;
+        z.emax = std::max(z.emax, e);
+        z.vmax = std::max(z.vmax, e * c.C * elt);
+        if (j > 0 && c.L[j - 1] == 2 * c.L[j]) {
+            int Hp, Wp;
+            qk_grid(c, j - 1, width, height, Hp, Wp);
+            z.cmax = std::max(z.cmax, (size_t)c.L[j] * Hp * Wp * c.C * elt);
+        }
+        z.reuse = z.reuse || c.reuse_depth[j];
+        z.last_e = e;
     }
-    const int n = c.n_scales - 1;
-    const size_t last_e = (size_t)c.L[n] * (height / c.k[n]) * (width / c.k[n]);
-    return 3 * vmax + cmax + emax * 7 * sizeof(float) + last_e * V * sizeof(float) +
+    return z;
+}
+
+// Bytes an LDM for `target` holds (three volumes, collapse buffer, decoded attributes, reused
+// depths, blend logits for V views, and a host-output staging buffer when host_out).
+size_t qk_ldm_bytes(const quark_config& c, int width, int height, int V, bool host_out) {
+    const LdmSizes z = ldm_sizes(c, width, height);
+    return 3 * z.vmax + z.cmax + z.emax * (z.reuse ? 8 : 7) * sizeof(float) + z.last_e * V * sizeof(float) +
            (host_out ? (size_t)width * height * 16 : 0);
 }
 
@@ -699,26 +780,23 @@ quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_bet
     quark_status s = qk_validate_camera(ctx, *target, "target");
     if (s != QUARK_OK) return s;
     const quark_config& c = ctx->cfg;
+    int Hs[QUARK_MAX_SCALES], Ws[QUARK_MAX_SCALES];
     for (int j = 0; j < c.n_scales; ++j)
-        if (target->height % c.k[j] || target->width % c.k[j])
-            return qk_fail(ctx, QUARK_EINVAL, "output %dx%d not divisible by k=%d", target->width, target->height, c.k[j]);
+        if (!qk_grid(c, j, target->width, target->height, Hs[j], Ws[j]))
+            return qk_fail(ctx, QUARK_EINVAL, "output %dx%d not divisible by the grid factor %g of step %d", target->width,
+                           target->height, qk_f(c, j), j);
     cudaSetDevice(ctx->device);
     quark_ldm* l = new quark_ldm();
     l->ctx = ctx;
     l->target = *target;
     l->async = async_stream != nullptr;
     l->stream = async_stream;
-    const size_t elt = c.precision == QUARK_BF16 ? 2 : 4;
-    size_t vmax = 0, emax = 0, cmax = 0;
     for (int j = 0; j < c.n_scales; ++j) {
-        size_t e = (size_t)c.L[j] * (target->height / c.k[j]) * (target->width / c.k[j]);
-        emax = std::max(emax, e);
-        vmax = std::max(vmax, e * c.C * elt);
-        if (j > 0 && c.L[j - 1] == 2 * c.L[j])
-            cmax = std::max(cmax, (size_t)c.L[j] * (target->height / c.k[j - 1]) * (target->width / c.k[j - 1]) * c.C * elt);
+        l->Hs[j] = Hs[j];
+        l->Ws[j] = Ws[j];
     }
-    const int n = c.n_scales - 1;
-    const size_t last_e = (size_t)c.L[n] * (target->height / c.k[n]) * (target->width / c.k[n]);
+    const LdmSizes z = ldm_sizes(c, target->width, target->height);
+    const size_t vmax = z.vmax, cmax = z.cmax, emax = z.emax, last_e = z.last_e;
     s = ldm_buf(l, &l->vol[0], vmax);
     if (s == QUARK_OK) s = ldm_buf(l, &l->vol[1], vmax);
     if (s == QUARK_OK) s = ldm_buf(l, &l->vattn, vmax);
@@ -728,6 +806,7 @@ quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_bet
     if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->depth, emax * sizeof(float));
     if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->t_raw, emax * sizeof(float));
     if (s == QUARK_OK) s = ldm_buf(l, (void**)&l->s_raw, emax * sizeof(float));
+    if (s == QUARK_OK && z.reuse) s = ldm_buf(l, (void**)&l->dsamp, emax * sizeof(float));
     l->last_e = last_e;
     if (s == QUARK_OK && V_beta > 0) {
         s = ldm_buf(l, (void**)&l->beta, last_e * V_beta * sizeof(float));
@@ -742,16 +821,22 @@ quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_bet
 }
 
 static void step_dims(const quark_ldm* l, int j, int& L, int& H, int& W) {
-    const quark_config& c = l->ctx->cfg;
-    L = c.L[j];
-    H = l->target.height / c.k[j];
-    W = l->target.width / c.k[j];
+    L = l->ctx->cfg.L[j];
+    H = l->Hs[j];
+    W = l->Ws[j];
 }
 
 extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int scale, quark_ldm* ldm,
                                           void* stream) {
     if (!pyr) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     return qk_update_fuse(ctx, pyr, pyr->V, scale, ldm, (cudaStream_t)stream);
+}
+
+// Whether the next step after `j` that samples the views reuses the depths step j samples at.
+static bool next_reuses(const quark_config& c, int j) {
+    for (int i = j + 1; i < c.n_scales; ++i)
+        if (qk_heads(c, i) > 0) return c.reuse_depth[i] != 0;
+    return false;
 }
 
 // One Update & Fuse step using the first V_use views of the pyramid.
@@ -771,6 +856,7 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     int L, H, W;
     step_dims(ldm, scale, L, H, W);
     const int k = c.k[scale];
+    const int heads = qk_heads(c, scale);
     quark_status s;
 
     if (last) {
@@ -817,93 +903,98 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
             if (s != QUARK_OK) return s;
             prev = ldm->collapsed;
         }
-        tr = (c.k[scale - 1] == 2 * k) ? TR_UP2 : TR_SAME;
+        tr = same_f(qk_f(c, scale - 1), qk_f(c, scale)) ? TR_SAME : TR_UP2;
     }
 
     // ---- sample-attend ----
-    AttendArgs aa{};
-    aa.prev = prev;
-    aa.Hp = Hp;
-    aa.Wp = Wp;
-    aa.feat = feat_override ? feat_override : pyr->level[level_index(k)];
-    aa.fh = pyr->H / k;
-    aa.fw = pyr->W / k;
-    aa.L = L;
-    aa.H = H;
-    aa.W = W;
-    aa.V = V_use;
-    aa.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
-    aa.w = ctx->wdev + ctx->off_attend[scale];
-    aa.out = ldm->vattn;
-    aa.beta = last ? ldm->beta : nullptr;
-    aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
-    aa.err = ctx->dev_err;
-    for (int m = 0; m < V_use; ++m) aa.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
-    if (c.ray_encoding) {
-        // gamma_k (Sec. 3.2.1) added to this level of the first V_use views, into LDM scratch
-        int k0 = 1;
-        for (int j = 0; j < c.n_scales; ++j) k0 = std::max(k0, c.k[j]);
-        RayArgs ra{};
-        ra.V = V_use;
-        ra.C = c.C;
-        ra.h0 = pyr->H / k0;
-        ra.w0 = pyr->W / k0;
-        ra.h = aa.fh;
-        ra.w = aa.fw;
-        ra.ratio = k0 / k;
-        ra.span = (float)(1.0 / c.near_m - 1.0 / c.far_m);
-        ra.w_ray = ctx->wdev + ctx->off_ray[level_index(k)];
-        for (int m = 0; m < V_use; ++m) ra.geo.v[m] = qk_ray_map(ldm->target, pyr->cams[m], k0);
-        const size_t gbytes = (size_t)V_use * ra.h0 * ra.w0 * c.C * sizeof(float);
-        const size_t fbytes = (size_t)V_use * ra.h * ra.w * c.C * (bf16 ? 2 : 4);
-        if (ldm->ray_g_bytes < gbytes) {
-            s = qk_ldm_scratch(ldm, (void**)&ldm->ray_g, gbytes);
+    if (heads > 0) {
+        AttendArgs aa{};
+        aa.prev = prev;
+        aa.Hp = Hp;
+        aa.Wp = Wp;
+        aa.feat = feat_override ? feat_override : pyr->level[level_index(k)];
+        aa.fh = pyr->H / k;
+        aa.fw = pyr->W / k;
+        aa.L = L;
+        aa.H = H;
+        aa.W = W;
+        aa.V = V_use;
+        aa.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+        aa.w = ctx->wdev + ctx->off_attend[scale];
+        aa.out = ldm->vattn;
+        aa.beta = last ? ldm->beta : nullptr;
+        aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + ctx->off_wat[scale] : nullptr;
+        aa.err = ctx->dev_err;
+        for (int m = 0; m < V_use; ++m) aa.geo.v[m] = qk_view_map(ldm->target, qk_f(c, scale), pyr->cams[m], k);
+        // reused depths (Update & Fuse steps with several fusion blocks sample once)
+        aa.depth_in = c.reuse_depth[scale] ? ldm->dsamp : nullptr;
+        aa.depth_out = !c.reuse_depth[scale] && next_reuses(c, scale) ? ldm->dsamp : nullptr;
+        if (c.ray_encoding) {
+            // gamma_k (Sec. 3.2.1) added to this level of the first V_use views, into LDM scratch
+            int k0 = 1;
+            for (int j = 0; j < c.n_scales; ++j) k0 = std::max(k0, c.k[j]);
+            RayArgs ra{};
+            ra.V = V_use;
+            ra.C = c.C;
+            ra.h0 = pyr->H / k0;
+            ra.w0 = pyr->W / k0;
+            ra.h = aa.fh;
+            ra.w = aa.fw;
+            ra.ratio = k0 / k;
+            ra.span = (float)(1.0 / c.near_m - 1.0 / c.far_m);
+            ra.w_ray = ctx->wdev + ctx->off_ray[level_index(k)];
+            for (int m = 0; m < V_use; ++m) ra.geo.v[m] = qk_ray_map(ldm->target, pyr->cams[m], k0);
+            const size_t gbytes = (size_t)V_use * ra.h0 * ra.w0 * c.C * sizeof(float);
+            const size_t fbytes = (size_t)V_use * ra.h * ra.w * c.C * (bf16 ? 2 : 4);
+            if (ldm->ray_g_bytes < gbytes) {
+                s = qk_ldm_scratch(ldm, (void**)&ldm->ray_g, gbytes);
+                if (s != QUARK_OK) return s;
+                ldm->ray_g_bytes = gbytes;
+            }
+            if (ldm->ray_feat_bytes < fbytes) {
+                s = qk_ldm_scratch(ldm, &ldm->ray_feat, fbytes);
+                if (s != QUARK_OK) return s;
+                ldm->ray_feat_bytes = fbytes;
+            }
+            ra.g = ldm->ray_g;
+            const void* level = aa.feat;
+            s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_ray_coarse(ra, st); });
+            if (s == QUARK_OK)
+                s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_ray_add(ra, level, ldm->ray_feat, bf16, st); });
             if (s != QUARK_OK) return s;
-            ldm->ray_g_bytes = gbytes;
+            aa.feat = ldm->ray_feat;
         }
-        if (ldm->ray_feat_bytes < fbytes) {
-            s = qk_ldm_scratch(ldm, &ldm->ray_feat, fbytes);
+        if (c.attn_mode == QUARK_ATTN_STANDARD) {
+            // keys and values (and on the last step the features) projected in image space, then sampled
+            const size_t texels = (size_t)V_use * aa.fh * aa.fw;
+            const size_t need = texels * (size_t)(last ? 3 : 2) * c.C * (bf16 ? 2 : 4);
+            if (ldm->kv_bytes < need) {
+                s = qk_ldm_scratch(ldm, &ldm->kv, need);
+                if (s != QUARK_OK) return s;
+                ldm->kv_bytes = need;
+            }
+            const float* wkv = ctx->wdev + ctx->off_std[scale] + StdLayout{c.C}.wkv();
+            const void* level = aa.feat;
+            s = qk_launch(ctx, st, KF_ATTEND,
+                          [&] { return launch_kv_project(level, texels, c.C, wkv, ldm->kv, last, bf16, st); });
             if (s != QUARK_OK) return s;
-            ldm->ray_feat_bytes = fbytes;
+            aa.feat = ldm->kv;
+            aa.w_std = ctx->wdev + ctx->off_std[scale];
+            s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend_std(aa, c.C, heads, tr, last, bf16, st); });
+        } else {
+            s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, heads, tr, last, bf16, st); });
         }
-        ra.g = ldm->ray_g;
-        const void* level = aa.feat;
-        s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_ray_coarse(ra, st); });
-        if (s == QUARK_OK)
-            s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_ray_add(ra, level, ldm->ray_feat, bf16, st); });
         if (s != QUARK_OK) return s;
-        aa.feat = ldm->ray_feat;
     }
-    if (c.attn_mode == QUARK_ATTN_STANDARD) {
-        // keys and values (and on the last step the features) projected in image space, then sampled
-        const size_t texels = (size_t)V_use * aa.fh * aa.fw;
-        const size_t need = texels * (size_t)(last ? 3 : 2) * c.C * (bf16 ? 2 : 4);
-        if (ldm->kv_bytes < need) {
-            s = qk_ldm_scratch(ldm, &ldm->kv, need);
-            if (s != QUARK_OK) return s;
-            ldm->kv_bytes = need;
-        }
-        const float* wkv = ctx->wdev + ctx->off_std[scale] + StdLayout{c.C}.wkv();
-        const void* level = aa.feat;
-        s = qk_launch(ctx, st, KF_ATTEND,
-                      [&] { return launch_kv_project(level, texels, c.C, wkv, ldm->kv, last, bf16, st); });
-        if (s != QUARK_OK) return s;
-        aa.feat = ldm->kv;
-        aa.w_std = ctx->wdev + ctx->off_std[scale];
-        s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend_std(aa, c.C, c.heads, tr, last, bf16, st); });
-    } else {
-        s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
-    }
-    if (s != QUARK_OK) return s;
 
     // ---- conv block + decode ----
     ConvArgs ca{};
-    ca.in = ldm->vattn;
+    ca.in = heads > 0 ? ldm->vattn : prev;  // a block without attention: the conv block on V_in
     ca.out = ldm->vol[1 - ldm->cur];
     ca.L = L;
     ca.H = H;
     ca.W = W;
-    ca.dp = aa.dp;
+    ca.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
     ca.w = ctx->wdev + ctx->off_conv[scale];
     // the raw depth / density logits are written here for the step that is rendered; every other
     // decoded attribute is produced on demand (qk_decode) when it is read
@@ -942,8 +1033,9 @@ quark_status qk_decode(quark_ctx* ctx, int scale, const void* vol, int L, int H,
 const void* qk_collapse_wtc(const quark_ctx* ctx, int scale) {
     if (!ctx->wat) return nullptr;
     const quark_config& c = ctx->cfg;
-    const size_t att_bytes = ((size_t)(c.heads * c.C + c.C) * c.C + (size_t)c.C * c.heads * c.C) * 2;
-    return (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes + att_bytes;
+    const int h = qk_heads(c, scale);
+    const size_t att_bytes = h > 0 ? ((size_t)(h * c.C + c.C) * c.C + (size_t)c.C * h * c.C) * 2 : 0;
+    return (const uint8_t*)ctx->wat + ctx->off_wat[scale] + att_bytes;
 }
 
 extern "C" quark_status quark_render_ldm(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr, float* rgba,
@@ -971,9 +1063,9 @@ quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid
     ra.rgba = (const float4*)pyr->rgba;
     ra.L = c.L[n];
     ra.V = V_use;
-    ra.Hl = l->target.height / c.k[n];
-    ra.Wl = l->target.width / c.k[n];
-    ra.s = c.k[n];
+    ra.Hl = l->Hs[n];
+    ra.Wl = l->Ws[n];
+    ra.s = (float)qk_f(c, n);
     ra.Hout = l->target.height;
     ra.Wout = l->target.width;
     ra.Hi = pyr->H;
@@ -1013,9 +1105,9 @@ extern "C" quark_status quark_render_depth(quark_ctx* ctx, const quark_ldm* ldm,
     ra.t_raw = l->t_raw;
     ra.s_raw = l->s_raw;
     ra.L = c.L[n];
-    ra.Hl = l->target.height / c.k[n];
-    ra.Wl = l->target.width / c.k[n];
-    ra.s = c.k[n];
+    ra.Hl = l->Hs[n];
+    ra.Wl = l->Ws[n];
+    ra.s = (float)qk_f(c, n);
     ra.Hout = l->target.height;
     ra.Wout = l->target.width;
     ra.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
@@ -1098,7 +1190,10 @@ extern "C" quark_status quark_ldm_read(quark_ldm* l, int field, void* dst, size_
     const void* src = nullptr;
     switch (field) {
         case QUARK_FIELD_VOLUME: src = l->vol[l->cur]; break;
-        case QUARK_FIELD_VOLUME_ATTN: src = l->vattn; break;
+        case QUARK_FIELD_VOLUME_ATTN:
+            // a block without attention leaves V_attn = V_in: the step's input, still in the other buffer
+            src = qk_heads(ctx->cfg, l->done) > 0 ? l->vattn : l->vol[1 - l->cur];
+            break;
         case QUARK_FIELD_COLOUR: src = l->colour; break;
         case QUARK_FIELD_ALPHA: src = l->alpha; break;
         case QUARK_FIELD_DEPTH: src = l->depth; break;

@@ -27,7 +27,7 @@ struct quark_ctx {
     size_t wbytes = 0;
     bool weights_loaded = false;
     size_t off_enc = 0;
-    size_t off_attend[QUARK_MAX_SCALES] = {};
+    size_t off_attend[QUARK_MAX_SCALES] = {};  // or (size_t)-1 for a block without attention
     size_t off_conv[QUARK_MAX_SCALES] = {};
     size_t off_collapse[QUARK_MAX_SCALES] = {};
     size_t off_std[QUARK_MAX_SCALES] = {};  // standard attention weights (StdLayout), or (size_t)-1
@@ -36,10 +36,11 @@ struct quark_ctx {
     void* wtc = nullptr;
     size_t wtc_bytes = 0;
     size_t wtc_step_bytes = 0;
-    // BF16 form: [Wq | W_beta] and W^O packed as tcgen05 B operands, per step
+    // BF16 form: [Wq | W_beta] and W^O (then the layer collapse's W1, W2) packed as tcgen05 B
+    // operands, per step at byte offset off_wat[j]
     void* wat = nullptr;
     size_t wat_bytes = 0;
-    size_t wat_step_bytes = 0;
+    size_t off_wat[QUARK_MAX_SCALES] = {};
     // device error word written by kernels whose bounded waits run out
     int* dev_err = nullptr;
     // device memory accounting against cfg.hbm_cap_bytes
@@ -89,6 +90,8 @@ struct quark_ldm {
     float* s_raw = nullptr;
     float* beta = nullptr;
     size_t beta_bytes = 0;
+    float* dsamp = nullptr;  // [L][H][W] depths of the latest sampling step, kept for reuse_depth
+    int Hs[QUARK_MAX_SCALES] = {}, Ws[QUARK_MAX_SCALES] = {};  // LDM grid of each step
     void* kv = nullptr;  // standard attention: the projected keys / values of the step's level
     size_t kv_bytes = 0;
     float* ray_g = nullptr;  // ray encoding: the projected coarse encoding of the step's level
@@ -110,6 +113,11 @@ quark_status qk_alloc(quark_ctx* ctx, void** p, size_t bytes);
 void qk_free(quark_ctx* ctx, void* p, size_t bytes);
 quark_status qk_launch(quark_ctx* ctx, cudaStream_t st, KernelFamily fam, const std::function<cudaError_t()>& fn);
 quark_status qk_validate_config(const quark_config* c);
+// Per-step schedule of a config (zero-filled fields = the uniform schedule).
+int qk_heads(const quark_config& c, int j);     // attention heads of step j, 0 = no attention
+double qk_f(const quark_config& c, int j);      // LDM grid factor of step j
+bool qk_uniform(const quark_config& c);         // no per-step heads, grid factors or reuse
+bool qk_grid(const quark_config& c, int j, int width, int height, int& H, int& W);  // false: not divisible
 quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what);
 quark::ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m);
 quark::ViewMap qk_ray_map(const quark_camera& tgt, const quark_camera& view, double k0);

@@ -169,9 +169,9 @@ __device__ __forceinline__ Taps4 bilinear_taps4(bool ok, float u, float v, int h
     return Taps4{ry0 + cx0, ry0 + cx1, ry1 + cx0, ry1 + cx1, gy0 * gx0, gy0 * gx1, gy1 * gx0, gy1 * gx1};
 }
 
-// Edge-clamped linear taps of a resize by integer `ratio` (pixel centres aligned):
+// Edge-clamped linear taps of a resize by `ratio` (pixel centres aligned; e.g. 2 or 3.75):
 // src = (dst + 0.5) / ratio - 0.5.
-__device__ __forceinline__ void resize_taps(int dst, int ratio, int n, int& i0, int& i1, float& w1) {
+__device__ __forceinline__ void resize_taps(int dst, float ratio, int n, int& i0, int& i1, float& w1) {
     float src = (dst + 0.5f) / ratio - 0.5f;
     float f = floorf(src);
     w1 = src - f;

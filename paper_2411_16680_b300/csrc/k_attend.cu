@@ -137,7 +137,7 @@ __device__ __forceinline__ void fma_tap16_x2(const __nv_bfloat16* p, float w, fl
 
 template <typename T, int C, int TR>
 __device__ __forceinline__ float volume_in(const AttendArgs& a, const float* sw, const AttendLayout& lay, int li, int y,
-                                           int x, size_t e, float (&vin)[C]) {
+                                           int x, size_t e, bool writer, float (&vin)[C]) {
     const int L = a.L;
     if (TR == TR_INIT) {
 #pragma unroll
@@ -186,7 +186,9 @@ __device__ __forceinline__ float volume_in(const AttendArgs& a, const float* sw,
         for (int c = 0; c < C; ++c) t = fmaf(vin[c], sw[lay.wd() + c], t);
         d = depth_from_logit(t, li, L, a.dp);
     }
-
+    // reused depths of an earlier step, or this step's depths kept for a later one
+    if (a.depth_in) d = __ldg(a.depth_in + e);
+    else if (a.depth_out && writer) a.depth_out[e] = d;
     return d;
 }
 
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_kernel(const AttendArgs a)
     const int c0 = sub * 16;
 
     float vin[C];
-    const float d = volume_in<T, C, TR>(a, sw, lay, li, y, x, e, vin);
+    const float d = volume_in<T, C, TR>(a, sw, lay, li, y, x, e, live && sub == 0, vin);
 
     // ---- RMSNorm and query projections ----
     float ms = 0.f;
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(ATT_THREADS) attend_std_kernel(const AttendArg
     const int c0 = sub * 16;
 
     float vin[C];
-    const float d = volume_in<T, C, TR>(a, sw, lay, li, y, x, e, vin);
+    const float d = volume_in<T, C, TR>(a, sw, lay, li, y, x, e, live && sub == 0, vin);
     float ms = 0.f;
 #pragma unroll
     for (int c = 0; c < C; ++c) ms = fmaf(vin[c], vin[c], ms);

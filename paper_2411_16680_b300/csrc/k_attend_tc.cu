@@ -175,8 +175,13 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         tpart += __shfl_xor_sync(0xffffffffu, tpart, off);
         ms += __shfl_xor_sync(0xffffffffu, ms, off);
     }
-    const float d = TR == TR_INIT ? depth_anchor(li, L, a.dp)
-                                  : depth_from_logit(misc[3 * C] + tpart, li, L, a.dp);
+    float d = TR == TR_INIT ? depth_anchor(li, L, a.dp) : depth_from_logit(misc[3 * C] + tpart, li, L, a.dp);
+    {
+        // reused depths of an earlier step, or this step's depths kept for a later one
+        const size_t de = ((size_t)li * H + yc) * W + xc;
+        if (a.depth_in) d = __ldg(a.depth_in + de);
+        else if (a.depth_out && live && sub == 0) a.depth_out[de] = d;
+    }
     const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
     {
         // this thread's 16 channels of X = N(V_in): two 8-channel groups, K-major A layout

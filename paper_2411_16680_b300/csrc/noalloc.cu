@@ -54,6 +54,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
         return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs one-to-many attention only (use quark_update_fuse)");
     if (ctx->cfg.ray_encoding)
         return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs without the ray encoding (use quark_update_fuse)");
+    if (!qk_uniform(ctx->cfg))
+        return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step takes the uniform schedule only (use quark_update_fuse)");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     const quark_config& c = ctx->cfg;
     if (scale < 0 || scale >= c.n_scales) return qk_fail(ctx, QUARK_EINVAL, "scale %d out of range", scale);
@@ -132,7 +134,7 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     aa.w = ctx->wdev + ctx->off_attend[scale];
     aa.out = vattn;
     aa.beta = last ? beta : nullptr;
-    aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + scale * ctx->wat_step_bytes : nullptr;
+    aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + ctx->off_wat[scale] : nullptr;
     aa.err = ctx->dev_err;
     for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(*target, k, pyr->cams[m], k);
     e = launch_attend(aa, c.C, c.heads, tr, last, bf16, st);

@@ -59,6 +59,8 @@ struct AttendArgs {
     const void* wtc;   // BF16 form: [Wq | W_beta] and W^O packed as tcgen05 B operands
     int* err;          // device error word (bounded waits)
     const float* w_std;  // standard mode: StdLayout (W^q, W^O); else NULL
+    const float* depth_in;  // [L][H][W] depths to sample at (reused from an earlier step), or NULL
+    float* depth_out;       // [L][H][W] the depths sampled at, kept for a later step, or NULL
     Geometry geo;
 };
 
@@ -103,7 +105,8 @@ struct RenderArgs {
     const float* s_raw;  // [Hl][Wl][L]
     const float* beta;   // [Hl][Wl][L][V]
     const float4* rgba;  // [V][Hi][Wi]
-    int L, V, Hl, Wl, s, Hout, Wout, Hi, Wi;
+    int L, V, Hl, Wl, Hout, Wout, Hi, Wi;
+    float s;             // upsampling factor of the last LDM grid to the output (e.g. 3.75)
     DepthParams dp;
     float4* out;         // [Hout][Wout]
     Geometry geo;

@@ -15,7 +15,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libquark.so")
 
-MAX_SCALES = 8
+MAX_SCALES = 32
 MAX_VIEWS = 64
 
 OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEDOUT, ENOTFOUND, EBUSY, EINTERNAL = range(9)
@@ -39,7 +39,8 @@ class Config(ct.Structure):
     _fields_ = [("C", ct.c_int), ("heads", ct.c_int), ("n_scales", ct.c_int), ("k", ct.c_int * MAX_SCALES),
                 ("L", ct.c_int * MAX_SCALES), ("near_m", ct.c_float), ("far_m", ct.c_float),
                 ("precision", ct.c_int), ("attn_mode", ct.c_int), ("ray_encoding", ct.c_int),
-                ("hbm_cap_bytes", ct.c_size_t)]
+                ("scale_heads", ct.c_int * MAX_SCALES), ("ldm_f", ct.c_float * MAX_SCALES),
+                ("reuse_depth", ct.c_int * MAX_SCALES), ("hbm_cap_bytes", ct.c_size_t)]
 
 
 _FP = ct.POINTER(ct.c_float)
@@ -177,6 +178,17 @@ def make_config(cfg, hbm_cap_bytes: int = 0) -> Config:
     c.precision = cfg.precision
     c.attn_mode = cfg.attn_mode
     c.ray_encoding = getattr(cfg, "ray_encoding", 0)
+    # model schedule: per-step heads (0 in the workload = a block without attention, -1 here),
+    # LDM grid factors and reused depths; unset = the uniform schedule (zero-filled)
+    if getattr(cfg, "scale_heads", None) is not None:
+        for j, h in enumerate(cfg.scale_heads):
+            c.scale_heads[j] = int(h) if int(h) > 0 else -1
+    if getattr(cfg, "ldm_f", None) is not None:
+        for j, f in enumerate(cfg.ldm_f):
+            c.ldm_f[j] = float(f)
+    if getattr(cfg, "reuse_depth", None) is not None:
+        for j, r in enumerate(cfg.reuse_depth):
+            c.reuse_depth[j] = int(r)
     c.hbm_cap_bytes = hbm_cap_bytes
     return c
 
@@ -280,7 +292,8 @@ class Context:
         w.enc_w, w.enc_b, w.v0 = p("enc_w"), p("enc_b"), p("v0")
         n = len(self.cfg.scales)
         for j in range(n):
-            w.attn_g[j], w.Wq[j], w.Wo[j] = p(f"attn_g_{j}"), p(f"Wq_{j}"), p(f"Wo_{j}")
+            if f"Wq_{j}" in W:  # absent for a block without attention
+                w.attn_g[j], w.Wq[j], w.Wo[j] = p(f"attn_g_{j}"), p(f"Wq_{j}"), p(f"Wo_{j}")
             w.conv_g[j], w.conv1_w[j], w.conv1_b[j] = p(f"conv_g_{j}"), p(f"conv1_w_{j}"), p(f"conv1_b_{j}")
             w.conv2_w[j], w.conv2_b[j] = p(f"conv2_w_{j}"), p(f"conv2_b_{j}")
             if f"col_w1_{j}" in W:

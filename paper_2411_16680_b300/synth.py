@@ -453,6 +453,41 @@ def scene_1080p(seed: int = 1234, V: int = 8, W: int = 1920, H: int = 1080) -> S
     return scene_raycast(seed=seed, V=V, W=W, H=H, f=1400.0 * W / 1920.0)
 
 
+def config_quark(out_w: int = 1920, out_h: int = 1080, C: int = 32) -> QuarkConfig:
+    """The paper's Quark model (appendix table "Model description for Quark"): an Initialize step
+    and five Update & Fuse steps, 24 fusion steps in all.  Per step: pyramid level k, layers L,
+    LDM grid factor f (36x64 -> 288x512 for a 1920x1080 output), the heads of each fusion block
+    and its residual CNN blocks.  A fusion block "A_h, C, C" is one step with attention and a
+    conv block, then one step with a conv block only; the first block of an Update & Fuse step
+    samples the views at the depths decoded from its input, the later blocks reuse them (one
+    set of update features per step).  The final render upsamples by s = 3.75."""
+    groups = [  # (k, L, f, heads of each fusion block, CNN blocks per fusion block)
+        (8, 24, 30.0, [4, 4, 4], 2),   # Initialize (flat layers at the depth anchors)
+        (8, 24, 30.0, [4, 4, 4], 2),   # Update & Fuse 0
+        (4, 24, 15.0, [4, 4, 4], 2),   # Update & Fuse 1 (x2 upsample)
+        (4, 24, 15.0, [4, 4], 1),      # Update & Fuse 2
+        (2, 12, 7.5, [2, 2], 1),       # Update & Fuse 3 (layer collapse, x2 upsample)
+        (1, 6, 3.75, [1, 1], 1),       # Update & Fuse 4 (layer collapse, x2 upsample)
+    ]
+    scales, f, heads, reuse = [], [], [], []
+    for k, L, ff, hs, n_cnn in groups:
+        for b, h in enumerate(hs):
+            for i in range(n_cnn):
+                scales.append((k, L))
+                f.append(ff)
+                heads.append(h if i == 0 else 0)
+                reuse.append(1 if i == 0 and b > 0 else 0)
+    return QuarkConfig(C=C, heads=4, scales=scales, near=1.0, far=100.0, out_h=out_h, out_w=out_w,
+                       scale_heads=heads, ldm_f=f, reuse_depth=reuse)
+
+
+def scene_quark(seed: int = 1234, V: int = 8, W: int = 480, H: int = 288, out_w: int = 1920,
+                out_h: int = 1080) -> Scene:
+    """Input views at the Quark table's resolution (480x288: a 36x60 level-8 feature map) and a
+    1920x1080 novel view covering the same frustum."""
+    return scene_raycast(seed=seed, V=V, W=W, H=H, f=350.0 * W / 480.0, out_w=out_w, out_h=out_h)
+
+
 def config_grad() -> QuarkConfig:
     """Differentiation workload: V=4 views 512x512, scales (2,16), (1,8), C=32, two heads."""
     return QuarkConfig(C=32, heads=2, scales=[(2, 16), (1, 8)], near=1.0, far=100.0, out_h=512, out_w=512)

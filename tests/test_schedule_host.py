@@ -1,0 +1,60 @@
+"""Model schedules on the host: the Quark workload follows the paper's model table (appendix,
+table "Model description for Quark"), and the C ABI rejects schedules its steps cannot run."""
+import pytest
+import torch
+
+from paper_2411_16680_b300 import quark, synth
+
+
+def test_quark_workload_matches_the_model_table():
+    """Per Update & Fuse step of the table: output layer dimensions (L, h, w) and encoded
+    feature map (h, w) for 480x288 input views and a 1920x1080 output; blocks A4,C,C x3 (x3
+    steps), A4,C,A4,C, A2,C,A2,C, A1,C,A1,C; final upsample 3.75."""
+    cfg = synth.config_quark()
+    assert cfg.n_scales == 24 and cfg.C == 32 and cfg.upsample_s == 3.75
+    groups = [(0, 6), (6, 12), (12, 18), (18, 20), (20, 22), (22, 24)]
+    table_out = [(24, 36, 64), (24, 36, 64), (24, 72, 128), (24, 72, 128), (12, 144, 256), (6, 288, 512)]
+    table_feat = [(36, 60), (36, 60), (72, 120), (72, 120), (144, 240), (288, 480)]
+    table_blocks = [[4, 0, 4, 0, 4, 0]] * 3 + [[4, 4], [2, 2], [1, 1]]
+    for (a, b), out, feat, blocks in zip(groups, table_out, table_feat, table_blocks):
+        assert all(cfg.ldm_shape(j) == out for j in range(a, b))
+        assert all((288 // cfg.scales[j][0], 480 // cfg.scales[j][0]) == feat for j in range(a, b))
+        assert [cfg.heads_of(j) for j in range(a, b)] == blocks
+        # one set of update features per step: only the step's first block decodes depths
+        assert [cfg.reuse_of(j) for j in range(a, b) if cfg.heads_of(j)] == [0] + [1] * (len([h for h in blocks if h]) - 1)
+    # layer collapse at the first block of steps 3 and 4 only
+    collapses = [j for j in range(1, 24) if cfg.scales[j - 1][1] == 2 * cfg.scales[j][1]]
+    assert collapses == [20, 22]
+
+
+def _bad(**kw):
+    base = dict(C=16, heads=2, scales=[(8, 4), (8, 4), (4, 4)], near=1.0, far=30.0, out_h=45, out_w=120,
+                ldm_f=[15, 15, 7.5], scale_heads=[4, 0, 2], reuse_depth=[0, 0, 0])
+    base.update(kw)
+    return synth.QuarkConfig(**base)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(scale_heads=[0, 4, 2]),                                   # step 0 without attention
+    dict(scale_heads=[4, 4, 0]),                                   # last step without attention
+    dict(reuse_depth=[1, 0, 0]),                                   # step 0 reusing depths
+    dict(scales=[(8, 4), (4, 4), (4, 4)], ldm_f=[15, 7.5, 7.5]),  # no-attention after a grid change
+    dict(scales=[(8, 4), (8, 2), (4, 2)]),                         # no-attention across a layer collapse
+    dict(reuse_depth=[0, 0, 1]),                                   # reuse across a grid change
+    dict(ldm_f=[15, 15, 5]),                                       # grid ratio 3
+    dict(scale_heads=[4, 0, 3]),                                   # 3 heads
+    dict(ldm_f=[15, -15, 7.5]),                                    # negative grid factor
+])
+def test_schedule_validation_rejects(kw):
+    with pytest.raises(quark.QuarkError) as e:
+        quark.Context(_bad(**kw))
+    assert e.value.status == quark.EINVAL, kw
+
+
+def test_valid_schedules_pass_validation():
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: creation would succeed")
+    for cfg in (_bad(), synth.config_quark(), _bad(scale_heads=[4, 0, 2], reuse_depth=[0, 0, 0])):
+        with pytest.raises(quark.QuarkError) as e:
+            quark.Context(cfg)
+        assert e.value.status == quark.ECUDA  # past validation, stopped only by the missing device
