@@ -34,6 +34,8 @@ from paper_2411_16680_b300 import accounting, synth  # noqa: E402
 WORKLOAD = "1080p novel view, V=8 views 1920x1080, scales (k,L)=(8,32),(4,16),(2,8),(1,4), C=32, h=2"
 QUARK_WORKLOAD = ("Quark model (appendix table): 1080p novel view from V=8 views 480x288, Initialize + 5 Update & "
                   "Fuse steps = 24 fusion steps, L 24/12/6, heads 4/2/1, LDM 36x64 -> 288x512, s=3.75, C=32")
+QUARKPLUS_WORKLOAD = ("Quark+ model (appendix table): 1080p novel view from V=8 views 720x432, Initialize + 5 Update "
+                      "& Fuse steps = 24 fusion steps, L 32/16/8, heads 4/2/1, LDM 54x96 -> 432x768, s=2.5, C=32")
 METRIC = "1080p novel-view fps (V=8) FP32 vs BF16 at >=40 dB vs oracle; p50/p99 latency"
 
 
@@ -421,9 +423,9 @@ def main():
     ap.add_argument("--ray", action="store_true", help="add the ray directional encoding (Sec. 3.2.1) to the features")
     ap.add_argument("--attn", default="one_to_many", choices=["one_to_many", "standard"],
                     help="attention of the fusion blocks (standard: K/V projections, the comparison mode)")
-    ap.add_argument("--model", default="uniform", choices=["uniform", "quark"],
-                    help="uniform: the 4-scale 1080p workload; quark: the paper's Quark model schedule "
-                         "(24 fusion steps, 480x288 views, 1080p output)")
+    ap.add_argument("--model", default="uniform", choices=["uniform", "quark", "quarkplus"],
+                    help="uniform: the 4-scale 1080p workload; quark / quarkplus: the paper's Quark / Quark+ "
+                         "model schedules (24 fusion steps, 480x288 / 720x432 views, 1080p output)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=120.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -442,9 +444,10 @@ def main():
     peaks = load_peaks()
 
     sw, sh = (int(v) for v in args.size.lower().split("x"))
-    quark_model = args.model == "quark"
+    quark_model = args.model in ("quark", "quarkplus")
     if quark_model:
-        workload = QUARK_WORKLOAD if (sw, sh) == (1920, 1080) else QUARK_WORKLOAD.replace("1080p", f"{sw}x{sh}")
+        wl = QUARK_WORKLOAD if args.model == "quark" else QUARKPLUS_WORKLOAD
+        workload = wl if (sw, sh) == (1920, 1080) else wl.replace("1080p", f"{sw}x{sh}")
     else:
         workload = WORKLOAD if (sw, sh) == (1920, 1080) else WORKLOAD.replace("1080p", f"{sw}x{sh}").replace(
             "1920x1080", f"{sw}x{sh}")
@@ -456,14 +459,16 @@ def main():
     if args.ray:
         workload += ", ray directional encoding"
     if quark_model:
-        base_cfg = synth.config_quark(out_w=sw, out_h=sh).replace(attn_mode=attn_mode, ray_encoding=int(args.ray))
+        make = synth.config_quark if args.model == "quark" else synth.config_quarkplus
+        base_cfg = make(out_w=sw, out_h=sh).replace(attn_mode=attn_mode, ray_encoding=int(args.ray))
     else:
         base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh, attn_mode=attn_mode,
                                                 ray_encoding=int(args.ray))
     if not 1 <= args.views <= 64:
         ap.error("--views must be in 1..64")
     if quark_model:
-        scene = synth.scene_quark(V=max(8, args.views), out_w=sw, out_h=sh)
+        vw, vh = (480, 288) if args.model == "quark" else (720, 432)
+        scene = synth.scene_quark(V=max(8, args.views), W=vw, H=vh, out_w=sw, out_h=sh)
     else:
         scene = synth.scene_1080p(W=sw, H=sh, V=max(8, args.views))
     if args.views < len(scene.cams):

@@ -27,6 +27,12 @@ Real-time, High-resolution, and General Neural View Synthesis", 2024):
   render        Sec. 3.1, Eq. (1): upsample the unactivated depth / density / blend
                 logits, activate, back-project the input images, blend with beta, over
                 composite (front to back, equivalent to the paper's back to front).
+  render and    Sec. 3.2.2 "Decoding and rendering the intermediate LDM", Eq.
+  refine        (overcomposite-result), and the Update Block: decode the volume entering an
+                Update & Fuse step (activated), bilinearly splat appearance and density into
+                every input view (operator P), over-composite there, and turn the rendered
+                views and the image features into the update features Delta that the step
+                samples instead of the image features.
 
 Conventions (the paper is silent on them; the same readings bind the CUDA path):
 pixel centres at (x + 0.5, y + 0.5); camera x right, y down, z forward; world->camera
@@ -392,7 +398,9 @@ class StepResult:
 
 
 def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
-                     rect_attn: Rect, rect_out: Rect, last: bool, mode: int = 0) -> StepResult:
+                     rect_attn: Rect, rect_out: Rect, last: bool, mode: int = 0, delta_fetch=None) -> StepResult:
+    """One fusion step.  The views' update features are the level-k image features (fetchers[k]),
+    or, with render-and-refine, the Update Block's output (delta_fetch, one fetcher per view)."""
     f64 = lambda a: np.asarray(a, np.float64)
     k, L = cfg.scales[j]          # pyramid level of the views, layers
     f = cfg.f_of(j)               # LDM grid factor relative to the output
@@ -433,7 +441,8 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
         Delta, x, V_attn = None, None, V_in
     else:
         # ---- back-project the views' level-k features at the current depths ----
-        Delta = sample_views(fetchers[k], scene.cams, scene.target, f, k, d, ys, xs)  # [L,h,w,V,C]
+        src = fetchers[k] if delta_fetch is None else delta_fetch
+        Delta = sample_views(src, scene.cams, scene.target, f, k, d, ys, xs)  # [L,h,w,V,C]
 
         # ---- fusion block: one-to-many attention ----
         x = rmsnorm(V_in, f64(W[f"attn_g_{j}"]))
@@ -547,6 +556,129 @@ def over_back_to_front(col, alpha):
 
 
 # ---------------------------------------------------------------------------------------------
+# Render and refine (Sec. 3.2.2 "Decoding and rendering the intermediate LDM", Eq.
+# (overcomposite-result), the Update Block of the Update & Fuse figure)
+# ---------------------------------------------------------------------------------------------
+
+SPLAT_EPS = 1e-2  # reading: splats are normalised by max(weight sum, SPLAT_EPS)
+
+
+def decode_intermediate(V, W, near, far):
+    """Intermediate LDM of a feature volume V [L, H, W, C], activated before projection:
+    depth by Eq. (depth_activation), density sigmoid(V w_sigma + b_sigma), appearance
+    sigmoid(V W_a + b_a).  Returns d [L, H, W], sigma [L, H, W], a [L, H, W, 3]."""
+    f64 = lambda x: np.asarray(x, np.float64)
+    L = V.shape[0]
+    ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
+    t = V @ f64(W["w_d"]) + f64(W["b_d"])[0]
+    sig = sigmoid(V @ f64(W["w_sigma"]) + f64(W["b_sigma"])[0])
+    a = sigmoid(V @ f64(W["W_a"]) + f64(W["b_a"]))
+    return depth_activation(t, ell, L, near, far), sig, a
+
+
+def splat_layers(cam_t, f, cam_m, k, h, w, d, vals):
+    """Forward projection P (Sec. 3.2.2): every LDM pixel x layer (grid factor f of the target)
+    at its depth d lands at continuous coordinates (u, v) of view m's level-k grid (h x w) and
+    adds its values, times the bilinear weights, to the four nearest pixel centres -- the
+    transpose of bilinear sampling, nothing outside the map or behind the camera.
+    d [L, H, W], vals [L, H, W, n] -> weighted sums [L, h, w, n] and weight sums [L, h, w]."""
+    L, H, Wd = d.shape
+    ys = np.arange(H, dtype=np.float64)[None, :, None]
+    xs = np.arange(Wd, dtype=np.float64)[None, None, :]
+    Xw = unproject(ys, xs, d, scaled_K(cam_t, f), cam_t)
+    u, v, valid = project(Xw, scaled_K(cam_m, k), cam_m)
+    # clamp far-away coordinates (their taps are outside the map either way) before the floor
+    x = np.clip(np.where(valid, u, -10.0) - 0.5, -3.0, w + 2.0)
+    y = np.clip(np.where(valid, v, -10.0) - 0.5, -3.0, h + 2.0)
+    x0, y0 = np.floor(x), np.floor(y)
+    fx, fy = x - x0, y - y0
+    x0, y0 = x0.astype(np.int64), y0.astype(np.int64)
+    li = np.broadcast_to(np.arange(L)[:, None, None], d.shape)
+    acc = np.zeros((L, h, w, vals.shape[-1]))
+    wsum = np.zeros((L, h, w))
+    for dy, dx, wt in ((0, 0, (1 - fy) * (1 - fx)), (0, 1, (1 - fy) * fx), (1, 0, fy * (1 - fx)), (1, 1, fy * fx)):
+        iy, ix = y0 + dy, x0 + dx
+        ok = valid & (iy >= 0) & (iy < h) & (ix >= 0) & (ix < w)
+        np.add.at(acc, (li[ok], iy[ok], ix[ok]), wt[ok][:, None] * vals[ok])
+        np.add.at(wsum, (li[ok], iy[ok], ix[ok]), wt[ok])
+    return acc, wsum
+
+
+def render_to_views(cfg, W, scene, Vc, f, k):
+    """Eq. (overcomposite-result): I~ = O(P(a, d), P(sigma, d)) in every input view, at level k.
+    Vc [L, H, W, C] is the volume entering the step (after any layer collapse) on its grid of
+    factor f.  Each layer's splat is normalised by its weight sum (reading: clamped below at
+    SPLAT_EPS, so sparsely covered pixels fade out), then the layers are over-composited front to
+    back in LDM order (l = L nearest first).  Returns [V, h, w, 4]: RGB and accumulated alpha."""
+    d, sig, a = decode_intermediate(Vc, W, cfg.near, cfg.far)
+    vals = np.concatenate([a, sig[..., None]], axis=-1)
+    out = []
+    for cam in scene.cams:
+        h, w = cam.height // k, cam.width // k
+        acc, wsum = splat_layers(scene.target, f, cam, k, h, w, d, vals)
+        lay = acc / np.maximum(wsum, SPLAT_EPS)[..., None]
+        rgb, T = np.zeros((h, w, 3)), np.ones((h, w))
+        for li in range(Vc.shape[0] - 1, -1, -1):
+            al = lay[li, ..., 3]
+            rgb = rgb + (T * al)[..., None] * lay[li, ..., :3]
+            T = T * (1.0 - al)
+        out.append(np.concatenate([rgb, (1.0 - T)[..., None]], axis=-1))
+    return np.stack(out)
+
+
+def update_block(W, j, F, It):
+    """Update Block of step j (reading; the paper calls it a small CNN on [I~, I_k, rho_k]):
+    F' = F + up(I~) W_r + b_r, Delta = F' + Conv(gelu(Conv(N(F')))) with 3x3 convs (zero pad),
+    the residual CNN block of Sec. 3.3 in image space.  F [h, w, C] are the view's level-k
+    features (with the ray directional encoding when it is on), It [h', w', 4] its rendering at
+    the previous step's level, upsampled x h / h' (1 or 2) with edge clamp."""
+    f64 = lambda x: np.asarray(x, np.float64)
+    h, w = F.shape[:2]
+    hp, wp = It.shape[:2]
+    Iu = resize_rect(It, (0, hp, 0, wp), hp, wp, h // hp, (0, h, 0, w))
+    Fp = F + Iu @ f64(W[f"upd_Wr_{j}"]) + f64(W[f"upd_br_{j}"])
+    n = rmsnorm(Fp, f64(W[f"upd_g_{j}"]))
+    full = (0, h, 0, w)
+    h1 = conv3x3_rect(n, full, h, w, f64(W[f"upd1_w_{j}"]), f64(W[f"upd1_b_{j}"]), full)
+    return Fp + conv3x3_rect(gelu(h1), full, h, w, f64(W[f"upd2_w_{j}"]), f64(W[f"upd2_b_{j}"]), full)
+
+
+class ArrayFetch:
+    """Texel fetch from a whole per-view map [h, w, C] (zero outside it)."""
+
+    def __init__(self, data):
+        self.data = data
+        self.h, self.w = data.shape[:2]
+
+    def prepare(self, ys_list, xs_list):
+        pass
+
+    def __call__(self, iy, ix):
+        inside = (iy >= 0) & (iy < self.h) & (ix >= 0) & (ix < self.w)
+        vals = self.data[np.clip(iy, 0, self.h - 1), np.clip(ix, 0, self.w - 1)]
+        return np.where(inside[..., None], vals, 0.0)
+
+
+def refine_features(cfg, W, scene, fetchers, j, prev: StepResult):
+    """Update features of step j with render-and-refine: the volume entering the step (collapsed
+    when L halves) rendered into the views at step j-1's level, then the Update Block on each
+    view's level-k_j features.  Whole frames only.  Returns one fetcher per view."""
+    f64 = lambda a: np.asarray(a, np.float64)
+    k, L = cfg.scales[j]
+    kp, Lp = cfg.scales[j - 1]
+    Vc = prev.V_out
+    if Lp == 2 * L:
+        Vc = layer_collapse(Vc, f64(W[f"col_w1_{j}"]), f64(W[f"col_b1_{j}"]), f64(W[f"col_w2_{j}"]),
+                            f64(W[f"col_b2_{j}"]))
+    It = render_to_views(cfg, W, scene, Vc, cfg.f_of(j - 1), kp)
+    out = []
+    for m, lf in enumerate(fetchers[k]):
+        lf.prepare([np.array([0, lf.h - 1])], [np.array([0, lf.w - 1])])  # the whole level (+ gamma)
+        out.append(ArrayFetch(update_block(W, j, lf.data, It[m])))
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 # Whole forward pass on a window of the output
 # ---------------------------------------------------------------------------------------------
 
@@ -601,11 +733,17 @@ def forward(cfg, W, scene, out_rect: Optional[Rect] = None, mode: int = 0):
         out_rect = (0, cfg.out_h, 0, cfg.out_w)
     rect_attn, rect_out = plan_rects(cfg, out_rect)
     fetchers = make_fetchers(cfg, scene, W)
+    refine = getattr(cfg, "render_refine", 0)
+    if refine:
+        assert out_rect == (0, cfg.out_h, 0, cfg.out_w), "render-and-refine renders whole views: whole frames only"
     steps: List[StepResult] = []
     prev = None
+    delta = None  # update features of the current Update & Fuse step (render-and-refine)
     for j in range(cfg.n_scales):
+        if refine and cfg.refines(j):
+            delta = refine_features(cfg, W, scene, fetchers, j, prev)
         prev = update_fuse_step(cfg, W, scene, fetchers, j, prev, rect_attn[j], rect_out[j],
-                                last=(j == cfg.n_scales - 1), mode=mode)
+                                last=(j == cfg.n_scales - 1), mode=mode, delta_fetch=delta)
         steps.append(prev)
     rgba = render_rect(cfg, scene, steps[-1], out_rect)
     return rgba, steps

@@ -64,6 +64,7 @@ class QuarkConfig:
     scale_heads: Optional[List[int]] = None
     ldm_f: Optional[List[float]] = None
     reuse_depth: Optional[List[int]] = None
+    render_refine: int = 0  # 1: update features from rendered input views (render-and-refine)
 
     @property
     def n_scales(self) -> int:
@@ -77,6 +78,11 @@ class QuarkConfig:
 
     def reuse_of(self, j: int) -> int:
         return 0 if self.reuse_depth is None else int(self.reuse_depth[j])
+
+    def refines(self, j: int) -> bool:
+        """Step j renders the intermediate LDM into the input views and runs the Update Block: the
+        first sampling block of every Update & Fuse step after the initialisation."""
+        return bool(self.render_refine) and j > 0 and self.heads_of(j) > 0 and not self.reuse_of(j)
 
     @property
     def upsample_s(self) -> float:
@@ -387,6 +393,11 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
         })
         if h > 0:
             s.update({f"Wq_std_{j}": (C, C), f"Wk_std_{j}": (C, C), f"Wv_std_{j}": (C, C), f"Wo_std_{j}": (C, C)})
+        if cfg.refines(j):
+            # Update Block: the rendered view (RGB + alpha) lifted to C channels, then a residual CNN
+            s.update({f"upd_Wr_{j}": (4, C), f"upd_br_{j}": (C,), f"upd_g_{j}": (C,),
+                      f"upd1_w_{j}": (3, 3, C, C), f"upd1_b_{j}": (C,), f"upd2_w_{j}": (3, 3, C, C),
+                      f"upd2_b_{j}": (C,)})
     s.update({"w_d": (C,), "b_d": (1,), "w_sigma": (C,), "b_sigma": (1,), "W_a": (C, 3), "b_a": (3,),
               "W_beta": (C, C)})
     for k in cfg.levels():
@@ -404,22 +415,23 @@ def make_weights(cfg: QuarkConfig, seed: int = 5678, std: float = 0.02, sharp: b
     out = {}
     for name, shp in weight_shapes(cfg).items():
         if not sharp:
-            if name.startswith(("attn_g", "conv_g")):
+            if name.startswith(("attn_g", "conv_g", "upd_g")):
                 w = 1.0 + std * rng.standard_normal(shp)
             else:
                 w = std * rng.standard_normal(shp)
         else:
-            if name.startswith(("attn_g", "conv_g")):
+            if name.startswith(("attn_g", "conv_g", "upd_g")):
                 w = 1.0 + 0.2 * rng.standard_normal(shp)
             elif name in ("v0",):
                 w = rng.standard_normal(shp)
-            elif name.startswith(("enc_b", "conv1_b", "conv2_b", "col_b")) or name in ("b_d", "b_sigma", "b_a"):
+            elif name.startswith(("enc_b", "conv1_b", "conv2_b", "col_b", "upd1_b", "upd2_b", "upd_br")) or \
+                    name in ("b_d", "b_sigma", "b_a"):
                 w = 0.3 * rng.standard_normal(shp)
             else:
                 fan_in = int(np.prod(shp[:-1])) if len(shp) > 1 else shp[0]
                 if name.startswith(("Wq", "W_beta")):
                     gain = 4.0
-                elif name.startswith(("Wo_", "conv2_w", "col_w2")):
+                elif name.startswith(("Wo_", "conv2_w", "col_w2", "upd2_w")):
                     gain = 0.4  # residual branches scaled down so the volume does not drift
                 else:
                     gain = 1.0
@@ -461,13 +473,24 @@ def config_quark(out_w: int = 1920, out_h: int = 1080, C: int = 32) -> QuarkConf
     conv block, then one step with a conv block only; the first block of an Update & Fuse step
     samples the views at the depths decoded from its input, the later blocks reuse them (one
     set of update features per step).  The final render upsamples by s = 3.75."""
+    return _schedule(24, 30.0, out_w, out_h, C)
+
+
+def config_quarkplus(out_w: int = 1920, out_h: int = 1080, C: int = 32) -> QuarkConfig:
+    """The paper's Quark+ model (appendix table "Model description for Quark+"): the Quark schedule
+    with 32 -> 16 -> 8 layers on LDM grids 54x96 -> 432x768 for a 1920x1080 output (grid factors
+    20, 10, 5, 2.5; the table's 432x768 output LDM gives the final upsample 2.5), from 720x432 views."""
+    return _schedule(32, 20.0, out_w, out_h, C)
+
+
+def _schedule(L0: int, f0: float, out_w: int, out_h: int, C: int) -> QuarkConfig:
     groups = [  # (k, L, f, heads of each fusion block, CNN blocks per fusion block)
-        (8, 24, 30.0, [4, 4, 4], 2),   # Initialize (flat layers at the depth anchors)
-        (8, 24, 30.0, [4, 4, 4], 2),   # Update & Fuse 0
-        (4, 24, 15.0, [4, 4, 4], 2),   # Update & Fuse 1 (x2 upsample)
-        (4, 24, 15.0, [4, 4], 1),      # Update & Fuse 2
-        (2, 12, 7.5, [2, 2], 1),       # Update & Fuse 3 (layer collapse, x2 upsample)
-        (1, 6, 3.75, [1, 1], 1),       # Update & Fuse 4 (layer collapse, x2 upsample)
+        (8, L0, f0, [4, 4, 4], 2),               # Initialize (flat layers at the depth anchors)
+        (8, L0, f0, [4, 4, 4], 2),               # Update & Fuse 0
+        (4, L0, f0 / 2, [4, 4, 4], 2),           # Update & Fuse 1 (x2 upsample)
+        (4, L0, f0 / 2, [4, 4], 1),              # Update & Fuse 2
+        (2, L0 // 2, f0 / 4, [2, 2], 1),         # Update & Fuse 3 (layer collapse, x2 upsample)
+        (1, L0 // 4, f0 / 8, [1, 1], 1),         # Update & Fuse 4 (layer collapse, x2 upsample)
     ]
     scales, f, heads, reuse = [], [], [], []
     for k, L, ff, hs, n_cnn in groups:
@@ -483,8 +506,8 @@ def config_quark(out_w: int = 1920, out_h: int = 1080, C: int = 32) -> QuarkConf
 
 def scene_quark(seed: int = 1234, V: int = 8, W: int = 480, H: int = 288, out_w: int = 1920,
                 out_h: int = 1080) -> Scene:
-    """Input views at the Quark table's resolution (480x288: a 36x60 level-8 feature map) and a
-    1920x1080 novel view covering the same frustum."""
+    """Input views at the Quark table's resolution (480x288: a 36x60 level-8 feature map; Quark+:
+    720x432, a 54x90 map) and a 1920x1080 novel view covering the same frustum."""
     return scene_raycast(seed=seed, V=V, W=W, H=H, f=350.0 * W / 480.0, out_w=out_w, out_h=out_h)
 
 

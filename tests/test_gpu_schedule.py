@@ -83,11 +83,13 @@ def test_explicit_default_schedule_is_bitwise_the_plain_pipeline(precision):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("model", ["quark", "quarkplus"])
 @pytest.mark.parametrize("precision", [synth.PREC_FP32, synth.PREC_BF16])
-def test_quark_model_schedule_matches_oracle(precision):
-    """The paper's Quark schedule (24 fusion steps, L 24/12/6, heads 4/2/1, factors 30 -> 3.75) at
-    a 240 x 120 output from 128 x 80 views."""
-    cfg = synth.config_quark(out_w=240, out_h=120).replace(precision=precision)
+def test_quark_model_schedule_matches_oracle(precision, model):
+    """The paper's Quark schedule (24 fusion steps, L 24/12/6, heads 4/2/1, factors 30 -> 3.75) and
+    Quark+ (L 32/16/8, factors 20 -> 2.5) at a 240 x 120 output from 128 x 80 views."""
+    make = synth.config_quark if model == "quark" else synth.config_quarkplus
+    cfg = make(out_w=240, out_h=120).replace(precision=precision)
     W = synth.make_weights(cfg, seed=8, sharp=True)
     scene = synth.scene_quark(seed=8, V=3, W=128, H=80, out_w=240, out_h=120)
     ref, ref_steps = O.forward(cfg.replace(precision=synth.PREC_FP32), W, scene)

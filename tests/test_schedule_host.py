@@ -27,6 +27,23 @@ def test_quark_workload_matches_the_model_table():
     assert collapses == [20, 22]
 
 
+def test_quarkplus_workload_matches_the_model_table():
+    """Quark+ table: output layer dimensions (32, 54, 96), (32, 54, 96), (32, 108, 192),
+    (32, 108, 192), (16, 216, 384), (8, 432, 768); feature maps 54x90 .. 432x720 of 720x432 views;
+    the same blocks as Quark; final upsample 1080 / 432 = 2.5."""
+    cfg = synth.config_quarkplus()
+    assert cfg.n_scales == 24 and cfg.upsample_s == 2.5
+    groups = [(0, 6), (6, 12), (12, 18), (18, 20), (20, 22), (22, 24)]
+    table_out = [(32, 54, 96), (32, 54, 96), (32, 108, 192), (32, 108, 192), (16, 216, 384), (8, 432, 768)]
+    table_feat = [(54, 90), (54, 90), (108, 180), (108, 180), (216, 360), (432, 720)]
+    for (a, b), out, feat in zip(groups, table_out, table_feat):
+        assert all(cfg.ldm_shape(j) == out for j in range(a, b))
+        assert all((432 // cfg.scales[j][0], 720 // cfg.scales[j][0]) == feat for j in range(a, b))
+    q = synth.config_quark()
+    assert [q.heads_of(j) for j in range(24)] == [cfg.heads_of(j) for j in range(24)]
+    assert [q.reuse_of(j) for j in range(24)] == [cfg.reuse_of(j) for j in range(24)]
+
+
 def _bad(**kw):
     base = dict(C=16, heads=2, scales=[(8, 4), (8, 4), (4, 4)], near=1.0, far=30.0, out_h=45, out_w=120,
                 ldm_f=[15, 15, 7.5], scale_heads=[4, 0, 2], reuse_depth=[0, 0, 0])
@@ -54,7 +71,7 @@ def test_schedule_validation_rejects(kw):
 def test_valid_schedules_pass_validation():
     if torch.cuda.is_available():
         pytest.skip("a GPU is present: creation would succeed")
-    for cfg in (_bad(), synth.config_quark(), _bad(scale_heads=[4, 0, 2], reuse_depth=[0, 0, 0])):
+    for cfg in (_bad(), synth.config_quark(), synth.config_quarkplus(), _bad(scale_heads=[4, 0, 2], reuse_depth=[0, 0, 0])):
         with pytest.raises(quark.QuarkError) as e:
             quark.Context(cfg)
         assert e.value.status == quark.ECUDA  # past validation, stopped only by the missing device
