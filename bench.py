@@ -421,6 +421,8 @@ def main():
     ap.add_argument("--forms", default="fp32,bf16", help="forms to time (comma separated)")
     ap.add_argument("--views", type=int, default=8, help="input views used (1..64; the view sweep and the per-view cost split)")
     ap.add_argument("--ray", action="store_true", help="add the ray directional encoding (Sec. 3.2.1) to the features")
+    ap.add_argument("--refine", action="store_true",
+                    help="render-and-refine (Sec. 3.2.2): update features from the rendered input views")
     ap.add_argument("--attn", default="one_to_many", choices=["one_to_many", "standard"],
                     help="attention of the fusion blocks (standard: K/V projections, the comparison mode)")
     ap.add_argument("--model", default="uniform", choices=["uniform", "quark", "quarkplus"],
@@ -458,12 +460,15 @@ def main():
         workload += ", standard attention"
     if args.ray:
         workload += ", ray directional encoding"
+    if args.refine:
+        workload += ", render-and-refine"
     if quark_model:
         make = synth.config_quark if args.model == "quark" else synth.config_quarkplus
         base_cfg = make(out_w=sw, out_h=sh).replace(attn_mode=attn_mode, ray_encoding=int(args.ray))
     else:
         base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh, attn_mode=attn_mode,
                                                 ray_encoding=int(args.ray))
+    base_cfg = base_cfg.replace(render_refine=int(args.refine))
     if not 1 <= args.views <= 64:
         ap.error("--views must be in 1..64")
     if quark_model:
@@ -477,6 +482,8 @@ def main():
     img_h, img_w = scene.images.shape[1:3]
 
     if args.impl == "reference":
+        if args.refine:
+            ap.error("--refine: the oracle's render-and-refine renders whole views; it is checked by the tests")
         if rank != 0:
             return 0
         cfg = base_cfg.replace(precision=synth.PREC_FP32)
@@ -523,8 +530,9 @@ def main():
                        "e2e_fps": round(world * args.steps / res["e2e_s"], 2),
                        "e2e_serial_fps": round(world * args.steps / res["serial_s"], 2)}
 
-    # accuracy of each form against the oracle on sampled windows (rank 0)
-    if rank == 0:
+    # accuracy of each form against the oracle on sampled windows (rank 0); the oracle's
+    # render-and-refine renders whole views, so that option is checked by the tests instead
+    if rank == 0 and not args.refine:
         import numpy as np
         from oracle import quark_oracle as O
         Ho, Wo = base_cfg.out_h, base_cfg.out_w
@@ -546,7 +554,7 @@ def main():
     cfg, res = results[head]
     f = forms[head]
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.refine:
         cfg64 = base_cfg.replace(precision=synth.PREC_FP32)
         fps_cpu, secs, desc = oracle_sample(cfg64, synth.make_weights(cfg64, sharp=args.sharp), scene, rows=6)
         cpu = {"value": round(fps_cpu, 6), "unit": "frames/s", "cores": blas_threads(), "kind": "oracle",

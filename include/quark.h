@@ -87,6 +87,16 @@ typedef struct {
  *              (32 values) on the coarsest level, bilinearly upsampled to level k and projected
  *              to C channels by W_ray of that level.  Needs the W_ray weights; not with
  *              quark_update_fuse_noalloc nor the differentiable stage.  0: off.
+ *   render_refine  1: render-and-refine (Sec. 3.2.2 "Decoding and rendering the intermediate
+ *              LDM", Eq. overcomposite-result, the Update Block): every Update & Fuse step after
+ *              the first (a step j > 0 that attends and does not reuse depths) decodes the volume
+ *              entering it, bilinearly splats its appearance and density into every input view at
+ *              step j-1's pyramid level (normalised by max(weight sum, 1e-2)), over-composites
+ *              them front to back into the rendered views I~ (RGB, alpha), and forms the update
+ *              features Delta = F' + Conv(gelu(Conv(N(F')))), F' = F + up(I~) W_r + b_r, from the
+ *              level-k features F (plus the ray encoding when on; up = x2 bilinear when the level
+ *              changes).  The step and the steps reusing its depths sample Delta instead of F.
+ *              Needs the upd_* weights.  0: off (Delta = F).
  *   hbm_cap_bytes  cap on this context's device allocations (0 = no cap)
  * Full model schedule (Sec. 3.2; tables "Model description for Quark / Quark+": an Update &
  * Fuse step back-projects its update features once and runs several fusion blocks, each an
@@ -99,7 +109,8 @@ typedef struct {
  *   reuse_depth[j]  1: sample the views at the depths the latest sampling step used instead of
  *              the depths decoded from this step's input (one set of update features per Update
  *              & Fuse step); needs the same grid and layers back to that step.  0: decode.
- * quark_update_fuse_noalloc and the differentiable stage take the uniform schedule only.     */
+ * quark_update_fuse_noalloc and the differentiable stage take the uniform schedule only, without
+ * render-and-refine.                                                                         */
 typedef struct {
     int C, heads, n_scales;
     int k[QUARK_MAX_SCALES];
@@ -108,6 +119,7 @@ typedef struct {
     int precision;
     int attn_mode;
     int ray_encoding;
+    int render_refine;
     int scale_heads[QUARK_MAX_SCALES];
     float ldm_f[QUARK_MAX_SCALES];
     int reuse_depth[QUARK_MAX_SCALES];
@@ -159,6 +171,16 @@ typedef struct {
     /* ray_encoding only (else may be NULL): [32][C] projection of the encoding for pyramid level
      * k = 1, 2, 4, 8 (index 0..3), for every level some step uses */
     const float* W_ray[4];
+    /* render_refine only (else may be NULL), per step j that renders (see render_refine): the
+     * Update Block, W_r [4][C], b_r [C], RMSNorm gain g [C], then the residual CNN block's
+     * conv1_w, conv2_w [3][3][C][C], conv1_b, conv2_b [C] */
+    const float* upd_Wr[QUARK_MAX_SCALES];
+    const float* upd_br[QUARK_MAX_SCALES];
+    const float* upd_g[QUARK_MAX_SCALES];
+    const float* upd1_w[QUARK_MAX_SCALES];
+    const float* upd1_b[QUARK_MAX_SCALES];
+    const float* upd2_w[QUARK_MAX_SCALES];
+    const float* upd2_b[QUARK_MAX_SCALES];
 } quark_weights;
 
 typedef struct quark_ctx quark_ctx;

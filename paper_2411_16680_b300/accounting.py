@@ -15,7 +15,7 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
     C = cfg.C
     elt = 2 if cfg.precision == 1 else 4
     out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "launches": 0}
-                                        for k in ("encode", "collapse", "attend", "conv_block", "render")}
+                                        for k in ("encode", "collapse", "attend", "conv_block", "render", "refine")}
     # encode: images in, every used level out, RGBA copy out
     e = out["encode"]
     e["bytes"] += V * img_h * img_w * (3 * 4 + 16)
@@ -45,6 +45,20 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
         if h == 0:
             continue  # a block without attention: its conv block only
         texels = V * (img_h // k) * (img_w // k)
+        if cfg.refines(j):
+            # render-and-refine: decode of the entering volume (its C channels in, 5 floats out), the
+            # splat (5 floats in; V x (colour, density, weight) sums written and read back by the
+            # composite), the rendered views, then F' = F + up(I~) W_r and the Update Block's conv
+            # block (F' in, Delta out); the attention then reads Delta in place of the level
+            r = out["refine"]
+            Lp, Hp, Wp = cfg.ldm_shape(j - 1)
+            kp = cfg.scales[j - 1][0]
+            Ep = L * Hp * Wp
+            rtex = V * (img_h // kp) * (img_w // kp)
+            r["bytes"] += Ep * C * elt + Ep * 5 * 4 + Ep * 5 * 4 + 2 * rtex * L * 5 * 4 + rtex * 16
+            r["bytes"] += 2 * texels * C * elt + rtex * 16 + 2 * texels * C * elt
+            r["flops"] += 2 * Ep * 5 * C + 2 * texels * (4 * C + (18 * C * C + 5 * C))
+            r["launches"] += 5
         # the sampled depths: read by a block that reuses them, written for the next sampling block
         # when that one reuses them
         nxt = next((i for i in range(j + 1, cfg.n_scales) if cfg.heads_of(i)), None)

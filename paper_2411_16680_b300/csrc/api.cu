@@ -79,7 +79,8 @@ void qk_free(quark_ctx* ctx, void* p, size_t bytes) {
 // Launch accounting
 // -------------------------------------------------------------------------------------------
 
-static const char* kFamilyNames[KF_COUNT] = {"encode", "collapse", "attend", "conv_block", "render", "backward"};
+static const char* kFamilyNames[KF_COUNT] = {"encode", "collapse", "attend", "conv_block", "render", "backward",
+                                              "refine"};
 
 static cudaEvent_t get_event(quark_ctx* ctx) {
     if (!ctx->event_pool.empty()) {
@@ -234,7 +235,13 @@ quark_status qk_validate_config(const quark_config* c) {
     if (c->attn_mode != QUARK_ATTN_ONE_TO_MANY && c->attn_mode != QUARK_ATTN_STANDARD)
         return qk_fail(nullptr, QUARK_EINVAL, "unknown attention mode %d", c->attn_mode);
     if (c->ray_encoding != 0 && c->ray_encoding != 1) return qk_fail(nullptr, QUARK_EINVAL, "ray_encoding must be 0 or 1");
+    if (c->render_refine != 0 && c->render_refine != 1)
+        return qk_fail(nullptr, QUARK_EINVAL, "render_refine must be 0 or 1");
     return QUARK_OK;
+}
+
+bool qk_refines(const quark_config& c, int j) {
+    return c.render_refine && j > 0 && qk_heads(c, j) > 0 && !c.reuse_depth[j];
 }
 
 extern "C" quark_status quark_create(const quark_config* cfg, int device, quark_ctx** out) {
@@ -267,6 +274,7 @@ extern "C" quark_status quark_destroy(quark_ctx* ctx) {
     qk_free(ctx, ctx->wdev, ctx->wbytes);
     qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
     qk_free(ctx, ctx->wat, ctx->wat_bytes);
+    qk_free(ctx, ctx->wupd, ctx->wupd_bytes);
     qk_free(ctx, ctx->dev_err, sizeof(int));
     qk_free(ctx, ctx->bwd_ws, ctx->bwd_ws_bytes);
     delete ctx;
@@ -396,6 +404,35 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             pad4();
         }
     }
+    // Update Blocks of the steps that render (ConvLayout with the decode fields copied, then W_r, b_r)
+    for (int j = 0; j < c.n_scales; ++j) {
+        ctx->off_upd[j] = (size_t)-1;
+        if (!qk_refines(c, j)) continue;
+        if (!need(w->upd_Wr[j], "upd_Wr") || !need(w->upd_br[j], "upd_br") || !need(w->upd_g[j], "upd_g") ||
+            !need(w->upd1_w[j], "upd1_w") || !need(w->upd1_b[j], "upd1_b") || !need(w->upd2_w[j], "upd2_w") ||
+            !need(w->upd2_b[j], "upd2_b"))
+            return QUARK_EINVAL;
+        ctx->off_upd[j] = blob.size();
+        put(w->upd_g[j], C);
+        put(w->upd1_w[j], 9 * (size_t)C * C);
+        put(w->upd1_b[j], C);
+        put(w->upd2_w[j], 9 * (size_t)C * C);
+        put(w->upd2_b[j], C);
+        put(w->w_d, C);
+        put(w->w_sigma, C);
+        put(w->W_a, 3 * (size_t)C);
+        put(w->b_a, 3);
+        blob.push_back(w->b_d);
+        blob.push_back(w->b_sigma);
+        blob.push_back(0.f);
+        blob.push_back(0.f);
+        blob.push_back(0.f);
+        if (blob.size() - ctx->off_upd[j] != (size_t)ConvLayout{C}.total())
+            return qk_fail(ctx, QUARK_EINTERNAL, "update block layout");
+        put(w->upd_Wr[j], 4 * (size_t)C);
+        put(w->upd_br[j], C);
+        pad4();
+    }
     for (int i = 0; i < 4; ++i) ctx->off_ray[i] = (size_t)-1;
     if (c.ray_encoding) {
         for (int j = 0; j < c.n_scales; ++j) {
@@ -469,6 +506,22 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         s = qk_alloc(ctx, &ctx->wat, ctx->wat_bytes);
         if (s != QUARK_OK) return s;
         QK_CUDA(ctx, cudaMemcpy(ctx->wat, at.data(), ctx->wat_bytes, cudaMemcpyHostToDevice));
+        if (c.render_refine) {
+            // Update Block convs, per step at j * wtc_step_bytes (steps that render)
+            std::vector<uint16_t> up(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
+            for (int j = 0; j < c.n_scales; ++j) {
+                if (!qk_refines(c, j)) continue;
+                uint16_t* d = up.data() + (size_t)j * 2 * 9 * C * C;
+                pack_conv_weights_bf16(w->upd1_w[j], C, d);
+                pack_conv_weights_bf16(w->upd2_w[j], C, d + 9 * (size_t)C * C);
+            }
+            qk_free(ctx, ctx->wupd, ctx->wupd_bytes);
+            ctx->wupd = nullptr;
+            ctx->wupd_bytes = up.size() * sizeof(uint16_t);
+            s = qk_alloc(ctx, &ctx->wupd, ctx->wupd_bytes);
+            if (s != QUARK_OK) return s;
+            QK_CUDA(ctx, cudaMemcpy(ctx->wupd, up.data(), ctx->wupd_bytes, cudaMemcpyHostToDevice));
+        }
         qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
         ctx->wtc = nullptr;
         ctx->wtc_bytes = tc.size() * sizeof(uint16_t);
@@ -832,6 +885,107 @@ extern "C" quark_status quark_update_fuse(quark_ctx* ctx, const quark_pyramid* p
     return qk_update_fuse(ctx, pyr, pyr->V, scale, ldm, (cudaStream_t)stream);
 }
 
+// Grow an LDM scratch buffer to at least `bytes`.
+static quark_status grow_scratch(quark_ldm* l, void** p, size_t& have, size_t bytes) {
+    if (have >= bytes) return QUARK_OK;
+    for (auto it = l->bufs.begin(); it != l->bufs.end(); ++it)
+        if (it->p == *p) {
+            qk_free(l->ctx, it->p, it->bytes);
+            l->bufs.erase(it);
+            break;
+        }
+    *p = nullptr;
+    have = 0;
+    quark_status s = qk_ldm_scratch(l, p, bytes);
+    if (s == QUARK_OK) have = bytes;
+    return s;
+}
+
+// Render-and-refine of step `scale` (Sec. 3.2.2, Eq. overcomposite-result, the Update Block): the
+// volume entering the step (`prev`, on step scale-1's Hp x Wp grid, already collapsed) decoded,
+// splatted into the first V views at step scale-1's level and over-composited there; then
+// Delta = F' + Conv(gelu(Conv(N(F')))), F' = F + up(I~) W_r + b_r, from the level-k features
+// `feat`, into ldm->delta.
+static quark_status refine_step(quark_ctx* ctx, const quark_pyramid* pyr, int V, int scale, quark_ldm* ldm,
+                                const void* prev, int Hp, int Wp, const void* feat, cudaStream_t st) {
+    const quark_config& c = ctx->cfg;
+    const bool bf16 = c.precision == QUARK_BF16;
+    const int C = c.C, L = c.L[scale], kp = c.k[scale - 1], k = c.k[scale];
+    const int hr = pyr->H / kp, wr = pyr->W / kp, h = pyr->H / k, w = pyr->W / k;
+    const DepthParams dp{(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
+    // scratch: splat sums (float4) and weights, the rendered views, the Update Block's input and output
+    const size_t ns = (size_t)V * L * hr * wr;
+    const size_t off_w = ns * sizeof(float4);
+    const size_t off_r = (off_w + ns * sizeof(float) + 255) & ~(size_t)255;
+    const size_t splat_bytes = off_r + (size_t)V * hr * wr * sizeof(float4);
+    const size_t feat_bytes = (size_t)V * h * w * C * (bf16 ? 2 : 4);
+    quark_status s = grow_scratch(ldm, &ldm->splat, ldm->splat_bytes, splat_bytes);
+    if (s == QUARK_OK) s = grow_scratch(ldm, &ldm->upd_in, ldm->upd_in_bytes, feat_bytes);
+    if (s == QUARK_OK) s = grow_scratch(ldm, &ldm->delta, ldm->delta_bytes, feat_bytes);
+    if (s != QUARK_OK) return s;
+    // intermediate LDM, activated (the LDM's decoded-attribute buffers; recomputed when read)
+    DecodeArgs da{};
+    da.vol = prev;
+    da.L = L;
+    da.H = Hp;
+    da.W = Wp;
+    da.dp = dp;
+    da.w = ctx->wdev + ctx->off_conv[scale];
+    da.colour = ldm->colour;
+    da.alpha = ldm->alpha;
+    da.depth = ldm->depth;
+    ldm->decoded = -1;
+    s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_decode(da, C, bf16, st); });
+    if (s != QUARK_OK) return s;
+    SplatArgs sa{};
+    sa.colour = ldm->colour;
+    sa.alpha = ldm->alpha;
+    sa.depth = ldm->depth;
+    sa.L = L;
+    sa.H = Hp;
+    sa.W = Wp;
+    sa.V = V;
+    sa.h = hr;
+    sa.w = wr;
+    sa.acc = (float4*)ldm->splat;
+    sa.wsum = (float*)((uint8_t*)ldm->splat + off_w);
+    sa.out = (float4*)((uint8_t*)ldm->splat + off_r);
+    for (int m = 0; m < V; ++m) sa.geo.v[m] = qk_view_map(ldm->target, qk_f(c, scale - 1), pyr->cams[m], kp);
+    QK_CUDA(ctx, cudaMemsetAsync(ldm->splat, 0, off_w + ns * sizeof(float), st));
+    s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_splat(sa, st); });
+    if (s == QUARK_OK) s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_composite_views(sa, st); });
+    if (s != QUARK_OK) return s;
+    RefineArgs ra{};
+    ra.feat = feat;
+    ra.rend = sa.out;
+    ra.V = V;
+    ra.C = C;
+    ra.h = h;
+    ra.w = w;
+    ra.hr = hr;
+    ra.wr = wr;
+    ra.ratio = kp / k;
+    ra.wr_b = ctx->wdev + ctx->off_upd[scale] + ConvLayout{C}.total();
+    ra.out = ldm->upd_in;
+    s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_refine_add(ra, bf16, st); });
+    if (s != QUARK_OK) return s;
+    // the Update Block's residual CNN block on the V view planes
+    ConvArgs cv{};
+    cv.in = ldm->upd_in;
+    cv.out = ldm->delta;
+    cv.L = V;
+    cv.H = h;
+    cv.W = w;
+    cv.dp = dp;
+    cv.w = ctx->wdev + ctx->off_upd[scale];
+    cv.wtc = ctx->wupd ? (const uint8_t*)ctx->wupd + scale * ctx->wtc_step_bytes : nullptr;
+    cv.err = ctx->dev_err;
+    s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_conv_block(cv, C, bf16, st); });
+    if (s != QUARK_OK) return s;
+    ldm->delta_ok = true;
+    return QUARK_OK;
+}
+
 // Whether the next step after `j` that samples the views reuses the depths step j samples at.
 static bool next_reuses(const quark_config& c, int j) {
     for (int i = j + 1; i < c.n_scales; ++i)
@@ -929,7 +1083,12 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
         // reused depths (Update & Fuse steps with several fusion blocks sample once)
         aa.depth_in = c.reuse_depth[scale] ? ldm->dsamp : nullptr;
         aa.depth_out = !c.reuse_depth[scale] && next_reuses(c, scale) ? ldm->dsamp : nullptr;
-        if (c.ray_encoding) {
+        // render-and-refine: this step renders the views and forms new update features, or it
+        // reuses those of its Update & Fuse step
+        const bool refining = qk_refines(c, scale) && !prev_override;
+        if (!c.reuse_depth[scale] && !refining) ldm->delta_ok = false;
+        const bool from_delta = c.render_refine && (refining || ldm->delta_ok);
+        if (c.ray_encoding && !(from_delta && !refining)) {
             // gamma_k (Sec. 3.2.1) added to this level of the first V_use views, into LDM scratch
             int k0 = 1;
             for (int j = 0; j < c.n_scales; ++j) k0 = std::max(k0, c.k[j]);
@@ -964,6 +1123,11 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
             if (s != QUARK_OK) return s;
             aa.feat = ldm->ray_feat;
         }
+        if (refining) {
+            s = refine_step(ctx, pyr, V_use, scale, ldm, prev, Hp, Wp, aa.feat, st);
+            if (s != QUARK_OK) return s;
+        }
+        if (from_delta) aa.feat = ldm->delta;
         if (c.attn_mode == QUARK_ATTN_STANDARD) {
             // keys and values (and on the last step the features) projected in image space, then sampled
             const size_t texels = (size_t)V_use * aa.fh * aa.fw;

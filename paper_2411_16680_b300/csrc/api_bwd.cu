@@ -21,6 +21,7 @@ static quark_status check_stage(quark_ctx* ctx, const quark_pyramid* pyr, const 
         return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage covers one-to-many attention");
     if (ctx->cfg.ray_encoding) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage runs without the ray encoding");
     if (!qk_uniform(ctx->cfg)) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage takes the uniform schedule only");
+    if (ctx->cfg.render_refine) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage runs without render-and-refine");
     if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     return QUARK_OK;
@@ -32,7 +33,8 @@ extern "C" quark_status quark_step_input(quark_ctx* ctx, quark_ldm* ldm, int sca
     if (c.precision != QUARK_FP32) return qk_fail(ctx, QUARK_EINVAL, "FP32 form only");
     if (c.attn_mode != QUARK_ATTN_ONE_TO_MANY) return qk_fail(ctx, QUARK_EINVAL, "one-to-many attention only");
     if (c.ray_encoding) return qk_fail(ctx, QUARK_EINVAL, "no ray encoding in the differentiable stage");
-    if (!qk_uniform(c)) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage takes the uniform schedule only");
+    if (!qk_uniform(c) || c.render_refine)
+        return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage takes the uniform schedule without render-and-refine");
     if (scale < 1 || scale >= c.n_scales || ldm->done != scale - 1)
         return qk_fail(ctx, QUARK_EINVAL, "step %d's input needs step %d done (latest: %d)", scale, scale - 1, ldm->done);
     cudaSetDevice(ctx->device);

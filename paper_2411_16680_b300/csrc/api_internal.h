@@ -11,7 +11,7 @@
 #include "quark.h"
 #include "quark_internal.cuh"
 
-enum KernelFamily { KF_ENCODE = 0, KF_COLLAPSE, KF_ATTEND, KF_CONV, KF_RENDER, KF_BACKWARD, KF_COUNT };
+enum KernelFamily { KF_ENCODE = 0, KF_COLLAPSE, KF_ATTEND, KF_CONV, KF_RENDER, KF_BACKWARD, KF_REFINE, KF_COUNT };
 
 struct PendingTiming {
     KernelFamily fam;
@@ -32,6 +32,9 @@ struct quark_ctx {
     size_t off_collapse[QUARK_MAX_SCALES] = {};
     size_t off_std[QUARK_MAX_SCALES] = {};  // standard attention weights (StdLayout), or (size_t)-1
     size_t off_ray[4] = {};                   // ray encoding projection per level index, or (size_t)-1
+    size_t off_upd[QUARK_MAX_SCALES] = {};    // Update Block (ConvLayout, then W_r, b_r), or (size_t)-1
+    void* wupd = nullptr;                     // BF16 form: Update Block convs packed as tcgen05 B operands
+    size_t wupd_bytes = 0;
     // BF16 form: conv weights packed as tcgen05 B operands, per step W1 then W2
     void* wtc = nullptr;
     size_t wtc_bytes = 0;
@@ -91,6 +94,14 @@ struct quark_ldm {
     float* beta = nullptr;
     size_t beta_bytes = 0;
     float* dsamp = nullptr;  // [L][H][W] depths of the latest sampling step, kept for reuse_depth
+    // render-and-refine scratch: splat sums, rendered views, Update Block input and output
+    void* splat = nullptr;
+    size_t splat_bytes = 0;
+    void* upd_in = nullptr;
+    size_t upd_in_bytes = 0;
+    void* delta = nullptr;  // [V][h][w][C] update features of the current Update & Fuse step
+    size_t delta_bytes = 0;
+    bool delta_ok = false;  // delta holds the current Update & Fuse step's features
     int Hs[QUARK_MAX_SCALES] = {}, Ws[QUARK_MAX_SCALES] = {};  // LDM grid of each step
     void* kv = nullptr;  // standard attention: the projected keys / values of the step's level
     size_t kv_bytes = 0;
@@ -117,6 +128,7 @@ quark_status qk_validate_config(const quark_config* c);
 int qk_heads(const quark_config& c, int j);     // attention heads of step j, 0 = no attention
 double qk_f(const quark_config& c, int j);      // LDM grid factor of step j
 bool qk_uniform(const quark_config& c);         // no per-step heads, grid factors or reuse
+bool qk_refines(const quark_config& c, int j);  // step j renders the views and runs the Update Block
 bool qk_grid(const quark_config& c, int j, int width, int height, int& H, int& W);  // false: not divisible
 quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what);
 quark::ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m);

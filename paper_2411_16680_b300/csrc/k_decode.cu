@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(256) decode_kernel(const DecodeArgs a) {
     a.colour[3 * el + 2] = sigmoidf_(rgb[2]);
     a.alpha[el] = sigmoidf_(s);
     a.depth[el] = depth_from_logit(t, li, a.L, a.dp);
-    a.t_raw[pix * a.L + li] = t;
-    a.s_raw[pix * a.L + li] = s;
+    if (a.t_raw) a.t_raw[pix * a.L + li] = t;
+    if (a.s_raw) a.s_raw[pix * a.L + li] = s;
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st) {

@@ -54,6 +54,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
         return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs one-to-many attention only (use quark_update_fuse)");
     if (ctx->cfg.ray_encoding)
         return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs without the ray encoding (use quark_update_fuse)");
+    if (ctx->cfg.render_refine)
+        return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step runs without render-and-refine (use quark_update_fuse)");
     if (!qk_uniform(ctx->cfg))
         return qk_fail(ctx, QUARK_EINVAL, "the no-alloc step takes the uniform schedule only (use quark_update_fuse)");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");

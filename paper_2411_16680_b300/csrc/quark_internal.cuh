@@ -85,8 +85,30 @@ struct DecodeArgs {
     float* colour;     // [L][H][W][3]
     float* alpha;      // [L][H][W]
     float* depth;      // [L][H][W]
-    float* t_raw;      // [H][W][L]
-    float* s_raw;      // [H][W][L]
+    float* t_raw;      // [H][W][L], or NULL (not written)
+    float* s_raw;      // [H][W][L], or NULL (not written)
+};
+
+// Render-and-refine (Sec. 3.2.2 "Decoding and rendering the intermediate LDM", Eq.
+// overcomposite-result; the Update Block): the intermediate LDM decoded from the volume entering
+// a step, splatted into every input view and over-composited there.
+struct SplatArgs {
+    const float* colour;  // [L][H][W][3] appearance of the intermediate LDM
+    const float* alpha;   // [L][H][W] density
+    const float* depth;   // [L][H][W]
+    int L, H, W, V;       // the LDM grid (previous step's) and the views
+    int h, w;             // the views' grid at the rendering level
+    float4* acc;          // [V][L][h][w] bilinear-weighted sums of (colour, density)
+    float* wsum;          // [V][L][h][w] weight sums
+    float4* out;          // [V][h][w] rendered views: RGB and accumulated alpha
+    Geometry geo;         // per view: LDM grid -> the view's grid at the rendering level
+};
+struct RefineArgs {
+    const void* feat;     // [V][h][w][C] level-k features (plus the ray encoding when on)
+    const float4* rend;   // [V][hr][wr] rendered views at the previous step's level
+    int V, C, h, w, hr, wr, ratio;  // ratio = h / hr (1 or 2)
+    const float* wr_b;    // W_r [4][C] then b_r [C]
+    void* out;            // [V][h][w][C] F' = F + up(I~) W_r + b_r (the Update Block's CNN input)
 };
 
 // Ray directional encoding of one step's pyramid level (Sec. 3.2.1).
@@ -174,5 +196,8 @@ cudaError_t launch_render(const RenderArgs& a, cudaStream_t st);
 cudaError_t launch_ray_coarse(const RayArgs& a, cudaStream_t st);
 cudaError_t launch_ray_add(const RayArgs& a, const void* feat, void* out, bool bf16, cudaStream_t st);
 cudaError_t launch_render_depth(const RenderArgs& a, float* depth, cudaStream_t st);
+cudaError_t launch_splat(const SplatArgs& a, cudaStream_t st);
+cudaError_t launch_composite_views(const SplatArgs& a, cudaStream_t st);
+cudaError_t launch_refine_add(const RefineArgs& a, bool bf16, cudaStream_t st);
 
 }  // namespace quark

@@ -39,7 +39,7 @@ class Config(ct.Structure):
     _fields_ = [("C", ct.c_int), ("heads", ct.c_int), ("n_scales", ct.c_int), ("k", ct.c_int * MAX_SCALES),
                 ("L", ct.c_int * MAX_SCALES), ("near_m", ct.c_float), ("far_m", ct.c_float),
                 ("precision", ct.c_int), ("attn_mode", ct.c_int), ("ray_encoding", ct.c_int),
-                ("scale_heads", ct.c_int * MAX_SCALES), ("ldm_f", ct.c_float * MAX_SCALES),
+                ("render_refine", ct.c_int), ("scale_heads", ct.c_int * MAX_SCALES), ("ldm_f", ct.c_float * MAX_SCALES),
                 ("reuse_depth", ct.c_int * MAX_SCALES), ("hbm_cap_bytes", ct.c_size_t)]
 
 
@@ -54,7 +54,9 @@ class Weights(ct.Structure):
                 ("w_d", _FP), ("b_d", ct.c_float), ("w_sigma", _FP), ("b_sigma", ct.c_float),
                 ("W_a", _FP), ("b_a", _FP), ("W_beta", _FP),
                 ("Wq_std", _PER), ("Wk_std", _PER), ("Wv_std", _PER), ("Wo_std", _PER),
-                ("W_ray", _FP * 4)]
+                ("W_ray", _FP * 4),
+                ("upd_Wr", _PER), ("upd_br", _PER), ("upd_g", _PER), ("upd1_w", _PER), ("upd1_b", _PER),
+                ("upd2_w", _PER), ("upd2_b", _PER)]
 
 
 class ServeConfig(ct.Structure):
@@ -178,6 +180,7 @@ def make_config(cfg, hbm_cap_bytes: int = 0) -> Config:
     c.precision = cfg.precision
     c.attn_mode = cfg.attn_mode
     c.ray_encoding = getattr(cfg, "ray_encoding", 0)
+    c.render_refine = getattr(cfg, "render_refine", 0)
     # model schedule: per-step heads (0 in the workload = a block without attention, -1 here),
     # LDM grid factors and reused depths; unset = the uniform schedule (zero-filled)
     if getattr(cfg, "scale_heads", None) is not None:
@@ -299,6 +302,10 @@ class Context:
             if f"col_w1_{j}" in W:
                 w.col_w1[j], w.col_b1[j] = p(f"col_w1_{j}"), p(f"col_b1_{j}")
                 w.col_w2[j], w.col_b2[j] = p(f"col_w2_{j}"), p(f"col_b2_{j}")
+            if f"upd_Wr_{j}" in W:  # render-and-refine: the step's Update Block
+                w.upd_Wr[j], w.upd_br[j], w.upd_g[j] = p(f"upd_Wr_{j}"), p(f"upd_br_{j}"), p(f"upd_g_{j}")
+                w.upd1_w[j], w.upd1_b[j] = p(f"upd1_w_{j}"), p(f"upd1_b_{j}")
+                w.upd2_w[j], w.upd2_b[j] = p(f"upd2_w_{j}"), p(f"upd2_b_{j}")
             if f"Wq_std_{j}" in W:
                 w.Wq_std[j], w.Wk_std[j] = p(f"Wq_std_{j}"), p(f"Wk_std_{j}")
                 w.Wv_std[j], w.Wo_std[j] = p(f"Wv_std_{j}"), p(f"Wo_std_{j}")
