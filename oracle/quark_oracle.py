@@ -97,9 +97,11 @@ def grow(r: Rect, n: int, H: int, W: int) -> Rect:
 # Cameras and the back-projection geometry (Sec. 3.1, operator P^T)
 # ---------------------------------------------------------------------------------------------
 
-def scaled_K(cam, k: float) -> np.ndarray:
-    """Intrinsics of a grid k times coarser than the camera's own pixels."""
-    return np.diag([1.0 / k, 1.0 / k, 1.0]) @ cam.K
+def scaled_K(cam, k) -> np.ndarray:
+    """Intrinsics of a grid k times coarser than the camera's own pixels; k is one factor, or
+    (k_rows, k_cols) for a grid whose factors differ along the two axes."""
+    ky, kx = (k, k) if np.isscalar(k) else k
+    return np.diag([1.0 / kx, 1.0 / ky, 1.0]) @ cam.K
 
 
 def unproject(ys, xs, d, K_t, cam_t):
@@ -152,12 +154,14 @@ def resize_taps(dst, ratio, n_src):
     return np.clip(i0, 0, n_src - 1), np.clip(i0 + 1, 0, n_src - 1), w1
 
 
-def resize_rect(src: np.ndarray, src_rect: Rect, H_src: int, W_src: int, ratio: int, out_rect: Rect):
-    """Bilinear resize (edge clamp) of src [..., h, w, C] held on src_rect, evaluated on out_rect."""
+def resize_rect(src: np.ndarray, src_rect: Rect, H_src: int, W_src: int, ratio, out_rect: Rect):
+    """Bilinear resize (edge clamp) of src [..., h, w, C] held on src_rect, evaluated on out_rect;
+    ratio is one factor or (rows, columns)."""
+    ry, rx = (ratio, ratio) if np.isscalar(ratio) else ratio
     ys = np.arange(out_rect[0], out_rect[1])
     xs = np.arange(out_rect[2], out_rect[3])
-    y0, y1, wy = resize_taps(ys, ratio, H_src)
-    x0, x1, wx = resize_taps(xs, ratio, W_src)
+    y0, y1, wy = resize_taps(ys, ry, H_src)
+    x0, x1, wx = resize_taps(xs, rx, W_src)
     for a in (y0, y1):
         assert a.min() >= src_rect[0] and a.max() < src_rect[1], "resize source rect too small"
     for a in (x0, x1):
@@ -403,7 +407,7 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
     or, with render-and-refine, the Update Block's output (delta_fetch, one fetcher per view)."""
     f64 = lambda a: np.asarray(a, np.float64)
     k, L = cfg.scales[j]          # pyramid level of the views, layers
-    f = cfg.f_of(j)               # LDM grid factor relative to the output
+    f = cfg.fyx_of(j)             # LDM grid factors (rows, columns) relative to the output
     _, H, Wd = cfg.ldm_shape(j)
     heads = cfg.heads_of(j)
     C = cfg.C
@@ -424,7 +428,8 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
                                 f64(W[f"col_w2_{j}"]), f64(W[f"col_b2_{j}"]))
         else:
             assert Lp == L
-        ratio = int(round(cfg.f_of(j - 1) / f))
+        ratio = H // Hp  # 1, or 2 for a x2 upsample (both axes)
+        assert ratio * Hp == H and ratio * Wp == Wd
         V_in = resize_rect(Vp, rp, Hp, Wp, ratio, rect_attn)
         if cfg.reuse_of(j) or heads == 0:
             # the depths of the latest scale that sampled (same grid and layers): reused for the
@@ -483,7 +488,7 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
 def render_rect(cfg, scene, last: StepResult, out_rect: Rect, return_layers: bool = False):
     """RGBA of the novel view on out_rect (full output resolution)."""
     L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
-    s = cfg.upsample_s
+    s = cfg.upsample_syx
     rect_beta = last.rect_attn
     ob = (last.rect_out[0] - rect_beta[0], last.rect_out[2] - rect_beta[2])
     hb, wb = last.V_out.shape[1], last.V_out.shape[2]
@@ -531,7 +536,7 @@ def render_depth_rect(cfg, last: StepResult, out_rect: Rect):
     back, D += T alpha_l d_l and T *= 1 - alpha_l, with 0 behind the last layer.  Reading: the
     over-composite itself, not normalised by the accumulated alpha."""
     L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
-    s = cfg.upsample_s
+    s = cfg.upsample_syx
     t_up = resize_rect(last.t[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
     s_up = resize_rect(last.s[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
     ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
@@ -670,7 +675,7 @@ def refine_features(cfg, W, scene, fetchers, j, prev: StepResult):
     if Lp == 2 * L:
         Vc = layer_collapse(Vc, f64(W[f"col_w1_{j}"]), f64(W[f"col_b1_{j}"]), f64(W[f"col_w2_{j}"]),
                             f64(W[f"col_b2_{j}"]))
-    It = render_to_views(cfg, W, scene, Vc, cfg.f_of(j - 1), kp)
+    It = render_to_views(cfg, W, scene, Vc, cfg.fyx_of(j - 1), kp)
     out = []
     for m, lf in enumerate(fetchers[k]):
         lf.prepare([np.array([0, lf.h - 1])], [np.array([0, lf.w - 1])])  # the whole level (+ gamma)
@@ -686,11 +691,11 @@ def plan_rects(cfg, out_rect: Rect):
     """Windows each scale must compute so that out_rect of the final render is exact."""
     n = cfg.n_scales
     _, Hl, Wl = cfg.ldm_shape(n - 1)
-    s = cfg.upsample_s
+    sy, sx = cfg.upsample_syx
     ys = np.arange(out_rect[0], out_rect[1])
     xs = np.arange(out_rect[2], out_rect[3])
-    y0, y1, _ = resize_taps(ys, s, Hl)
-    x0, x1, _ = resize_taps(xs, s, Wl)
+    y0, y1, _ = resize_taps(ys, sy, Hl)
+    x0, x1, _ = resize_taps(xs, sx, Wl)
     need = (int(y0.min()), int(y1.max()) + 1, int(x0.min()), int(x1.max()) + 1)
     rect_out = [None] * n
     rect_attn = [None] * n
@@ -699,8 +704,8 @@ def plan_rects(cfg, out_rect: Rect):
         rect_out[j] = need
         rect_attn[j] = grow(need, 2, H, W)
         if j > 0:
-            ratio = int(round(cfg.f_of(j - 1) / cfg.f_of(j)))
             _, Hp, Wp = cfg.ldm_shape(j - 1)
+            ratio = H // Hp
             ys = np.arange(rect_attn[j][0], rect_attn[j][1])
             xs = np.arange(rect_attn[j][2], rect_attn[j][3])
             a0, a1, _ = resize_taps(ys, ratio, Hp)

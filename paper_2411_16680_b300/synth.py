@@ -65,6 +65,10 @@ class QuarkConfig:
     ldm_f: Optional[List[float]] = None
     reuse_depth: Optional[List[int]] = None
     render_refine: int = 0  # 1: update features from rendered input views (render-and-refine)
+    # aspect-adaptive LDM dims: the output size the grid factors are given for (e.g. 1920 x 1080);
+    # other outputs get grids of the same area per layer at their own aspect (None: off)
+    model_w: Optional[int] = None
+    model_h: Optional[int] = None
 
     @property
     def n_scales(self) -> int:
@@ -88,8 +92,29 @@ class QuarkConfig:
     def upsample_s(self) -> float:
         return self.f_of(self.n_scales - 1)
 
+    @property
+    def upsample_syx(self) -> Tuple[float, float]:
+        """Final upsample factors (rows, columns): out_h / H and out_w / W of the last grid."""
+        return self.fyx_of(self.n_scales - 1)
+
+    def fyx_of(self, j: int) -> Tuple[float, float]:
+        """Grid factors of step j along rows and columns: output size over grid size."""
+        _, H, W = self.ldm_shape(j)
+        return self.out_h / H, self.out_w / W
+
     def ldm_shape(self, j: int) -> Tuple[int, int, int]:
         L = self.scales[j][1]
+        if self.model_w:
+            # same area per layer as the model's grids, at the output's aspect (Sec. 4: the LDM
+            # keeps its pixel count for any output, the final upsample adapts); the coarsest grid
+            # is rounded, the finer ones are its x2 multiples
+            f0 = self.f_of(0)
+            area = (self.model_h / f0) * (self.model_w / f0)
+            aspect = self.out_w / self.out_h
+            h0 = max(1, int(np.floor(np.sqrt(area / aspect) + 0.5)))
+            w0 = max(1, int(np.floor(h0 * aspect + 0.5)))
+            m = int(round(f0 / self.f_of(j)))
+            return L, h0 * m, w0 * m
         f = self.f_of(j)
         H, W = int(round(self.out_h / f)), int(round(self.out_w / f))
         assert abs(H * f - self.out_h) < 1e-6 and abs(W * f - self.out_w) < 1e-6, "output not divisible by f"

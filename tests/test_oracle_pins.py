@@ -751,3 +751,50 @@ def test_zero_update_block_is_the_plain_pipeline():
     W2 = synth.make_weights(cfg, seed=3, sharp=True)
     c, _ = O.forward(cfg, W2, sc)
     assert np.abs(c - b).max() > 1e-3  # the rendered views do change the result
+
+
+# --------------------------------------------------------------------------------------------
+# Aspect-adaptive LDM dimensions: the same area per layer for any output aspect
+# --------------------------------------------------------------------------------------------
+
+def test_aspect_adaptive_grids_keep_the_area_per_layer():
+    """Sec. 4: the LDM keeps the model's number of pixels per layer whatever the output, and the
+    final upsample adapts.  Quark targets 1920x1080 (grids 36x64 .. 288x512)."""
+    q = synth.config_quark()
+    ad = lambda w, h: q.replace(model_w=1920, model_h=1080, out_w=w, out_h=h)
+    for w, h in [(1920, 1080), (1280, 720), (3840, 2160)]:
+        c = ad(w, h)
+        assert [c.ldm_shape(j) for j in range(24)] == [q.ldm_shape(j) for j in range(24)]
+        assert c.upsample_syx == (h / 288, w / 512)
+    # 4:3 outputs (the paper's 1024x768 and 2048x1536 benchmarks): coarsest grid 42x56 (2352 px,
+    # 4:3 exactly, against 36x64 = 2304), final 336x448; the upsample is 2.2857 or 4.5714 per axis
+    for w, h in [(1024, 768), (2048, 1536)]:
+        c = ad(w, h)
+        assert c.ldm_shape(0) == (24, 42, 56) and c.ldm_shape(23) == (6, 336, 448)
+        assert c.upsample_syx == (h / 336, w / 448)
+        assert abs(42 * 56 / 2304 - 1) < 0.03
+
+
+def test_scaled_intrinsics_per_axis():
+    """A grid with factors (ky, kx) maps a camera pixel (u, v) to (u / kx, v / ky)."""
+    cam = synth.make_camera(64, 48, 50.0, (0.1, 0.0, 0.0), target=(0.0, 0.0, 10.0), cx=31.0, cy=25.0)
+    rng = np.random.default_rng(4)
+    Xw = rng.uniform(-2, 2, (20, 3)) + np.array([0, 0, 8.0])
+    u1, v1, _ = O.project(Xw, O.scaled_K(cam, 1.0), cam)
+    u2, v2, _ = O.project(Xw, O.scaled_K(cam, (3.25, 3.125)), cam)
+    np.testing.assert_allclose(u2, u1 / 3.125, rtol=1e-13)
+    np.testing.assert_allclose(v2, v1 / 3.25, rtol=1e-13)
+
+
+def test_anisotropic_grids_window_exactly():
+    """An output whose aspect differs from the model's gets different factors along rows and
+    columns (here 3.25 and 3.125); windows of the output still equal the full frame."""
+    cfg = synth.config_quark(out_w=240, out_h=120, C=8).replace(model_w=240, model_h=120, out_w=200, out_h=130)
+    assert cfg.ldm_shape(0)[1:] == (5, 8) and cfg.ldm_shape(23)[1:] == (40, 64)
+    assert cfg.upsample_syx == (3.25, 3.125)
+    sc = synth.scene_quark(seed=8, V=2, W=128, H=80, out_w=200, out_h=130)
+    W = synth.make_weights(cfg, seed=8, sharp=True)
+    full, _ = O.forward(cfg, W, sc)
+    for rect in [(0, 9, 0, 13), (60, 71, 97, 120), (129, 130, 0, 200)]:
+        part, _ = O.forward(cfg, W, sc, rect)
+        np.testing.assert_allclose(part, full[rect[0]:rect[1], rect[2]:rect[3]], atol=1e-13)
