@@ -428,6 +428,8 @@ def main():
     ap.add_argument("--model", default="uniform", choices=["uniform", "quark", "quarkplus"],
                     help="uniform: the 4-scale 1080p workload; quark / quarkplus: the paper's Quark / Quark+ "
                          "model schedules (24 fusion steps, 480x288 / 720x432 views, 1080p output)")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="aspect-adaptive LDM dimensions: grids of the 1920x1080 model's area at the --size aspect")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=120.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -469,6 +471,9 @@ def main():
         base_cfg = synth.config_1080p().replace(out_w=sw, out_h=sh, attn_mode=attn_mode,
                                                 ray_encoding=int(args.ray))
     base_cfg = base_cfg.replace(render_refine=int(args.refine))
+    if args.adaptive:
+        base_cfg = base_cfg.replace(model_w=1920, model_h=1080)
+        workload += ", aspect-adaptive LDM (1920x1080 model area)"
     if not 1 <= args.views <= 64:
         ap.error("--views must be in 1..64")
     if quark_model:

@@ -106,6 +106,13 @@ typedef struct {
  *              (the conv block only: same grid and layers as step j-1, j > 0)
  *   ldm_f[j]   LDM grid factor relative to the target (0: k[j]); the target's width and height
  *              must be multiples of it (e.g. 30, 15, 7.5, 3.75 for 1920 x 1080)
+ *   model_width, model_height  aspect-adaptive LDM dimensions (Sec. 4): 0, 0 = off; else the
+ *              output size the grid factors are given for (e.g. 1920 x 1080).  An LDM for any other
+ *              output keeps the model's area per layer at the output's own aspect: step 0's grid is
+ *              h0 = floor(sqrt(A / a) + 0.5), w0 = floor(h0 a + 0.5) (A = the model's step-0 grid
+ *              area, a = output width / height), step j's grid is (h0, w0) x f_0 / f_j, and the
+ *              target maps onto a grid with the factors width / W_j and height / H_j, which may
+ *              differ (the final upsample too).  The output need not be divisible by anything.
  *   reuse_depth[j]  1: sample the views at the depths the latest sampling step used instead of
  *              the depths decoded from this step's input (one set of update features per Update
  *              & Fuse step); needs the same grid and layers back to that step.  0: decode.
@@ -123,6 +130,7 @@ typedef struct {
     int scale_heads[QUARK_MAX_SCALES];
     float ldm_f[QUARK_MAX_SCALES];
     int reuse_depth[QUARK_MAX_SCALES];
+    int model_width, model_height;
     size_t hbm_cap_bytes;
 } quark_config;
 

@@ -168,12 +168,25 @@ int qk_heads(const quark_config& c, int j) {
 double qk_f(const quark_config& c, int j) { return c.ldm_f[j] > 0.f ? (double)c.ldm_f[j] : (double)c.k[j]; }
 
 bool qk_uniform(const quark_config& c) {
+    if (c.model_width || c.model_height) return false;
     for (int j = 0; j < QUARK_MAX_SCALES; ++j)
         if (c.scale_heads[j] != 0 || c.ldm_f[j] != 0.f || c.reuse_depth[j] != 0) return false;
     return true;
 }
 
 bool qk_grid(const quark_config& c, int j, int width, int height, int& H, int& W) {
+    if (c.model_width > 0) {
+        // aspect-adaptive: the model's step-0 grid area at the output's aspect, then x2 multiples
+        const double f0 = qk_f(c, 0);
+        const double area = (c.model_height / f0) * (c.model_width / f0);
+        const double aspect = (double)width / height;
+        const int h0 = std::max(1, (int)std::floor(std::sqrt(area / aspect) + 0.5));
+        const int w0 = std::max(1, (int)std::floor(h0 * aspect + 0.5));
+        const int m = (int)std::lround(f0 / qk_f(c, j));
+        H = h0 * m;
+        W = w0 * m;
+        return true;
+    }
     const double f = qk_f(c, j);
     H = (int)std::lround(height / f);
     W = (int)std::lround(width / f);
@@ -237,6 +250,8 @@ quark_status qk_validate_config(const quark_config* c) {
     if (c->ray_encoding != 0 && c->ray_encoding != 1) return qk_fail(nullptr, QUARK_EINVAL, "ray_encoding must be 0 or 1");
     if (c->render_refine != 0 && c->render_refine != 1)
         return qk_fail(nullptr, QUARK_EINVAL, "render_refine must be 0 or 1");
+    if (c->model_width < 0 || c->model_height < 0 || (c->model_width > 0) != (c->model_height > 0))
+        return qk_fail(nullptr, QUARK_EINVAL, "model_width and model_height must both be 0 or both positive");
     return QUARK_OK;
 }
 
@@ -598,8 +613,8 @@ ViewMap qk_ray_map(const quark_camera& tgt, const quark_camera& view, double k0)
     return m;
 }
 
-ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m) {
-    double Kt_inv[9] = {k_t / tgt.fx, 0, -tgt.cx / tgt.fx, 0, k_t / tgt.fy, -tgt.cy / tgt.fy, 0, 0, 1};
+ViewMap qk_view_map(const quark_camera& tgt, double k_tx, double k_ty, const quark_camera& view, double k_m) {
+    double Kt_inv[9] = {k_tx / tgt.fx, 0, -tgt.cx / tgt.fx, 0, k_ty / tgt.fy, -tgt.cy / tgt.fy, 0, 0, 1};
     double Km[9] = {view.fx / k_m, 0, view.cx / k_m, 0, view.fy / k_m, view.cy / k_m, 0, 0, 1};
     double Rrel[9] = {0};  // R_m R_t^T
     for (int i = 0; i < 3; ++i)
@@ -950,7 +965,9 @@ static quark_status refine_step(quark_ctx* ctx, const quark_pyramid* pyr, int V,
     sa.acc = (float4*)ldm->splat;
     sa.wsum = (float*)((uint8_t*)ldm->splat + off_w);
     sa.out = (float4*)((uint8_t*)ldm->splat + off_r);
-    for (int m = 0; m < V; ++m) sa.geo.v[m] = qk_view_map(ldm->target, qk_f(c, scale - 1), pyr->cams[m], kp);
+    for (int m = 0; m < V; ++m)
+        sa.geo.v[m] = qk_view_map(ldm->target, (double)ldm->target.width / Wp, (double)ldm->target.height / Hp,
+                                  pyr->cams[m], kp);
     QK_CUDA(ctx, cudaMemsetAsync(ldm->splat, 0, off_w + ns * sizeof(float), st));
     s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_splat(sa, st); });
     if (s == QUARK_OK) s = qk_launch(ctx, st, KF_REFINE, [&] { return launch_composite_views(sa, st); });
@@ -1057,7 +1074,7 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
             if (s != QUARK_OK) return s;
             prev = ldm->collapsed;
         }
-        tr = same_f(qk_f(c, scale - 1), qk_f(c, scale)) ? TR_SAME : TR_UP2;
+        tr = ldm->Hs[scale] == Hp ? TR_SAME : TR_UP2;  // the grid keeps its size or doubles
     }
 
     // ---- sample-attend ----
@@ -1079,7 +1096,9 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
         aa.beta = last ? ldm->beta : nullptr;
         aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + ctx->off_wat[scale] : nullptr;
         aa.err = ctx->dev_err;
-        for (int m = 0; m < V_use; ++m) aa.geo.v[m] = qk_view_map(ldm->target, qk_f(c, scale), pyr->cams[m], k);
+        for (int m = 0; m < V_use; ++m)
+            aa.geo.v[m] = qk_view_map(ldm->target, (double)ldm->target.width / W, (double)ldm->target.height / H,
+                                      pyr->cams[m], k);
         // reused depths (Update & Fuse steps with several fusion blocks sample once)
         aa.depth_in = c.reuse_depth[scale] ? ldm->dsamp : nullptr;
         aa.depth_out = !c.reuse_depth[scale] && next_reuses(c, scale) ? ldm->dsamp : nullptr;
@@ -1229,13 +1248,14 @@ quark_status qk_render(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid
     ra.V = V_use;
     ra.Hl = l->Hs[n];
     ra.Wl = l->Ws[n];
-    ra.s = (float)qk_f(c, n);
+    ra.sx = (float)((double)l->target.width / l->Ws[n]);
+    ra.sy = (float)((double)l->target.height / l->Hs[n]);
     ra.Hout = l->target.height;
     ra.Wout = l->target.width;
     ra.Hi = pyr->H;
     ra.Wi = pyr->W;
     ra.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
-    for (int m = 0; m < V_use; ++m) ra.geo.v[m] = qk_view_map(l->target, 1.0, pyr->cams[m], 1.0);
+    for (int m = 0; m < V_use; ++m) ra.geo.v[m] = qk_view_map(l->target, 1.0, 1.0, pyr->cams[m], 1.0);
     const size_t out_bytes = (size_t)ra.Hout * ra.Wout * sizeof(float4);
     if (host_out && l->out_bytes < out_bytes) {
         for (auto it = l->bufs.begin(); it != l->bufs.end(); ++it)
@@ -1271,7 +1291,8 @@ extern "C" quark_status quark_render_depth(quark_ctx* ctx, const quark_ldm* ldm,
     ra.L = c.L[n];
     ra.Hl = l->Hs[n];
     ra.Wl = l->Ws[n];
-    ra.s = (float)qk_f(c, n);
+    ra.sx = (float)((double)l->target.width / l->Ws[n]);
+    ra.sy = (float)((double)l->target.height / l->Hs[n]);
     ra.Hout = l->target.height;
     ra.Wout = l->target.width;
     ra.dp = {(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};

@@ -148,13 +148,13 @@ extern "C" quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid
     ra.V = V;
     ra.Hl = H;
     ra.Wl = W;
-    ra.s = k;
+    ra.sx = ra.sy = (float)k;
     ra.Hout = ldm->target.height;
     ra.Wout = ldm->target.width;
     ra.Hi = pyr->H;
     ra.Wi = pyr->W;
     ra.dp = dp;
-    for (int m = 0; m < V; ++m) ra.geo.v[m] = qk_view_map(ldm->target, 1.0, pyr->cams[m], 1.0);
+    for (int m = 0; m < V; ++m) ra.geo.v[m] = qk_view_map(ldm->target, 1.0, 1.0, pyr->cams[m], 1.0);
     auto L_ = [&](auto fn) { return qk_launch(ctx, st, KF_BACKWARD, fn); };
     if ((s = L_([&] { return launch_render_bwd(ra, dl_drgb, dt_raw, ds_raw, dbeta, st); })) != QUARK_OK) return s;
     // decode adjoint -> G = dL/dV_out
@@ -222,7 +222,7 @@ extern "C" quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid
     ab.Wq = wa + al.wq();
     ab.Wo = wa + al.wo();
     ab.Wb = wa + al.wb();
-    for (int m = 0; m < V; ++m) ab.geo.v[m] = qk_view_map(ldm->target, k, pyr->cams[m], k);
+    for (int m = 0; m < V; ++m) ab.geo.v[m] = qk_view_map(ldm->target, k, k, pyr->cams[m], k);
     ab.dv_in = dv_in;
     ab.dfeat = dfeat;
     ab.x_out = Xn;

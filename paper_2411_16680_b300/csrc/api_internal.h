@@ -131,7 +131,9 @@ bool qk_uniform(const quark_config& c);         // no per-step heads, grid facto
 bool qk_refines(const quark_config& c, int j);  // step j renders the views and runs the Update Block
 bool qk_grid(const quark_config& c, int j, int width, int height, int& H, int& W);  // false: not divisible
 quark_status qk_validate_camera(const quark_ctx* ctx, const quark_camera& c, const char* what);
-quark::ViewMap qk_view_map(const quark_camera& tgt, double k_t, const quark_camera& view, double k_m);
+// View map from a target grid with factors (k_tx, k_ty) (target pixels per grid pixel along x, y)
+// to view `view`'s level-k_m grid.
+quark::ViewMap qk_view_map(const quark_camera& tgt, double k_tx, double k_ty, const quark_camera& view, double k_m);
 quark::ViewMap qk_ray_map(const quark_camera& tgt, const quark_camera& view, double k0);
 size_t qk_ldm_bytes(const quark_config& c, int width, int height, int V, bool host_out);
 quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_beta, cudaStream_t async_stream,

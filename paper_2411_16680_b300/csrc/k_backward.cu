@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(BW_THREADS) render_bwd_kernel(const RenderArgs
     const int L = a.L, V = a.V;
     int y0, y1, x0, x1;
     float wy, wx;
-    resize_taps(Y, a.s, a.Hl, y0, y1, wy);
-    resize_taps(X, a.s, a.Wl, x0, x1, wx);
+    resize_taps(Y, a.sy, a.Hl, y0, y1, wy);
+    resize_taps(X, a.sx, a.Wl, x0, x1, wx);
     const size_t q[4] = {(size_t)y0 * a.Wl + x0, (size_t)y0 * a.Wl + x1, (size_t)y1 * a.Wl + x0,
                          (size_t)y1 * a.Wl + x1};
     const float qw[4] = {(1 - wy) * (1 - wx), (1 - wy) * wx, wy * (1 - wx), wy * wx};

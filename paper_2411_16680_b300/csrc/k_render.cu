@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) 
     const int L = a.L, V = a.V;
     const float pxc = X + 0.5f, pyc = Y + 0.5f;
     float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
-    if (a.s == 1) {
+    if (a.sx == 1.f && a.sy == 1.f) {
         // the LDM grid is the output grid: the upsample is the identity
         for (int li = L - 1; li >= 0; --li) {
             const float d = depth_from_logit(a.t_raw[idx * L + li], li, L, a.dp);
@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) 
     } else {
         int y0, y1, x0, x1;
         float wy, wx;
-        resize_taps(Y, a.s, a.Hl, y0, y1, wy);
-        resize_taps(X, a.s, a.Wl, x0, x1, wx);
+        resize_taps(Y, a.sy, a.Hl, y0, y1, wy);
+        resize_taps(X, a.sx, a.Wl, x0, x1, wx);
         const size_t q00 = (size_t)y0 * a.Wl + x0, q01 = (size_t)y0 * a.Wl + x1;
         const size_t q10 = (size_t)y1 * a.Wl + x0, q11 = (size_t)y1 * a.Wl + x1;
         auto up = [&](const float* f, size_t stride, size_t off) {
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(RD_THREADS) render_depth_kernel(const RenderAr
     const int X = (int)(idx % a.Wout), Y = (int)(idx / a.Wout);
     const int L = a.L;
     float D = 0.f, T = 1.f;
-    if (a.s == 1) {
+    if (a.sx == 1.f && a.sy == 1.f) {
         for (int li = L - 1; li >= 0; --li) {
             const float d = depth_from_logit(a.t_raw[idx * L + li], li, L, a.dp);
             const float al = sigmoidf_(a.s_raw[idx * L + li]);
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(RD_THREADS) render_depth_kernel(const RenderAr
     } else {
         int y0, y1, x0, x1;
         float wy, wx;
-        resize_taps(Y, a.s, a.Hl, y0, y1, wy);
-        resize_taps(X, a.s, a.Wl, x0, x1, wx);
+        resize_taps(Y, a.sy, a.Hl, y0, y1, wy);
+        resize_taps(X, a.sx, a.Wl, x0, x1, wx);
         const size_t q00 = (size_t)y0 * a.Wl + x0, q01 = (size_t)y0 * a.Wl + x1;
         const size_t q10 = (size_t)y1 * a.Wl + x0, q11 = (size_t)y1 * a.Wl + x1;
         auto up = [&](const float* f, int li) {

@@ -138,7 +138,7 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     aa.beta = last ? beta : nullptr;
     aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + ctx->off_wat[scale] : nullptr;
     aa.err = ctx->dev_err;
-    for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(*target, k, pyr->cams[m], k);
+    for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(*target, k, k, pyr->cams[m], k);
     e = launch_attend(aa, c.C, c.heads, tr, last, bf16, st);
     ctx->launches++;
     if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "attend launch: %s", cudaGetErrorString(e));

@@ -128,7 +128,7 @@ struct RenderArgs {
     const float* beta;   // [Hl][Wl][L][V]
     const float4* rgba;  // [V][Hi][Wi]
     int L, V, Hl, Wl, Hout, Wout, Hi, Wi;
-    float s;             // upsampling factor of the last LDM grid to the output (e.g. 3.75)
+    float sx, sy;        // upsampling factors of the last LDM grid to the output (e.g. 3.75)
     DepthParams dp;
     float4* out;         // [Hout][Wout]
     Geometry geo;

@@ -40,7 +40,8 @@ class Config(ct.Structure):
                 ("L", ct.c_int * MAX_SCALES), ("near_m", ct.c_float), ("far_m", ct.c_float),
                 ("precision", ct.c_int), ("attn_mode", ct.c_int), ("ray_encoding", ct.c_int),
                 ("render_refine", ct.c_int), ("scale_heads", ct.c_int * MAX_SCALES), ("ldm_f", ct.c_float * MAX_SCALES),
-                ("reuse_depth", ct.c_int * MAX_SCALES), ("hbm_cap_bytes", ct.c_size_t)]
+                ("reuse_depth", ct.c_int * MAX_SCALES), ("model_width", ct.c_int), ("model_height", ct.c_int),
+                ("hbm_cap_bytes", ct.c_size_t)]
 
 
 _FP = ct.POINTER(ct.c_float)
@@ -192,6 +193,8 @@ def make_config(cfg, hbm_cap_bytes: int = 0) -> Config:
     if getattr(cfg, "reuse_depth", None) is not None:
         for j, r in enumerate(cfg.reuse_depth):
             c.reuse_depth[j] = int(r)
+    if getattr(cfg, "model_w", None):
+        c.model_width, c.model_height = int(cfg.model_w), int(cfg.model_h)
     c.hbm_cap_bytes = hbm_cap_bytes
     return c
 

@@ -102,3 +102,33 @@ def test_quark_model_schedule_matches_oracle(precision, model):
         assert np.abs(out - ref).max() <= RGBA_TOL_BF16
         assert psnr(out, ref) >= PSNR_MIN_BF16
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("precision", [synth.PREC_FP32, synth.PREC_BF16])
+def test_aspect_adaptive_grids_match_oracle(precision):
+    """Aspect-adaptive LDM dimensions (Sec. 4): a 200 x 130 output of a schedule given for
+    240 x 120 gets grids 5x8 .. 40x64 (the model's area per layer at its aspect) and different
+    factors along rows and columns (final upsample 3.25 x 3.125)."""
+    cfg = synth.config_quark(out_w=240, out_h=120).replace(model_w=240, model_h=120, out_w=200, out_h=130,
+                                                           precision=precision)
+    assert cfg.upsample_syx == (3.25, 3.125)
+    W = synth.make_weights(cfg, seed=9, sharp=True)
+    scene = synth.scene_quark(seed=9, V=3, W=128, H=80, out_w=200, out_h=130)
+    ref, ref_steps = O.forward(cfg.replace(precision=synth.PREC_FP32), W, scene)
+    out, steps, _ = run_gpu(cfg, W, scene, per_step=precision == synth.PREC_FP32)
+    if precision == synth.PREC_FP32:
+        for j, (g, r) in enumerate(zip(steps, ref_steps)):
+            assert_rel(g["V_out"], r.V_out, REL_TOL_FP32, f"step {j} V_out")
+        assert np.abs(out - ref).max() <= RGBA_TOL_FP32
+    else:
+        assert np.abs(out - ref).max() <= RGBA_TOL_BF16
+        assert psnr(out, ref) >= PSNR_MIN_BF16
+
+
+def test_aspect_adaptive_at_the_model_aspect_is_bitwise_the_plain_schedule():
+    cfg = synth.config_quark(out_w=240, out_h=120)
+    W = synth.make_weights(cfg, seed=10, sharp=True)
+    scene = synth.scene_quark(seed=10, V=3, W=128, H=80, out_w=240, out_h=120)
+    a, _, _ = run_gpu(cfg, W, scene, per_step=False)
+    b, _, _ = run_gpu(cfg.replace(model_w=240, model_h=120), W, scene, per_step=False)
+    assert np.array_equal(a, b)
