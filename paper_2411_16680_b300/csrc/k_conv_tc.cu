@@ -180,21 +180,22 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
 
         // ---- conv1: TC_MID_H row blocks ----
         if (tid == 0) {
-            const uint32_t a0 = umma::smem_u32(s_in), b0 = umma::smem_u32(s_w1);
+            // descriptors built once; each MMA adds its constant start offset (in 16-byte units) to
+            // the start-address field, which stays below 2^14 for any shared-memory address
             constexpr uint32_t LBO_A = S::NPIX_IN * 16;
-            for (int r = 0; r < TC_MID_H; ++r) {
-                uint32_t acc = 0;
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3, dx = tap % 3;
+            const uint64_t ad0 = umma::desc(umma::smem_u32(s_in), LBO_A, 128);
+            const uint64_t bd0 = umma::desc(umma::smem_u32(s_w1), LBO_W, 128);
+#pragma unroll
+            for (int r = 0; r < TC_MID_H; ++r)
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
                     for (int kk = 0; kk < C / 16; ++kk) {
-                        const uint64_t ad = umma::desc(a0 + ((r + dy) * TC_IN_W + dx) * 16 + 2 * kk * LBO_A, LBO_A, 128);
-                        const uint64_t bd = umma::desc(b0 + tap * C * C * 2 + 2 * kk * LBO_W, LBO_W, 128);
-                        umma::mma_bf16(tmem + r * C, ad, bd, idesc, acc);
-                        acc = 1;
+                        const int dy = tap / 3, dx = tap % 3;
+                        const uint32_t ao = (((r + dy) * TC_IN_W + dx) * 16 + 2 * kk * LBO_A) >> 4;
+                        const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
+                        umma::mma_bf16(tmem + r * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
                     }
-                }
-            }
             umma::commit(mbar);
         }
         failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, TC_WAIT_NS));
@@ -226,21 +227,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
 
             // ---- conv2: TC_R row blocks, reusing TMEM columns ----
             if (tid == 0) {
-                const uint32_t a0 = umma::smem_u32(s_mid), b0 = umma::smem_u32(s_w2);
                 constexpr uint32_t LBO_A = S::NPIX_MID * 16;
-                for (int r = 0; r < TC_R; ++r) {
-                    uint32_t acc = 0;
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;
+                const uint64_t ad0 = umma::desc(umma::smem_u32(s_mid), LBO_A, 128);
+                const uint64_t bd0 = umma::desc(umma::smem_u32(s_w2), LBO_W, 128);
+#pragma unroll
+                for (int r = 0; r < TC_R; ++r)
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
                         for (int kk = 0; kk < C / 16; ++kk) {
-                            const uint64_t ad = umma::desc(a0 + ((r + dy) * TC_M + dx) * 16 + 2 * kk * LBO_A, LBO_A, 128);
-                            const uint64_t bd = umma::desc(b0 + tap * C * C * 2 + 2 * kk * LBO_W, LBO_W, 128);
-                            umma::mma_bf16(tmem + r * C, ad, bd, idesc, acc);
-                            acc = 1;
+                            const int dy = tap / 3, dx = tap % 3;
+                            const uint32_t ao = (((r + dy) * TC_M + dx) * 16 + 2 * kk * LBO_A) >> 4;
+                            const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
+                            umma::mma_bf16(tmem + r * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
                         }
-                    }
-                }
                 umma::commit(mbar);
             }
             failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, TC_WAIT_NS));
