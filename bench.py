@@ -287,8 +287,14 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     w = work[fam]
     bytes_per_launch = w["bytes"] / w["launches"]
     flops_per_launch = w["flops"] / w["launches"]
-    alu_bound = fam in ("conv_block",) or (fam == "attend" and cfg.precision == 0)
-    if fam == "conv_block":
+    if fam == "conv_block" and cfg.precision == 1:
+        # the BF16 conv block runs on the tensor cores: its FLOPs against the sustained BF16 peak
+        # (a kernel timed inside a long step)
+        achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        r = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+             "peak_source": f"{peaks['source']} BF16 dense, sustained"}
+    elif fam == "conv_block":
         achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
         peak = accounting.fp32_alu_peak_tflops(peaks["sm_max_mhz"])
         r = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
