@@ -1,7 +1,7 @@
 // Final render (Sec. 3.1 Eq. 1; Sec. 3.2.3 "Upsampling & Activation").  One thread per output
 // pixel: bilinear upsample by s of the raw depth / density / blend logits of the last LDM (a
 // direct read when s = 1), activation (Eq. depth_activation, sigmoid, softmax over views in one
-// online pass), back-projection of every input image onto each layer (zero padding), blend, and
+// online pass on ex2.approx), back-projection of every input image onto each layer (zero padding), blend, and
 // the over operator front to back (l = L nearest first): C += T alpha c, T *= (1 - alpha).
 // Output RGBA with A = 1 - T.
 #include "device_common.cuh"
@@ -22,28 +22,66 @@ __device__ __forceinline__ float4 sample_rgba(const float4* __restrict__ img, in
     return r;
 }
 
+// 2^x and 1/x on the special-function unit (PTX ex2.approx / rcp.approx, flush-to-zero): the blend
+// softmax runs in log2 units and the perspective divide is one reciprocal.
+__device__ __forceinline__ float rd_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rd_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Sec. 3.1 reprojection of the output pixel centre (px, py) at depth d into view m's image.
+__device__ __forceinline__ bool rd_reproject(const ViewMap& m, float px, float py, float d, float& u, float& v) {
+    const float X = fmaf(d, fmaf(m.A[0], px, fmaf(m.A[1], py, m.A[2])), m.b[0]);
+    const float Y = fmaf(d, fmaf(m.A[3], px, fmaf(m.A[4], py, m.A[5])), m.b[1]);
+    const float Z = fmaf(d, fmaf(m.A[6], px, fmaf(m.A[7], py, m.A[8])), m.b[2]);
+    if (!(Z > 1e-6f)) return false;
+    const float iz = rd_rcp(Z);
+    u = X * iz;
+    v = Y * iz;
+    return true;
+}
+
+constexpr float RD_LOG2E = 1.4426950408889634f;
+
 // One layer's contribution: blend-weighted colour of the V views with an online softmax over the
-// views (running maximum, rescaled sums), so the logits are read once.
-template <typename LogitFn>
-__device__ __forceinline__ void blend_layer(const RenderArgs& a, LogitFn logit, float pxc, float pyc, float d,
-                                            float& cr, float& cg, float& cb) {
+// views (running maximum, rescaled sums, in log2 units), so the logits are read once.  logit4(m0,
+// b) fills the logits of views m0 .. m0 + 3 (V a multiple of 4: one 16-byte load per LDM corner),
+// logit1(m) one view's.
+template <bool VEC4, typename Logit4, typename Logit1>
+__device__ __forceinline__ void blend_layer(const RenderArgs& a, Logit4 logit4, Logit1 logit1, float pxc, float pyc,
+                                            float d, float& cr, float& cg, float& cb) {
     const size_t img_stride = (size_t)a.Hi * a.Wi;
     float mx = -INFINITY, sum = 0.f, lr = 0.f, lg = 0.f, lb = 0.f;
-    for (int m = 0; m < a.V; ++m) {
-        const float b = logit(m);
+    auto view = [&](int m, float b) {
         const float mn = fmaxf(mx, b);
-        const float sc = expf(mx - mn), p = expf(b - mn);
+        const float sc = rd_ex2(mx - mn), p = rd_ex2(b - mn);
         sum = fmaf(sum, sc, p);
         lr *= sc;
         lg *= sc;
         lb *= sc;
         float u = 0.f, v = 0.f;
-        const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
+        const bool ok = rd_reproject(a.geo.v[m], pxc, pyc, d, u, v);
         const float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, ok, u, v);
         lr = fmaf(p, c.x, lr);
         lg = fmaf(p, c.y, lg);
         lb = fmaf(p, c.z, lb);
         mx = mn;
+    };
+    if constexpr (VEC4) {
+        for (int m0 = 0; m0 < a.V; m0 += 4) {
+            float b[4];
+            logit4(m0, b);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) view(m0 + i, b[i] * RD_LOG2E);
+        }
+    } else {
+        for (int m = 0; m < a.V; ++m) view(m, logit1(m) * RD_LOG2E);
     }
     const float is = 1.0f / sum;
     cr = lr * is;
@@ -51,6 +89,7 @@ __device__ __forceinline__ void blend_layer(const RenderArgs& a, LogitFn logit, 
     cb = lb * is;
 }
 
+template <bool VEC4>
 __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)a.Hout * a.Wout) return;
@@ -65,7 +104,16 @@ __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) 
             const float al = sigmoidf_(a.s_raw[idx * L + li]);
             const float* bl = a.beta + (idx * L + li) * V;
             float r, g, b;
-            blend_layer(a, [&](int m) { return __ldg(bl + m); }, pxc, pyc, d, r, g, b);
+            blend_layer<VEC4>(
+                a,
+                [&](int m0, float (&o)[4]) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(bl + m0));
+                    o[0] = t.x;
+                    o[1] = t.y;
+                    o[2] = t.z;
+                    o[3] = t.w;
+                },
+                [&](int m) { return __ldg(bl + m); }, pxc, pyc, d, r, g, b);
             const float w = T * al;
             cr = fmaf(w, r, cr);
             cg = fmaf(w, g, cg);
@@ -89,7 +137,23 @@ __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) 
             const float al = sigmoidf_(up(a.s_raw, L, li));
             const size_t bstride = (size_t)L * V, boff = (size_t)li * V;
             float r, g, b;
-            blend_layer(a, [&](int m) { return up(a.beta, bstride, boff + m); }, pxc, pyc, d, r, g, b);
+            blend_layer<VEC4>(
+                a,
+                [&](int m0, float (&o)[4]) {
+                    const float4 t00 = __ldg(reinterpret_cast<const float4*>(a.beta + q00 * bstride + boff + m0));
+                    const float4 t01 = __ldg(reinterpret_cast<const float4*>(a.beta + q01 * bstride + boff + m0));
+                    const float4 t10 = __ldg(reinterpret_cast<const float4*>(a.beta + q10 * bstride + boff + m0));
+                    const float4 t11 = __ldg(reinterpret_cast<const float4*>(a.beta + q11 * bstride + boff + m0));
+                    auto lerp2 = [&](float v00, float v01, float v10, float v11) {
+                        const float top = v00 * (1 - wx) + v01 * wx, bot = v10 * (1 - wx) + v11 * wx;
+                        return top * (1 - wy) + bot * wy;
+                    };
+                    o[0] = lerp2(t00.x, t01.x, t10.x, t11.x);
+                    o[1] = lerp2(t00.y, t01.y, t10.y, t11.y);
+                    o[2] = lerp2(t00.z, t01.z, t10.z, t11.z);
+                    o[3] = lerp2(t00.w, t01.w, t10.w, t11.w);
+                },
+                [&](int m) { return up(a.beta, bstride, boff + m); }, pxc, pyc, d, r, g, b);
             const float w = T * al;
             cr = fmaf(w, r, cr);
             cg = fmaf(w, g, cg);
@@ -146,7 +210,10 @@ cudaError_t launch_render_depth(const RenderArgs& a, float* depth, cudaStream_t 
 
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st) {
     const size_t n = (size_t)a.Hout * a.Wout;
-    render_kernel<<<(unsigned)((n + RD_THREADS - 1) / RD_THREADS), RD_THREADS, 0, st>>>(a);
+    const unsigned grid = (unsigned)((n + RD_THREADS - 1) / RD_THREADS);
+    // V a multiple of 4: a pixel's logits of 4 views are 16 contiguous, 16-byte-aligned bytes
+    if (a.V % 4 == 0) render_kernel<true><<<grid, RD_THREADS, 0, st>>>(a);
+    else render_kernel<false><<<grid, RD_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 
