@@ -1,13 +1,16 @@
 // Layer Collapse of the BF16 form on tcgen05 tensor cores (Sec. 3.2.2): each pair (l = 2j-1, 2j)
 // of the previous step's volume becomes 0.5 (a + b) + gelu([a; b] W1 + b1) W2 + b2.
 //
-// A CTA owns 128 pixels of one layer pair (M = 128, one element per thread):
+// Persistent CTAs (six per SM; weights staged and TMEM allocated once) stride over tiles of 128
+// pixels of one layer pair (M = 128, one element per thread):
 //   1. a and b (BF16) are copied as they are into shared memory as the K-major A operand
 //      X = [a | b] (K = 2C); 0.5 (a + b) is kept in FP32 registers.
 //   2. X W1 (N = C) into TMEM; + b1, GELU (polynomial erf form), BF16 -> shared memory as the
 //      A operand G (K = C).
 //   3. G W2 (N = C) into the next TMEM columns; + b2 + 0.5 (a + b); stored as BF16.
 // Each MMA chain signals an mbarrier through tcgen05.commit; every wait is bounded.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "umma.cuh"
 
@@ -45,12 +48,10 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t plane = (size_t)a.H * a.W;
-    const size_t pix = (size_t)blockIdx.x * CL_M + tid;
-    const bool live = pix < plane;
-    const size_t pixc = live ? pix : plane - 1;
-    const int j = blockIdx.y;
+    const int tiles_p = (int)((plane + CL_M - 1) / CL_M);
+    const int ntiles = tiles_p * a.L;
 
-    // weights: packed BF16 B operands (W1 then W2, contiguous), FP32 biases
+    // weights (once per CTA): packed BF16 B operands (W1 then W2, contiguous), FP32 biases
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.wtc);
         uint4* dst = reinterpret_cast<uint4*>(sm + S::w1_off);
@@ -62,51 +63,73 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
             s_b[C + i] = a.w[lay.b2() + i];
         }
     }
-    // X row of this element: channel group g (8 bf16) of row m at g * 128 * 16 + m * 16
-    float avg[C];
-    {
-        const uint4* pa = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
-                                                         ((size_t)(2 * j) * plane + pixc) * C);
-        const uint4* pb = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
-                                                         ((size_t)(2 * j + 1) * plane + pixc) * C);
-#pragma unroll
-        for (int g = 0; g < C / 8; ++g) {
-            const uint4 ua = __ldg(pa + g), ub = __ldg(pb + g);
-            *reinterpret_cast<uint4*>(s_x + ((size_t)g * CL_M + tid) * 16) = ua;
-            *reinterpret_cast<uint4*>(s_x + ((size_t)(C / 8 + g) * CL_M + tid) * 16) = ub;
-            const __nv_bfloat162* ha = reinterpret_cast<const __nv_bfloat162*>(&ua);
-            const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&ub);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float2 fa = __bfloat1622float2(ha[i]), fb = __bfloat1622float2(hb[i]);
-                avg[8 * g + 2 * i] = 0.5f * (fa.x + fb.x);
-                avg[8 * g + 2 * i + 1] = 0.5f * (fa.y + fb.y);
-            }
-        }
-    }
     if (warp == 0) umma::tmem_alloc(tslot, S::tmem_cols);
     if (tid == 0) umma::mbar_init(mbar, 1);
-    umma::fence_smem_to_async();
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(CL_M, C);
+    constexpr uint32_t LBO_A1 = CL_M * 16, LBO_B = C * 16;
+    uint32_t phase = 0;
+    bool failed = false;
+    int fail_code = 0;
 
-    // ---- H = X W1 ----
-    if (tid == 0) {
-        constexpr uint32_t idesc = umma::idesc_bf16_f32(CL_M, C);
-        const uint32_t a0 = umma::smem_u32(s_x), b0 = umma::smem_u32(sm + S::w1_off);
-        constexpr uint32_t LBO_A = CL_M * 16, LBO_B = C * 16;
+    // persistent: tiles of 128 pixels of one output layer j, the layer pair (2j, 2j+1) in
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j = tile / tiles_p;
+        const size_t pix = (size_t)(tile % tiles_p) * CL_M + tid;
+        const bool live = pix < plane;
+        const size_t pixc = live ? pix : plane - 1;
+        // X row of this element: channel group g (8 bf16) of row m at g * 128 * 16 + m * 16
+        // (the previous tile's MMAs, which read X and G, completed before its epilogue)
+        float avg[C];
+        {
+            const uint4* pa = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
+                                                             ((size_t)(2 * j) * plane + pixc) * C);
+            const uint4* pb = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
+                                                             ((size_t)(2 * j + 1) * plane + pixc) * C);
+            uint4 ua[C / 8], ub[C / 8];
 #pragma unroll
-        for (int kk = 0; kk < 2 * C / 16; ++kk)
-            umma::mma_bf16(tmem, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128), umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128),
-                           idesc, kk > 0);
-        umma::commit(mbar);
-    }
-    bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, CL_WAIT_NS));
-    uint32_t failed_phase = 0;
-    umma::fence_after_sync();
-    if (!failed) {
+            for (int g = 0; g < C / 8; ++g) {
+                ua[g] = __ldg(pa + g);
+                ub[g] = __ldg(pb + g);
+            }
+#pragma unroll
+            for (int g = 0; g < C / 8; ++g) {
+                *reinterpret_cast<uint4*>(s_x + ((size_t)g * CL_M + tid) * 16) = ua[g];
+                *reinterpret_cast<uint4*>(s_x + ((size_t)(C / 8 + g) * CL_M + tid) * 16) = ub[g];
+                const __nv_bfloat162* ha = reinterpret_cast<const __nv_bfloat162*>(&ua[g]);
+                const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&ub[g]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 fa = __bfloat1622float2(ha[i]), fb = __bfloat1622float2(hb[i]);
+                    avg[8 * g + 2 * i] = 0.5f * (fa.x + fb.x);
+                    avg[8 * g + 2 * i + 1] = 0.5f * (fa.y + fb.y);
+                }
+            }
+        }
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+
+        // ---- H = X W1 ----
+        if (tid == 0) {
+            const uint64_t ad = umma::desc(umma::smem_u32(s_x), LBO_A1, 128);
+            const uint64_t bd = umma::desc(umma::smem_u32(sm + S::w1_off), LBO_B, 128);
+#pragma unroll
+            for (int kk = 0; kk < 2 * C / 16; ++kk)
+                umma::mma_bf16(tmem, ad + ((2 * kk * LBO_A1) >> 4), bd + ((2 * kk * LBO_B) >> 4), idesc, kk > 0);
+            umma::commit(mbar);
+        }
+        failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, CL_WAIT_NS));
+        umma::fence_after_sync();
+        if (failed) {
+            fail_code = 5;
+            break;
+        }
+        phase ^= 1;
         // G = gelu(H + b1) -> BF16 A operand (K = C)
 #pragma unroll
         for (int ch = 0; ch < C / 16; ++ch) {
@@ -125,28 +148,28 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
                 *reinterpret_cast<uint4*>(s_g + ((size_t)(2 * ch + g) * CL_M + tid) * 16) = u;
             }
         }
-    }
-    umma::fence_smem_to_async();
-    umma::fence_before_sync();
-    __syncthreads();
-    umma::fence_after_sync();
+        umma::fence_smem_to_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
 
-    if (!failed) {
         // ---- G W2 into TMEM columns [C, 2C) ----
         if (tid == 0) {
-            constexpr uint32_t idesc = umma::idesc_bf16_f32(CL_M, C);
-            const uint32_t a0 = umma::smem_u32(s_g), b0 = umma::smem_u32(sm + S::w2_off);
-            constexpr uint32_t LBO_A = CL_M * 16, LBO_B = C * 16;
+            const uint64_t ad = umma::desc(umma::smem_u32(s_g), LBO_A1, 128);
+            const uint64_t bd = umma::desc(umma::smem_u32(sm + S::w2_off), LBO_B, 128);
 #pragma unroll
             for (int kk = 0; kk < C / 16; ++kk)
-                umma::mma_bf16(tmem + C, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128),
-                               umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128), idesc, kk > 0);
+                umma::mma_bf16(tmem + C, ad + ((2 * kk * LBO_A1) >> 4), bd + ((2 * kk * LBO_B) >> 4), idesc, kk > 0);
             umma::commit(mbar);
         }
-        failed = __syncthreads_or(!umma::mbar_wait(mbar, 1, CL_WAIT_NS));
-        failed_phase = 1;
+        failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, CL_WAIT_NS));
         umma::fence_after_sync();
-        if (!failed) {
+        if (failed) {
+            fail_code = 6;
+            break;
+        }
+        phase ^= 1;
+        {
             uint4* po = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + ((size_t)j * plane + pixc) * C);
 #pragma unroll
             for (int ch = 0; ch < C / 16; ++ch) {
@@ -166,9 +189,15 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
                 }
             }
         }
+        // this tile's TMEM reads before the next tile's MMAs
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
     }
-    if (failed && tid == 0) atomicExch(a.err, 5 + (int)failed_phase);
-    if (failed) umma::mbar_wait(mbar, failed_phase, CL_WAIT_NS);
+    if (failed && tid == 0) {
+        atomicExch(a.err, fail_code);
+        umma::mbar_wait(mbar, phase, CL_WAIT_NS);
+    }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
@@ -177,8 +206,18 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
 
 cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
     const size_t plane = (size_t)a.H * a.W;
-    const dim3 grid((unsigned)((plane + CL_M - 1) / CL_M), (unsigned)a.L);
+    const long ntiles = (long)((plane + CL_M - 1) / CL_M) * a.L;
+    if (ntiles == 0) return cudaSuccess;
+    // persistent CTAs: six per SM (shared memory and TMEM columns allow it)
+    const unsigned grid = (unsigned)std::min<long>(ntiles, 6L * sms);
 #define QK_CL_LAUNCH(CV)                                                                               \
     do {                                                                                               \
         auto k = collapse_tc_kernel<CV>;                                                               \
