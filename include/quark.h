@@ -313,6 +313,18 @@ size_t quark_ldm_field_bytes(const quark_ldm* ldm, int field);
  * device; synchronous).  `bytes` must equal the level's size. */
 quark_status quark_pyramid_read(const quark_pyramid* pyr, int k, void* dst, size_t bytes);
 
+/* Sampling geometry as the Update & Fuse kernels compute it (inspection; Sec. 3.1 operator P^T and
+ * the bilinear tap rule): for n target-grid pixel centres (px[i], py[i]) of a grid with factors
+ * (k_tx, k_ty) relative to `target` (target pixels per grid pixel along x and y), at depths
+ * depth[i] (metres), the continuous coordinates uv[i] = (u, v) in `view`'s level-k_m grid and the
+ * origin of the four bilinear taps taps[i] = (floor(u - 0.5), floor(v - 0.5)), with the device
+ * arithmetic of the context's precision form (FP32: IEEE divide; BF16: one reciprocal).
+ * valid[i] = 0 where the point is behind the view (camera z <= 1e-6; uv and taps then 0).  All
+ * arrays are host memory, [n] (px, py, depth, valid) or [n][2] (uv, taps); synchronous. */
+quark_status quark_sample_coords(quark_ctx* ctx, const quark_camera* target, double k_tx, double k_ty,
+                                 const quark_camera* view, double k_m, int n, const float* px, const float* py,
+                                 const float* depth, float* uv, int* taps, int* valid);
+
 quark_status quark_release_pyramid(quark_pyramid* pyr);
 quark_status quark_release_ldm(quark_ldm* ldm);
 

@@ -135,6 +135,29 @@ __device__ __forceinline__ bool reproject(const ViewMap& m, float px, float py, 
     return true;
 }
 
+// 2^x and 1/x on the special-function unit (PTX ex2.approx / rcp.approx, flush-to-zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// reproject with the perspective divide as one reciprocal (the BF16 form's sampling and the render)
+__device__ __forceinline__ bool reproject_rcp(const ViewMap& m, float px, float py, float d, float& u, float& v) {
+    const float X = fmaf(d, fmaf(m.A[0], px, fmaf(m.A[1], py, m.A[2])), m.b[0]);
+    const float Y = fmaf(d, fmaf(m.A[3], px, fmaf(m.A[4], py, m.A[5])), m.b[1]);
+    const float Z = fmaf(d, fmaf(m.A[6], px, fmaf(m.A[7], py, m.A[8])), m.b[2]);
+    if (!(Z > 1e-6f)) return false;
+    const float iz = rcp_approx(Z);
+    u = X * iz;
+    v = Y * iz;
+    return true;
+}
+
 // Bilinear taps with zero padding at continuous pixel coordinates (u, v) of an h x w map
 // (pixel centres at +0.5).  Returns false when no tap can touch the map (the sample is 0).
 struct Taps {

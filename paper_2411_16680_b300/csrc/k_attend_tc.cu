@@ -77,30 +77,8 @@ __device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, floa
     D[6] = __ffma2_rn(bf2_to_f2(b.z), w2, D[6]);
     D[7] = __ffma2_rn(bf2_to_f2(b.w), w2, D[7]);
 }
-// 2^x and 1/x on the special-function unit (PTX ex2.approx / rcp.approx, flush-to-zero).  The
-// softmax below works in log2 units, so that each weight is one ex2.
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-// Sec. 3.2.2 reprojection of the target pixel centre (px, py) at depth d into one view
-// (X = d A p + b, then the perspective divide), with the divide as one reciprocal.
-__device__ __forceinline__ bool reproject_rcp(const ViewMap& m, float px, float py, float d, float& u, float& v) {
-    const float X = fmaf(d, fmaf(m.A[0], px, fmaf(m.A[1], py, m.A[2])), m.b[0]);
-    const float Y = fmaf(d, fmaf(m.A[3], px, fmaf(m.A[4], py, m.A[5])), m.b[1]);
-    const float Z = fmaf(d, fmaf(m.A[6], px, fmaf(m.A[7], py, m.A[8])), m.b[2]);
-    if (!(Z > 1e-6f)) return false;
-    const float iz = rcp_approx(Z);
-    u = X * iz;
-    v = Y * iz;
-    return true;
-}
+// The softmax below works in log2 units, so that each weight is one ex2 (ex2_approx); the
+// reprojection divides with one reciprocal (reproject_rcp).
 template <int C, int NH, int TR, bool LAST>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;

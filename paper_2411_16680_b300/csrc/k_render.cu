@@ -22,31 +22,8 @@ __device__ __forceinline__ float4 sample_rgba(const float4* __restrict__ img, in
     return r;
 }
 
-// 2^x and 1/x on the special-function unit (PTX ex2.approx / rcp.approx, flush-to-zero): the blend
-// softmax runs in log2 units and the perspective divide is one reciprocal.
-__device__ __forceinline__ float rd_ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rd_rcp(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Sec. 3.1 reprojection of the output pixel centre (px, py) at depth d into view m's image.
-__device__ __forceinline__ bool rd_reproject(const ViewMap& m, float px, float py, float d, float& u, float& v) {
-    const float X = fmaf(d, fmaf(m.A[0], px, fmaf(m.A[1], py, m.A[2])), m.b[0]);
-    const float Y = fmaf(d, fmaf(m.A[3], px, fmaf(m.A[4], py, m.A[5])), m.b[1]);
-    const float Z = fmaf(d, fmaf(m.A[6], px, fmaf(m.A[7], py, m.A[8])), m.b[2]);
-    if (!(Z > 1e-6f)) return false;
-    const float iz = rd_rcp(Z);
-    u = X * iz;
-    v = Y * iz;
-    return true;
-}
-
+// The blend softmax runs in log2 units (ex2_approx); the perspective divide is one reciprocal
+// (reproject_rcp).
 constexpr float RD_LOG2E = 1.4426950408889634f;
 
 // One layer's contribution: blend-weighted colour of the V views with an online softmax over the
@@ -60,13 +37,13 @@ __device__ __forceinline__ void blend_layer(const RenderArgs& a, Logit4 logit4, 
     float mx = -INFINITY, sum = 0.f, lr = 0.f, lg = 0.f, lb = 0.f;
     auto view = [&](int m, float b) {
         const float mn = fmaxf(mx, b);
-        const float sc = rd_ex2(mx - mn), p = rd_ex2(b - mn);
+        const float sc = ex2_approx(mx - mn), p = ex2_approx(b - mn);
         sum = fmaf(sum, sc, p);
         lr *= sc;
         lg *= sc;
         lb *= sc;
         float u = 0.f, v = 0.f;
-        const bool ok = rd_reproject(a.geo.v[m], pxc, pyc, d, u, v);
+        const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
         const float4 c = sample_rgba(a.rgba + m * img_stride, a.Hi, a.Wi, ok, u, v);
         lr = fmaf(p, c.x, lr);
         lg = fmaf(p, c.y, lg);

@@ -135,6 +135,8 @@ def lib():
             "quark_serve_stop": ([vp], ct.c_int),
             "quark_update_fuse_noalloc": ([vp, vp, ct.c_int, ct.POINTER(Camera), vp, vp, vp, vp, vp, vp, vp, vp, vp],
                                           ct.c_int),
+            "quark_sample_coords": ([vp, ct.POINTER(Camera), ct.c_double, ct.c_double, ct.POINTER(Camera), ct.c_double,
+                                     ct.c_int, vp, vp, vp, vp, vp, vp], ct.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -372,6 +374,19 @@ class Context:
         g = StageGrads(*[_ptr(grads[n]) for n in STAGE_GRAD_FIELDS])
         _check(lib().quark_stage_backward(self.handle, pyr.handle, _ptr(feat), _ptr(v_in), ldm.handle, _ptr(dl_drgb),
                                           _ptr(dv_in), _ptr(dfeat), ct.byref(g), _stream(stream)), self.handle)
+
+    def sample_coords(self, target, k_tx: float, k_ty: float, view, k_m: float, px, py, depth):
+        """quark_sample_coords: (u, v) [n, 2] float32, tap origins [n, 2] int32 and validity [n] of target
+        grid pixel centres (px, py) at depths `depth` in `view`'s level-k_m grid, as the kernels compute them."""
+        px, py, depth = (np.ascontiguousarray(x, np.float32).ravel() for x in (px, py, depth))
+        n = px.size
+        uv = np.zeros((n, 2), np.float32)
+        taps = np.zeros((n, 2), np.int32)
+        valid = np.zeros(n, np.int32)
+        t, v = make_camera(target), make_camera(view)
+        _check(lib().quark_sample_coords(self.handle, ct.byref(t), k_tx, k_ty, ct.byref(v), k_m, n, _ptr(px), _ptr(py),
+                                         _ptr(depth), _ptr(uv), _ptr(taps), _ptr(valid)), self.handle)
+        return uv, taps, valid
 
     def check_device(self):
         """Synchronise and raise if a kernel's bounded device-side wait ran out."""
