@@ -141,6 +141,28 @@ def oracle_sample(cfg, W, scene, rows: int = 2):
 
 
 # ----------------------------------------------------------------------------------------------
+# Ranks: independent replicas, one process per GPU; the only collectives are the barriers around the
+# timed regions and the max over ranks of their durations
+# ----------------------------------------------------------------------------------------------
+
+def max_over_ranks(values, world, device):
+    """Each entry's largest value over all ranks (the job takes as long as its slowest rank); the
+    values themselves on one rank.  `device` holds the collective's tensor: a CUDA device under
+    NCCL, "cpu" under gloo."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(world, steps, seconds):
+    """Whole-job throughput: each of `world` ranks completes `steps` units within `seconds`."""
+    return world * steps / seconds
+
+
+# ----------------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------------
 
@@ -201,10 +223,7 @@ def run_form(cfg, W, scene, steps, warmup, rank, world, dev, peaks, flush_bytes=
     else:
         lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
         total_ms = ev[0].elapsed_time(ev[steps])
-    t = torch.tensor([total_ms], device=f"cuda:{dev}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks([total_ms], world, f"cuda:{dev}")[0]
 
     # end to end through the public API: pinned host images in, host RGBA out, every step.
     # Serial: one frame at a time (copy in, solve, copy out, synchronise).  Pipelined, as a video
@@ -242,10 +261,7 @@ def run_form(cfg, W, scene, steps, warmup, rank, world, dev, peaks, flush_bytes=
     for st in streams:
         st.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s, serial_s], device=f"cuda:{dev}")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s, serial_s = (float(v) for v in te.tolist())
+    e2e_s, serial_s = max_over_ranks([e2e_s, serial_s], world, f"cuda:{dev}")
     rgba = out.cpu().numpy()
     for p_ in pyr_h:
         p_.release()
@@ -451,6 +467,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference" and rank != 0:
+        return 0  # the reference arm runs on rank 0 alone; the other ranks exit without work
     peaks = load_peaks()
 
     sw, sh = (int(v) for v in args.size.lower().split("x"))
@@ -533,13 +551,13 @@ def main():
         res = run_form(cfg, W, scene, args.steps, args.warmup, rank, world, dev, peaks,
                        flush_bytes=(512 << 20) if quark_model else 0)
         results[form] = (cfg, res)
-        fps = world * args.steps / (res["total_ms"] * 1e-3)
+        fps = job_rate(world, args.steps, res["total_ms"] * 1e-3)
         lat = sorted(res["lat"])
         forms[form] = {"fps": round(fps, 2), "ms_per_step": round(res["total_ms"] / args.steps, 3),
                        "p50_ms": round(statistics.median(lat), 3),
                        "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
-                       "e2e_fps": round(world * args.steps / res["e2e_s"], 2),
-                       "e2e_serial_fps": round(world * args.steps / res["serial_s"], 2)}
+                       "e2e_fps": round(job_rate(world, args.steps, res["e2e_s"]), 2),
+                       "e2e_serial_fps": round(job_rate(world, args.steps, res["serial_s"]), 2)}
 
     # accuracy of each form against the oracle on sampled windows (rank 0); the oracle's
     # render-and-refine renders whole views, so that option is checked by the tests instead
