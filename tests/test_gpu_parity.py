@@ -229,3 +229,30 @@ def test_1080p_sampled_outputs(precision):
         ref, _ = O.forward(cfg, W, scene, r)
         err = np.abs(out[r[0]:r[1], r[2]:r[3]] - ref).max()
         assert err <= tol, f"{r}: max-abs {err:.3e}"
+
+
+@pytest.mark.parametrize("precision", [synth.PREC_FP32, synth.PREC_BF16])
+def test_maximum_view_count(precision):
+    """QUARK_MAX_VIEWS (64) views through every step and the render; one more is refused."""
+    cfg = synth.QuarkConfig(C=16, heads=2, scales=[(2, 4), (1, 2)], near=1.0, far=40.0, out_h=24, out_w=40,
+                            precision=precision)
+    scene = synth.scene_raycast(seed=13, V=quark.MAX_VIEWS, W=40, H=24, f=30.0, arc=0.8)
+    W = synth.make_weights(cfg, seed=2, sharp=True)
+    ref, ref_steps = O.forward(cfg, W, scene)
+    out, steps, _ = run_gpu(cfg, W, scene, per_step=precision == synth.PREC_FP32)
+    if precision == synth.PREC_FP32:
+        for j, (g, r) in enumerate(zip(steps, ref_steps)):
+            assert_rel(g["V_out"], r.V_out, REL_TOL_FP32, f"step {j} V_out")
+        assert_rel(steps[-1]["beta"], ref_steps[-1].beta_logits, REL_TOL_FP32, "beta")
+        assert np.abs(out - ref).max() <= RGBA_TOL_FP32
+    else:
+        assert np.abs(out - ref).max() <= RGBA_TOL_BF16 and psnr(out, ref) >= PSNR_MIN_BF16
+    ctx = quark.Context(cfg)
+    try:
+        cams = list(scene.cams) + [scene.cams[0]]
+        images = np.concatenate([scene.images, scene.images[:1]])
+        with pytest.raises(quark.QuarkError) as e:
+            ctx.encode_pyramid(images, cams)
+        assert e.value.status == quark.EINVAL
+    finally:
+        ctx.close()

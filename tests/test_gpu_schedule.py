@@ -132,3 +132,20 @@ def test_aspect_adaptive_at_the_model_aspect_is_bitwise_the_plain_schedule():
     a, _, _ = run_gpu(cfg, W, scene, per_step=False)
     b, _, _ = run_gpu(cfg.replace(model_w=240, model_h=120), W, scene, per_step=False)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [synth.PREC_FP32, synth.PREC_BF16])
+def test_quark_model_1080p_sampled_windows(precision):
+    """The paper's Quark schedule at full size (V = 8 views 480x288, 1920x1080 output), in the launch
+    configuration the bench times; the oracle computes two output windows from scratch through all
+    24 fusion steps (their halos grow back through every conv and upsample)."""
+    cfg = synth.config_quark().replace(precision=precision)
+    W = synth.make_weights(cfg, sharp=True)
+    scene = synth.scene_quark()
+    out, _, _ = run_gpu(cfg, W, scene, per_step=False)
+    assert np.isfinite(out).all()
+    tol = RGBA_TOL_FP32 if precision == synth.PREC_FP32 else RGBA_TOL_BF16
+    for r in [(0, 3, 0, 3), (540, 543, 958, 961)]:
+        ref, _ = O.forward(cfg.replace(precision=synth.PREC_FP32), W, scene, r)
+        err = np.abs(out[r[0]:r[1], r[2]:r[3]] - ref).max()
+        assert err <= tol, f"{r}: max-abs {err:.3e}"
