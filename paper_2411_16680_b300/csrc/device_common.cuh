@@ -105,6 +105,24 @@ __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + e
 // polynomial in t = 2 x^2 / 25 - 1 for |x| <= 5; beyond, x^2 is clamped to 25 and Phi saturates
 // to 1 or 0.  Maximum absolute error 3.6e-6 against the exact erf form (coefficients and error
 // from gen_gelu_poly.py).
+// GELU in its tanh form (Hendrycks & Gimpel, 2016), 0.5 x (1 + tanh(sqrt(2 / pi) (x + 0.044715 x^3))),
+// on packed FP32x2 with the tanh on the special-function unit (PTX tanh.approx).  It stays within
+// 5e-4 of the erf form everywhere (4.7e-4 at x = 2.7, where a BF16 value's half-ulp is 5.3e-3), so
+// the BF16 form uses it where the result is rounded to BF16 (the conv block's mid tile).
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 gelu_tanh2(float2 x) {
+    constexpr float K0 = 0.7978845608028654f;    // sqrt(2 / pi)
+    constexpr float K1 = 0.035677408136300125f;  // 0.044715 sqrt(2 / pi)
+    const float2 x2 = __fmul2_rn(x, x);
+    const float2 inner = __fmul2_rn(x, __ffma2_rn(x2, make_float2(K1, K1), make_float2(K0, K0)));
+    const float2 hx = __fmul2_rn(x, make_float2(0.5f, 0.5f));
+    return __ffma2_rn(hx, make_float2(tanh_approx(inner.x), tanh_approx(inner.y)), hx);
+}
+
 __device__ __forceinline__ float2 gelu_poly2(float2 x) {
     constexpr float c[12] = {1.413636357e-01f, -7.029806077e-02f, 5.153302103e-02f, -4.040101916e-02f,
                              3.127557412e-02f, -2.353477105e-02f, 1.720164344e-02f, -1.048013940e-02f,

@@ -12,8 +12,9 @@
 // ends; the two columns past each row's last valid mid column and the pixels past the last row are
 // computed and discarded (a valid pixel's taps never reach them).  M = 128 pixels per block,
 // N = C, K = 9 taps x C.  Conv1 fills NB1 = ceil((R + 2) P / 128) blocks in TMEM (columns i * C ..),
-// the epilogue writes gelu(conv1 + b1) back to shared memory as BF16 in the same layout (zero
-// outside the plane: conv2's padding), and conv2 fills NB2 = ceil(R P / 128) blocks.  The host picks
+// the epilogue writes gelu(conv1 + b1) (tanh form on the special-function unit: within 5e-4 of the
+// erf form, below the BF16 rounding of the stored value) back to shared memory as BF16 in the same
+// layout (zero outside the plane: conv2's padding), and conv2 fills NB2 = ceil(R P / 128) blocks.  The host picks
 // (OW, R) per plane size to minimise MMA blocks per output (tall narrow tiles waste least: two
 // columns per row instead of a part-empty last block), with enough tiles for every SM.  Two
 // persistent CTAs share an SM and stride over the tiles (the packed weights are staged once per
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
                 const bool inside = row < R + 2 && cx < OW + 2 && gy >= 0 && gy < H && gx >= 0 && gx < W;
 #pragma unroll
                 for (int c = 0; c < C; c += 2) {
-                    const float2 g = gelu_poly2(__fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(misc[C + c], misc[C + c + 1])));
+                    const float2 g = gelu_tanh2(__fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(misc[C + c], misc[C + c + 1])));
                     v[c] = inside ? g.x : 0.f;
                     v[c + 1] = inside ? g.y : 0.f;
                 }
