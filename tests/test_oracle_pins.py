@@ -798,3 +798,27 @@ def test_anisotropic_grids_window_exactly():
     for rect in [(0, 9, 0, 13), (60, 71, 97, 120), (129, 130, 0, 200)]:
         part, _ = O.forward(cfg, W, sc, rect)
         np.testing.assert_allclose(part, full[rect[0]:rect[1], rect[2]:rect[3]], atol=1e-13)
+
+
+def test_update_block_lift_closed_form():
+    """With its CNN zeroed the Update Block is F + up(I~) W_r + b_r; at a x2 level change the
+    rendering is upsampled with edge clamp and pixel centres aligned (here written out by hand)."""
+    rng = np.random.default_rng(6)
+    C = 8
+    F = rng.standard_normal((6, 8, C))
+    It = rng.uniform(0, 1, (3, 4, 4))
+    W = {"upd_Wr_1": rng.standard_normal((4, C)), "upd_br_1": rng.standard_normal(C), "upd_g_1": np.ones(C),
+         "upd1_w_1": np.zeros((3, 3, C, C)), "upd1_b_1": np.zeros(C), "upd2_w_1": np.zeros((3, 3, C, C)),
+         "upd2_b_1": np.zeros(C)}
+    got = O.update_block(W, 1, F, It)
+    up = np.zeros((6, 8, 4))
+    for y in range(6):
+        for x in range(8):
+            sy, sx = (y + 0.5) / 2 - 0.5, (x + 0.5) / 2 - 0.5
+            y0, x0 = int(np.floor(sy)), int(np.floor(sx))
+            fy, fx = sy - y0, sx - x0
+            cy = lambda i: min(max(i, 0), 2)
+            cx = lambda i: min(max(i, 0), 3)
+            up[y, x] = ((1 - fy) * (1 - fx) * It[cy(y0), cx(x0)] + (1 - fy) * fx * It[cy(y0), cx(x0 + 1)] +
+                        fy * (1 - fx) * It[cy(y0 + 1), cx(x0)] + fy * fx * It[cy(y0 + 1), cx(x0 + 1)])
+    np.testing.assert_allclose(got, F + up @ W["upd_Wr_1"] + W["upd_br_1"], atol=1e-12)
