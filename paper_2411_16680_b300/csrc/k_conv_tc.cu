@@ -16,10 +16,17 @@
 // erf form, below the BF16 rounding of the stored value) back to shared memory as BF16 in the same
 // layout (zero outside the plane: conv2's padding), and conv2 fills NB2 = ceil(R P / 128) blocks.  The host picks
 // (OW, R) per plane size to minimise MMA blocks per output (tall narrow tiles waste least: two
-// columns per row instead of a part-empty last block), with enough tiles for every SM.  Two
-// persistent CTAs share an SM and stride over the tiles (the packed weights are staged once per
-// CTA), so one CTA's loads and epilogues overlap the other's MMAs.  One thread issues the MMAs;
-// completion is signalled through an mbarrier with a bounded wait.
+// columns per row instead of a part-empty last block), with enough tiles for every SM.
+//
+// One persistent CTA per SM, warp-specialised, strides over the tiles with two input buffers:
+//   loader warps (4)    normalise tile k into buffer k % 2 once conv2 of tile k - 2 has released it;
+//   MMA warp (1 thread) conv1 of tile k into TMEM columns [0, 256) once its input is ready and the
+//                       epilogue has read conv1 of tile k - 1; conv2 into columns [256, 512) once
+//                       the mid tile is written and the epilogue has read conv2 of tile k - 1;
+//   epilogue warps (8)  gelu(conv1) -> mid tile (in the input buffer, which conv1 has read), then
+//                       the residual and the stores of conv2,
+// so the loads of one tile, the MMAs of the next and the epilogues of the previous overlap.  The
+// packed weights are staged once.  mbarriers order the roles; every wait is bounded.
 #include <algorithm>
 
 #include "device_common.cuh"
@@ -28,8 +35,10 @@
 namespace quark {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 256;
-constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s bound on every MMA wait
+constexpr int TC_LOAD_WARPS = 4, TC_EPI_WARPS = 8;
+constexpr int TC_MMA_WARP = TC_LOAD_WARPS;  // the warp after the loaders
+constexpr int TC_THREADS = 32 * (TC_LOAD_WARPS + 1 + TC_EPI_WARPS);
+constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s bound on every wait
 
 // Tile geometry of one launch (host-chosen): pitch P = OW + 4, R output rows, NB1 / NB2 MMA blocks
 // of conv1 / conv2.
@@ -40,18 +49,20 @@ struct ConvTile {
 template <int C>
 struct TcSmem {
     static constexpr int G = C / 8;
-    static constexpr int NPIX = C == 32 ? 1152 : 2304;  // pixels of the input / mid tile buffer
-    static constexpr int NB_MAX = 256 / C;              // conv1 blocks that fit the TMEM allocation
-    // the mid tile reuses the input tile's memory: conv1 has finished reading it when the first
-    // epilogue writes gelu(conv1)
-    static constexpr int in_off = 0;
-    static constexpr int w1_off = in_off + G * NPIX * 16;
+    static constexpr int NPIX = C == 32 ? 1152 : 2304;  // pixels of an input / mid tile buffer
+    static constexpr int NB_MAX = 256 / C;              // MMA blocks per conv in half the TMEM
+    // a tile's mid tile reuses its input buffer: conv1 has finished reading it when the epilogue
+    // writes gelu(conv1)
+    static constexpr int buf_bytes = G * NPIX * 16;     // input buffers b = 0, 1 at b * buf_bytes
+    static constexpr int w1_off = 2 * buf_bytes;
     static constexpr int w2_off = w1_off + 9 * C * C * 2;
     static constexpr int misc_off = w2_off + 9 * C * C * 2;
     static constexpr int misc_n = 8 * C + 8;
-    static constexpr int bar_off = misc_off + misc_n * 4;
-    static constexpr int total = bar_off + 16;
-    static_assert(2 * (total + 1024) <= 233472, "two CTAs per SM");
+    // barriers: input full [2], input free [2], conv1 done, conv2 done, conv1 read, conv2 read, drain
+    static constexpr int bar_off = (misc_off + misc_n * 4 + 7) / 8 * 8;
+    static constexpr int err_off = bar_off + 9 * 8;
+    static constexpr int total = err_off + 16;
+    static_assert(total + 1024 <= 233472, "one CTA per SM");
 };
 
 template <int C>
@@ -76,24 +87,30 @@ __device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[C]) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const ConvArgs a, const ConvTile tg) {
+__global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const ConvArgs a, const ConvTile tg) {
     using S = TcSmem<C>;
-    constexpr uint32_t TMEM_COLS = 256;  // NB_MAX blocks of C accumulator columns
     const ConvLayout lay{C};
     extern __shared__ __align__(128) uint8_t sm[];
-    uint8_t* s_in = sm + S::in_off;
-    uint8_t* s_mid = sm + S::in_off;
     uint8_t* s_w1 = sm + S::w1_off;
     uint8_t* s_w2 = sm + S::w2_off;
     float* misc = reinterpret_cast<float*>(sm + S::misc_off);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::bar_off);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::bar_off + 8);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::bar_off);
+    uint64_t* full = bars;           // [2] input normalised (loader arrivals)
+    uint64_t* freed = bars + 2;      // [2] input buffer free again (conv2 of its tile complete)
+    uint64_t* c1done = bars + 4;     // conv1 complete
+    uint64_t* c2done = bars + 5;     // conv2 complete
+    uint64_t* e1done = bars + 6;     // conv1 read and the mid tile written (epilogue arrivals)
+    uint64_t* e2done = bars + 7;     // conv2 read (epilogue arrivals)
+    uint64_t* drain = bars + 8;      // every MMA issued has completed
+    int* s_err = reinterpret_cast<int*>(sm + S::err_off);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::err_off + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int H = a.H, W = a.W, L = a.L;
     const int P = tg.P, R = tg.R, OW = P - 4;
     const size_t plane = (size_t)H * W;
     const int ntiles = tg.tiles_x * tg.tiles_y * L;
+    constexpr int NLOAD = 32 * TC_LOAD_WARPS, NEPI = 32 * TC_EPI_WARPS;
 
     // ---- constants and packed BF16 weights ----
     for (int i = tid; i < C; i += TC_THREADS) {
@@ -115,102 +132,162 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
             d2[i] = __ldg(src + n + i);
         }
     }
-    if (warp == 0) umma::tmem_alloc(tslot, TMEM_COLS);
-    if (tid == 0) umma::mbar_init(mbar, 1);
+    if (warp == 0) umma::tmem_alloc(tslot, 512);
+    if (tid == 0) {
+        umma::mbar_init(full, NLOAD);
+        umma::mbar_init(full + 1, NLOAD);
+        umma::mbar_init(freed, 1);
+        umma::mbar_init(freed + 1, 1);
+        umma::mbar_init(c1done, 1);
+        umma::mbar_init(c2done, 1);
+        umma::mbar_init(e1done, NEPI);
+        umma::mbar_init(e2done, NEPI);
+        umma::mbar_init(drain, 1);
+        *s_err = 0;
+    }
+    umma::fence_smem_to_async();
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
     constexpr uint32_t idesc = umma::idesc_bf16_f32(TC_M, C);
-    constexpr uint32_t LBO_W = C * 16;       // B: N = C rows of 16 B per core-matrix column
-    constexpr uint32_t LBO_A = S::NPIX * 16;  // A: channel-group stride of the input / mid tile
-    const int q = warp & 3, half = warp >> 2;
-    const int col = q * 32 + lane;  // the pixel of a block (TMEM lane) this thread reads
-    uint32_t phase = 0;             // parity of the next completion of mbar
-    bool failed = false;
-    int fail_code = 0;
+    constexpr uint32_t LBO_W = C * 16;        // B: N = C rows of 16 B per core-matrix column
+    constexpr uint32_t LBO_A = S::NPIX * 16;  // A: channel-group stride of an input / mid tile
+    constexpr uint32_t TB = 256;              // TMEM column of conv2's accumulators
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
-        const int li = tile / (tg.tiles_x * tg.tiles_y);
-        const __nv_bfloat16* vin = reinterpret_cast<const __nv_bfloat16*>(a.in) + (size_t)li * plane * C;
-
-        // ---- normalised input tile: rows y0-2 .. y0+R+1, columns x0-2 .. x0+OW+1 (pitch P) ----
-        // (the mid tile of the previous tile, which shares this memory, was last read by its conv2,
-        // complete before that tile's epilogue)
-        // two pixels per thread per iteration: both pixels' loads are in flight before either is used
-        const int NIN = (R + 4) * P;
-        for (int p0 = tid; p0 < NIN; p0 += 2 * TC_THREADS) {
-            uint4 raw[2][C / 8];
-            bool in[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int p = p0 + u * TC_THREADS;
-                const int gy = y0 - 2 + p / P, gx = x0 - 2 + p % P;
-                in[u] = p < NIN && gy >= 0 && gy < H && gx >= 0 && gx < W;
-                const uint4* src = reinterpret_cast<const uint4*>(vin + ((size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0)) * C);
-#pragma unroll
-                for (int g = 0; g < C / 8; ++g) raw[u][g] = in[u] ? __ldg(src + g) : make_uint4(0, 0, 0, 0);
+    if (warp < TC_LOAD_WARPS) {
+        // ---- loader: normalised input tile k into buffer k % 2 ----
+        int k = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+            const int b = k & 1;
+            // the buffer's previous tile (k - 2) is complete; the first two waits pass at once
+            if (!umma::mbar_wait(freed + b, ((k >> 1) & 1) ^ 1, TC_WAIT_NS)) {
+                atomicOr(s_err, 1);
+                break;
             }
+            uint8_t* s_in = sm + (size_t)b * S::buf_bytes;
+            const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
+            const int li = tile / (tg.tiles_x * tg.tiles_y);
+            const __nv_bfloat16* vin = reinterpret_cast<const __nv_bfloat16*>(a.in) + (size_t)li * plane * C;
+            // rows y0-2 .. y0+R+1, columns x0-2 .. x0+OW+1 (pitch P); two pixels in flight per thread
+            const int NIN = (R + 4) * P;
+            for (int p0 = tid; p0 < NIN; p0 += 2 * NLOAD) {
+                uint4 raw[2][C / 8];
+                bool in[2];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int p = p0 + u * TC_THREADS;
-                if (p >= NIN) break;
-                float v[C];
+                for (int u = 0; u < 2; ++u) {
+                    const int p = p0 + u * NLOAD;
+                    const int gy = y0 - 2 + p / P, gx = x0 - 2 + p % P;
+                    in[u] = p < NIN && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                    const uint4* src =
+                        reinterpret_cast<const uint4*>(vin + ((size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0)) * C);
 #pragma unroll
-                for (int g = 0; g < C / 8; ++g) {
-                    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw[u][g]);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float2 f = __bfloat1622float2(h[j]);
-                        v[8 * g + 2 * j] = f.x;
-                        v[8 * g + 2 * j + 1] = f.y;
-                    }
+                    for (int g = 0; g < C / 8; ++g) raw[u][g] = in[u] ? __ldg(src + g) : make_uint4(0, 0, 0, 0);
                 }
-                float ms = 0.f;
 #pragma unroll
-                for (int c = 0; c < C; ++c) ms = fmaf(v[c], v[c], ms);
-                const float r = in[u] ? 1.0f / sqrtf(ms / C + 1e-6f) : 0.f;
+                for (int u = 0; u < 2; ++u) {
+                    const int p = p0 + u * NLOAD;
+                    if (p >= NIN) break;
+                    float v[C];
 #pragma unroll
-                for (int c = 0; c < C; ++c) v[c] = v[c] * r * misc[c];
-                store_pixel_bf16<C>(s_in, S::NPIX, p, v);
-            }
-        }
-        umma::fence_smem_to_async();
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
-
-        // ---- conv1: blocks of 128 mid pixels; tap (dy, dx) starts dy * P + dx pixels later ----
-        if (tid == 0) {
-            // descriptors built once; each MMA adds its start offset (in 16-byte units, one pixel)
-            // to the start-address field, which stays below 2^14 for any shared-memory address
-            const uint64_t ad0 = umma::desc(umma::smem_u32(s_in), LBO_A, 128);
-            const uint64_t bd0 = umma::desc(umma::smem_u32(s_w1), LBO_W, 128);
-            for (int i = 0; i < tg.nb1; ++i) {
+                    for (int g = 0; g < C / 8; ++g) {
+                        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw[u][g]);
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-                    for (int kk = 0; kk < C / 16; ++kk) {
-                        const int dy = tap / 3, dx = tap % 3;
-                        const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
-                        const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
-                        umma::mma_bf16(tmem + i * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
+                        for (int j = 0; j < 4; ++j) {
+                            const float2 f = __bfloat1622float2(h[j]);
+                            v[8 * g + 2 * j] = f.x;
+                            v[8 * g + 2 * j + 1] = f.y;
+                        }
                     }
+                    float ms = 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) ms = fmaf(v[c], v[c], ms);
+                    const float r = in[u] ? 1.0f / sqrtf(ms / C + 1e-6f) : 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) v[c] = v[c] * r * misc[c];
+                    store_pixel_bf16<C>(s_in, S::NPIX, p, v);
+                }
             }
-            umma::commit(mbar);
+            umma::fence_smem_to_async();  // these writes, before the MMAs that read them
+            umma::mbar_arrive(full + b);
         }
-        failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, TC_WAIT_NS));
-        umma::fence_after_sync();
-        if (failed) {
-            fail_code = 1;
-            break;
+    } else if (warp == TC_MMA_WARP) {
+        // ---- MMA issue (one thread) ----
+        if (lane == 0) {
+            int k = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
+                const int b = k & 1;
+                uint8_t* s_in = sm + (size_t)b * S::buf_bytes;
+                ok = umma::mbar_wait(full + b, (k >> 1) & 1, TC_WAIT_NS) &&
+                     (k == 0 || umma::mbar_wait(e1done, (k - 1) & 1, TC_WAIT_NS));
+                if (!ok) break;
+                umma::fence_after_sync();
+                {
+                    // descriptors built once; each MMA adds its start offset (16-byte units: one
+                    // pixel) to the start-address field, which stays below 2^14
+                    const uint64_t ad0 = umma::desc(umma::smem_u32(s_in), LBO_A, 128);
+                    const uint64_t bd0 = umma::desc(umma::smem_u32(s_w1), LBO_W, 128);
+                    for (int i = 0; i < tg.nb1; ++i) {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                            for (int kk = 0; kk < C / 16; ++kk) {
+                                const int dy = tap / 3, dx = tap % 3;
+                                const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
+                                const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
+                                umma::mma_bf16(tmem + i * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
+                            }
+                    }
+                    umma::commit(c1done);
+                }
+                ok = umma::mbar_wait(e1done, k & 1, TC_WAIT_NS) &&
+                     (k == 0 || umma::mbar_wait(e2done, (k - 1) & 1, TC_WAIT_NS));
+                if (!ok) break;
+                umma::fence_after_sync();
+                {
+                    const uint64_t ad0 = umma::desc(umma::smem_u32(s_in), LBO_A, 128);  // the mid tile
+                    const uint64_t bd0 = umma::desc(umma::smem_u32(s_w2), LBO_W, 128);
+                    for (int i = 0; i < tg.nb2; ++i) {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                            for (int kk = 0; kk < C / 16; ++kk) {
+                                const int dy = tap / 3, dx = tap % 3;
+                                const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
+                                const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
+                                umma::mma_bf16(tmem + TB + i * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
+                            }
+                    }
+                    umma::commit(c2done);
+                    umma::commit(freed + b);  // the buffer is free once conv2 has read the mid tile
+                }
+            }
+            if (!ok) atomicOr(s_err, 2);
+            // nothing of ours may still run on the tensor cores when TMEM is released
+            umma::commit(drain);
+            if (!umma::mbar_wait(drain, 0, TC_WAIT_NS)) atomicOr(s_err, 2);
         }
-        phase ^= 1;
-        {
-            // ---- epilogue 1: gelu(conv1 + b1) -> BF16 mid tile, zero outside the plane and on the
-            // discarded pixels ----
-            for (int i = half; i < tg.nb1; i += 2) {
+    } else {
+        // ---- epilogues: TC_EPI_WARPS / 4 warps per TMEM lane quarter ----
+        constexpr int NGRP = TC_EPI_WARPS / 4;
+        static_assert(TC_EPI_WARPS % 4 == 0, "the epilogue warps cover the four TMEM lane quarters evenly");
+        const int q = warp & 3, grp = (warp - TC_MMA_WARP - 1) >> 2;
+        const int col = q * 32 + lane;  // the pixel of a block (TMEM lane) this thread reads
+        int k = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+            const int b = k & 1;
+            uint8_t* s_mid = sm + (size_t)b * S::buf_bytes;
+            const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
+            const int li = tile / (tg.tiles_x * tg.tiles_y);
+            const __nv_bfloat16* vin = reinterpret_cast<const __nv_bfloat16*>(a.in) + (size_t)li * plane * C;
+            if (!umma::mbar_wait(c1done, k & 1, TC_WAIT_NS)) {
+                atomicOr(s_err, 4);
+                break;
+            }
+            umma::fence_after_sync();
+            // gelu(conv1 + b1) -> BF16 mid tile, zero outside the plane and on the discarded pixels
+            for (int i = grp; i < tg.nb1; i += NGRP) {
                 float v[C];
                 tmem_load_row<C>(tmem + ((uint32_t)(q * 32) << 16) + i * C, v);
                 const int idx = i * TC_M + col;
@@ -227,90 +304,65 @@ __global__ void __launch_bounds__(TC_THREADS, 2) conv_block_tc_kernel(const Conv
             }
             umma::fence_smem_to_async();
             umma::fence_before_sync();
-            __syncthreads();
-            umma::fence_after_sync();
-
-            // ---- conv2: blocks of 128 output pixels, reusing TMEM columns ----
-            if (tid == 0) {
-                const uint64_t ad0 = umma::desc(umma::smem_u32(s_mid), LBO_A, 128);
-                const uint64_t bd0 = umma::desc(umma::smem_u32(s_w2), LBO_W, 128);
-                for (int i = 0; i < tg.nb2; ++i) {
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-                        for (int kk = 0; kk < C / 16; ++kk) {
-                            const int dy = tap / 3, dx = tap % 3;
-                            const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
-                            const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
-                            umma::mma_bf16(tmem + i * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
-                        }
-                }
-                umma::commit(mbar);
-            }
-            failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, TC_WAIT_NS));
-            umma::fence_after_sync();
-            if (failed) {
-                fail_code = 2;
+            umma::mbar_arrive(e1done);
+            if (!umma::mbar_wait(c2done, k & 1, TC_WAIT_NS)) {
+                atomicOr(s_err, 4);
                 break;
             }
-            phase ^= 1;
-            {
-                // ---- epilogue 2: residual, V_out, decode ----
-                for (int i = half; i < tg.nb2; i += 2) {
-                    float v[C];
-                    tmem_load_row<C>(tmem + ((uint32_t)(q * 32) << 16) + i * C, v);
-                    const int idx = i * TC_M + col;
-                    const int row = idx / P, cx = idx - row * P;
-                    const int gy = y0 + row, gx = x0 + cx;
-                    if (row >= R || cx >= OW || gy >= H || gx >= W) continue;
-                    const size_t pix = (size_t)gy * W + gx;
-                    const size_t el = (size_t)li * plane + pix;
-                    float t = misc[8 * C + 3], s = misc[8 * C + 4];
-                    uint4* out = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + el * C);
+            umma::fence_after_sync();
+            // residual, V_out, decode
+            for (int i = grp; i < tg.nb2; i += NGRP) {
+                float v[C];
+                tmem_load_row<C>(tmem + ((uint32_t)(q * 32) << 16) + TB + i * C, v);
+                const int idx = i * TC_M + col;
+                const int row = idx / P, cx = idx - row * P;
+                const int gy = y0 + row, gx = x0 + cx;
+                if (row >= R || cx >= OW || gy >= H || gx >= W) continue;
+                const size_t pix = (size_t)gy * W + gx;
+                const size_t el = (size_t)li * plane + pix;
+                float t = misc[8 * C + 3], s = misc[8 * C + 4];
+                uint4* out = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + el * C);
 #pragma unroll
-                    for (int c0 = 0; c0 < C; c0 += 16) {
-                        float rr[16];
-                        load16(vin + pix * C + c0, rr);
-                        uint4 u[2];
-                        __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
+                for (int c0 = 0; c0 < C; c0 += 16) {
+                    float rr[16];
+                    load16(vin + pix * C + c0, rr);
+                    uint4 u[2];
+                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int c = c0 + 2 * j;
-                            hh[j] = __floats2bfloat162_rn(rr[2 * j] + v[c] + misc[2 * C + c],
-                                                          rr[2 * j + 1] + v[c + 1] + misc[2 * C + c + 1]);
-                            // the logits from V' as stored, as the on-demand decode computes them
-                            const float2 o = __bfloat1622float2(hh[j]);
-                            t = fmaf(o.y, misc[3 * C + c + 1], fmaf(o.x, misc[3 * C + c], t));
-                            s = fmaf(o.y, misc[4 * C + c + 1], fmaf(o.x, misc[4 * C + c], s));
-                        }
-                        out[c0 / 8] = u[0];
-                        out[c0 / 8 + 1] = u[1];
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = c0 + 2 * j;
+                        hh[j] = __floats2bfloat162_rn(rr[2 * j] + v[c] + misc[2 * C + c],
+                                                      rr[2 * j + 1] + v[c + 1] + misc[2 * C + c + 1]);
+                        // the logits from V' as stored, as the on-demand decode computes them
+                        const float2 o = __bfloat1622float2(hh[j]);
+                        t = fmaf(o.y, misc[3 * C + c + 1], fmaf(o.x, misc[3 * C + c], t));
+                        s = fmaf(o.y, misc[4 * C + c + 1], fmaf(o.x, misc[4 * C + c], s));
                     }
-                    if (a.t_raw) {
-                        a.t_raw[pix * L + li] = t;
-                        a.s_raw[pix * L + li] = s;
-                    }
+                    out[c0 / 8] = u[0];
+                    out[c0 / 8 + 1] = u[1];
+                }
+                if (a.t_raw) {
+                    a.t_raw[pix * L + li] = t;
+                    a.s_raw[pix * L + li] = s;
                 }
             }
+            umma::fence_before_sync();
+            umma::mbar_arrive(e2done);
         }
-        umma::fence_before_sync();  // this tile's TMEM reads before the next tile's MMAs
-    }
-    // on a timeout, give the MMAs still in flight another bounded wait before freeing TMEM
-    if (failed && tid == 0) {
-        atomicExch(a.err, fail_code);
-        umma::mbar_wait(mbar, phase, TC_WAIT_NS);
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 0) umma::tmem_dealloc(tmem, TMEM_COLS);
+    if (tid == 0 && *s_err) atomicExch(a.err, *s_err & 2 ? 2 : 1);
+    if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
-// Tile geometry for a W x H plane (L planes) that minimises the MMA blocks of the slowest CTA: for
-// every column split (OW = ceil(W / tx)) and row count R whose input tile fits the buffer (including
-// the reads of the last block, NB1 * 128 + 2 P + 2 pixels) and whose conv1 blocks fit TMEM, the
-// cost is the tiles per CTA slot times (NB1 + NB2 + 3), the 3 standing for a tile's load and
-// epilogue overheads.
+// Tile geometry for a W x H plane (L planes) that minimises the MMA blocks of the busiest CTA: for
+// every column split (OW = ceil(W / tx)) and row count R whose input tile fits a buffer (including
+// the reads of the last block, NB1 * 128 + 2 P + 2 pixels) and whose conv1 blocks fit half the
+// TMEM, the cost is the tiles per CTA times (NB1 + NB2 + 3), the 3 standing for a tile's load and
+// epilogue overheads.  (Weighting the pipeline's fill and drain, which favours more and smaller
+// tiles on small planes, measured slower.)
 template <int C>
 static ConvTile choose_tile(int W, int H, int L, int slots) {
     using S = TcSmem<C>;
@@ -363,13 +415,13 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
     for (const Entry& c : cache)
         if (c.t.P && c.W == a.W && c.H == a.H && c.L == a.L) tg = c.t;
     if (!tg.P) {
-        tg = choose_tile<C>(a.W, a.H, a.L, 2 * sms);
+        tg = choose_tile<C>(a.W, a.H, a.L, sms);
         if (!tg.P) return cudaErrorInvalidValue;
         cache[next] = Entry{a.W, a.H, a.L, tg};
         next = (next + 1) % 8;
     }
     const long ntiles = (long)tg.tiles_x * tg.tiles_y * a.L;
-    const int grid = (int)std::min<long>(ntiles, 2L * sms);
+    const int grid = (int)std::min<long>(ntiles, (long)sms);
     k<<<grid, TC_THREADS, smem, st>>>(a, tg);
     return cudaGetLastError();
 }
