@@ -24,6 +24,7 @@ namespace quark {
 constexpr int AT_M = 128;
 constexpr int AT_TW = 16, AT_TH = 8;  // pixel tile of the 128 elements
 constexpr uint64_t AT_WAIT_NS = 1000000000ull;
+constexpr float AT_SLACK = 20.f;  // log2 units: a factor of about 1e6
 
 // Shared memory of one CTA.  Only the query columns in use are copied (the blend query exists
 // on the last step only) and the blend logits are staged for the V views present, so that the
@@ -47,35 +48,45 @@ struct AtSmem {
 
 
 
-// Packed FP32x2 arithmetic (sm_100 family): two channels per instruction.
-__device__ __forceinline__ float2 bf2_to_f2(uint32_t x) {
-    return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+// Bilinear interpolation of BF16 features on the mixed-precision FMA (PTX fma.rn.f32.bf16, sm_100
+// family): d = a b + c with BF16 a (a feature channel, straight from its half of the loaded word)
+// and b (the tap weight, rounded to BF16 once per tap), FP32 c and d -- one rounding per tap, FP32
+// accumulation, no conversion of the features.
+__device__ __forceinline__ float fma_bf16(uint16_t a, uint16_t b, float c) {
+    float d;
+    asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
 }
+__device__ __forceinline__ float2 fma_bf16x2(uint32_t x, uint16_t w, float2 c) {
+    return make_float2(fma_bf16((uint16_t)(x & 0xffffu), w, c.x), fma_bf16((uint16_t)(x >> 16), w, c.y));
+}
+__device__ __forceinline__ uint16_t bf16_bits(float w) { return __bfloat16_as_ushort(__float2bfloat16_rn(w)); }
 __device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
     const uint4* q = reinterpret_cast<const uint4*>(p);
     const uint4 a = __ldg(q), b = __ldg(q + 1);
-    const float2 w2 = make_float2(w, w);
-    D[0] = __fmul2_rn(bf2_to_f2(a.x), w2);
-    D[1] = __fmul2_rn(bf2_to_f2(a.y), w2);
-    D[2] = __fmul2_rn(bf2_to_f2(a.z), w2);
-    D[3] = __fmul2_rn(bf2_to_f2(a.w), w2);
-    D[4] = __fmul2_rn(bf2_to_f2(b.x), w2);
-    D[5] = __fmul2_rn(bf2_to_f2(b.y), w2);
-    D[6] = __fmul2_rn(bf2_to_f2(b.z), w2);
-    D[7] = __fmul2_rn(bf2_to_f2(b.w), w2);
+    const uint16_t wb = bf16_bits(w);
+    const float2 z = make_float2(0.f, 0.f);
+    D[0] = fma_bf16x2(a.x, wb, z);
+    D[1] = fma_bf16x2(a.y, wb, z);
+    D[2] = fma_bf16x2(a.z, wb, z);
+    D[3] = fma_bf16x2(a.w, wb, z);
+    D[4] = fma_bf16x2(b.x, wb, z);
+    D[5] = fma_bf16x2(b.y, wb, z);
+    D[6] = fma_bf16x2(b.z, wb, z);
+    D[7] = fma_bf16x2(b.w, wb, z);
 }
 __device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
     const uint4* q = reinterpret_cast<const uint4*>(p);
     const uint4 a = __ldg(q), b = __ldg(q + 1);
-    const float2 w2 = make_float2(w, w);
-    D[0] = __ffma2_rn(bf2_to_f2(a.x), w2, D[0]);
-    D[1] = __ffma2_rn(bf2_to_f2(a.y), w2, D[1]);
-    D[2] = __ffma2_rn(bf2_to_f2(a.z), w2, D[2]);
-    D[3] = __ffma2_rn(bf2_to_f2(a.w), w2, D[3]);
-    D[4] = __ffma2_rn(bf2_to_f2(b.x), w2, D[4]);
-    D[5] = __ffma2_rn(bf2_to_f2(b.y), w2, D[5]);
-    D[6] = __ffma2_rn(bf2_to_f2(b.z), w2, D[6]);
-    D[7] = __ffma2_rn(bf2_to_f2(b.w), w2, D[7]);
+    const uint16_t wb = bf16_bits(w);
+    D[0] = fma_bf16x2(a.x, wb, D[0]);
+    D[1] = fma_bf16x2(a.y, wb, D[1]);
+    D[2] = fma_bf16x2(a.z, wb, D[2]);
+    D[3] = fma_bf16x2(a.w, wb, D[3]);
+    D[4] = fma_bf16x2(b.x, wb, D[4]);
+    D[5] = fma_bf16x2(b.y, wb, D[5]);
+    D[6] = fma_bf16x2(b.z, wb, D[6]);
+    D[7] = fma_bf16x2(b.w, wb, D[7]);
 }
 // The softmax below works in log2 units, so that each weight is one ex2 (ex2_approx); the
 // reprojection divides with one reciprocal (reproject_rcp).
@@ -262,7 +273,11 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 }
 #pragma unroll
                 for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                if (s > mx[h]) {  // the running maximum moves: rescale (rare after the first views)
+                // The softmax is invariant to the reference subtracted from its logits, so the
+                // reference moves only when a logit passes it by AT_SLACK (log2 units): taken at the
+                // first view and then almost never, the branch stays uniform across the warp.
+                // Weights stay <= 2^AT_SLACK, far from FP32 overflow.
+                if (s > mx[h] + AT_SLACK) {
                     const float cs = ex2_approx(mx[h] - s);
                     const float2 cs2 = make_float2(cs, cs);
                     l[h] *= cs;
