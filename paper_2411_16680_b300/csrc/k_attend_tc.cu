@@ -61,9 +61,17 @@ __device__ __forceinline__ float2 fma_bf16x2(uint32_t x, uint16_t w, float2 c) {
     return make_float2(fma_bf16((uint16_t)(x & 0xffffu), w, c.x), fma_bf16((uint16_t)(x >> 16), w, c.y));
 }
 __device__ __forceinline__ uint16_t bf16_bits(float w) { return __bfloat16_as_ushort(__float2bfloat16_rn(w)); }
+// One thread's 16 BF16 channels of a texel (32 bytes, 32-byte aligned: a texel is C x 2 bytes and
+// a thread's channel group starts at a multiple of 16 channels) in one 256-bit read-only load
+// (sm_100 family): a whole L1 sector per thread and half the load instructions of two 128-bit loads.
+__device__ __forceinline__ void ldg256(const void* p, uint4& a, uint4& b) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
 __device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    uint4 a, b;
+    ldg256(p, a, b);
     const uint16_t wb = bf16_bits(w);
     const float2 z = make_float2(0.f, 0.f);
     D[0] = fma_bf16x2(a.x, wb, z);
@@ -76,8 +84,8 @@ __device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, floa
     D[7] = fma_bf16x2(b.w, wb, z);
 }
 __device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    uint4 a, b;
+    ldg256(p, a, b);
     const uint16_t wb = bf16_bits(w);
     D[0] = fma_bf16x2(a.x, wb, D[0]);
     D[1] = fma_bf16x2(a.y, wb, D[1]);
@@ -127,13 +135,26 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     // ---- volume entering the step, depth, RMSNorm ----
     // Each thread of an element's group holds its own 16 channels (vres); the depth logit and the
     // mean square are partial sums over those channels, completed with shuffles in the group.
+    // Through the view loop the entering volume is held only as BF16 pairs (vpk) for the residual:
+    // the stored words when the step keeps the resolution; when it doubles it, the x2-upsampled
+    // volume rounded to BF16 (as it would be stored), which the norm and the depth use too.  The
+    // first step's constant v0 is read again from shared memory.
     __syncthreads();
     float vres[16];
+    uint32_t vpk[8];
     if (TR == TR_INIT) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) vres[i] = misc[c0 + i];
     } else if (TR == TR_SAME) {
-        load16(reinterpret_cast<const __nv_bfloat16*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0, vres);
+        uint4 u0, u1;
+        ldg256(reinterpret_cast<const __nv_bfloat16*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0, u0, u1);
+        vpk[0] = u0.x; vpk[1] = u0.y; vpk[2] = u0.z; vpk[3] = u0.w;
+        vpk[4] = u1.x; vpk[5] = u1.y; vpk[6] = u1.z; vpk[7] = u1.w;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            vres[2 * j] = __uint_as_float(vpk[j] << 16);
+            vres[2 * j + 1] = __uint_as_float(vpk[j] & 0xffff0000u);
+        }
     } else {
         int ya, yb, xa, xb;
         float wy, wx;
@@ -141,16 +162,31 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         resize_taps(xc, 2, a.Wp, xa, xb, wx);
         const __nv_bfloat16* base =
             reinterpret_cast<const __nv_bfloat16*>(a.prev) + (size_t)li * a.Hp * a.Wp * C + c0;
-        float t00[16], t01[16], t10[16], t11[16];
-        load16(base + ((size_t)ya * a.Wp + xa) * C, t00);
-        load16(base + ((size_t)ya * a.Wp + xb) * C, t01);
-        load16(base + ((size_t)yb * a.Wp + xa) * C, t10);
-        load16(base + ((size_t)yb * a.Wp + xb) * C, t11);
+        uint4 r[4][2];
+        ldg256(base + ((size_t)ya * a.Wp + xa) * C, r[0][0], r[0][1]);
+        ldg256(base + ((size_t)ya * a.Wp + xb) * C, r[1][0], r[1][1]);
+        ldg256(base + ((size_t)yb * a.Wp + xa) * C, r[2][0], r[2][1]);
+        ldg256(base + ((size_t)yb * a.Wp + xb) * C, r[3][0], r[3][1]);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float top = t00[i] + wx * (t01[i] - t00[i]);
-            const float bot = t10[i] + wx * (t11[i] - t10[i]);
-            vres[i] = top + wy * (bot - top);
+        for (int j = 0; j < 8; ++j) {
+            float t[4][2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t w = (&r[q][j / 4].x)[j % 4];
+                t[q][0] = __uint_as_float(w << 16);
+                t[q][1] = __uint_as_float(w & 0xffff0000u);
+            }
+            float v2[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float top = t[0][i] + wx * (t[1][i] - t[0][i]);
+                const float bot = t[2][i] + wx * (t[3][i] - t[2][i]);
+                v2[i] = top + wy * (bot - top);
+            }
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v2[0], v2[1]);
+            vpk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+            vres[2 * j] = __uint_as_float(vpk[j] << 16);
+            vres[2 * j + 1] = __uint_as_float(vpk[j] & 0xffff0000u);
         }
     }
     float tpart = 0.f, ms = 0.f;
@@ -229,9 +265,9 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     umma::fence_after_sync();
 
     if (!failed) {
-        // the queries stay in shared memory (read once per view) to keep registers for the gathers
+        // the queries stay in shared memory (read once per pair of views) to keep registers for the gathers
         const float4* qh4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + c0);
-        // the blend query stays in shared memory (read once per view) to keep registers for the loop
+        // the blend query likewise
         const float4* qb4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
 
         // ---- views: sample, online softmax (log2 units), weighted sum (FP32) ----
@@ -245,64 +281,110 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) o[h][j] = make_float2(0.f, 0.f);
         }
-        const __nv_bfloat16* feat_m = reinterpret_cast<const __nv_bfloat16*>(a.feat) + c0;
+        const __nv_bfloat16* feat0 = reinterpret_cast<const __nv_bfloat16*>(a.feat) + c0;
         const int vstride = a.fh * a.fw * C;  // < 2^31 for every accepted level size
-        for (int m = 0; m < a.V; ++m, feat_m += vstride) {
-            // the four taps are always fetched (clamped into the map, weight zero outside it): no
-            // branch, so the eight loads of the view are in flight together
+        // Bilinear sample of view m: the four taps are always fetched (clamped into the map, weight
+        // zero outside it), with no branch, so all the loads of the view are in flight together.
+        auto sample = [&](int m, float2 (&D)[8]) {
             float u = 0.f, v = 0.f;
             const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
             const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
-            float2 D[8];
-            mul_taps16(feat_m + tp.i00 * C, tp.w00, D);
-            fma_taps16(feat_m + tp.i01 * C, tp.w01, D);
-            fma_taps16(feat_m + tp.i10 * C, tp.w10, D);
-            fma_taps16(feat_m + tp.i11 * C, tp.w11, D);
+            const __nv_bfloat16* f = feat0 + (size_t)m * vstride;
+            mul_taps16(f + tp.i00 * C, tp.w00, D);
+            fma_taps16(f + tp.i01 * C, tp.w01, D);
+            fma_taps16(f + tp.i10 * C, tp.w10, D);
+            fma_taps16(f + tp.i11 * C, tp.w11, D);
+        };
+        // One online-softmax step of head h: logit s (log2 units, this element's full sum), sample D.
+        // The softmax is invariant to the reference subtracted from its logits, so the reference
+        // moves only when a logit passes it by AT_SLACK (log2 units): taken at the first view and
+        // then almost never, the branch stays uniform across the warp.  Weights stay <= 2^AT_SLACK,
+        // far from FP32 overflow.
+        auto accumulate = [&](int h, float s, const float2 (&D)[8]) {
+            if (s > mx[h] + AT_SLACK) {
+                const float cs = ex2_approx(mx[h] - s);
+                const float2 cs2 = make_float2(cs, cs);
+                l[h] *= cs;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) o[h][j] = __fmul2_rn(o[h][j], cs2);
+                mx[h] = s;
+            }
+            const float p = ex2_approx(s - mx[h]);
+            const float2 p2 = make_float2(p, p);
+            l[h] += p;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[h][j] = __ffma2_rn(p2, D[j], o[h][j]);
+        };
+        auto group_sum = [](float s) {
+#pragma unroll
+            for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            return s;
+        };
+        // Views in pairs: each query float4 is read from shared memory once for two samples (the
+        // shared-memory reads of the queries were the larger part of the L1 data-pipe traffic).
+        // Each view's arithmetic, and the order of the softmax steps, is that of one view at a time.
+        int m = 0;
+        for (; m + 1 < a.V; m += 2) {
+            float2 Da[8], Db[8];
+            sample(m, Da);
+            sample(m + 1, Db);
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
-                float s;
-                {
-                    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+                float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 q4 = qh4[h * C / 4 + i];
-                        acc0 = __ffma2_rn(make_float2(q4.x, q4.y), D[2 * i], acc0);
-                        acc1 = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], acc1);
-                    }
-                    s = (acc0.x + acc1.x) + (acc0.y + acc1.y);
+                for (int i = 0; i < 4; ++i) {
+                    const float4 q4 = qh4[h * C / 4 + i];
+                    a0 = __ffma2_rn(make_float2(q4.x, q4.y), Da[2 * i], a0);
+                    a1 = __ffma2_rn(make_float2(q4.z, q4.w), Da[2 * i + 1], a1);
+                    b0 = __ffma2_rn(make_float2(q4.x, q4.y), Db[2 * i], b0);
+                    b1 = __ffma2_rn(make_float2(q4.z, q4.w), Db[2 * i + 1], b1);
                 }
-#pragma unroll
-                for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                // The softmax is invariant to the reference subtracted from its logits, so the
-                // reference moves only when a logit passes it by AT_SLACK (log2 units): taken at the
-                // first view and then almost never, the branch stays uniform across the warp.
-                // Weights stay <= 2^AT_SLACK, far from FP32 overflow.
-                if (s > mx[h] + AT_SLACK) {
-                    const float cs = ex2_approx(mx[h] - s);
-                    const float2 cs2 = make_float2(cs, cs);
-                    l[h] *= cs;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) o[h][j] = __fmul2_rn(o[h][j], cs2);
-                    mx[h] = s;
-                }
-                const float p = ex2_approx(s - mx[h]);
-                const float2 p2 = make_float2(p, p);
-                l[h] += p;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) o[h][j] = __ffma2_rn(p2, D[j], o[h][j]);
+                const float sa = group_sum((a0.x + a1.x) + (a0.y + a1.y));
+                const float sb = group_sum((b0.x + b1.x) + (b0.y + b1.y));
+                accumulate(h, sa, Da);
+                accumulate(h, sb, Db);
             }
             if constexpr (LAST) {
-                float2 acc = make_float2(0.f, 0.f);
+                float2 ba = make_float2(0.f, 0.f), bb = ba;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const float4 q4 = qb4[i];
-                    acc = __ffma2_rn(make_float2(q4.x, q4.y), D[2 * i], acc);
-                    acc = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], acc);
+                    ba = __ffma2_rn(make_float2(q4.x, q4.y), Da[2 * i], ba);
+                    ba = __ffma2_rn(make_float2(q4.z, q4.w), Da[2 * i + 1], ba);
+                    bb = __ffma2_rn(make_float2(q4.x, q4.y), Db[2 * i], bb);
+                    bb = __ffma2_rn(make_float2(q4.z, q4.w), Db[2 * i + 1], bb);
                 }
-                float s = acc.x + acc.y;
+                const float sa = group_sum(ba.x + ba.y), sb = group_sum(bb.x + bb.y);
+                if (sub == 0) {
+                    s_beta[e * a.V + m] = sa;
+                    s_beta[e * a.V + m + 1] = sb;
+                }
+            }
+        }
+        if (m < a.V) {  // the last view of an odd count
+            float2 D[8];
+            sample(m, D);
 #pragma unroll
-                for (int off = 1; off < TPE; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                if (sub == 0) s_beta[e * a.V + m] = s;
+            for (int h = 0; h < NH; ++h) {
+                float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 q4 = qh4[h * C / 4 + i];
+                    a0 = __ffma2_rn(make_float2(q4.x, q4.y), D[2 * i], a0);
+                    a1 = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], a1);
+                }
+                accumulate(h, group_sum((a0.x + a1.x) + (a0.y + a1.y)), D);
+            }
+            if constexpr (LAST) {
+                float2 ba = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 q4 = qb4[i];
+                    ba = __ffma2_rn(make_float2(q4.x, q4.y), D[2 * i], ba);
+                    ba = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], ba);
+                }
+                const float sa = group_sum(ba.x + ba.y);
+                if (sub == 0) s_beta[e * a.V + m] = sa;
             }
         }
         // head outputs -> BF16 A operand (K = h * C + channel)
@@ -354,15 +436,25 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         __syncthreads();
         umma::fence_after_sync();
         if (!failed && live) {
-            float out[16];
+            float vin[16], out[16];
+            if (TR == TR_INIT) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) vin[i] = misc[c0 + i];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    vin[2 * j] = __uint_as_float(vpk[j] << 16);
+                    vin[2 * j + 1] = __uint_as_float(vpk[j] & 0xffff0000u);
+                }
+            }
             const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + c0);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 float4 t = src[i];
-                out[4 * i] = vres[4 * i] + t.x;
-                out[4 * i + 1] = vres[4 * i + 1] + t.y;
-                out[4 * i + 2] = vres[4 * i + 2] + t.z;
-                out[4 * i + 3] = vres[4 * i + 3] + t.w;
+                out[4 * i] = vin[4 * i] + t.x;
+                out[4 * i + 1] = vin[4 * i + 1] + t.y;
+                out[4 * i + 2] = vin[4 * i + 2] + t.z;
+                out[4 * i + 3] = vin[4 * i + 3] + t.w;
             }
             {
                 uint4 u[2];
@@ -422,6 +514,8 @@ static cudaError_t launch_tc_c(const AttendArgs& a, int heads, Transition tr, bo
 
 cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
+    // 256-bit loads of the taps and of the entering volume
+    if (reinterpret_cast<uintptr_t>(a.feat) % 32 || reinterpret_cast<uintptr_t>(a.prev) % 32) return cudaErrorMisalignedAddress;
     if (C == 16) return launch_tc_c<16>(a, heads, tr, last, st);
     if (C == 32) return launch_tc_c<32>(a, heads, tr, last, st);
     return cudaErrorInvalidValue;
