@@ -303,28 +303,34 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     w = work[fam]
     bytes_per_launch = w["bytes"] / w["launches"]
     flops_per_launch = w["flops"] / w["launches"]
-    if fam == "conv_block" and cfg.precision == 1:
-        # the BF16 conv block runs on the tensor cores: its FLOPs against the sustained BF16 peak
-        # (a kernel timed inside a long step)
-        achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
-        peak = peaks["bf16_tflops_sustained"]
-        r = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
-             "peak_source": f"{peaks['source']} BF16 dense, sustained"}
-    elif fam == "conv_block":
-        achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
-        peak = accounting.fp32_alu_peak_tflops(peaks["sm_max_mhz"])
-        r = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-             "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 FLOP x {peaks['sm_max_mhz']:.0f} MHz"}
-    else:
-        achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]
-        r = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-             "peak_source": f"{peaks['source']} copy bandwidth"}
-    r["frac"] = round(r["achieved"] / r["peak"], 4)
+    # Every roofline the launch meets: HBM for its compulsory bytes, the tensor pipe for its
+    # contractions on tcgen05 (BF16 form), the FP32 SIMT pipes for the rest of its FLOPs.  The
+    # binding one is the one whose time at peak is longest; its fraction is the headline.
+    tensor_flops = w.get("tensor_flops", 0.0) / w["launches"]
+    alu_flops = flops_per_launch - tensor_flops
+    sec = per_launch_ms * 1e-3
+    alu_peak = accounting.fp32_alu_peak_tflops(peaks["sm_max_mhz"])
+    cands = {
+        "hbm": (bytes_per_launch / (peaks["hbm_gbs"] * 1e9), bytes_per_launch / sec / 1e9, peaks["hbm_gbs"], "GB/s",
+                f"{peaks['source']} copy bandwidth"),
+        "alu": (alu_flops / (alu_peak * 1e12), alu_flops / sec / 1e12, round(alu_peak, 1), "TFLOP/s",
+                f"derived: 148 SMs x 128 FP32 lanes x 2 FLOP x {peaks['sm_max_mhz']:.0f} MHz"),
+    }
+    if tensor_flops > 0:
+        tp = peaks["bf16_tflops_sustained"]
+        cands["tensor"] = (tensor_flops / (tp * 1e12), tensor_flops / sec / 1e12, tp, "TFLOP/s",
+                           f"{peaks['source']} BF16 dense, sustained")
+    bound = max(cands, key=lambda k: cands[k][0])
+    _, ach, peak, unit, src = cands[bound]
+    r = {"bound": bound, "achieved": round(ach, 2 if unit != "GB/s" else 1), "peak": peak, "unit": unit,
+         "peak_source": src}
+    r["fractions"] = {k: round(v[1] / v[2], 4) for k, v in cands.items()}
+    r["frac"] = r["fractions"][bound]
     r["kernel"] = fam
     r["traffic"] = measured_traffic(fam, cfg, bytes_per_launch)
     r["algorithmic_bytes_per_launch"] = int(bytes_per_launch)
     r["algorithmic_flops_per_launch"] = int(flops_per_launch)
+    r["tensor_flops_per_launch"] = int(tensor_flops)
     r["avg_launch_ms"] = round(per_launch_ms, 4)
     r["kernels_ms_per_frame"] = {k: round(v[1] / max(steps_done, 1), 4) for k, v in res["ktimes"].items()}
     return r

@@ -14,8 +14,11 @@ from typing import Dict
 def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, float]]:
     C = cfg.C
     elt = 2 if cfg.precision == 1 else 4
-    out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "launches": 0}
+    # "tensor_flops": the part of "flops" that runs on the tensor cores (BF16 form); the rest runs
+    # on the FP32 SIMT pipes
+    out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "tensor_flops": 0.0, "launches": 0}
                                         for k in ("encode", "collapse", "attend", "conv_block", "render", "refine")}
+    tc = cfg.precision == 1
     # encode: images in, every used level out, RGBA copy out
     e = out["encode"]
     e["bytes"] += V * img_h * img_w * (3 * 4 + 16)
@@ -37,10 +40,12 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
                 c = out["collapse"]
                 c["bytes"] += (Lp + L) * Hp * Wp * C * elt
                 c["flops"] += 2 * 3 * C * C * L * Hp * Wp
+                c["tensor_flops"] += 2 * 3 * C * C * L * Hp * Wp if tc else 0
                 c["launches"] += 1
         cb = out["conv_block"]
         cb["bytes"] += 2 * E * C * elt + (2 * E * 4 if last else 0)  # V in and out; raw logits of the last step
         cb["flops"] += 2 * (18 * C * C + 5 * C) * E
+        cb["tensor_flops"] += 2 * 18 * C * C * E if tc else 0
         cb["launches"] += 1
         if h == 0:
             continue  # a block without attention: its conv block only
@@ -80,8 +85,13 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
             a["launches"] += 2
         else:
             a["bytes"] += vin + texels * C * elt + E * C * elt + (E * V * 4 if last else 0)
-            macs = 2 * h * C * C + 2 * V * h * C + 4 * V * C + (C * C + V * C if last else 0)
+            # per element: the projections X W^q (+ the blend query X W^beta) and O W^O (tensor cores
+            # in the BF16 form), per view the bilinear sample, h logits, h weighted sums and the
+            # blend logit (SIMT)
+            proj = 2 * h * C * C + (C * C if last else 0)
+            macs = proj + 2 * V * h * C + 4 * V * C + (V * C if last else 0)
             a["flops"] += 2 * macs * E
+            a["tensor_flops"] += 2 * proj * E if tc else 0
             a["launches"] += 1
     L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
     r = out["render"]

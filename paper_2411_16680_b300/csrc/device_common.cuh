@@ -12,6 +12,14 @@ namespace quark {
 
 // ---- 16-channel vector loads/stores in the storage type --------------------------------------
 
+// 32 bytes of read-only data in one 256-bit load (sm_100 family; global memory only; `p` 32-byte
+// aligned): a whole L1 sector per thread, half the load instructions of two 128-bit loads.
+__device__ __forceinline__ void ldg256(const void* p, uint4& a, uint4& b) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
+
 __device__ __forceinline__ void load16(const float* __restrict__ p, float (&o)[16]) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll

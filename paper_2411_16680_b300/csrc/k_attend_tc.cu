@@ -61,14 +61,8 @@ __device__ __forceinline__ float2 fma_bf16x2(uint32_t x, uint16_t w, float2 c) {
     return make_float2(fma_bf16((uint16_t)(x & 0xffffu), w, c.x), fma_bf16((uint16_t)(x >> 16), w, c.y));
 }
 __device__ __forceinline__ uint16_t bf16_bits(float w) { return __bfloat16_as_ushort(__float2bfloat16_rn(w)); }
-// One thread's 16 BF16 channels of a texel (32 bytes, 32-byte aligned: a texel is C x 2 bytes and
-// a thread's channel group starts at a multiple of 16 channels) in one 256-bit read-only load
-// (sm_100 family): a whole L1 sector per thread and half the load instructions of two 128-bit loads.
-__device__ __forceinline__ void ldg256(const void* p, uint4& a, uint4& b) {
-    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
-                 : "l"(p));
-}
+// The taps: one thread's 16 BF16 channels of a texel (32 bytes, 32-byte aligned: a texel is C x 2
+// bytes and a thread's channel group starts at a multiple of 16 channels) in one 256-bit load.
 __device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
     uint4 a, b;
     ldg256(p, a, b);

@@ -179,10 +179,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                     const int p = p0 + u * NLOAD;
                     const int gy = y0 - 2 + p / P, gx = x0 - 2 + p % P;
                     in[u] = p < NIN && gy >= 0 && gy < H && gx >= 0 && gx < W;
-                    const uint4* src =
-                        reinterpret_cast<const uint4*>(vin + ((size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0)) * C);
+                    // a pixel's channels in 256-bit loads (whole sectors), from the clamped address
+                    const __nv_bfloat16* src = vin + ((size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0)) * C;
 #pragma unroll
-                    for (int g = 0; g < C / 8; ++g) raw[u][g] = in[u] ? __ldg(src + g) : make_uint4(0, 0, 0, 0);
+                    for (int g = 0; g < C / 16; ++g) ldg256(src + 16 * g, raw[u][2 * g], raw[u][2 * g + 1]);
+#pragma unroll
+                    for (int g = 0; g < C / 8; ++g)
+                        if (!in[u]) raw[u][g] = make_uint4(0, 0, 0, 0);
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
@@ -428,6 +431,7 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
 
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(a.in) % 32) return cudaErrorMisalignedAddress;  // 256-bit pixel loads
     if (C == 16) return launch_tc<16>(a, st);
     if (C == 32) return launch_tc<32>(a, st);
     return cudaErrorInvalidValue;
