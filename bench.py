@@ -305,7 +305,8 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     flops_per_launch = w["flops"] / w["launches"]
     # Every roofline the launch meets: HBM for its compulsory bytes, the tensor pipe for its
     # contractions on tcgen05 (BF16 form), the FP32 SIMT pipes for the rest of its FLOPs.  The
-    # binding one is the one whose time at peak is longest; its fraction is the headline.
+    # headline is the sampling kernels' HBM roofline (the conv block's tensor roofline in the BF16
+    # form, its SIMT one in FP32); "binding" names the one whose time at peak is longest.
     tensor_flops = w.get("tensor_flops", 0.0) / w["launches"]
     alu_flops = flops_per_launch - tensor_flops
     sec = per_launch_ms * 1e-3
@@ -320,11 +321,13 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
         tp = peaks["bf16_tflops_sustained"]
         cands["tensor"] = (tensor_flops / (tp * 1e12), tensor_flops / sec / 1e12, tp, "TFLOP/s",
                            f"{peaks['source']} BF16 dense, sustained")
-    bound = max(cands, key=lambda k: cands[k][0])
+    binding = max(cands, key=lambda k: cands[k][0])
+    bound = ("tensor" if "tensor" in cands else "alu") if fam == "conv_block" else "hbm"
     _, ach, peak, unit, src = cands[bound]
     r = {"bound": bound, "achieved": round(ach, 2 if unit != "GB/s" else 1), "peak": peak, "unit": unit,
          "peak_source": src}
     r["fractions"] = {k: round(v[1] / v[2], 4) for k, v in cands.items()}
+    r["binding"] = binding
     r["frac"] = r["fractions"][bound]
     r["kernel"] = fam
     r["traffic"] = measured_traffic(fam, cfg, bytes_per_launch)
