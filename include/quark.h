@@ -276,7 +276,9 @@ quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, q
  *   v_out     this step's output volume [L][H][W][C], same element type
  *   colour [L][H][W][3], alpha / depth [L][H][W], t_raw / s_raw [H][W][L] (float32)
  *   beta      blend logits [H][W][L][V] (float32), required on the last step, else ignored
- * All buffers are device memory owned by the caller.  The two intermediates (the volume after
+ * All buffers are device memory owned by the caller; v_prev, v_out and beta must start on a
+ * 32-byte boundary (the kernels move them in 16- and 32-byte vectors; cudaMalloc and PyTorch's
+ * allocator give 256), else QUARK_EINVAL.  The two intermediates (the volume after
  * the attention block and, where L halves, the collapsed volume) live in one static device
  * array of QUARK_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds until the
  * process exits; a step whose intermediates need more returns QUARK_EINVAL (use

@@ -494,10 +494,14 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             uint16_t* bo = bq + (size_t)NQ * C;
             const size_t att_elems = h > 0 ? (size_t)NQ * C + (size_t)C * h * C : 0;
             if (h > 0) {
+                // the logit scale 1/sqrt(C) is folded into W^q and W^beta, and for the attention
+                // heads also log2(e) (their softmax runs on exp2)
+                const double qs = 1.0 / std::sqrt((double)C), log2e = 1.4426950408889634;
                 for (int n = 0; n < NQ; ++n)
                     for (int k = 0; k < C; ++k) {
-                        float v = n < h * C ? w->Wq[j][(size_t)k * h * C + n] : w->W_beta[(size_t)k * C + (n - h * C)];
-                        bq[(size_t)(k / 8) * NQ * 8 + n * 8 + k % 8] = to_bf16_bits(v);
+                        const double v = n < h * C ? w->Wq[j][(size_t)k * h * C + n] * qs * log2e
+                                                   : w->W_beta[(size_t)k * C + (n - h * C)] * qs;
+                        bq[(size_t)(k / 8) * NQ * 8 + n * 8 + k % 8] = to_bf16_bits((float)v);
                     }
                 for (int n = 0; n < C; ++n)
                     for (int k = 0; k < h * C; ++k)

@@ -240,18 +240,16 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     uint32_t failed_phase = 0;
     umma::fence_after_sync();
     if (!failed) {
-        // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16
+        // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16.  The logit
+        // scale 1/sqrt(C), and for the attention heads log2(e) (the softmax below runs on ex2), is
+        // folded into the packed W^q and W^beta.
         const int q = warp & 3, grp = warp >> 2;
-        // the 1/sqrt(C) of the logits is folded into the queries here, and for the attention heads
-        // also log2(e), so that the softmax below runs on ex2
-        const float qscale = rsqrtf((float)C);
         for (int ch = grp; ch < NQ_USED / 16; ch += TPE) {
             float v[16];
             umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
-            const float f = ch * 16 < NH * C ? qscale * 1.4426950408889634f : qscale;
             float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i] * f, v[4 * i + 1] * f, v[4 * i + 2] * f, v[4 * i + 3] * f);
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
     }
     umma::fence_before_sync();
@@ -462,9 +460,16 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         }
         if constexpr (LAST) {
             // blend logits of the element, contiguous [m] in the [H][W][L][V] layout
-            if (!failed && live)
-                for (int m = sub; m < a.V; m += TPE)
-                    __stcs(a.beta + (((size_t)y * W + x) * L + li) * a.V + m, s_beta[e * a.V + m]);
+            if (!failed && live) {
+                float* dst = a.beta + (((size_t)y * W + x) * L + li) * a.V;
+                const float* src = s_beta + e * a.V;
+                if (a.V % (4 * TPE) == 0) {  // 16-byte runs: the element's views split across its lanes
+                    for (int m = 4 * sub; m < a.V; m += 4 * TPE)
+                        __stcs(reinterpret_cast<float4*>(dst + m), *reinterpret_cast<const float4*>(src + m));
+                } else {
+                    for (int m = sub; m < a.V; m += TPE) __stcs(dst + m, src[m]);
+                }
+            }
         }
     }
     if (failed && tid == 0) atomicExch(a.err, 3 + (int)failed_phase);

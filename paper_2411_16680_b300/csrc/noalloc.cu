@@ -64,6 +64,9 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     if (scale > 0 && !v_prev) return qk_fail(ctx, QUARK_EINVAL, "step %d needs the previous step's volume", scale);
     const bool last = scale == c.n_scales - 1;
     if (last && !beta) return qk_fail(ctx, QUARK_EINVAL, "the last step writes blend logits: beta is NULL");
+    if (reinterpret_cast<uintptr_t>(v_out) % 32 || (scale > 0 && reinterpret_cast<uintptr_t>(v_prev) % 32) ||
+        (last && reinterpret_cast<uintptr_t>(beta) % 32))
+        return qk_fail(ctx, QUARK_EINVAL, "v_prev, v_out and beta must be 32-byte aligned");
     quark_status s = qk_validate_camera(ctx, *target, "target");
     if (s != QUARK_OK) return s;
     for (int j = 0; j < c.n_scales; ++j)

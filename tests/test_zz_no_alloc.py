@@ -87,3 +87,20 @@ def test_noalloc_refuses_a_step_larger_than_its_scratch():
         ctx.update_fuse_noalloc(pyr, 0, target, None, small, small, small, small, small, small, small)
     assert e.value.status == quark.EINVAL
     assert "static scratch" in str(e.value)
+
+
+def test_noalloc_refuses_unaligned_buffers():
+    # the kernels move v_prev, v_out and beta in 16- and 32-byte vectors: a buffer that does not
+    # start on a 32-byte boundary is refused before any launch
+    cfg = synth.QuarkConfig(C=32, heads=1, scales=[(1, 4)], near=1.0, far=60.0, out_h=16, out_w=16)
+    scene = synth.scene_noise_pair(V=1, W=16, H=16)
+    ctx = quark.Context(cfg)
+    ctx.load_weights(synth.make_weights(cfg))
+    pyr = ctx.encode_pyramid(torch.tensor(scene.images, device="cuda"), scene.cams)
+    target = synth.make_camera(16, 16, 14.0, (0.0, 0.0, 0.0))
+    buf = torch.zeros(1 << 16, device="cuda")
+    shifted = buf[1:]  # 4 bytes past a 256-byte boundary
+    with pytest.raises(quark.QuarkError) as e:
+        ctx.update_fuse_noalloc(pyr, 0, target, None, shifted, buf, buf, buf, buf, buf, buf)
+    assert e.value.status == quark.EINVAL
+    assert "32-byte aligned" in str(e.value)
