@@ -239,6 +239,13 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, AT_WAIT_NS));
     uint32_t failed_phase = 0;
     umma::fence_after_sync();
+    if (TR != TR_INIT && !failed) {
+        // X has been read by the MMA: its tile now keeps the entering volume's BF16 pairs (element
+        // e's channels at (e C + c) x 2 bytes) for the residual of the output epilogue
+        uint4* dst = reinterpret_cast<uint4*>(s_x + ((size_t)e * C + c0) * 2);
+        dst[0] = make_uint4(vpk[0], vpk[1], vpk[2], vpk[3]);
+        dst[1] = make_uint4(vpk[4], vpk[5], vpk[6], vpk[7]);
+    }
     if (!failed) {
         // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16.  The logit
         // scale 1/sqrt(C), and for the attention heads log2(e) (the softmax below runs on ex2), is
@@ -415,47 +422,37 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         failed_phase = 1;
         umma::fence_after_sync();
         if (!failed) {
+            // TMEM lane -> element er, columns ch * 16 .. + 15: residual (the entering volume, from
+            // the X tile, or v0 on the first step) added here and V_attn stored as BF16
             const int q = warp & 3, grp = warp >> 2;
+            const int er = q * 32 + lane;
+            const int ex = blockIdx.y * AT_TW + er % AT_TW, ey = blockIdx.z * AT_TH + er / AT_TW;
             for (int ch = grp; ch < C / 16; ch += TPE) {
                 float v[16];
                 umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
-                float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
+                if (ex < W && ey < H) {
+                    if (TR == TR_INIT) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            }
-        }
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
-        if (!failed && live) {
-            float vin[16], out[16];
-            if (TR == TR_INIT) {
+                        for (int i = 0; i < 16; ++i) v[i] += misc[ch * 16 + i];
+                    } else {
+                        const uint4* src = reinterpret_cast<const uint4*>(s_x + ((size_t)er * C + ch * 16) * 2);
+                        const uint4 p0 = src[0], p1 = src[1];
+                        const uint32_t pk[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
-                for (int i = 0; i < 16; ++i) vin[i] = misc[c0 + i];
-            } else {
+                        for (int j = 0; j < 8; ++j) {
+                            v[2 * j] += __uint_as_float(pk[j] << 16);
+                            v[2 * j + 1] += __uint_as_float(pk[j] & 0xffff0000u);
+                        }
+                    }
+                    uint4 u[2];
+                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    vin[2 * j] = __uint_as_float(vpk[j] << 16);
-                    vin[2 * j + 1] = __uint_as_float(vpk[j] & 0xffff0000u);
+                    for (int j = 0; j < 8; ++j) hh[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) +
+                                                          (((size_t)li * H + ey) * W + ex) * C + ch * 16);
+                    __stcs(dst, u[0]);  // streaming: V_attn is read back only by the next kernel
+                    __stcs(dst + 1, u[1]);
                 }
-            }
-            const float4* src = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + c0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float4 t = src[i];
-                out[4 * i] = vin[4 * i] + t.x;
-                out[4 * i + 1] = vin[4 * i + 1] + t.y;
-                out[4 * i + 2] = vin[4 * i + 2] + t.z;
-                out[4 * i + 3] = vin[4 * i + 3] + t.w;
-            }
-            {
-                uint4 u[2];
-                __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) hh[j] = __floats2bfloat162_rn(out[2 * j], out[2 * j + 1]);
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + (((size_t)li * H + y) * W + x) * C + c0);
-                __stcs(dst, u[0]);  // streaming: V_attn is read back only by the next kernel
-                __stcs(dst + 1, u[1]);
             }
         }
         if constexpr (LAST) {
