@@ -20,6 +20,19 @@ __device__ __forceinline__ void ldg256(const void* p, uint4& a, uint4& b) {
                  : "l"(p));
 }
 
+// 32 bytes stored in one 256-bit store (sm_100 family; global memory only; `p` 32-byte aligned);
+// stcs256 with the streaming (evict-first) hint, for data the next kernel reads once.
+__device__ __forceinline__ void stg256(void* p, const uint4& a, const uint4& b) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+__device__ __forceinline__ void stcs256(void* p, const uint4& a, const uint4& b) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+
 __device__ __forceinline__ void load16(const float* __restrict__ p, float (&o)[16]) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll

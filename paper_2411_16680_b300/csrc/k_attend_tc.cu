@@ -448,10 +448,9 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                     __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) hh[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) +
-                                                          (((size_t)li * H + ey) * W + ex) * C + ch * 16);
-                    __stcs(dst, u[0]);  // streaming: V_attn is read back only by the next kernel
-                    __stcs(dst + 1, u[1]);
+                    // one 256-bit streaming store: V_attn is read back only by the next kernel
+                    stcs256(reinterpret_cast<__nv_bfloat16*>(a.out) + (((size_t)li * H + ey) * W + ex) * C + ch * 16,
+                            u[0], u[1]);
                 }
             }
         }
@@ -510,8 +509,10 @@ static cudaError_t launch_tc_c(const AttendArgs& a, int heads, Transition tr, bo
 
 cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
-    // 256-bit loads of the taps and of the entering volume
-    if (reinterpret_cast<uintptr_t>(a.feat) % 32 || reinterpret_cast<uintptr_t>(a.prev) % 32) return cudaErrorMisalignedAddress;
+    // 256-bit loads of the taps and of the entering volume, 256-bit stores of V_attn
+    if (reinterpret_cast<uintptr_t>(a.feat) % 32 || reinterpret_cast<uintptr_t>(a.prev) % 32 ||
+        reinterpret_cast<uintptr_t>(a.out) % 32)
+        return cudaErrorMisalignedAddress;
     if (C == 16) return launch_tc_c<16>(a, heads, tr, last, st);
     if (C == 32) return launch_tc_c<32>(a, heads, tr, last, st);
     return cudaErrorInvalidValue;

@@ -324,11 +324,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                 const size_t pix = (size_t)gy * W + gx;
                 const size_t el = (size_t)li * plane + pix;
                 float t = misc[8 * C + 3], s = misc[8 * C + 4];
-                uint4* out = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + el * C);
+                __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.out) + el * C;
 #pragma unroll
                 for (int c0 = 0; c0 < C; c0 += 16) {
+                    // the residual's 16 channels in one 256-bit load, V' in one 256-bit store
                     float rr[16];
-                    load16(vin + pix * C + c0, rr);
+                    {
+                        uint4 r0, r1;
+                        ldg256(vin + pix * C + c0, r0, r1);
+                        const uint32_t pk[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            rr[2 * j] = __uint_as_float(pk[j] << 16);
+                            rr[2 * j + 1] = __uint_as_float(pk[j] & 0xffff0000u);
+                        }
+                    }
                     uint4 u[2];
                     __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
 #pragma unroll
@@ -341,8 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                         t = fmaf(o.y, misc[3 * C + c + 1], fmaf(o.x, misc[3 * C + c], t));
                         s = fmaf(o.y, misc[4 * C + c + 1], fmaf(o.x, misc[4 * C + c], s));
                     }
-                    out[c0 / 8] = u[0];
-                    out[c0 / 8 + 1] = u[1];
+                    stg256(out + c0, u[0], u[1]);
                 }
                 if (a.t_raw) {
                     a.t_raw[pix * L + li] = t;
@@ -431,7 +440,8 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
 
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
-    if (reinterpret_cast<uintptr_t>(a.in) % 32) return cudaErrorMisalignedAddress;  // 256-bit pixel loads
+    // 256-bit pixel loads and stores
+    if (reinterpret_cast<uintptr_t>(a.in) % 32 || reinterpret_cast<uintptr_t>(a.out) % 32) return cudaErrorMisalignedAddress;
     if (C == 16) return launch_tc<16>(a, st);
     if (C == 32) return launch_tc<32>(a, st);
     return cudaErrorInvalidValue;
