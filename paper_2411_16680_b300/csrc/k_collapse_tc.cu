@@ -85,15 +85,14 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
         // (the previous tile's MMAs, which read X and G, completed before its epilogue)
         float avg[C];
         {
-            const uint4* pa = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
-                                                             ((size_t)(2 * j) * plane + pixc) * C);
-            const uint4* pb = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(a.in) +
-                                                             ((size_t)(2 * j + 1) * plane + pixc) * C);
+            // the pixel's channels of both layers in 256-bit loads (whole sectors)
+            const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(a.in) + ((size_t)(2 * j) * plane + pixc) * C;
+            const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(a.in) + ((size_t)(2 * j + 1) * plane + pixc) * C;
             uint4 ua[C / 8], ub[C / 8];
 #pragma unroll
-            for (int g = 0; g < C / 8; ++g) {
-                ua[g] = __ldg(pa + g);
-                ub[g] = __ldg(pb + g);
+            for (int g = 0; g < C / 16; ++g) {
+                ldg256(pa + 16 * g, ua[2 * g], ua[2 * g + 1]);
+                ldg256(pb + 16 * g, ub[2 * g], ub[2 * g + 1]);
             }
 #pragma unroll
             for (int g = 0; g < C / 8; ++g) {
@@ -170,23 +169,23 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
         }
         phase ^= 1;
         {
-            uint4* po = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + ((size_t)j * plane + pixc) * C);
+            __nv_bfloat16* po = reinterpret_cast<__nv_bfloat16*>(a.out) + ((size_t)j * plane + pixc) * C;
 #pragma unroll
             for (int ch = 0; ch < C / 16; ++ch) {
                 float ov[16];
                 tmem_row16(tmem, warp, C + ch * 16, ov);
+                uint4 u[2];
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
-                    uint4 u;
-                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u[g]);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int c = ch * 16 + 8 * g + 2 * i;
                         hh[i] = __floats2bfloat162_rn(avg[c] + s_b[C + c] + ov[8 * g + 2 * i],
                                                       avg[c + 1] + s_b[C + c + 1] + ov[8 * g + 2 * i + 1]);
                     }
-                    if (live) po[2 * ch + g] = u;
                 }
+                if (live) stg256(po + ch * 16, u[0], u[1]);  // 16 channels, one 256-bit store
             }
         }
         // this tile's TMEM reads before the next tile's MMAs
@@ -206,6 +205,8 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
 
 cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
+    // 256-bit pixel loads and stores
+    if (reinterpret_cast<uintptr_t>(a.in) % 32 || reinterpret_cast<uintptr_t>(a.out) % 32) return cudaErrorMisalignedAddress;
     static int sms = 0;
     if (!sms) {
         int dev = 0;

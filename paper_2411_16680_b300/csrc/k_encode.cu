@@ -26,19 +26,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // 16 channels of one texel of a level at p (T = float or bf16)
+// (256-bit stores: a whole 32-byte sector per store; the levels are 32-byte aligned)
 __device__ __forceinline__ void store16x2(float* p, const float2 (&v)[8]) {
-    float4* q = reinterpret_cast<float4*>(p);
+    uint4 u[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+    for (int i = 0; i < 4; ++i)
+        u[i] = make_uint4(__float_as_uint(v[2 * i].x), __float_as_uint(v[2 * i].y), __float_as_uint(v[2 * i + 1].x),
+                          __float_as_uint(v[2 * i + 1].y));
+    stg256(p, u[0], u[1]);
+    stg256(p + 8, u[2], u[3]);
 }
 __device__ __forceinline__ void store16x2(__nv_bfloat16* p, const float2 (&v)[8]) {
     uint4 u[2];
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(u);
 #pragma unroll
     for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[j].x, v[j].y);
-    uint4* q = reinterpret_cast<uint4*>(p);
-    q[0] = u[0];
-    q[1] = u[1];
+    stg256(p, u[0], u[1]);
 }
 
 // 2x2 mean of the 16-channel texels held by this lane and its partners at lane ^ dx and ^ dy
@@ -200,6 +203,8 @@ static cudaError_t launch_t(const EncodeArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_encode(const EncodeArgs& a, int C, bool bf16, cudaStream_t st) {
+    for (int i = 0; i < 4; ++i)  // 256-bit stores of the levels
+        if (reinterpret_cast<uintptr_t>(a.level[i]) % 32) return cudaErrorMisalignedAddress;
     if (C == 16) return bf16 ? launch_t<__nv_bfloat16, 16>(a, st) : launch_t<float, 16>(a, st);
     if (C == 32) return bf16 ? launch_t<__nv_bfloat16, 32>(a, st) : launch_t<float, 32>(a, st);
     return cudaErrorInvalidValue;
