@@ -412,8 +412,10 @@ quark_status quark_serve_stop(quark_server* srv);
 quark_status quark_step_input(quark_ctx* ctx, quark_ldm* ldm, int scale, float* v_in, void* stream);
 
 /* Forward of the stage: last step from v_in [L][H][W][C] with level features feat [V][h][w][C]
- * (device float32, e.g. a copy of the pyramid's level), then the render into rgba [H][W][4]
- * (device).  `pyr` provides the cameras and the images the render samples. */
+ * (device float32, e.g. a copy of the pyramid's level; 32-byte aligned, as cudaMalloc and
+ * PyTorch's allocator give, since the sampling reads it in 256-bit loads, else QUARK_EINVAL), then
+ * the render into rgba [H][W][4] (device).  `pyr` provides the cameras and the images the render
+ * samples. */
 quark_status quark_stage_forward(quark_ctx* ctx, const quark_pyramid* pyr, const float* feat, const float* v_in,
                                  quark_ldm* ldm, float* rgba, void* stream);
 

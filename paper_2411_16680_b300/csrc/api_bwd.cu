@@ -66,6 +66,7 @@ extern "C" quark_status quark_stage_forward(quark_ctx* ctx, const quark_pyramid*
     quark_status s = check_stage(ctx, pyr, ldm);
     if (s != QUARK_OK) return s;
     if (!feat || !v_in || !rgba) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(feat) % 32) return qk_fail(ctx, QUARK_EINVAL, "feat must be 32-byte aligned");
     const int last = ctx->cfg.n_scales - 1;
     s = qk_update_fuse(ctx, pyr, pyr->V, last, ldm, (cudaStream_t)stream, v_in, feat);
     if (s != QUARK_OK) return s;

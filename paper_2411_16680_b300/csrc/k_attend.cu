@@ -111,15 +111,18 @@ __device__ __forceinline__ void fma_row16_x2(const float* w, float x, float2 (&a
         acc[2 * i + 1] = __ffma2_rn(x2, make_float2(t.z, t.w), acc[2 * i + 1]);
     }
 }
-// D[j] += w * texel[2j .. 2j+1] for 16 FP32 channels at p (global memory)
+// D[j] += w * texel[2j .. 2j+1] for 16 FP32 channels at p (global memory, 32-byte aligned): two
+// 256-bit loads, each a whole 32-byte sector
 __device__ __forceinline__ void fma_tap16_x2(const float* p, float w, float2 (&D)[8]) {
-    const float4* q = reinterpret_cast<const float4*>(p);
     const float2 w2 = make_float2(w, w);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 t = __ldg(q + i);
-        D[2 * i] = __ffma2_rn(make_float2(t.x, t.y), w2, D[2 * i]);
-        D[2 * i + 1] = __ffma2_rn(make_float2(t.z, t.w), w2, D[2 * i + 1]);
+    for (int i = 0; i < 2; ++i) {
+        uint4 a, b;
+        ldg256(p + 8 * i, a, b);
+        D[4 * i] = __ffma2_rn(make_float2(__uint_as_float(a.x), __uint_as_float(a.y)), w2, D[4 * i]);
+        D[4 * i + 1] = __ffma2_rn(make_float2(__uint_as_float(a.z), __uint_as_float(a.w)), w2, D[4 * i + 1]);
+        D[4 * i + 2] = __ffma2_rn(make_float2(__uint_as_float(b.x), __uint_as_float(b.y)), w2, D[4 * i + 2]);
+        D[4 * i + 3] = __ffma2_rn(make_float2(__uint_as_float(b.z), __uint_as_float(b.w)), w2, D[4 * i + 3]);
     }
 }
 
@@ -127,8 +130,8 @@ __device__ __forceinline__ void fma_tap16_x2(const float* p, float w, float2 (&D
 // volume at this layer, or its x2 bilinear upsample (Sec. 3.2.2) -- and the depth its views are
 // sampled at (anchors at step 0, else Eq. depth_activation of t = V w_d + b_d).
 __device__ __forceinline__ void fma_tap16_x2(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 u[2] = {__ldg(q), __ldg(q + 1)};
+    uint4 u[2];
+    ldg256(p, u[0], u[1]);
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(u);
     const float2 w2 = make_float2(w, w);
 #pragma unroll
@@ -621,6 +624,7 @@ static cudaError_t launch_std_c(const AttendArgs& a, int heads, Transition tr, b
 // a.feat is the projected map of launch_kv_project (2C channels per texel, 3C on the last step).
 cudaError_t launch_attend_std(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                               cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(a.feat) % 32) return cudaErrorMisalignedAddress;  // 256-bit tap loads
     if (!a.w_std) return cudaErrorInvalidValue;
     if (C == 16) return bf16 ? launch_std_c<__nv_bfloat16, 16>(a, heads, tr, last, st) : launch_std_c<float, 16>(a, heads, tr, last, st);
     if (C == 32) return bf16 ? launch_std_c<__nv_bfloat16, 32>(a, heads, tr, last, st) : launch_std_c<float, 32>(a, heads, tr, last, st);
@@ -664,6 +668,7 @@ static cudaError_t launch_c(const AttendArgs& a, int heads, Transition tr, bool 
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                           cudaStream_t st) {
     if (bf16) return launch_attend_tc(a, C, heads, tr, last, st);
+    if (reinterpret_cast<uintptr_t>(a.feat) % 32) return cudaErrorMisalignedAddress;  // 256-bit tap loads
     if (C == 16) return launch_c<float, 16>(a, heads, tr, last, st);
     if (C == 32) return launch_c<float, 32>(a, heads, tr, last, st);
     return cudaErrorInvalidValue;
