@@ -276,8 +276,9 @@ quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, q
  *   v_out     this step's output volume [L][H][W][C], same element type
  *   colour [L][H][W][3], alpha / depth [L][H][W], t_raw / s_raw [H][W][L] (float32)
  *   beta      blend logits [H][W][L][V] (float32), required on the last step, else ignored
- * All buffers are device memory owned by the caller; v_prev, v_out and beta must start on a
- * 32-byte boundary (the kernels move them in 16- and 32-byte vectors; cudaMalloc and PyTorch's
+ * All buffers are device memory of the context's device, owned by the caller (host memory, or
+ * memory of another device, is refused with QUARK_EINVAL before any launch; the check allocates
+ * nothing); v_prev, v_out and beta must start on a 32-byte boundary (the kernels move them in 16- and 32-byte vectors; cudaMalloc and PyTorch's
  * allocator give 256), else QUARK_EINVAL.  The two intermediates (the volume after
  * the attention block and, where L halves, the collapsed volume) live in one static device
  * array of QUARK_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds until the
@@ -286,7 +287,10 @@ quark_status quark_render_novel_view(quark_ctx* ctx, const quark_pyramid* pyr, q
  * contents (each call overwrites what it reads), so calls whose work overlaps on the GPU --
  * on different streams, or from different contexts on one device -- race; serialise them.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture. */
+ * with that device current and keeps it for the life of the process; make that first call
+ * before any stream capture.  A device reset (cudaDeviceReset) invalidates that address, as it
+ * does every context and handle of this library on the device: do not use the library on a
+ * device after resetting it. */
 #define QUARK_NOALLOC_SCRATCH_BYTES (32u << 20)
 quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_pyramid* pyr, int scale,
                                        const quark_camera* target, const void* v_prev, void* v_out,
@@ -326,6 +330,13 @@ quark_status quark_pyramid_read(const quark_pyramid* pyr, int k, void* dst, size
 quark_status quark_sample_coords(quark_ctx* ctx, const quark_camera* target, double k_tx, double k_ty,
                                  const quark_camera* view, double k_m, int n, const float* px, const float* py,
                                  const float* depth, float* uv, int* taps, int* valid);
+
+/* Output tile of the conv-block kernel of the context's precision form for an L x H x W volume
+ * (inspection, so that tests can place windows on its tile seams; Sec. 3.3 conv block): tiles of
+ * *tile_rows rows by *tile_cols columns start at multiples of those in y and x (the last ones
+ * ragged).  FP32 form: the fixed 16 x 8 tile; BF16 form: the tile the tensor-core kernel chooses
+ * for this plane size on the context's device. */
+quark_status quark_conv_tiles(quark_ctx* ctx, int L, int H, int W, int* tile_cols, int* tile_rows);
 
 quark_status quark_release_pyramid(quark_pyramid* pyr);
 quark_status quark_release_ldm(quark_ldm* ldm);
@@ -449,6 +460,16 @@ quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid* pyr, cons
  * kernel's bounded wait (on tensor-core completion) ran out since the last check, in which case
  * that launch's outputs are invalid; the error word is then cleared. */
 quark_status quark_check_device(quark_ctx* ctx);
+
+/* Test of the error path of the bounded waits (the context stays usable; nothing faults): the
+ * next BF16 one-to-many sampling launch of this context (a quark_update_fuse step with attention)
+ * leaves its query MMA chain unissued, so that its wait on the chain's completion -- an mbarrier
+ * nothing arrives at -- runs out after 1 ms.  The kernel then records the timeout in the error
+ * word, skips its outputs, frees its tensor memory and returns; quark_check_device reports
+ * QUARK_ETIMEDOUT and clears the word, and later launches run normally.  The outputs of that one
+ * step (and of anything computed from them) are invalid.  EINVAL for the FP32 form or standard
+ * attention. */
+quark_status quark_test_wait_timeout(quark_ctx* ctx);
 
 /* Kernel accounting.  quark_launch_count returns the number of kernels this context has
  * launched since creation or the last reset.  With profiling on, every launch is bracketed

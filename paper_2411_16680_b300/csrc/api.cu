@@ -557,6 +557,14 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     return QUARK_OK;
 }
 
+extern "C" quark_status quark_test_wait_timeout(quark_ctx* ctx) {
+    if (!ctx) return qk_fail(nullptr, QUARK_EINVAL, "NULL context");
+    if (ctx->cfg.precision != QUARK_BF16 || ctx->cfg.attn_mode != QUARK_ATTN_ONE_TO_MANY)
+        return qk_fail(ctx, QUARK_EINVAL, "the wait-timeout test needs the BF16 form with one-to-many attention");
+    ctx->test_wait_armed = true;
+    return QUARK_OK;
+}
+
 extern "C" quark_status quark_check_device(quark_ctx* ctx) {
     if (!ctx) return qk_fail(nullptr, QUARK_EINVAL, "NULL context");
     cudaSetDevice(ctx->device);
@@ -1169,6 +1177,10 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
             aa.w_std = ctx->wdev + ctx->off_std[scale];
             s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend_std(aa, c.C, heads, tr, last, bf16, st); });
         } else {
+            if (ctx->test_wait_armed && bf16) {
+                aa.test_wait_ns = 1000000;  // 1 ms: the test's wait runs out at once, not after 1 s
+                ctx->test_wait_armed = false;
+            }
             s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, heads, tr, last, bf16, st); });
         }
         if (s != QUARK_OK) return s;

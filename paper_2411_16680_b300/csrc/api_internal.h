@@ -46,6 +46,8 @@ struct quark_ctx {
     size_t off_wat[QUARK_MAX_SCALES] = {};
     // device error word written by kernels whose bounded waits run out
     int* dev_err = nullptr;
+    // quark_test_wait_timeout: the next tensor-core sampling launch leaves its query MMA unissued
+    bool test_wait_armed = false;
     // device memory accounting against cfg.hbm_cap_bytes
     std::mutex mem_mu;
     size_t bytes = 0;

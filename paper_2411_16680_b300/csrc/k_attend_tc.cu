@@ -226,7 +226,11 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     const uint32_t tmem = *tslot;
 
     // ---- Q = X [Wq | W^beta] ----
-    if (tid == 0) {
+    // (a test of the error path leaves the chain unissued: nothing arrives on the mbarrier, the
+    // wait below runs out after test_wait_ns, and the drain wait at the end finds nothing in flight)
+    const bool test_skip = a.test_wait_ns != 0;
+    const uint64_t wait_ns = test_skip ? a.test_wait_ns : AT_WAIT_NS;
+    if (tid == 0 && !test_skip) {
         constexpr uint32_t idesc = umma::idesc_bf16_f32(AT_M, NQ_USED);
         const uint32_t a0 = umma::smem_u32(s_x), b0 = umma::smem_u32(s_wq);
         constexpr uint32_t LBO_A = AT_M * 16, LBO_B = S::NQ * 16;
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                            idesc, kk > 0);
         umma::commit(mbar);
     }
-    bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, AT_WAIT_NS));
+    bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, wait_ns));
     uint32_t failed_phase = 0;
     umma::fence_after_sync();
     if (TR != TR_INIT && !failed) {
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         }
     }
     if (failed && tid == 0) atomicExch(a.err, 3 + (int)failed_phase);
-    if (failed) umma::mbar_wait(mbar, failed_phase, AT_WAIT_NS);
+    if (failed) umma::mbar_wait(mbar, failed_phase, wait_ns);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();

@@ -438,6 +438,20 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t conv_tc_tile_shape(int C, int W, int H, int L, int* cols, int* rows) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    ConvTile t{};
+    if (C == 16) t = choose_tile<16>(W, H, L, sms);
+    else if (C == 32) t = choose_tile<32>(W, H, L, sms);
+    if (!t.P) return cudaErrorInvalidValue;
+    *cols = t.P - 4;
+    *rows = t.R;
+    return cudaSuccess;
+}
+
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
     // 256-bit pixel loads and stores

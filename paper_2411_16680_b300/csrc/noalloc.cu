@@ -41,6 +41,23 @@ quark_status scratch_address(const quark_ctx* ctx, int dev, unsigned char** out)
 }
 
 size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// A caller buffer must be device (or managed) memory of the context's device: the kernels
+// dereference it.  cudaPointerGetAttributes allocates nothing; host memory (pageable or pinned)
+// and memory of another device are refused before any launch.
+quark_status check_device_buffer(const quark_ctx* ctx, const void* p, const char* what) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return qk_fail(ctx, QUARK_EINVAL, "%s is not a device pointer", what);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return qk_fail(ctx, QUARK_EINVAL, "%s must be device memory (got host memory)", what);
+    if (at.device != ctx->device)
+        return qk_fail(ctx, QUARK_EINVAL, "%s is memory of device %d, the context runs on device %d", what, at.device,
+                       ctx->device);
+    return QUARK_OK;
+}
 }  // namespace
 
 extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_pyramid* pyr, int scale,
@@ -69,6 +86,13 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
         return qk_fail(ctx, QUARK_EINVAL, "v_prev, v_out and beta must be 32-byte aligned");
     quark_status s = qk_validate_camera(ctx, *target, "target");
     if (s != QUARK_OK) return s;
+    {
+        const void* bufs[] = {scale > 0 ? v_prev : nullptr, v_out, colour, alpha, depth, t_raw, s_raw,
+                              last ? beta : nullptr};
+        const char* names[] = {"v_prev", "v_out", "colour", "alpha", "depth", "t_raw", "s_raw", "beta"};
+        for (int i = 0; i < 8; ++i)
+            if (bufs[i] && (s = check_device_buffer(ctx, bufs[i], names[i])) != QUARK_OK) return s;
+    }
     for (int j = 0; j < c.n_scales; ++j)
         if (target->height % c.k[j] || target->width % c.k[j])
             return qk_fail(ctx, QUARK_EINVAL, "output %dx%d not divisible by k=%d", target->width, target->height,
@@ -115,9 +139,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
             ca.w = ctx->wdev + ctx->off_collapse[scale];
             ca.wtc = qk_collapse_wtc(ctx, scale);
             ca.err = ctx->dev_err;
-            e = launch_collapse(ca, c.C, bf16, st);
-            ctx->launches++;
-            if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "collapse launch: %s", cudaGetErrorString(e));
+            s = qk_launch(ctx, st, KF_COLLAPSE, [&] { return launch_collapse(ca, c.C, bf16, st); });
+            if (s != QUARK_OK) return s;
             prev = collapsed;
         }
         tr = (c.k[scale - 1] == 2 * k) ? TR_UP2 : TR_SAME;
@@ -142,9 +165,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     aa.wtc = ctx->wat ? (const uint8_t*)ctx->wat + ctx->off_wat[scale] : nullptr;
     aa.err = ctx->dev_err;
     for (int m = 0; m < pyr->V; ++m) aa.geo.v[m] = qk_view_map(*target, k, k, pyr->cams[m], k);
-    e = launch_attend(aa, c.C, c.heads, tr, last, bf16, st);
-    ctx->launches++;
-    if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "attend launch: %s", cudaGetErrorString(e));
+    s = qk_launch(ctx, st, KF_ATTEND, [&] { return launch_attend(aa, c.C, c.heads, tr, last, bf16, st); });
+    if (s != QUARK_OK) return s;
 
     ConvArgs cv{};
     cv.in = vattn;
@@ -156,9 +178,8 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     cv.w = ctx->wdev + ctx->off_conv[scale];
     cv.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
     cv.err = ctx->dev_err;
-    e = launch_conv_block(cv, c.C, bf16, st);
-    ctx->launches++;
-    if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "conv block launch: %s", cudaGetErrorString(e));
+    s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(cv, c.C, bf16, st); });
+    if (s != QUARK_OK) return s;
     // the decoded attributes, from the volume just written (the regular step makes them on demand)
     return qk_decode(ctx, scale, v_out, L, H, W, colour, alpha, depth, t_raw, s_raw, st);
 }

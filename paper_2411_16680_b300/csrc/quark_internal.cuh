@@ -61,6 +61,10 @@ struct AttendArgs {
     const float* w_std;  // standard mode: StdLayout (W^q, W^O); else NULL
     const float* depth_in;  // [L][H][W] depths to sample at (reused from an earlier step), or NULL
     float* depth_out;       // [L][H][W] the depths sampled at, kept for a later step, or NULL
+    // Test of the bounded-wait error path (quark_test_wait_timeout), tensor-core kernel only: when
+    // set, the query MMA chain is not issued, so the wait on its completion runs out after
+    // test_wait_ns; 0 in normal launches
+    uint64_t test_wait_ns;
     Geometry geo;
 };
 
@@ -186,6 +190,8 @@ cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, 
                           cudaStream_t st);
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st);
+// Output tile (columns, rows) the tensor-core conv block uses for an L x H x W volume.
+cudaError_t conv_tc_tile_shape(int C, int W, int H, int L, int* cols, int* rows);
 cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st);
 cudaError_t launch_kv_project(const void* feat, size_t texels, int C, const float* wkv, void* out, bool with_f, bool bf16,

@@ -137,6 +137,9 @@ def lib():
                                           ct.c_int),
             "quark_sample_coords": ([vp, ct.POINTER(Camera), ct.c_double, ct.c_double, ct.POINTER(Camera), ct.c_double,
                                      ct.c_int, vp, vp, vp, vp, vp, vp], ct.c_int),
+            "quark_test_wait_timeout": ([vp], ct.c_int),
+            "quark_conv_tiles": ([vp, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)],
+                                 ct.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -387,6 +390,16 @@ class Context:
         _check(lib().quark_sample_coords(self.handle, ct.byref(t), k_tx, k_ty, ct.byref(v), k_m, n, _ptr(px), _ptr(py),
                                          _ptr(depth), _ptr(uv), _ptr(taps), _ptr(valid)), self.handle)
         return uv, taps, valid
+
+    def conv_tiles(self, L: int, H: int, W: int):
+        """quark_conv_tiles: (columns, rows) of the conv-block kernel's output tile for an L x H x W volume."""
+        cols, rows = ct.c_int(0), ct.c_int(0)
+        _check(lib().quark_conv_tiles(self.handle, L, H, W, ct.byref(cols), ct.byref(rows)), self.handle)
+        return cols.value, rows.value
+
+    def test_wait_timeout(self):
+        """quark_test_wait_timeout: the next BF16 sampling launch's bounded wait runs out (error-path test)."""
+        _check(lib().quark_test_wait_timeout(self.handle), self.handle)
 
     def check_device(self):
         """Synchronise and raise if a kernel's bounded device-side wait ran out."""

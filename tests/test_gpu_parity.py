@@ -166,7 +166,13 @@ def test_bf16_form(sharp):
         ref, ref_steps = O.forward(cfg, W, scene)
         out, steps, _ = run_gpu(cfg, W, scene, per_step=True)
         for j, (g, r) in enumerate(zip(steps, ref_steps)):
-            assert_rel(g["V_out"], r.V_out, REL_TOL_BF16_VOLUME, f"bf16 step {j} V_out")
+            # the volumes after the attention block and after the conv block, and the raw depth /
+            # density logits decoded from the stored BF16 volume (Sec. 3.2.3)
+            for name in ("V_attn", "V_out", "t", "s"):
+                assert_rel(g[name], getattr(r, name), REL_TOL_BF16_VOLUME, f"bf16 step {j} {name}")
+            if "beta" in g:
+                # blend logits: BF16 query and sampled features, FP32 dot product (Sec. 3.2.3)
+                assert_rel(g["beta"], r.beta_logits, REL_TOL_BF16_VOLUME, f"bf16 step {j} beta")
         err = np.abs(out - ref).max()
         assert err <= RGBA_TOL_BF16, f"bf16 rgba max-abs {err:.3e}"
         assert psnr(out, ref) >= PSNR_MIN_BF16
@@ -214,18 +220,45 @@ def test_hbm_cap_refuses_instead_of_overcommitting():
 FULL_RECTS = [(0, 4, 0, 4), (538, 542, 958, 962), (1076, 1080, 1916, 1920), (300, 303, 1500, 1506)]
 
 
+# Attention-kernel tiles are 16 x 8 LDM pixels at every step: output pixel (1024, 512) lies on a
+# tile corner of every step whose grid factor divides 8, the corner (128 j, 64 i) of each.
+ATTEND_SEAM_RECTS = [(510, 514, 1022, 1026), (62, 66, 1790, 1794)]
+
+
+def conv_seam_rects(ctx, cfg):
+    """Output windows straddling a tile corner of the conv-block kernel at every step: the tile the
+    kernel of the context's form uses for that step's plane (quark_conv_tiles), one corner near
+    the middle of the plane and the last interior corner next to the ragged tiles."""
+    rects = []
+    for j, (k, L) in enumerate(cfg.scales):
+        H, W = cfg.out_h // k, cfg.out_w // k
+        cols, rows = ctx.conv_tiles(L, H, W)
+        ty, tx = (H - 1) // rows, (W - 1) // cols  # index of the last (ragged) tile row / column
+        for iy, ix in ((max(1, ty // 2), max(1, tx // 2)), (ty, tx)):
+            if iy < 1 or ix < 1:
+                continue
+            y, x = iy * rows * k, ix * cols * k  # output coordinates of the corner
+            rects.append((y - 2, y + 2, x - 2, x + 2))
+    return rects
+
+
 @pytest.mark.parametrize("precision", [synth.PREC_FP32, synth.PREC_BF16])
 def test_1080p_sampled_outputs(precision):
     """V=8 1920x1080 views, scales (8,32),(4,16),(2,8),(1,4), C=32, h=2, 1080p output, in the
-    launch configuration the bench times; the oracle computes a few output windows (corners and
-    the centre) from scratch through every scale."""
+    launch configuration the bench times; the oracle computes output windows from scratch through
+    every scale: corners and the centre of the frame, windows across the attention kernel's tile
+    corners, and windows across the conv-block kernel's tile corners at every step (the BF16
+    kernel picks its tile per plane size, so these windows sit where its tiling changes)."""
     cfg = synth.config_1080p().replace(precision=precision)
     scene = synth.scene_1080p()
     W = synth.make_weights(cfg, sharp=True)
+    ctx = quark.Context(cfg)
+    rects = FULL_RECTS + ATTEND_SEAM_RECTS + conv_seam_rects(ctx, cfg)
+    ctx.close()
     out, _, _ = run_gpu(cfg, W, scene, per_step=False)
     assert np.isfinite(out).all()
     tol = RGBA_TOL_FP32 if precision == synth.PREC_FP32 else RGBA_TOL_BF16
-    for r in FULL_RECTS:
+    for r in rects:
         ref, _ = O.forward(cfg, W, scene, r)
         err = np.abs(out[r[0]:r[1], r[2]:r[3]] - ref).max()
         assert err <= tol, f"{r}: max-abs {err:.3e}"
