@@ -456,6 +456,84 @@ quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid* pyr, cons
                                   quark_ldm* ldm, const float* dl_drgb, float* dv_in, float* dfeat,
                                   const quark_stage_grads* grads, void* stream);
 
+/* ---- Backward pass through the whole network (spec form 3; the paper trains the whole
+ * network end to end through its differentiable render, Sec. 3.1 and Sec. 3.4) ---------------
+ * One backward call mirrors each forward call, in reverse order:
+ *     quark_render_ldm_bwd                       (Sec. 3.1 Eq. 1, Sec. 3.2.3)
+ *     quark_update_fuse_bwd(scale = n-1 .. 0)    (Sec. 3.2.2, Sec. 3.3)
+ *     quark_encode_pyramid_bwd                   (Sec. 3.2.1)
+ * FP32 form, uniform schedule, one-to-many attention, C = 16 or 32, without the ray encoding or
+ * render-and-refine (EINVAL otherwise).  The forward must have run with quark_ldm_keep_steps on
+ * the LDM and with every view of the pyramid.  The backward recomputes what it needs (the
+ * volume entering each step, the normalised inputs and the first convolution of each conv block,
+ * the sampled features -- nothing sampled is stored by the forward); the loss may depend on the
+ * output RGB (not on its alpha channel).  All gradient buffers are device float32, caller-owned.
+ * Weight gradients and the feature gradients are ACCUMULATED into (+=), so that the
+ * contributions of every step and of several scenes sum in one set of buffers: zero them before
+ * the first call.  The feature gradients are summed with atomics, so their last bits depend on
+ * scheduling; everything else is deterministic. */
+
+/* Weight gradients, shaped as the quark_weights fields.  A call needs the fields of the weights it
+ * differentiates (EINVAL if NULL); the others may be NULL.  The appearance decoder W_a, b_a does
+ * not reach the render (its colours are the input images', blended by beta), so it has no field. */
+typedef struct {
+    float* enc_w;   /* [3][3][3][C] */
+    float* enc_b;   /* [C] */
+    float* v0;      /* [C] */
+    float* attn_g[QUARK_MAX_SCALES];
+    float* Wq[QUARK_MAX_SCALES];
+    float* Wo[QUARK_MAX_SCALES];
+    float* conv_g[QUARK_MAX_SCALES];
+    float* conv1_w[QUARK_MAX_SCALES];
+    float* conv1_b[QUARK_MAX_SCALES];
+    float* conv2_w[QUARK_MAX_SCALES];
+    float* conv2_b[QUARK_MAX_SCALES];
+    float* col_w1[QUARK_MAX_SCALES];  /* only where L halves into step j */
+    float* col_b1[QUARK_MAX_SCALES];
+    float* col_w2[QUARK_MAX_SCALES];
+    float* col_b2[QUARK_MAX_SCALES];
+    float* w_d;     /* [C] */
+    float* b_d;     /* [1] */
+    float* w_sigma; /* [C] */
+    float* b_sigma; /* [1] */
+    float* W_beta;  /* [C][C] */
+} quark_grads;
+
+/* keep = 1: every later quark_update_fuse on this LDM also copies its step's output volume and
+ * the attention block's output ([L][H][W][C] each) into per-step buffers of the LDM, allocated on
+ * first use and freed with the LDM; the backward pass reads them.  keep = 0: no copies. */
+quark_status quark_ldm_keep_steps(quark_ldm* ldm, int keep);
+
+/* Backward of quark_render_ldm (after every step ran on `ldm` with pyramid `pyr`):
+ *   dl_drgb  [H_out][W_out][3] gradient of the loss w.r.t. the output RGB (device)
+ *   dv_out   [L][H][W][C] gradient w.r.t. the last step's output volume (written), through the
+ *            raw depth and density logits (the depth moves the image samples, Eq. depth_activation)
+ *   dbeta    [H][W][L][V] gradient w.r.t. the last step's blend logits (written)
+ *   g        w_d, b_d, w_sigma, b_sigma accumulated */
+quark_status quark_render_ldm_bwd(quark_ctx* ctx, const quark_ldm* ldm, const quark_pyramid* pyr,
+                                  const float* dl_drgb, float* dv_out, float* dbeta, const quark_grads* g,
+                                  void* stream);
+
+/* Backward of quark_update_fuse step `scale`:
+ *   dv_out   [L][H][W][C] gradient w.r.t. the step's output volume (from the next step's
+ *            backward, or from quark_render_ldm_bwd for the last step); read only
+ *   dbeta    last step: the blend-logit gradient from quark_render_ldm_bwd; else ignored
+ *   dv_prev  [L'][H'][W'][C] gradient w.r.t. step scale-1's output volume, through the x2
+ *            upsample and the layer collapse (written); step 0: ignored (its input is v0)
+ *   dfeat    [V][H_img/k][W_img/k][C] gradient w.r.t. pyramid level k = k[scale] (accumulated)
+ *   g        the step's attention, conv-block and layer-collapse weights, W_beta (last step), v0
+ *            (step 0), w_d and b_d (steps > 0: their depths are decoded from the entering volume)
+ *            accumulated */
+quark_status quark_update_fuse_bwd(quark_ctx* ctx, const quark_pyramid* pyr, int scale, quark_ldm* ldm,
+                                   const float* dv_out, const float* dbeta, float* dv_prev, float* dfeat,
+                                   const quark_grads* g, void* stream);
+
+/* Backward of quark_encode_pyramid: from the gradients of the pyramid levels k = 1, 2, 4, 8
+ * (dfeat[0..3], [V][H/k][W/k][C] each, NULL where no step used the level) through the 2x2
+ * mean-pool chain and the 3x3 conv, accumulates g->enc_w and g->enc_b. */
+quark_status quark_encode_pyramid_bwd(quark_ctx* ctx, const quark_pyramid* pyr, const float* const* dfeat,
+                                      const quark_grads* g, void* stream);
+
 /* Synchronise the context's device and report device-side failures: QUARK_ETIMEDOUT if a
  * kernel's bounded wait (on tensor-core completion) ran out since the last check, in which case
  * that launch's outputs are invalid; the error word is then cleared. */

@@ -1203,6 +1203,16 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     ca.err = ctx->dev_err;
     s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(ca, c.C, bf16, st); });
     if (s != QUARK_OK) return s;
+    if (ldm->keep) {
+        // the step's volumes, kept for quark_update_fuse_bwd
+        const size_t bytes = (size_t)L * H * W * c.C * (bf16 ? 2 : 4);
+        if (!ldm->hist_out[scale] && (s = ldm_buf(ldm, &ldm->hist_out[scale], bytes)) != QUARK_OK) return s;
+        if (!ldm->hist_attn[scale] && (s = ldm_buf(ldm, &ldm->hist_attn[scale], bytes)) != QUARK_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(ldm->hist_out[scale], ca.out, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ldm->hist_attn[scale], ca.in, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "keeping step %d's volumes: %s", scale, cudaGetErrorString(e));
+    }
     ldm->cur = 1 - ldm->cur;
     ldm->done = scale;
     ldm->decoded = -1;

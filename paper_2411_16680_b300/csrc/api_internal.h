@@ -119,6 +119,11 @@ struct quark_ldm {
     int decoded = -1;  // step whose decoded attributes (colour, alpha, depth, logits) are current
     bool async = false;            // buffers from the stream-ordered allocator on `stream`
     cudaStream_t stream = nullptr;
+    // quark_ldm_keep_steps: every step's output volume and attention-block output, kept for the
+    // backward pass (allocated on first use)
+    bool keep = false;
+    void* hist_out[QUARK_MAX_SCALES] = {};
+    void* hist_attn[QUARK_MAX_SCALES] = {};
 };
 
 quark_status qk_fail(const quark_ctx* ctx, quark_status st, const char* fmt, ...);

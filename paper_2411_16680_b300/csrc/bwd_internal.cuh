@@ -10,6 +10,8 @@ struct AttendBwdArgs {
     const float* feat;     // pyramid level [V][fh][fw][C]
     const float* dv_attn;  // [L][H][W][C] gradient of the attention block's output
     const float* dbeta;    // [H][W][L][V] gradient of the blend logits
+    const float* v0;       // step 0 (initialisation): V_in = v0 [C] everywhere and the depths are the
+                           // anchors (no depth gradient); v_in is then unused.  NULL otherwise
     int L, H, W, V, fh, fw, last;
     DepthParams dp;
     const float* g;        // attention RMSNorm gain [C]
@@ -53,5 +55,10 @@ cudaError_t launch_rmsnorm_bwd(const float* v, const float* g, const float* dn, 
 cudaError_t launch_attend_bwd(const AttendBwdArgs& a, int C, int heads, cudaStream_t st);
 cudaError_t launch_xty(const XtyArgs& a, float* out, int accumulate, cudaStream_t st);
 cudaError_t launch_upsample2(const float* in, float* out, int L, int Hp, int Wp, int C, cudaStream_t st);
+// Adjoints of the step transitions and of the encoder's pooling (k_network_bwd.cu).
+cudaError_t launch_upsample2_bwd(const float* dout, float* din, int L, int Hp, int Wp, int C, cudaStream_t st);
+cudaError_t launch_collapse_bwd(const float* vprev, const float* dcol, int L, int H, int W, int C, const float* w,
+                                float* dvprev, float* g_out, float* dh_out, float* cat_out, cudaStream_t st);
+cudaError_t launch_pool_chain_bwd(const float* const dlev[4], int V, int H, int W, int C, float* out, cudaStream_t st);
 
 }  // namespace quark

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(BW_THREADS) attend_bwd_kernel(const AttendBwdA
     const int L = a.L, V = a.V;
 
     float vin[C], xn[C];
-    for (int c = 0; c < C; ++c) vin[c] = a.v_in[e * C + c];
+    for (int c = 0; c < C; ++c) vin[c] = a.v0 ? a.v0[c] : a.v_in[e * C + c];
     float t = sw[2 * C];
     float ms = 0.f;
 #pragma unroll
@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(BW_THREADS) attend_bwd_kernel(const AttendBwdA
     const float r = 1.0f / sqrtf(ms / C + 1e-6f);
 #pragma unroll
     for (int c = 0; c < C; ++c) xn[c] = sg[c] * vin[c] * r;
-    const float d = depth_from_logit(t, li, L, a.dp);
+    // the initialisation samples at the depth anchors, which no weight moves
+    const float d = a.v0 ? depth_anchor(li, L, a.dp) : depth_from_logit(t, li, L, a.dp);
     const float scale = 1.0f / sqrtf((float)C);
 
     float q[NH][C], qb[C];
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(BW_THREADS) attend_bwd_kernel(const AttendBwdA
             for (int c = 0; c < C; ++c) s = fmaf(dqb[c], swb[k * C + c], s);
         dx[k] = s;
     }
-    const float dt = dd * ddepth_dt(t, d, L, a.dp);
+    const float dt = a.v0 ? 0.f : dd * ddepth_dt(t, d, L, a.dp);
     float dot = 0.f;
 #pragma unroll
     for (int c = 0; c < C; ++c) dot = fmaf(sg[c] * dx[c], vin[c], dot);

@@ -89,6 +89,35 @@ class StageGrads(ct.Structure):
     _fields_ = [(n, ct.c_void_p) for n in STAGE_GRAD_FIELDS]
 
 
+# quark_grads: whole-network weight gradients (shared fields, then per-step arrays)
+GRAD_SHARED_HEAD = ("enc_w", "enc_b", "v0")
+GRAD_PER_STEP = ("attn_g", "Wq", "Wo", "conv_g", "conv1_w", "conv1_b", "conv2_w", "conv2_b", "col_w1", "col_b1",
+                 "col_w2", "col_b2")
+GRAD_SHARED_TAIL = ("w_d", "b_d", "w_sigma", "b_sigma", "W_beta")
+
+
+class Grads(ct.Structure):
+    _fields_ = ([(n, ct.c_void_p) for n in GRAD_SHARED_HEAD] +
+                [(n, ct.c_void_p * MAX_SCALES) for n in GRAD_PER_STEP] +
+                [(n, ct.c_void_p) for n in GRAD_SHARED_TAIL])
+
+
+def make_grads(grads: Dict) -> Grads:
+    """quark_grads from a dict of device tensors keyed by make_weights names (e.g. "Wq_1", "w_d");
+    absent names are NULL."""
+    g = Grads()
+    for n in GRAD_SHARED_HEAD + GRAD_SHARED_TAIL:
+        if n in grads:
+            setattr(g, n, _ptr(grads[n]))
+    for n in GRAD_PER_STEP:
+        arr = getattr(g, n)
+        for j in range(MAX_SCALES):
+            key = f"{n}_{j}"
+            if key in grads:
+                arr[j] = _ptr(grads[key])
+    return g
+
+
 _lib = None
 
 
@@ -138,6 +167,10 @@ def lib():
             "quark_sample_coords": ([vp, ct.POINTER(Camera), ct.c_double, ct.c_double, ct.POINTER(Camera), ct.c_double,
                                      ct.c_int, vp, vp, vp, vp, vp, vp], ct.c_int),
             "quark_test_wait_timeout": ([vp], ct.c_int),
+            "quark_ldm_keep_steps": ([vp, ct.c_int], ct.c_int),
+            "quark_render_ldm_bwd": ([vp, vp, vp, vp, vp, vp, ct.POINTER(Grads), vp], ct.c_int),
+            "quark_update_fuse_bwd": ([vp, vp, ct.c_int, vp, vp, vp, vp, vp, ct.POINTER(Grads), vp], ct.c_int),
+            "quark_encode_pyramid_bwd": ([vp, vp, ct.POINTER(vp), ct.POINTER(Grads), vp], ct.c_int),
             "quark_conv_tiles": ([vp, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)],
                                  ct.c_int),
         }
@@ -245,6 +278,10 @@ class Pyramid:
 class LDM:
     def __init__(self, ctx: "Context", handle: ct.c_void_p):
         self.ctx, self.handle = ctx, handle
+
+    def keep_steps(self, keep: bool = True):
+        """quark_ldm_keep_steps: keep every step's volumes for the backward pass."""
+        _check(lib().quark_ldm_keep_steps(self.handle, int(keep)), self.ctx.handle)
 
     def field_bytes(self, field: int) -> int:
         return lib().quark_ldm_field_bytes(self.handle, field)
@@ -377,6 +414,29 @@ class Context:
         g = StageGrads(*[_ptr(grads[n]) for n in STAGE_GRAD_FIELDS])
         _check(lib().quark_stage_backward(self.handle, pyr.handle, _ptr(feat), _ptr(v_in), ldm.handle, _ptr(dl_drgb),
                                           _ptr(dv_in), _ptr(dfeat), ct.byref(g), _stream(stream)), self.handle)
+
+    # ---- backward pass through the whole network ----
+    def render_ldm_bwd(self, ldm: LDM, pyr: Pyramid, dl_drgb, dv_out, dbeta, grads: Dict, stream=None):
+        """quark_render_ldm_bwd: writes dv_out, dbeta; accumulates the decoder gradients in `grads`."""
+        g = make_grads(grads)
+        _check(lib().quark_render_ldm_bwd(self.handle, ldm.handle, pyr.handle, _ptr(dl_drgb), _ptr(dv_out),
+                                          _ptr(dbeta), ct.byref(g), _stream(stream)), self.handle)
+
+    def update_fuse_bwd(self, pyr: Pyramid, scale: int, ldm: LDM, dv_out, dbeta, dv_prev, dfeat, grads: Dict,
+                        stream=None):
+        """quark_update_fuse_bwd: writes dv_prev; accumulates dfeat and the step's weight gradients."""
+        g = make_grads(grads)
+        p = lambda x: None if x is None else _ptr(x)
+        _check(lib().quark_update_fuse_bwd(self.handle, pyr.handle, scale, ldm.handle, _ptr(dv_out), p(dbeta),
+                                           p(dv_prev), _ptr(dfeat), ct.byref(g), _stream(stream)), self.handle)
+
+    def encode_pyramid_bwd(self, pyr: Pyramid, dfeat: Dict, grads: Dict, stream=None):
+        """quark_encode_pyramid_bwd: dfeat maps pyramid factors k (1, 2, 4, 8) to level gradients;
+        accumulates enc_w, enc_b in `grads`."""
+        arr = (ct.c_void_p * 4)(*[_ptr(dfeat[k]) if k in dfeat else None for k in (1, 2, 4, 8)])
+        g = make_grads(grads)
+        _check(lib().quark_encode_pyramid_bwd(self.handle, pyr.handle, arr, ct.byref(g), _stream(stream)),
+               self.handle)
 
     def sample_coords(self, target, k_tx: float, k_ty: float, view, k_m: float, px, py, depth):
         """quark_sample_coords: (u, v) [n, 2] float32, tap origins [n, 2] int32 and validity [n] of target
