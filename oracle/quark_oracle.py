@@ -19,7 +19,9 @@ Real-time, High-resolution, and General Neural View Synthesis", 2024):
                 project into each input view, bilinearly sample the view's feature map.
   attention     Sec. 3.3: One-to-many attention, head_i = Attention(N(V) W_i^q, D, D),
                 MultiHead = concat(heads) W^O, V' = V + MultiHead(N(V), D); N = RMSNorm.
-  conv block    Sec. 3.3: V' = V + Conv(gelu(Conv(N(V)))), 3x3 per layer plane.
+  conv block    Sec. 3.3: V' = V + Conv(gelu(Conv(N(V)))), 3x3 per layer plane; with the
+                conv_kernel option 1 the convolutions are 1x1, i.e. the position-wise MLP block
+                of a Transformer that the residual convolution block mirrors.
   decode        Sec. 3.2.2 "Decoding": sigma = sigmoid(V W_sigma), c = sigmoid(V W_a),
                 depth by Eq. (depth_activation).
   blend logits  Sec. 3.2.3: the one-to-many attention logits of the final block against
@@ -198,6 +200,19 @@ def conv3x3_rect(x: np.ndarray, x_rect: Rect, H: int, W: int, w: np.ndarray, b: 
         for dx in range(3):
             out += padded[..., dy:dy + oh, dx:dx + ow, :] @ w[dy, dx]
     return out
+
+
+def conv_rect(x: np.ndarray, x_rect: Rect, H: int, W: int, w: np.ndarray, b: np.ndarray, out_rect: Rect):
+    """The fusion block's convolution with kernel w [k, k, Cin, Cout]: k = 3 is conv3x3_rect; k = 1
+    is the position-wise linear map of a Transformer's MLP block, which the residual convolution
+    block of Sec. 3.3 mirrors (the conv_kernel option): y = x w[0, 0] + b on out_rect."""
+    if w.shape[0] == 3:
+        return conv3x3_rect(x, x_rect, H, W, w, b, out_rect)
+    assert w.shape[:2] == (1, 1)
+    oy, ox = out_rect[0] - x_rect[0], out_rect[2] - x_rect[2]
+    assert oy >= 0 and ox >= 0 and out_rect[1] <= x_rect[1] and out_rect[3] <= x_rect[3], "conv input missing"
+    xs = x[..., oy:oy + out_rect[1] - out_rect[0], ox:ox + out_rect[3] - out_rect[2], :]
+    return xs @ w[0, 0] + b
 
 
 # ---------------------------------------------------------------------------------------------
@@ -467,8 +482,8 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
     # ---- fusion block: residual conv block V + Conv(gelu(Conv(N(V)))) ----
     n = rmsnorm(V_attn, f64(W[f"conv_g_{j}"]))
     mid_rect = grow(rect_out, 1, H, Wd)
-    h1 = conv3x3_rect(n, rect_attn, H, Wd, f64(W[f"conv1_w_{j}"]), f64(W[f"conv1_b_{j}"]), mid_rect)
-    h2 = conv3x3_rect(gelu(h1), mid_rect, H, Wd, f64(W[f"conv2_w_{j}"]), f64(W[f"conv2_b_{j}"]), rect_out)
+    h1 = conv_rect(n, rect_attn, H, Wd, f64(W[f"conv1_w_{j}"]), f64(W[f"conv1_b_{j}"]), mid_rect)
+    h2 = conv_rect(gelu(h1), mid_rect, H, Wd, f64(W[f"conv2_w_{j}"]), f64(W[f"conv2_b_{j}"]), rect_out)
     oy, ox = rect_out[0] - rect_attn[0], rect_out[2] - rect_attn[2]
     V_out = V_attn[:, oy:oy + h2.shape[1], ox:ox + h2.shape[2]] + h2
 

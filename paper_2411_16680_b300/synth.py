@@ -69,6 +69,9 @@ class QuarkConfig:
     # other outputs get grids of the same area per layer at their own aspect (None: off)
     model_w: Optional[int] = None
     model_h: Optional[int] = None
+    # kernel size of the fusion blocks' residual convolutions: 3 (Sec. 3.3) or 1 (the position-wise
+    # MLP block of a Transformer, which the residual convolution block mirrors)
+    conv_kernel: int = 3
 
     @property
     def n_scales(self) -> int:
@@ -398,7 +401,7 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
     enc_w (3, 3, 3, C): 3x3 encoder conv [dy, dx, c_in, c_out]; enc_b (C,)
     v0 (C,): learned initial feature (Sec. 3.2.2, Initialization)
     per scale j: attn_g_j (C,), Wq_j (C, h*C), Wo_j (h*C, C)          one-to-many attention (Sec. 3.3)
-                 conv_g_j (C,), conv1_w_j (3,3,C,C), conv1_b_j, conv2_w_j, conv2_b_j   residual conv block
+                 conv_g_j (C,), conv1_w_j (k,k,C,C), conv1_b_j, conv2_w_j, conv2_b_j   residual conv block (k = conv_kernel)
                  col_w1_j (2C, C), col_b1_j (C,), col_w2_j (C, C), col_b2_j (C,)      layer collapse MLP
                  Wq_std_j, Wk_std_j, Wv_std_j, Wo_std_j (C, C)         standard cross-attention mode
     w_d (C,), b_d (1,), w_sigma (C,), b_sigma (1,), W_a (C, 3), b_a (3,)   LDM decoders
@@ -411,9 +414,10 @@ def weight_shapes(cfg: QuarkConfig) -> Dict[str, Tuple[int, ...]]:
         h = cfg.heads_of(j)
         if h > 0:
             s.update({f"attn_g_{j}": (C,), f"Wq_{j}": (C, h * C), f"Wo_{j}": (h * C, C)})
+        ks = cfg.conv_kernel
         s.update({
-            f"conv_g_{j}": (C,), f"conv1_w_{j}": (3, 3, C, C), f"conv1_b_{j}": (C,),
-            f"conv2_w_{j}": (3, 3, C, C), f"conv2_b_{j}": (C,),
+            f"conv_g_{j}": (C,), f"conv1_w_{j}": (ks, ks, C, C), f"conv1_b_{j}": (C,),
+            f"conv2_w_{j}": (ks, ks, C, C), f"conv2_b_{j}": (C,),
             f"col_w1_{j}": (2 * C, C), f"col_b1_{j}": (C,), f"col_w2_{j}": (C, C), f"col_b2_{j}": (C,),
         })
         if h > 0:

@@ -184,6 +184,50 @@ def test_conv3x3_matches_conv2d_and_delta_kernel():
                                atol=1e-12)
 
 
+def test_conv1x1_matches_conv2d_and_centre_tap_3x3():
+    """The conv_kernel = 1 form of the fusion block's convolution (the position-wise MLP of a
+    Transformer block, Sec. 3.3): torch's 1x1 conv2d, and the 3x3 path with the kernel at the
+    centre tap and zeros elsewhere, on a window."""
+    rng = np.random.default_rng(15)
+    x = rng.standard_normal((2, 9, 11, 6))
+    w = rng.standard_normal((1, 1, 6, 4))
+    b = rng.standard_normal(4)
+    ours = O.conv_rect(x, (0, 9, 0, 11), 9, 11, w, b, (0, 9, 0, 11))
+    ref = TF.conv2d(torch.tensor(x).permute(0, 3, 1, 2), torch.tensor(w).permute(3, 2, 0, 1),
+                    torch.tensor(b)).permute(0, 2, 3, 1).numpy()
+    np.testing.assert_allclose(ours, ref, atol=1e-12)
+    w3 = np.zeros((3, 3, 6, 4))
+    w3[1, 1] = w[0, 0]
+    part = O.conv_rect(x[:, 2:8, 0:6], (2, 8, 0, 6), 9, 11, w, b, (3, 7, 0, 5))
+    np.testing.assert_allclose(part, O.conv3x3_rect(x, (0, 9, 0, 11), 9, 11, w3, b, (3, 7, 0, 5)), atol=1e-12)
+
+
+def test_pipeline_with_1x1_blocks_equals_centre_tap_3x3_blocks():
+    """A whole two-step pipeline with conv_kernel = 1 equals the default pipeline whose 3x3 conv
+    weights hold the same matrices at the centre tap and zeros elsewhere (full frame and a
+    window)."""
+    cfg1 = synth.QuarkConfig(C=8, heads=2, scales=[(2, 4), (1, 2)], near=1.0, far=40.0, out_h=24, out_w=32,
+                             conv_kernel=1)
+    cfg3 = cfg1.replace(conv_kernel=3)
+    sc = synth.scene_raycast(seed=4, V=3, W=32, H=24, f=28.0, arc=0.3)
+    W1 = synth.make_weights(cfg1, seed=8, sharp=True)
+    assert W1["conv1_w_0"].shape == (1, 1, 8, 8)
+    W3 = dict(W1)
+    for j in range(cfg1.n_scales):
+        for n in (f"conv1_w_{j}", f"conv2_w_{j}"):
+            w3 = np.zeros((3, 3, 8, 8), np.float32)
+            w3[1, 1] = W1[n][0, 0]
+            W3[n] = w3
+    a, sa = O.forward(cfg1, W1, sc)
+    b, sb = O.forward(cfg3, W3, sc)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+    for x, y in zip(sa, sb):
+        np.testing.assert_allclose(x.V_out, y.V_out, atol=1e-12)
+    r = (5, 11, 7, 15)
+    aw, _ = O.forward(cfg1, W1, sc, r)
+    np.testing.assert_allclose(aw, a[r[0]:r[1], r[2]:r[3]], atol=1e-12)
+
+
 def test_pyramid_matches_conv_then_avgpool_chain():
     sc = synth.scene_noise_pair(V=1, W=32, H=24)
     rng = np.random.default_rng(6)
