@@ -113,6 +113,10 @@ typedef struct {
  *              area, a = output width / height), step j's grid is (h0, w0) x f_0 / f_j, and the
  *              target maps onto a grid with the factors width / W_j and height / H_j, which may
  *              differ (the final upsample too).  The output need not be divisible by anything.
+ *   conv_kernel  kernel size of the fusion blocks' residual convolutions (Sec. 3.3): 3 (0 = 3), or 1,
+ *              the position-wise MLP block of a Transformer that the residual convolution block
+ *              mirrors (V + W2 gelu(W1 N(V) + b1) + b2 per element; conv1_w / conv2_w are then
+ *              [1][1][C][C]).  The Update Block of render-and-refine keeps 3x3 convolutions.
  *   reuse_depth[j]  1: sample the views at the depths the latest sampling step used instead of
  *              the depths decoded from this step's input (one set of update features per Update
  *              & Fuse step); needs the same grid and layers back to that step.  0: decode.
@@ -131,6 +135,7 @@ typedef struct {
     float ldm_f[QUARK_MAX_SCALES];
     int reuse_depth[QUARK_MAX_SCALES];
     int model_width, model_height;
+    int conv_kernel;
     size_t hbm_cap_bytes;
 } quark_config;
 
@@ -141,7 +146,7 @@ typedef struct {
  *   per step j (h = that step's heads):
  *     attn_g[j] [C], Wq[j] [C][h*C], Wo[j] [h*C][C]      RMSNorm gain, one-to-many attention
  *                                                       (NULL for a block without attention)
- *     conv_g[j] [C], conv1_w[j], conv2_w[j] [3][3][C][C], conv1_b[j], conv2_b[j] [C]
+ *     conv_g[j] [C], conv1_w[j], conv2_w[j] [k][k][C][C] (k = conv_kernel), conv1_b[j], conv2_b[j] [C]
  *                                                       residual conv block (Sec. 3.3)
  *     col_w1[j] [2C][C], col_b1[j] [C], col_w2[j] [C][C], col_b2[j] [C]
  *                                                       layer collapse into step j (Sec. 3.2.2);

@@ -86,8 +86,9 @@ def _rmsnorm(v, g):
 
 
 def _conv(x, w, b):
-    """3x3 per layer plane, zero pad: x [L, H, W, C], w [3, 3, Cin, Cout]."""
-    y = torch.nn.functional.conv2d(x.permute(0, 3, 1, 2), w.permute(3, 2, 0, 1), b, padding=1)
+    """k x k per layer plane (k = 3, or 1 for the conv_kernel option), zero pad: x [L, H, W, C],
+    w [k, k, Cin, Cout]."""
+    y = torch.nn.functional.conv2d(x.permute(0, 3, 1, 2), w.permute(3, 2, 0, 1), b, padding=w.shape[0] // 2)
     return y.permute(0, 2, 3, 1)
 
 

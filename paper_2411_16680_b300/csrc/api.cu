@@ -252,6 +252,8 @@ quark_status qk_validate_config(const quark_config* c) {
         return qk_fail(nullptr, QUARK_EINVAL, "render_refine must be 0 or 1");
     if (c->model_width < 0 || c->model_height < 0 || (c->model_width > 0) != (c->model_height > 0))
         return qk_fail(nullptr, QUARK_EINVAL, "model_width and model_height must both be 0 or both positive");
+    if (c->conv_kernel != 0 && c->conv_kernel != 1 && c->conv_kernel != 3)
+        return qk_fail(nullptr, QUARK_EINVAL, "conv_kernel must be 3 or 1 (0 = 3; got %d)", c->conv_kernel);
     return QUARK_OK;
 }
 
@@ -335,6 +337,24 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     if (!need(w->enc_w, "enc_w") || !need(w->enc_b, "enc_b") || !need(w->v0, "v0") || !need(w->w_d, "w_d") ||
         !need(w->w_sigma, "w_sigma") || !need(w->W_a, "W_a") || !need(w->b_a, "b_a") || !need(w->W_beta, "W_beta"))
         return QUARK_EINVAL;
+    // the fusion blocks' conv weights as 3x3 kernels: 1x1 weights (conv_kernel 1) sit at the centre
+    // tap, zeros elsewhere, so every kernel, the decode and the backward share one layout
+    std::vector<std::vector<float>> tap9(2 * (size_t)c.n_scales);
+    const float* cw1[QUARK_MAX_SCALES] = {};
+    const float* cw2[QUARK_MAX_SCALES] = {};
+    for (int j = 0; j < c.n_scales; ++j) {
+        cw1[j] = w->conv1_w[j];
+        cw2[j] = w->conv2_w[j];
+        if (c.conv_kernel == 1 && w->conv1_w[j] && w->conv2_w[j]) {
+            for (int q = 0; q < 2; ++q) {
+                std::vector<float>& t = tap9[2 * j + q];
+                t.assign(9 * (size_t)C * C, 0.f);
+                std::memcpy(t.data() + 4 * (size_t)C * C, q ? w->conv2_w[j] : w->conv1_w[j], (size_t)C * C * 4);
+            }
+            cw1[j] = tap9[2 * j].data();
+            cw2[j] = tap9[2 * j + 1].data();
+        }
+    }
     std::vector<float> blob;
     auto put = [&](const float* p, size_t n) {
         size_t off = blob.size();
@@ -374,9 +394,9 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         const ConvLayout cl{C};
         ctx->off_conv[j] = blob.size();
         put(w->conv_g[j], C);
-        put(w->conv1_w[j], 9 * (size_t)C * C);
+        put(cw1[j], 9 * (size_t)C * C);
         put(w->conv1_b[j], C);
-        put(w->conv2_w[j], 9 * (size_t)C * C);
+        put(cw2[j], 9 * (size_t)C * C);
         put(w->conv2_b[j], C);
         put(w->w_d, C);
         put(w->w_sigma, C);
@@ -472,8 +492,8 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         std::vector<uint16_t> tc(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
         for (int j = 0; j < c.n_scales; ++j) {
             uint16_t* d = tc.data() + (size_t)j * 2 * 9 * C * C;
-            pack_conv_weights_bf16(w->conv1_w[j], C, d);
-            pack_conv_weights_bf16(w->conv2_w[j], C, d + 9 * (size_t)C * C);
+            pack_conv_weights_bf16(cw1[j], C, d);
+            pack_conv_weights_bf16(cw2[j], C, d + 9 * (size_t)C * C);
         }
         // attention: B_q rows n < hC from Wq[k][n], rows hC.. from W_beta[k][n - hC] (K = C);
         // B_o rows n < C from Wo[k][n] (K = hC); element (n, k) at (k / 8) * N * 8 + n * 8 + k % 8
@@ -1201,6 +1221,7 @@ quark_status qk_update_fuse(quark_ctx* ctx, const quark_pyramid* pyr, int V_use,
     ca.s_raw = last ? ldm->s_raw : nullptr;
     ca.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
     ca.err = ctx->dev_err;
+    ca.ks = c.conv_kernel == 1 ? 1 : 3;
     s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(ca, c.C, bf16, st); });
     if (s != QUARK_OK) return s;
     if (ldm->keep) {

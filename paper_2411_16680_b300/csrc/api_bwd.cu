@@ -134,6 +134,9 @@ extern "C" quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid
 
     const ConvLayout cl{C};
     const AttendLayout al{C, h};
+    // 1x1 fusion-block convolutions sit at the centre tap of the 3x3 layout (exact in the 3x3
+    // adjoints); their weight gradient is the unshifted product
+    const int ctaps = c.conv_kernel == 1 ? 1 : 9;
     const float* wc = ctx->wdev + ctx->off_conv[n];
     const float* wa = ctx->wdev + ctx->off_attend[n];
     DepthParams dp{(float)(1.0 / c.near_m - 1.0 / c.far_m), (float)(1.0 / c.far_m)};
@@ -195,9 +198,9 @@ extern "C" quark_status quark_stage_backward(quark_ctx* ctx, const quark_pyramid
         return L_([&] { return launch_xty(xa, out, acc, st); });
     };
     // conv block and decoder weight gradients
-    if ((s = xty(H1, C, G, C, C, C, 9, 1, g->conv2_w, 0)) != QUARK_OK) return s;
+    if ((s = xty(H1, C, G, C, C, C, ctaps, 1, g->conv2_w, 0)) != QUARK_OK) return s;
     if ((s = xty(nullptr, 0, G, C, 1, C, 1, 0, g->conv2_b, 0)) != QUARK_OK) return s;
-    if ((s = xty(Nn, C, dH1, C, C, C, 9, 0, g->conv1_w, 0)) != QUARK_OK) return s;
+    if ((s = xty(Nn, C, dH1, C, C, C, ctaps, 0, g->conv1_w, 0)) != QUARK_OK) return s;
     if ((s = xty(nullptr, 0, dH1, C, 1, C, 1, 0, g->conv1_b, 0)) != QUARK_OK) return s;
     if ((s = xty(nullptr, 0, dgt, C, 1, C, 1, 0, g->conv_g, 0)) != QUARK_OK) return s;
     if ((s = xty(V_out, C, dts, 2, C, 1, 1, 0, g->w_d, 0)) != QUARK_OK) return s;
@@ -453,6 +456,9 @@ extern "C" quark_status quark_update_fuse_bwd(quark_ctx* ctx, const quark_pyrami
 
     const ConvLayout cl{C};
     const AttendLayout al{C, h};
+    // 1x1 fusion-block convolutions sit at the centre tap of the 3x3 layout (exact in the 3x3
+    // adjoints); their weight gradient is the unshifted product
+    const int ctaps = c.conv_kernel == 1 ? 1 : 9;
     const float* wc = ctx->wdev + ctx->off_conv[scale];
     const float* wa = ctx->wdev + ctx->off_attend[scale];
     const float* V_attn = (const float*)ldm->hist_attn[scale];
@@ -486,9 +492,9 @@ extern "C" quark_status quark_update_fuse_bwd(quark_ctx* ctx, const quark_pyrami
         return s;
     if ((s = L_([&] { return launch_rmsnorm_bwd(V_attn, wc + cl.g(), dN, dv_out, dVa, dgt, E, C, st); })) != QUARK_OK)
         return s;
-    if ((s = xty(H1, C, dv_out, C, C, C, 9, 1, L, H, W, g->conv2_w[scale])) != QUARK_OK) return s;
+    if ((s = xty(H1, C, dv_out, C, C, C, ctaps, 1, L, H, W, g->conv2_w[scale])) != QUARK_OK) return s;
     if ((s = xty(nullptr, 0, dv_out, C, 1, C, 1, 0, L, H, W, g->conv2_b[scale])) != QUARK_OK) return s;
-    if ((s = xty(Nn, C, dH1, C, C, C, 9, 0, L, H, W, g->conv1_w[scale])) != QUARK_OK) return s;
+    if ((s = xty(Nn, C, dH1, C, C, C, ctaps, 0, L, H, W, g->conv1_w[scale])) != QUARK_OK) return s;
     if ((s = xty(nullptr, 0, dH1, C, 1, C, 1, 0, L, H, W, g->conv1_b[scale])) != QUARK_OK) return s;
     if ((s = xty(nullptr, 0, dgt, C, 1, C, 1, 0, L, H, W, g->conv_g[scale])) != QUARK_OK) return s;
 

@@ -183,8 +183,9 @@ static cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// FP32 form: this SIMT kernel.  BF16 form: the tcgen05 kernel (k_conv_tc.cu).
+// FP32 form: this SIMT kernel.  BF16 form: the tcgen05 kernel (k_conv_tc.cu).  1x1 kernels: k_mlp.cu.
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st) {
+    if (a.ks == 1) return launch_mlp_block(a, C, bf16, st);  // 1x1 convolutions: per element
     if (bf16) return launch_conv_block_tc(a, C, st);
     if (C == 16) return launch_t<float, 16>(a, st);
     if (C == 32) return launch_t<float, 32>(a, st);

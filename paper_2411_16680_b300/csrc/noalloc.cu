@@ -178,6 +178,7 @@ extern "C" quark_status quark_update_fuse_noalloc(quark_ctx* ctx, const quark_py
     cv.w = ctx->wdev + ctx->off_conv[scale];
     cv.wtc = ctx->wtc ? (const uint8_t*)ctx->wtc + scale * ctx->wtc_step_bytes : nullptr;
     cv.err = ctx->dev_err;
+    cv.ks = c.conv_kernel == 1 ? 1 : 3;
     s = qk_launch(ctx, st, KF_CONV, [&] { return launch_conv_block(cv, c.C, bf16, st); });
     if (s != QUARK_OK) return s;
     // the decoded attributes, from the volume just written (the regular step makes them on demand)

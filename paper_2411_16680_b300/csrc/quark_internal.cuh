@@ -78,6 +78,7 @@ struct ConvArgs {
     float* s_raw;      // [H][W][L] raw density logits, or NULL (not written)
     const void* wtc;   // BF16 form: W1 then W2 packed as tcgen05 B operands (see pack_conv_weights_bf16)
     int* err;          // device error word: set when a bounded wait inside the kernel runs out
+    int ks;            // kernel size: 3, or 1 (the weights at the centre tap; k_mlp.cu); 0 = 3
 };
 
 // Decode of the LDM attributes from a stored volume (Sec. 3.2.2 "Decoding", Eq. depth_activation).
@@ -190,6 +191,7 @@ cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, 
                           cudaStream_t st);
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st);
+cudaError_t launch_mlp_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
 // Output tile (columns, rows) the tensor-core conv block uses for an L x H x W volume.
 cudaError_t conv_tc_tile_shape(int C, int W, int H, int L, int* cols, int* rows);
 cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st);

@@ -41,6 +41,7 @@ class Config(ct.Structure):
                 ("precision", ct.c_int), ("attn_mode", ct.c_int), ("ray_encoding", ct.c_int),
                 ("render_refine", ct.c_int), ("scale_heads", ct.c_int * MAX_SCALES), ("ldm_f", ct.c_float * MAX_SCALES),
                 ("reuse_depth", ct.c_int * MAX_SCALES), ("model_width", ct.c_int), ("model_height", ct.c_int),
+                ("conv_kernel", ct.c_int),
                 ("hbm_cap_bytes", ct.c_size_t)]
 
 
@@ -233,6 +234,7 @@ def make_config(cfg, hbm_cap_bytes: int = 0) -> Config:
             c.reuse_depth[j] = int(r)
     if getattr(cfg, "model_w", None):
         c.model_width, c.model_height = int(cfg.model_w), int(cfg.model_h)
+    c.conv_kernel = int(getattr(cfg, "conv_kernel", 3))
     c.hbm_cap_bytes = hbm_cap_bytes
     return c
 
