@@ -566,7 +566,10 @@ def main():
                        "p50_ms": round(statistics.median(lat), 3),
                        "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
                        "e2e_fps": round(job_rate(world, args.steps, res["e2e_s"]), 2),
-                       "e2e_serial_fps": round(job_rate(world, args.steps, res["serial_s"]), 2)}
+                       "e2e_serial_fps": round(job_rate(world, args.steps, res["serial_s"]), 2),
+                       # device time per frame of each kernel family (CUDA events around each launch)
+                       "kernel_ms_per_frame": {k: round(v[1] / args.steps, 4) for k, v in res["ktimes"].items()
+                                               if v[0]}}
 
     # accuracy of each form against the oracle on sampled windows (rank 0); the oracle's
     # render-and-refine renders whole views, so that option is checked by the tests instead

@@ -11,8 +11,8 @@
 //      depth, RMSNorm -> X (BF16) in shared memory as a K-major tcgen05 A operand.
 //   2. One MMA chain Q = X [Wq | W^beta] (N = hC (+C), K = C) into TMEM; copied to shared memory.
 //   3. Per element, two threads (16 channels each) reproject into every view, bilinearly sample
-//      the BF16 level-k features, and run the online softmax over views (FP32), exactly as the
-//      SIMT kernel; the last step also writes the blend logits.
+//      the BF16 level-k features on packed BF16 pairs, and run the online softmax over views
+//      (FP32); the last step also writes the blend logits.
 //   4. The head outputs O (BF16) go back to shared memory as an A operand; one MMA chain
 //      O W^O (N = C, K = hC) into TMEM; residual add in FP32; V_attn stored as BF16.
 // Completion of each MMA chain is signalled through an mbarrier; every wait is bounded.
@@ -48,47 +48,52 @@ struct AtSmem {
 
 
 
-// Bilinear interpolation of BF16 features on the mixed-precision FMA (PTX fma.rn.f32.bf16, sm_100
-// family): d = a b + c with BF16 a (a feature channel, straight from its half of the loaded word)
-// and b (the tap weight, rounded to BF16 once per tap), FP32 c and d -- one rounding per tap, FP32
-// accumulation, no conversion of the features.
-__device__ __forceinline__ float fma_bf16(uint16_t a, uint16_t b, float c) {
-    float d;
-    asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
-    return d;
+// Bilinear interpolation on packed BF16 pairs: each 32-bit word of a tap holds two channels, and
+// one fma.rn.bf16x2 adds both channels' weighted taps (BF16 products and sums, one rounding per
+// step), so the four taps of 16 channels take 32 instructions on the packed pairs as loaded.  The
+// sampled features are BF16 in the precision form; the dot products and the softmax below take
+// them to FP32.  One thread's 16 BF16 channels of a texel (32 bytes, 32-byte aligned: a texel is
+// C x 2 bytes and a thread's channel group starts at a multiple of 16 channels) come in one
+// 256-bit load.
+__device__ __forceinline__ uint32_t bf2_mul(uint32_t x, __nv_bfloat162 w) {
+    const __nv_bfloat162 r = __hmul2(*reinterpret_cast<const __nv_bfloat162*>(&x), w);
+    return *reinterpret_cast<const uint32_t*>(&r);
 }
-__device__ __forceinline__ float2 fma_bf16x2(uint32_t x, uint16_t w, float2 c) {
-    return make_float2(fma_bf16((uint16_t)(x & 0xffffu), w, c.x), fma_bf16((uint16_t)(x >> 16), w, c.y));
+__device__ __forceinline__ uint32_t bf2_fma(uint32_t x, __nv_bfloat162 w, uint32_t c) {
+    const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162*>(&x), w,
+                                     *reinterpret_cast<const __nv_bfloat162*>(&c));
+    return *reinterpret_cast<const uint32_t*>(&r);
 }
-__device__ __forceinline__ uint16_t bf16_bits(float w) { return __bfloat16_as_ushort(__float2bfloat16_rn(w)); }
-// The taps: one thread's 16 BF16 channels of a texel (32 bytes, 32-byte aligned: a texel is C x 2
-// bytes and a thread's channel group starts at a multiple of 16 channels) in one 256-bit load.
-__device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
+__device__ __forceinline__ void mul_taps16(const __nv_bfloat16* p, float w, uint32_t (&D)[8]) {
     uint4 a, b;
     ldg256(p, a, b);
-    const uint16_t wb = bf16_bits(w);
-    const float2 z = make_float2(0.f, 0.f);
-    D[0] = fma_bf16x2(a.x, wb, z);
-    D[1] = fma_bf16x2(a.y, wb, z);
-    D[2] = fma_bf16x2(a.z, wb, z);
-    D[3] = fma_bf16x2(a.w, wb, z);
-    D[4] = fma_bf16x2(b.x, wb, z);
-    D[5] = fma_bf16x2(b.y, wb, z);
-    D[6] = fma_bf16x2(b.z, wb, z);
-    D[7] = fma_bf16x2(b.w, wb, z);
+    const __nv_bfloat162 w2 = __float2bfloat162_rn(w);
+    D[0] = bf2_mul(a.x, w2);
+    D[1] = bf2_mul(a.y, w2);
+    D[2] = bf2_mul(a.z, w2);
+    D[3] = bf2_mul(a.w, w2);
+    D[4] = bf2_mul(b.x, w2);
+    D[5] = bf2_mul(b.y, w2);
+    D[6] = bf2_mul(b.z, w2);
+    D[7] = bf2_mul(b.w, w2);
 }
-__device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, float2 (&D)[8]) {
+__device__ __forceinline__ void fma_taps16(const __nv_bfloat16* p, float w, uint32_t (&D)[8]) {
     uint4 a, b;
     ldg256(p, a, b);
-    const uint16_t wb = bf16_bits(w);
-    D[0] = fma_bf16x2(a.x, wb, D[0]);
-    D[1] = fma_bf16x2(a.y, wb, D[1]);
-    D[2] = fma_bf16x2(a.z, wb, D[2]);
-    D[3] = fma_bf16x2(a.w, wb, D[3]);
-    D[4] = fma_bf16x2(b.x, wb, D[4]);
-    D[5] = fma_bf16x2(b.y, wb, D[5]);
-    D[6] = fma_bf16x2(b.z, wb, D[6]);
-    D[7] = fma_bf16x2(b.w, wb, D[7]);
+    const __nv_bfloat162 w2 = __float2bfloat162_rn(w);
+    D[0] = bf2_fma(a.x, w2, D[0]);
+    D[1] = bf2_fma(a.y, w2, D[1]);
+    D[2] = bf2_fma(a.z, w2, D[2]);
+    D[3] = bf2_fma(a.w, w2, D[3]);
+    D[4] = bf2_fma(b.x, w2, D[4]);
+    D[5] = bf2_fma(b.y, w2, D[5]);
+    D[6] = bf2_fma(b.z, w2, D[6]);
+    D[7] = bf2_fma(b.w, w2, D[7]);
+}
+// the sampled channel pairs as FP32 pairs (a BF16 value is the high half of its FP32 word)
+__device__ __forceinline__ void unpack16(const uint32_t (&H)[8], float2 (&D)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) D[j] = make_float2(__uint_as_float(H[j] << 16), __uint_as_float(H[j] & 0xffff0000u));
 }
 // The softmax below works in log2 units, so that each weight is one ex2 (ex2_approx); the
 // reprojection divides with one reciprocal (reproject_rcp).
@@ -293,10 +298,12 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
             const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
             const __nv_bfloat16* f = feat0 + (size_t)m * vstride;
-            mul_taps16(f + tp.i00 * C, tp.w00, D);
-            fma_taps16(f + tp.i01 * C, tp.w01, D);
-            fma_taps16(f + tp.i10 * C, tp.w10, D);
-            fma_taps16(f + tp.i11 * C, tp.w11, D);
+            uint32_t Hs[8];
+            mul_taps16(f + tp.i00 * C, tp.w00, Hs);
+            fma_taps16(f + tp.i01 * C, tp.w01, Hs);
+            fma_taps16(f + tp.i10 * C, tp.w10, Hs);
+            fma_taps16(f + tp.i11 * C, tp.w11, Hs);
+            unpack16(Hs, D);
         };
         // One online-softmax step of head h: logit s (log2 units, this element's full sum), sample D.
         // The softmax is invariant to the reference subtracted from its logits, so the reference
