@@ -125,18 +125,47 @@ def blas_threads():
         return os.cpu_count() or 1
 
 
-def oracle_sample(cfg, W, scene, rows: int = 2):
-    """Oracle on `rows` output rows at the frame centre, through every scale; returns (fps, secs,
-    description).  The fps extrapolates the sampled rows to the full frame."""
+# The oracle is timed on one fixed band of output rows at the frame centre, the same band for the
+# cpu_baseline and for the reference arm.
+ORACLE_BAND_ROWS = 8
+
+
+def oracle_band(cfg):
+    y0 = cfg.out_h // 2 - ORACLE_BAND_ROWS // 2
+    return (y0, y0 + ORACLE_BAND_ROWS, 0, cfg.out_w)
+
+
+def oracle_work_ratio(cfg, rect):
+    """LDM elements a whole frame computes over those the oracle computes for the band `rect`: the
+    band's windows grow backwards through every scale's halo (two 3x3 convs, the x2 upsample, the
+    render's upsample), so its per-row cost is far above a whole frame's, and the timed band is
+    extrapolated by this ratio rather than by rows."""
     from oracle import quark_oracle as O
-    y0 = cfg.out_h // 2 - rows // 2
-    rect = (y0, y0 + rows, 0, cfg.out_w)
-    t0 = time.perf_counter()
-    O.forward(cfg, W, scene, rect, mode=cfg.attn_mode)
-    dt = time.perf_counter() - t0
-    fps = (rows / cfg.out_h) / dt
+    rect_attn, _ = O.plan_rects(cfg, rect)
+    band = sum(cfg.scales[j][1] * (r[1] - r[0]) * (r[3] - r[2]) for j, r in enumerate(rect_attn))
+    full = 0
+    for j in range(cfg.n_scales):
+        L, H, W = cfg.ldm_shape(j)
+        full += L * H * W
+    return full / band
+
+
+def oracle_sample(cfg, W, scene, runs: int = 1):
+    """The oracle on the fixed band through every scale, `runs` times; returns (fps, seconds of the
+    median run, description).  fps = 1 / (median seconds x oracle_work_ratio)."""
+    from oracle import quark_oracle as O
+    rect = oracle_band(cfg)
+    ratio = oracle_work_ratio(cfg, rect)
+    times = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        O.forward(cfg, W, scene, rect, mode=cfg.attn_mode)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
+    fps = 1.0 / (dt * ratio)
     desc = (f"oracle (float64 numpy) on output rows {rect[0]}-{rect[1] - 1} x all {cfg.out_w} columns of the "
-            f"{cfg.out_w}x{cfg.out_h} frame through every scale; fps scaled by {cfg.out_h}/{rows}")
+            f"{cfg.out_w}x{cfg.out_h} frame through every scale, median of {runs}; seconds per frame = band "
+            f"seconds x {ratio:.2f}, the LDM elements of the whole frame over those of the band's windows")
     return fps, dt, desc
 
 
@@ -310,12 +339,16 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     tensor_flops = w.get("tensor_flops", 0.0) / w["launches"]
     alu_flops = flops_per_launch - tensor_flops
     sec = per_launch_ms * 1e-3
-    alu_peak = accounting.fp32_alu_peak_tflops(peaks["sm_max_mhz"])
+    if peaks.get("fp32_tflops"):
+        alu_peak = peaks["fp32_tflops"]
+        alu_src = "measured FP32 FMA peak (quark_measure_fp32_peak, the faster of scalar and packed FP32x2)"
+    else:
+        alu_peak = accounting.fp32_alu_peak_tflops(peaks["sm_max_mhz"])
+        alu_src = f"derived: 148 SMs x 128 FP32 lanes x 2 FLOP x {peaks['sm_max_mhz']:.0f} MHz"
     cands = {
         "hbm": (bytes_per_launch / (peaks["hbm_gbs"] * 1e9), bytes_per_launch / sec / 1e9, peaks["hbm_gbs"], "GB/s",
                 f"{peaks['source']} copy bandwidth"),
-        "alu": (alu_flops / (alu_peak * 1e12), alu_flops / sec / 1e12, round(alu_peak, 1), "TFLOP/s",
-                f"derived: 148 SMs x 128 FP32 lanes x 2 FLOP x {peaks['sm_max_mhz']:.0f} MHz"),
+        "alu": (alu_flops / (alu_peak * 1e12), alu_flops / sec / 1e12, round(alu_peak, 1), "TFLOP/s", alu_src),
     }
     if tensor_flops > 0:
         tp = peaks["bf16_tflops_sustained"]
@@ -339,11 +372,12 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
     return r
 
 
-def run_serve(args):
-    """Serving workload: Poisson arrivals (mean `rate`/s, seed 42) for `duration` s after `serve_warmup`
+def serve_stream(rate, duration, warmup, slots, queue, sharp=False):
+    """Serving workload: Poisson arrivals (mean `rate`/s, seed 42) for `duration` s after `warmup`
     s; output resolution uniform over {1280x720, 1920x1080, 3840x2160}; V uniform over {4, 8, 12, 16}
     (the first V of 16 resident views); time step uniform over 4 resident 16-view 1080p steps;
-    pose = arc midpoint + U(-0.2, 0.2) m per axis; BF16 form; admission capped at 150 GB."""
+    pose = arc midpoint + U(-0.2, 0.2) m per axis; BF16 form; admission capped at 150 GB.  Returns
+    the measurements of the window after the warm-up."""
     import dataclasses
     import threading
     import numpy as np
@@ -351,18 +385,18 @@ def run_serve(args):
     from paper_2411_16680_b300 import quark
 
     cfg = synth.config_1080p().replace(precision=synth.PREC_BF16)
-    W = synth.make_weights(cfg, sharp=args.sharp)
+    W = synth.make_weights(cfg, sharp=sharp)
     base = synth.scene_raycast(seed=1234, V=16, W=1920, H=1080, f=1400.0)
     ctx = quark.Context(cfg)
     ctx.load_weights(W)
-    srv = quark.Server(ctx, n_slots=args.slots, queue_capacity=args.queue, hbm_cap_bytes=150 << 30)
+    srv = quark.Server(ctx, n_slots=slots, queue_capacity=queue, hbm_cap_bytes=150 << 30)
     for t in range(4):
         imgs = np.clip(base.images * (1.0 - 0.03 * t) + 0.02 * t, 0.0, 1.0).astype(np.float32)
         srv.set_timestep(t, torch.tensor(imgs, device="cuda"), base.cams)
     rng = np.random.default_rng(42)
     res = [(1280, 720), (1920, 1080), (3840, 2160)]
-    total = args.serve_warmup + args.duration
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, int(total * args.rate * 1.5) + 10))
+    total = warmup + duration
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, int(total * rate * 1.5) + 10))
     arrivals = arrivals[arrivals < total]
     reqs = []
     for a in arrivals:
@@ -411,7 +445,7 @@ def run_serve(args):
         try:
             tk = srv.submit(ts, tgt, V, b)
         except quark.QuarkError:
-            rejected[0 if a < args.serve_warmup else 1] += 1
+            rejected[0 if a < warmup else 1] += 1
             with lock:
                 pools[r].append(b)
             continue
@@ -422,19 +456,30 @@ def run_serve(args):
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.stop()
-    win = [d for d in done if d[0] >= args.serve_warmup]
+    win = [d for d in done if d[0] >= warmup]
     lat = sorted(d[1] for d in win)
-    n_off = sum(1 for r in reqs if r[0] >= args.serve_warmup)
+    n_off = sum(1 for r in reqs if r[0] >= warmup)
     pct = lambda p: round(lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))], 2) if lat else None
+    n_rej = rejected[1]
+    return {"rate": rate, "duration": duration, "warmup": warmup, "slots": slots, "queue": queue,
+            "completed": len(win), "offered": n_off, "rejected": n_rej, "p50": pct(0.5), "p99": pct(0.99),
+            "hbm_high_water_gb": round(st.hbm_high_water / 2**30, 1), "wall_s": round(wall, 1),
+            "completed_per_s": round(len(win) / duration, 2)}
+
+
+def run_serve(args):
+    """--serve: the serving workload on its own (see serve_stream), one JSON line."""
+    r = serve_stream(args.rate, args.duration, args.serve_warmup, args.slots, args.queue, args.sharp)
     line = {"metric": "serving: novel views/s on a Poisson request stream (mixed 720p/1080p/4K, V 4-16), p50/p99",
-            "value": round(len(win) / args.duration, 2), "unit": "requests/s", "n_gpus": 1,
+            "value": r["completed_per_s"], "unit": "requests/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "bf16", "data": "synthetic (seeded ray-cast scene; random-init weights)",
             "config": {"workload": "serving", "offered_rate_per_s": args.rate, "duration_s": args.duration,
                        "warmup_s": args.serve_warmup, "slots": args.slots, "queue_capacity": args.queue,
                        "hbm_cap_gb": 150, "time_steps": 4, "views_resident": 16},
-            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99)},
-            "offered": n_off, "completed": len(win), "rejected_queue_full": rejected[1],
-            "hbm_high_water_gb": round(st.hbm_high_water / 2**30, 1), "wall_s": round(wall, 1)}
+            "latency_ms": {"p50": r["p50"], "p99": r["p99"]},
+            "offered": r["offered"], "completed": r["completed"], "rejected_queue_full": r["rejected"],
+            "hbm_high_water_gb": r["hbm_high_water_gb"], "wall_s": r["wall_s"]}
+
     print(json.dumps(line))
     return 0
 
@@ -462,6 +507,8 @@ def main():
     ap.add_argument("--adaptive", action="store_true",
                     help="aspect-adaptive LDM dimensions: grids of the 1920x1080 model's area at the --size aspect")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the shortened serving stream the default run reports under `serve`")
     ap.add_argument("--rate", type=float, default=120.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--serve-warmup", type=float, default=5.0)
@@ -530,7 +577,7 @@ def main():
         for _ in range(args.warmup):
             pass  # the oracle has no warm-up state
         for _ in range(args.steps):
-            f, s, desc = oracle_sample(cfg, W, scene, rows=1)
+            f, s, desc = oracle_sample(cfg, W, scene, runs=1)
             fps_l.append(f)
             secs += s
         fps = statistics.median(fps_l)
@@ -540,7 +587,8 @@ def main():
                 "data": "synthetic (seeded ray-cast scene; random-init weights)",
                 "config": {"workload": workload, "form": "oracle", "l2": "inputs larger than L2"},
                 "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": blas_threads(),
-                                 "kind": "oracle", "sample": desc},
+                                 "kind": "oracle", "sample": desc,
+                                 "band_seconds_per_step": round(secs / max(args.steps, 1), 2)},
                 "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -551,6 +599,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     dev = local
+    # the FP32 SIMT roofline's denominator, measured on this device (a few tens of ms)
+    from paper_2411_16680_b300 import quark as _q
+    fma_tf, ffma2_tf = _q.measure_fp32_peak(dev)
+    peaks["fp32_tflops"] = max(fma_tf, ffma2_tf)
+    peaks["fp32_measured"] = {"fma_tflops": round(fma_tf, 1), "ffma2_tflops": round(ffma2_tf, 1)}
 
     forms = {}
     results = {}
@@ -597,9 +650,23 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.refine:
         cfg64 = base_cfg.replace(precision=synth.PREC_FP32)
-        fps_cpu, secs, desc = oracle_sample(cfg64, synth.make_weights(cfg64, sharp=args.sharp), scene, rows=6)
+        fps_cpu, secs, desc = oracle_sample(cfg64, synth.make_weights(cfg64, sharp=args.sharp), scene, runs=3)
         cpu = {"value": round(fps_cpu, 6), "unit": "frames/s", "cores": blas_threads(), "kind": "oracle",
                "sample": desc, "seconds": round(secs, 1)}
+    # the serving form on a shortened copy of its request stream (offered 120 req/s, 3 s warm-up,
+    # 12 s measured), single-GPU runs of the default workload only
+    serve = None
+    default_run = not (quark_model or args.refine or args.ray or args.adaptive or attn_mode == synth.ATTN_STANDARD
+                       or args.views != 8 or (sw, sh) != (1920, 1080))
+    if rank == 0 and world == 1 and default_run and not args.no_serve:
+        r = serve_stream(120.0, 12.0, 3.0, 8, 64, args.sharp)
+        serve = {"offered_rate_per_s": 120.0, "measured_s": 12.0, "warmup_s": 3.0,
+                 "completed_per_s": r["completed_per_s"], "p50_ms": r["p50"], "p99_ms": r["p99"],
+                 "offered": r["offered"], "completed": r["completed"], "rejected_queue_full": r["rejected"],
+                 "shed_fraction": round(r["rejected"] / max(r["offered"], 1), 3),
+                 "hbm_high_water_gb": r["hbm_high_water_gb"],
+                 "workload": "Poisson stream; 720p/1080p/4K outputs; V in {4, 8, 12, 16} of 16 resident 1080p "
+                             "views; 4 time steps; BF16; 8 slots, queue 64, 150 GB admission cap"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": f["fps"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -610,6 +677,8 @@ def main():
                        "l2": ("512 MB L2 flush before every timed frame (outside its events); e2e without flush"
                               if quark_model else "inputs larger than L2 (2.8 GB pyramid per frame), no flush")},
             "latency_ms": {"p50": f["p50_ms"], "p99": f["p99_ms"]},
+            "fp32_peak_measured": peaks.get("fp32_measured"),
+            "serve": serve,
             "forms": forms,
             "e2e": {"value": f["e2e_fps"], "unit": "frames/s", "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},

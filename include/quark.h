@@ -554,6 +554,13 @@ quark_status quark_check_device(quark_ctx* ctx);
  * attention. */
 quark_status quark_test_wait_timeout(quark_ctx* ctx);
 
+/* Measured FP32 SIMT peak of CUDA device `device` (synchronous; allocates and frees a small
+ * buffer): the FLOP rate of kernels that keep every FP32 lane busy with independent fused
+ * multiply-add chains, as scalar FMAs (*fma_tflops) and as packed FP32x2 FMAs (*ffma2_tflops), in
+ * TFLOP/s (2 FLOP per lane-FMA), best of three timed launches.  The denominator of the FP32
+ * roofline fractions of the benchmark.  No counterpart in the paper. */
+quark_status quark_measure_fp32_peak(int device, double* fma_tflops, double* ffma2_tflops);
+
 /* Kernel accounting.  quark_launch_count returns the number of kernels this context has
  * launched since creation or the last reset.  With profiling on, every launch is bracketed
  * by CUDA events on its own stream and quark_kernel_times (which synchronises) returns, per

@@ -168,6 +168,7 @@ def lib():
             "quark_sample_coords": ([vp, ct.POINTER(Camera), ct.c_double, ct.c_double, ct.POINTER(Camera), ct.c_double,
                                      ct.c_int, vp, vp, vp, vp, vp, vp], ct.c_int),
             "quark_test_wait_timeout": ([vp], ct.c_int),
+            "quark_measure_fp32_peak": ([ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], ct.c_int),
             "quark_ldm_keep_steps": ([vp, ct.c_int], ct.c_int),
             "quark_render_ldm_bwd": ([vp, vp, vp, vp, vp, vp, ct.POINTER(Grads), vp], ct.c_int),
             "quark_update_fuse_bwd": ([vp, vp, ct.c_int, vp, vp, vp, vp, vp, ct.POINTER(Grads), vp], ct.c_int),
@@ -190,6 +191,13 @@ def exported_symbols() -> List[str]:
                         "quark_ldm_read", "quark_ldm_field_bytes", "quark_release_pyramid", "quark_release_ldm",
                         "quark_last_error", "quark_launch_count", "quark_reset_counters", "quark_set_profiling",
                         "quark_kernel_times")]
+
+
+def measure_fp32_peak(device: int = 0):
+    """quark_measure_fp32_peak: (scalar FMA, packed FP32x2 FMA) TFLOP/s of the device's FP32 lanes."""
+    a, b = ct.c_double(0.0), ct.c_double(0.0)
+    _check(lib().quark_measure_fp32_peak(device, ct.byref(a), ct.byref(b)))
+    return a.value, b.value
 
 
 def _check(status: int, ctx=None):
