@@ -292,6 +292,7 @@ extern "C" quark_status quark_destroy(quark_ctx* ctx) {
     qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
     qk_free(ctx, ctx->wat, ctx->wat_bytes);
     qk_free(ctx, ctx->wupd, ctx->wupd_bytes);
+    qk_free(ctx, ctx->wenc, ctx->wenc_bytes);
     qk_free(ctx, ctx->dev_err, sizeof(int));
     qk_free(ctx, ctx->bwd_ws, ctx->bwd_ws_bytes);
     delete ctx;
@@ -545,6 +546,20 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         s = qk_alloc(ctx, &ctx->wat, ctx->wat_bytes);
         if (s != QUARK_OK) return s;
         QK_CUDA(ctx, cudaMemcpy(ctx->wat, at.data(), ctx->wat_bytes, cudaMemcpyHostToDevice));
+        {
+            // encoder conv as a tcgen05 B operand: N = C output channels x K = 32 (the 27 taps x
+            // input channels in (dy, dx, c_in) order, then zeros), element (n, k) at
+            // (k / 8) * C * 8 + n * 8 + k % 8
+            std::vector<uint16_t> be((size_t)32 * C, 0);
+            for (int n = 0; n < C; ++n)
+                for (int k = 0; k < 27; ++k) be[(size_t)(k / 8) * C * 8 + n * 8 + k % 8] = to_bf16_bits(w->enc_w[(size_t)k * C + n]);
+            qk_free(ctx, ctx->wenc, ctx->wenc_bytes);
+            ctx->wenc = nullptr;
+            ctx->wenc_bytes = be.size() * sizeof(uint16_t);
+            s = qk_alloc(ctx, &ctx->wenc, ctx->wenc_bytes);
+            if (s != QUARK_OK) return s;
+            QK_CUDA(ctx, cudaMemcpy(ctx->wenc, be.data(), ctx->wenc_bytes, cudaMemcpyHostToDevice));
+        }
         if (c.render_refine) {
             // Update Block convs, per step at j * wtc_step_bytes (steps that render)
             std::vector<uint16_t> up(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
@@ -780,7 +795,16 @@ extern "C" quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images
         a.w = ctx->wdev + ctx->off_enc;
         a.rgba = (float4*)p->rgba;
         for (int i = 0; i < 4; ++i) a.level[i] = p->level[i];
-        s = qk_launch(ctx, st, KF_ENCODE, [&] { return launch_encode(a, c.C, c.precision == QUARK_BF16, st); });
+        if (c.precision == QUARK_BF16) {
+            // BF16 form: the encoder conv on tcgen05 (BF16 operands, FP32 accumulation)
+            bool aligned = true;
+            for (int i = 0; i < 4; ++i) aligned = aligned && reinterpret_cast<uintptr_t>(a.level[i]) % 32 == 0;
+            s = aligned ? qk_launch(ctx, st, KF_ENCODE,
+                                    [&] { return launch_encode_tc(a, c.C, ctx->wenc, ctx->dev_err, st); })
+                        : qk_fail(ctx, QUARK_EINTERNAL, "pyramid level not 32-byte aligned");
+        } else {
+            s = qk_launch(ctx, st, KF_ENCODE, [&] { return launch_encode(a, c.C, false, st); });
+        }
     }
     if (s != QUARK_OK) {
         if (fresh) pyramid_free(p);

@@ -44,6 +44,9 @@ struct quark_ctx {
     void* wat = nullptr;
     size_t wat_bytes = 0;
     size_t off_wat[QUARK_MAX_SCALES] = {};
+    // BF16 form: the encoder conv packed as a tcgen05 B operand (C x 32)
+    void* wenc = nullptr;
+    size_t wenc_bytes = 0;
     // device error word written by kernels whose bounded waits run out
     int* dev_err = nullptr;
     // quark_test_wait_timeout: the next tensor-core sampling launch leaves its query MMA unissued

@@ -185,6 +185,7 @@ struct CollapseLayout {
 
 // Launchers (k_*.cu).  Each returns the launch's cudaError_t.
 cudaError_t launch_encode(const EncodeArgs& a, int C, bool bf16, cudaStream_t st);
+cudaError_t launch_encode_tc(const EncodeArgs& a, int C, const void* wtc, int* err, cudaStream_t st);
 cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st);
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
