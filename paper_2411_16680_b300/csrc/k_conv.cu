@@ -7,7 +7,7 @@
 // FP32 SIMT form.  One CTA per 16x8 output tile of one layer plane: the normalised input tile
 // with a 2-pixel halo and the gelu(Conv1) tile with a 1-pixel halo stay in shared memory, so
 // V is read once and written once; the 3x3 weights of each conv are staged in shared memory in
-// turn.  Each thread produces all C output channels of one pixel.
+// turn.  Each work item is a register tile of 2 x 2 pixels x 8 output channels.
 #include "device_common.cuh"
 
 namespace quark {
@@ -17,13 +17,15 @@ constexpr int CV_IW = CV_TW + 4, CV_IH = CV_TH + 4;  // input tile incl. halo 2
 constexpr int CV_MW = CV_TW + 2, CV_MH = CV_TH + 2;  // mid tile incl. halo 1
 constexpr int CV_THREADS = CV_TW * CV_TH;
 
+constexpr int CV_TAPS = 3;  // taps of weights staged in shared memory at a time
+
 template <int C>
 struct ConvSmem {
     static constexpr int P = C + 1;  // padded pixel stride (bank spread)
     static constexpr int in_off = 0;
     static constexpr int mid_off = in_off + CV_IH * CV_IW * P;
     static constexpr int w_off = ((mid_off + CV_MH * CV_MW * P) + 3) & ~3;
-    static constexpr int misc_off = w_off + 9 * C * C;
+    static constexpr int misc_off = w_off + CV_TAPS * C * C;
     static constexpr int total = misc_off + 8 * C + 8;
 };
 
@@ -67,12 +69,13 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     }
     if (tid == 3) misc[8 * C + 3] = a.w[lay.bd()];
     if (tid == 4) misc[8 * C + 4] = a.w[lay.bs()];
-    {
-        const float4* src = reinterpret_cast<const float4*>(a.w + lay.w1());
-        float4* dst = reinterpret_cast<float4*>(sw);
-        for (int i = tid; i < 9 * C * C / 4; i += CV_THREADS) dst[i] = src[i];
-    }
     __syncthreads();
+    // taps [t0, t0 + CV_TAPS) of a conv's weights into shared memory (the caller synchronises)
+    auto stage = [&](int woff, int t0) {
+        const float4* src = reinterpret_cast<const float4*>(a.w + woff + (size_t)t0 * C * C);
+        float4* dst = reinterpret_cast<float4*>(sw);
+        for (int i = tid; i < CV_TAPS * C * C / 4; i += CV_THREADS) dst[i] = src[i];
+    };
 
     // ---- normalised input tile (zero outside the plane) ----
     for (int p = tid; p < CV_IH * CV_IW; p += CV_THREADS) {
@@ -102,73 +105,142 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     __syncthreads();
 
     // ---- gelu(Conv1) on the mid tile (zero outside the plane: Conv2's padding) ----
-    for (int p = tid; p < CV_MH * CV_MW; p += CV_THREADS) {
-        const int my = p / CV_MW, mx = p % CV_MW;
-        const int gy = Y0 - 1 + my, gx = X0 - 1 + mx;
-        float* dst = smid + p * P;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            float2 acc[C / 2];
-#pragma unroll
-            for (int j = 0; j < C / 2; ++j) acc[j] = make_float2(misc[C + 2 * j], misc[C + 2 * j + 1]);
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const float* src = sin + ((my + tap / 3) * CV_IW + mx + tap % 3) * P;
-                const float* wt = sw + tap * C * C;
+    // Register tiles: a work item is a 2 x 2 block of pixels x 8 output channels (32 FP32
+    // accumulators); per tap and input channel it reads four inputs and two float4 weight quads
+    // from shared memory for 16 packed FMAs.  Items: block-major with the channel group fastest, so
+    // a warp's lanes read 8 blocks' inputs (each broadcast to 4 lanes) and one 128-byte weight row.
+    // The weights come in chunks of CV_TAPS taps, so each thread keeps its items' accumulators
+    // (at most two items: 9 x 5 blocks x G groups <= 2 x 128) across the chunks.
+    constexpr int G = C / 8;  // output-channel groups
+    auto accumulate = [&](float2 (&acc)[4][4], const float* s00, int rowp, const float* wt) {
 #pragma unroll 4
-                for (int ci = 0; ci < C; ++ci) fma_row_x2<C>(wt + ci * C, src[ci], acc);
-            }
+        for (int ci = 0; ci < C; ++ci) {
+            const float x[4] = {s00[ci], s00[P + ci], s00[rowp + ci], s00[rowp + P + ci]};
+            const float4 w0 = *reinterpret_cast<const float4*>(wt + ci * C);
+            const float4 w1 = *reinterpret_cast<const float4*>(wt + ci * C + 4);
+            const float2 wp[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                                  make_float2(w1.z, w1.w)};
 #pragma unroll
-            for (int j = 0; j < C / 2; ++j) {
-                dst[2 * j] = gelu_erf(acc[j].x);
-                dst[2 * j + 1] = gelu_erf(acc[j].y);
-            }
-        } else {
+            for (int q = 0; q < 4; ++q) {
+                const float2 x2 = make_float2(x[q], x[q]);
 #pragma unroll
-            for (int c = 0; c < C; ++c) dst[c] = 0.f;
+                for (int j = 0; j < 4; ++j) acc[q][j] = __ffma2_rn(x2, wp[j], acc[q][j]);
+            }
         }
-    }
-    __syncthreads();
+    };
     {
-        const float4* src = reinterpret_cast<const float4*>(a.w + lay.w2());
-        float4* dst = reinterpret_cast<float4*>(sw);
-        for (int i = tid; i < 9 * C * C / 4; i += CV_THREADS) dst[i] = src[i];
+        constexpr int MBX = CV_MW / 2, MBY = CV_MH / 2;  // 9 x 5 blocks of the mid tile
+        constexpr int NIT = MBX * MBY * G;
+        static_assert(NIT <= 2 * CV_THREADS, "at most two conv1 items per thread");
+        float2 acc[2][4][4];
+        int bx[2], by[2], gi[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int it = min(tid + k * CV_THREADS, NIT - 1);
+            gi[k] = it % G;
+            bx[k] = (it / G) % MBX;
+            by[k] = (it / G) / MBX;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[k][q][j] = make_float2(misc[C + gi[k] * 8 + 2 * j], misc[C + gi[k] * 8 + 2 * j + 1]);
+        }
+        const bool second = tid + CV_THREADS < NIT;
+        for (int t0 = 0; t0 < 9; t0 += CV_TAPS) {
+            stage(lay.w1(), t0);
+            __syncthreads();
+#pragma unroll
+            for (int tt = 0; tt < CV_TAPS; ++tt) {
+                const int dy = (t0 + tt) / 3, dx = (t0 + tt) % 3;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 1 && !second) break;
+                    accumulate(acc[k], sin + ((2 * by[k] + dy) * CV_IW + 2 * bx[k] + dx) * P, CV_IW * P,
+                               sw + tt * C * C + gi[k] * 8);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 1 && !second) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int my = 2 * by[k] + (q >> 1), mx = 2 * bx[k] + (q & 1);
+                const int gy = Y0 - 1 + my, gx = X0 - 1 + mx;
+                const bool inside = gy >= 0 && gy < H && gx >= 0 && gx < W;
+                float* dst = smid + (my * CV_MW + mx) * P + gi[k] * 8;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    dst[2 * j] = inside ? gelu_erf(acc[k][q][j].x) : 0.f;
+                    dst[2 * j + 1] = inside ? gelu_erf(acc[k][q][j].y) : 0.f;
+                }
+            }
+        }
     }
     __syncthreads();
 
-    // ---- Conv2, residual, decode ----
-    const int oy = tid / CV_TW, ox = tid % CV_TW;
-    const int gy = Y0 + oy, gx = X0 + ox;
-    if (gy >= H || gx >= W) return;
-    float2 acc[C / 2];
+    // ---- Conv2, residual, decode: 8 x 4 blocks of 2 x 2 output pixels x G channel groups ----
+    constexpr int OBX = CV_TW / 2, OBY = CV_TH / 2;
+    static_assert(OBX * OBY * G <= CV_THREADS, "one conv2 item per thread");
+    {
+        const bool active = tid < OBX * OBY * G;
+        const int it = active ? tid : 0;
+        const int g = it % G, b = it / G;
+        const int bx = b % OBX, by = b / OBX;
+        float2 acc[4][4];
 #pragma unroll
-    for (int j = 0; j < C / 2; ++j) acc[j] = make_float2(misc[2 * C + 2 * j], misc[2 * C + 2 * j + 1]);
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const float* src = smid + ((oy + tap / 3) * CV_MW + ox + tap % 3) * P;
-        const float* wt = sw + tap * C * C;
-#pragma unroll 4
-        for (int ci = 0; ci < C; ++ci) fma_row_x2<C>(wt + ci * C, src[ci], acc);
-    }
-    const size_t pix = (size_t)gy * W + gx;
-    const T* res = vin + pix * C;
-    T* out = reinterpret_cast<T*>(a.out) + ((size_t)li * plane + pix) * C;
-    float t = misc[8 * C + 3], s = misc[8 * C + 4];
+            for (int j = 0; j < 4; ++j)
+                acc[q][j] = make_float2(misc[2 * C + g * 8 + 2 * j], misc[2 * C + g * 8 + 2 * j + 1]);
+        for (int t0 = 0; t0 < 9; t0 += CV_TAPS) {
+            stage(lay.w2(), t0);
+            __syncthreads();
+            if (active) {
 #pragma unroll
-    for (int c0 = 0; c0 < C; c0 += 16) {
-        float r[16], o[16];
-        load16(res + c0, r);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int c = c0 + i;
-            o[i] = r[i] + (i & 1 ? acc[c / 2].y : acc[c / 2].x);
-            t = fmaf(o[i], misc[3 * C + c], t);
-            s = fmaf(o[i], misc[4 * C + c], s);
+                for (int tt = 0; tt < CV_TAPS; ++tt) {
+                    const int dy = (t0 + tt) / 3, dx = (t0 + tt) % 3;
+                    accumulate(acc, smid + ((2 * by + dy) * CV_MW + 2 * bx + dx) * P, CV_MW * P,
+                               sw + tt * C * C + g * 8);
+                }
+            }
+            __syncthreads();
         }
-        store16(out + c0, o);
-    }
-    if (a.t_raw) {
-        a.t_raw[pix * L + li] = t;
-        a.s_raw[pix * L + li] = s;
+        if (!active) return;  // whole warps (64 or 128 items): the shuffles below see full warps
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gy = Y0 + 2 * by + (q >> 1), gx = X0 + 2 * bx + (q & 1);
+            const bool inside = gy < H && gx < W;
+            const size_t pix = (size_t)(inside ? gy : 0) * W + (inside ? gx : 0);
+            float t = 0.f, sd = 0.f;
+            if (inside) {
+                const float* res = reinterpret_cast<const float*>(vin) + pix * C + g * 8;
+                float* out = reinterpret_cast<float*>(a.out) + ((size_t)li * plane + pix) * C + g * 8;
+                const float4 r0 = __ldg(reinterpret_cast<const float4*>(res));
+                const float4 r1 = __ldg(reinterpret_cast<const float4*>(res) + 1);
+                const float o[8] = {r0.x + acc[q][0].x, r0.y + acc[q][0].y, r0.z + acc[q][1].x, r0.w + acc[q][1].y,
+                                    r1.x + acc[q][2].x, r1.y + acc[q][2].y, r1.z + acc[q][3].x, r1.w + acc[q][3].y};
+                reinterpret_cast<float4*>(out)[0] = make_float4(o[0], o[1], o[2], o[3]);
+                reinterpret_cast<float4*>(out)[1] = make_float4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    t = fmaf(o[i], misc[3 * C + g * 8 + i], t);
+                    sd = fmaf(o[i], misc[4 * C + g * 8 + i], sd);
+                }
+            }
+            // the logits sum over the G channel groups, held by consecutive lanes
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) {
+                t += __shfl_xor_sync(0xffffffffu, t, off);
+                sd += __shfl_xor_sync(0xffffffffu, sd, off);
+            }
+            if (inside && g == 0 && a.t_raw) {
+                a.t_raw[pix * L + li] = t + misc[8 * C + 3];
+                a.s_raw[pix * L + li] = sd + misc[8 * C + 4];
+            }
+        }
     }
 }
 
