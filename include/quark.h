@@ -60,7 +60,9 @@ typedef struct {
 } quark_camera;
 
 /* Network shape (Sec. 3.2; tables "Model description for Quark / Quark+").
- *   C          channels of features, pyramid and feature volume: 16 or 32
+ *   C          channels of features, pyramid and feature volume: 16, 32 or 64 (the paper's models
+ *              use 32; the BF16 form takes C = 64 with 1 or 2 heads per step; the backward pass
+ *              and the differentiable stage take 16 or 32)
  *   heads      attention heads h: 1, 2 or 4 (one-to-many: per-head width C, appendix A;
  *              standard: per-head width C/h)
  *   n_scales   number of fusion steps j, 1..32 (one per fusion block of the model tables)
@@ -205,7 +207,8 @@ typedef struct quark_ldm quark_ldm;
 quark_status quark_create(const quark_config* cfg, int device, quark_ctx** out);
 
 /* Free a context and every device buffer it owns.  Handles made from it must be released
- * first.  NULL is accepted. */
+ * first: while any pyramid or LDM of the context is alive the call returns QUARK_EBUSY and frees
+ * nothing.  NULL is accepted. */
 quark_status quark_destroy(quark_ctx* ctx);
 
 /* Copy (and pack for the kernels) the network weights.  Synchronous. */

@@ -198,7 +198,8 @@ static bool same_f(double a, double b) { return std::fabs(a - b) <= 1e-6 * b; }
 
 quark_status qk_validate_config(const quark_config* c) {
     if (!c) return qk_fail(nullptr, QUARK_EINVAL, "NULL config");
-    if (c->C != 16 && c->C != 32) return qk_fail(nullptr, QUARK_EINVAL, "C must be 16 or 32 (got %d)", c->C);
+    if (c->C != 16 && c->C != 32 && c->C != 64)
+        return qk_fail(nullptr, QUARK_EINVAL, "C must be 16, 32 or 64 (got %d)", c->C);
     if (c->heads != 1 && c->heads != 2 && c->heads != 4)
         return qk_fail(nullptr, QUARK_EINVAL, "heads must be 1, 2 or 4 (got %d)", c->heads);
     if (c->n_scales < 1 || c->n_scales > QUARK_MAX_SCALES)
@@ -238,6 +239,10 @@ quark_status qk_validate_config(const quark_config* c) {
         if (h > 0) sampled = j;
         if (c->attn_mode == QUARK_ATTN_STANDARD && h > 0 && c->C % h)
             return qk_fail(nullptr, QUARK_EINVAL, "standard attention needs C divisible by heads (step %d)", j);
+        if (c->precision == QUARK_BF16 && c->attn_mode == QUARK_ATTN_ONE_TO_MANY && c->C == 64 && h == 4)
+            return qk_fail(nullptr, QUARK_EINVAL,
+                           "the BF16 form runs one-to-many attention with C = 64 for 1 or 2 heads (step %d has 4: "
+                           "its 5C = 320 query columns exceed one tensor-core MMA's 256)", j);
     }
     if (qk_heads(*c, c->n_scales - 1) == 0)
         return qk_fail(nullptr, QUARK_EINVAL, "the last step must attend (its attention gives the blend logits)");
@@ -281,6 +286,10 @@ extern "C" quark_status quark_create(const quark_config* cfg, int device, quark_
 
 extern "C" quark_status quark_destroy(quark_ctx* ctx) {
     if (!ctx) return QUARK_OK;
+    // a pyramid or LDM keeps a pointer to its context: destroying the context under it would
+    // leave its release with freed state
+    if (const int n = ctx->live_handles.load())
+        return qk_fail(ctx, QUARK_EBUSY, "%d pyramid / LDM handle(s) of this context are still alive: release them first", n);
     cudaSetDevice(ctx->device);
     for (auto& p : ctx->pending) {
         cudaEventSynchronize(p.e1);
@@ -707,6 +716,7 @@ static void pyramid_free(quark_pyramid* p) {
     for (int i = 0; i < 4; ++i) qk_free(ctx, p->level[i], p->level_bytes[i]);
     qk_free(ctx, p->rgba, p->rgba_bytes);
     qk_free(ctx, p->staging, p->staging_bytes);
+    ctx->live_handles.fetch_sub(1);
     delete p;
 }
 
@@ -758,6 +768,7 @@ extern "C" quark_status quark_encode_pyramid(quark_ctx* ctx, const float* images
     if (fresh) {
         p = new quark_pyramid();
         p->ctx = ctx;
+        ctx->live_handles.fetch_add(1);
         p->V = V;
         p->H = H;
         p->W = W;
@@ -824,6 +835,7 @@ static void ldm_free(quark_ldm* l) {
         if (l->async) cudaFreeAsync(b.p, l->stream);
         else qk_free(ctx, b.p, b.bytes);
     }
+    ctx->live_handles.fetch_sub(1);
     delete l;
 }
 
@@ -912,6 +924,7 @@ quark_status qk_ldm_create(quark_ctx* ctx, const quark_camera* target, int V_bet
     cudaSetDevice(ctx->device);
     quark_ldm* l = new quark_ldm();
     l->ctx = ctx;
+    ctx->live_handles.fetch_add(1);
     l->target = *target;
     l->async = async_stream != nullptr;
     l->stream = async_stream;

@@ -26,6 +26,7 @@ static quark_status check_stage(quark_ctx* ctx, const quark_pyramid* pyr, const 
     if (ctx->cfg.ray_encoding) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage runs without the ray encoding");
     if (!qk_uniform(ctx->cfg)) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage takes the uniform schedule only");
     if (ctx->cfg.render_refine) return qk_fail(ctx, QUARK_EINVAL, "the differentiable stage runs without render-and-refine");
+    if (ctx->cfg.C > 32) return qk_fail(ctx, QUARK_EINVAL, "the backward pass covers C = 16, 32");
     if (pyr->ctx != ctx || ldm->ctx != ctx) return qk_fail(ctx, QUARK_EINVAL, "handle from another context");
     if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
     return QUARK_OK;

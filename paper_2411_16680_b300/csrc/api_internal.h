@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <functional>
 #include <mutex>
 #include <string>
@@ -61,6 +62,8 @@ struct quark_ctx {
     std::vector<cudaEvent_t> event_pool;
     double fam_ms[KF_COUNT] = {};
     uint64_t fam_n[KF_COUNT] = {};
+    // pyramids and LDMs of this context not yet released (quark_destroy refuses while any remain)
+    std::atomic<int> live_handles{0};
     // differentiable stage: backward workspace (grown on demand)
     void* bwd_ws = nullptr;
     size_t bwd_ws_bytes = 0;

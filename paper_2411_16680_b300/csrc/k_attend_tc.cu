@@ -514,7 +514,11 @@ template <int C>
 static cudaError_t launch_tc_c(const AttendArgs& a, int heads, Transition tr, bool last, cudaStream_t st) {
     if (heads == 1) return launch_tc_nh<C, 1>(a, tr, last, st);
     if (heads == 2) return launch_tc_nh<C, 2>(a, tr, last, st);
-    if (heads == 4) return launch_tc_nh<C, 4>(a, tr, last, st);
+    // four heads: (4 + 1) C query columns; at C = 64 that is 320, above the 256 columns of one
+    // M = 128 MMA (and its shared memory above 227 KB), so that configuration is not built
+    if constexpr (C <= 32) {
+        if (heads == 4) return launch_tc_nh<C, 4>(a, tr, last, st);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -526,6 +530,7 @@ cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition t
         return cudaErrorMisalignedAddress;
     if (C == 16) return launch_tc_c<16>(a, heads, tr, last, st);
     if (C == 32) return launch_tc_c<32>(a, heads, tr, last, st);
+    if (C == 64) return launch_tc_c<64>(a, heads, tr, last, st);
     return cudaErrorInvalidValue;
 }
 

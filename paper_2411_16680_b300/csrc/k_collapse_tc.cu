@@ -217,8 +217,9 @@ cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st) {
     const size_t plane = (size_t)a.H * a.W;
     const long ntiles = (long)((plane + CL_M - 1) / CL_M) * a.L;
     if (ntiles == 0) return cudaSuccess;
-    // persistent CTAs: six per SM (shared memory and TMEM columns allow it)
-    const unsigned grid = (unsigned)std::min<long>(ntiles, 6L * sms);
+    // persistent CTAs: six per SM (shared memory and TMEM columns allow it at C <= 32; at C = 64,
+    // 72 KB of shared memory and 128 TMEM columns each: three)
+    const unsigned grid = (unsigned)std::min<long>(ntiles, (C == 64 ? 3L : 6L) * sms);
 #define QK_CL_LAUNCH(CV)                                                                               \
     do {                                                                                               \
         auto k = collapse_tc_kernel<CV>;                                                               \
@@ -228,6 +229,7 @@ cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st) {
     } while (0)
     if (C == 16) QK_CL_LAUNCH(16);
     else if (C == 32) QK_CL_LAUNCH(32);
+    else if (C == 64) QK_CL_LAUNCH(64);
     else return cudaErrorInvalidValue;
 #undef QK_CL_LAUNCH
     return cudaGetLastError();

@@ -42,8 +42,13 @@ __device__ __forceinline__ void fma_row_x2(const float* w, float x, float2 (&acc
     }
 }
 
+// threads of a CTA: 128 (256 at C = 64, where the tile has twice the channel groups to cover)
+template <int C>
+constexpr int cv_threads() { return C == 64 ? 2 * CV_THREADS : CV_THREADS; }
+
 template <typename T, int C>
-__global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(cv_threads<C>()) conv_block_kernel(const ConvArgs a) {
+    constexpr int NT = cv_threads<C>();
     using S = ConvSmem<C>;
     constexpr int P = S::P;
     const ConvLayout lay{C};
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     const size_t plane = (size_t)H * W;
     const T* vin = reinterpret_cast<const T*>(a.in) + (size_t)li * plane * C;
 
-    for (int i = tid; i < C; i += CV_THREADS) {
+    for (int i = tid; i < C; i += NT) {
         misc[i] = a.w[lay.g() + i];
         misc[C + i] = a.w[lay.b1() + i];
         misc[2 * C + i] = a.w[lay.b2() + i];
@@ -74,11 +79,11 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     auto stage = [&](int woff, int t0) {
         const float4* src = reinterpret_cast<const float4*>(a.w + woff + (size_t)t0 * C * C);
         float4* dst = reinterpret_cast<float4*>(sw);
-        for (int i = tid; i < CV_TAPS * C * C / 4; i += CV_THREADS) dst[i] = src[i];
+        for (int i = tid; i < CV_TAPS * C * C / 4; i += NT) dst[i] = src[i];
     };
 
     // ---- normalised input tile (zero outside the plane) ----
-    for (int p = tid; p < CV_IH * CV_IW; p += CV_THREADS) {
+    for (int p = tid; p < CV_IH * CV_IW; p += NT) {
         const int gy = Y0 - 2 + p / CV_IW, gx = X0 - 2 + p % CV_IW;
         float* dst = sin + p * P;
         if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
@@ -131,12 +136,12 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
     {
         constexpr int MBX = CV_MW / 2, MBY = CV_MH / 2;  // 9 x 5 blocks of the mid tile
         constexpr int NIT = MBX * MBY * G;
-        static_assert(NIT <= 2 * CV_THREADS, "at most two conv1 items per thread");
+        static_assert(NIT <= 2 * NT, "at most two conv1 items per thread");
         float2 acc[2][4][4];
         int bx[2], by[2], gi[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int it = min(tid + k * CV_THREADS, NIT - 1);
+            const int it = min(tid + k * NT, NIT - 1);
             gi[k] = it % G;
             bx[k] = (it / G) % MBX;
             by[k] = (it / G) / MBX;
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
                 for (int j = 0; j < 4; ++j)
                     acc[k][q][j] = make_float2(misc[C + gi[k] * 8 + 2 * j], misc[C + gi[k] * 8 + 2 * j + 1]);
         }
-        const bool second = tid + CV_THREADS < NIT;
+        const bool second = tid + NT < NIT;
         for (int t0 = 0; t0 < 9; t0 += CV_TAPS) {
             stage(lay.w1(), t0);
             __syncthreads();
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(CV_THREADS) conv_block_kernel(const ConvArgs a
 
     // ---- Conv2, residual, decode: 8 x 4 blocks of 2 x 2 output pixels x G channel groups ----
     constexpr int OBX = CV_TW / 2, OBY = CV_TH / 2;
-    static_assert(OBX * OBY * G <= CV_THREADS, "one conv2 item per thread");
+    static_assert(OBX * OBY * G <= NT, "one conv2 item per thread");
     {
         const bool active = tid < OBX * OBY * G;
         const int it = active ? tid : 0;
@@ -251,7 +256,7 @@ static cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + CV_TW - 1) / CV_TW, (a.H + CV_TH - 1) / CV_TH, a.L);
-    k<<<grid, CV_THREADS, smem, st>>>(a);
+    k<<<grid, cv_threads<C>(), smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -261,6 +266,7 @@ cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t 
     if (bf16) return launch_conv_block_tc(a, C, st);
     if (C == 16) return launch_t<float, 16>(a, st);
     if (C == 32) return launch_t<float, 32>(a, st);
+    if (C == 64) return launch_t<float, 64>(a, st);
     return cudaErrorInvalidValue;
 }
 

@@ -49,7 +49,9 @@ struct ConvTile {
 template <int C>
 struct TcSmem {
     static constexpr int G = C / 8;
-    static constexpr int NPIX = C == 32 ? 1152 : 2304;  // pixels of an input / mid tile buffer
+    // pixels of an input / mid tile buffer (two buffers and both convs' weights in 227 KB; at
+    // C = 64 the weights alone take 144 KB)
+    static constexpr int NPIX = C == 64 ? 312 : C == 32 ? 1152 : 2304;
     static constexpr int NB_MAX = 256 / C;              // MMA blocks per conv in half the TMEM
     // a tile's mid tile reuses its input buffer: conv1 has finished reading it when the epilogue
     // writes gelu(conv1)
@@ -79,7 +81,10 @@ __device__ __forceinline__ void store_pixel_bf16(uint8_t* base, int npix, int p,
 
 template <int C>
 __device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[C]) {
-    if constexpr (C == 32) {
+    if constexpr (C == 64) {
+        umma::ld_32x32b_x32(taddr, *reinterpret_cast<float(*)[32]>(v));
+        umma::ld_32x32b_x32(taddr + 32, *reinterpret_cast<float(*)[32]>(v + 32));
+    } else if constexpr (C == 32) {
         umma::ld_32x32b_x32(taddr, v);
     } else {
         umma::ld_32x32b_x16(taddr, v);
@@ -446,6 +451,7 @@ cudaError_t conv_tc_tile_shape(int C, int W, int H, int L, int* cols, int* rows)
     ConvTile t{};
     if (C == 16) t = choose_tile<16>(W, H, L, sms);
     else if (C == 32) t = choose_tile<32>(W, H, L, sms);
+    else if (C == 64) t = choose_tile<64>(W, H, L, sms);
     if (!t.P) return cudaErrorInvalidValue;
     *cols = t.P - 4;
     *rows = t.R;
@@ -458,6 +464,7 @@ cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st) {
     if (reinterpret_cast<uintptr_t>(a.in) % 32 || reinterpret_cast<uintptr_t>(a.out) % 32) return cudaErrorMisalignedAddress;
     if (C == 16) return launch_tc<16>(a, st);
     if (C == 32) return launch_tc<32>(a, st);
+    if (C == 64) return launch_tc<64>(a, st);
     return cudaErrorInvalidValue;
 }
 

@@ -52,6 +52,9 @@ cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st
     } else if (C == 32) {
         if (bf16) decode_kernel<__nv_bfloat16, 32><<<grid, 256, 0, st>>>(a);
         else decode_kernel<float, 32><<<grid, 256, 0, st>>>(a);
+    } else if (C == 64) {
+        if (bf16) decode_kernel<__nv_bfloat16, 64><<<grid, 256, 0, st>>>(a);
+        else decode_kernel<float, 64><<<grid, 256, 0, st>>>(a);
     } else {
         return cudaErrorInvalidValue;
     }

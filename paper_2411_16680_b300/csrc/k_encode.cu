@@ -72,7 +72,7 @@ __device__ __forceinline__ void fetch_patch(const EncodeArgs& a, int tile, int t
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(64 * (C / 16), 4) encode_kernel(EncodeArgs a, int tiles_x, int tiles_y) {
+__global__ void __launch_bounds__(64 * (C / 16), C == 64 ? 2 : 4) encode_kernel(EncodeArgs a, int tiles_x, int tiles_y) {
     constexpr int NT = 64 * (C / 16);
     __shared__ float patch_buf[2][ENC_P][ENC_P][3];
     __shared__ __align__(16) float w[28 * C];  // [tap = (dy * 3 + dx) * 3 + ci][C], then bias [C]
@@ -207,6 +207,7 @@ cudaError_t launch_encode(const EncodeArgs& a, int C, bool bf16, cudaStream_t st
         if (reinterpret_cast<uintptr_t>(a.level[i]) % 32) return cudaErrorMisalignedAddress;
     if (C == 16) return bf16 ? launch_t<__nv_bfloat16, 16>(a, st) : launch_t<float, 16>(a, st);
     if (C == 32) return bf16 ? launch_t<__nv_bfloat16, 32>(a, st) : launch_t<float, 32>(a, st);
+    if (C == 64) return bf16 ? launch_t<__nv_bfloat16, 64>(a, st) : launch_t<float, 64>(a, st);
     return cudaErrorInvalidValue;
 }
 

@@ -35,7 +35,7 @@ struct EtSmem {
     static constexpr int bias_off = l4_off + 2 * 4 * C * 4;         // fp32 [C]
     static constexpr int bar_off = (bias_off + C * 4 + 7) / 8 * 8;
     static constexpr int total = bar_off + 16;
-    static constexpr uint32_t tmem_cols = 32;
+    static constexpr uint32_t tmem_cols = C <= 32 ? 32 : 64;
 };
 
 __device__ __forceinline__ void et_cp_async4(float* smem, const float* gmem, bool valid) {
@@ -67,7 +67,7 @@ __device__ __forceinline__ void et_store16(__nv_bfloat16* p, const float* v) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(ET_M, 8) encode_tc_kernel(const EncodeArgs a, const void* wtc, int* err, int tiles_x,
+__global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const EncodeArgs a, const void* wtc, int* err, int tiles_x,
                                                          int tiles_y) {
     using S = EtSmem<C>;
     extern __shared__ __align__(128) uint8_t sm[];
@@ -157,7 +157,13 @@ __global__ void __launch_bounds__(ET_M, 8) encode_tc_kernel(const EncodeArgs a, 
 
         // ---- level 1 and the 2x2 means (lanes ^ 1: x + 1, ^ 16: y + 1) ----
         float f[C];
-        if constexpr (C == 32) {
+        if constexpr (C == 64) {
+            float hi[32];
+            umma::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16), *reinterpret_cast<float(*)[32]>(f));
+            umma::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + 32, hi);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) f[32 + c] = hi[c];
+        } else if constexpr (C == 32) {
             umma::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16), f);
         } else {
             umma::ld_32x32b_x16(tmem + ((uint32_t)(warp * 32) << 16), f);
@@ -255,12 +261,12 @@ __global__ void __launch_bounds__(ET_M, 8) encode_tc_kernel(const EncodeArgs a, 
 }
 
 // CTAs of 128 threads resident per SM: registers (64 K per SM, allocated per warp in units of 256),
-// shared memory (228 KB per SM, 1 KB reserved per CTA) and TMEM (512 columns, 32 per CTA)
-static int et_ctas_per_sm(int regs, int smem) {
+// shared memory (228 KB per SM, 1 KB reserved per CTA) and TMEM (512 columns, 32 or 64 per CTA)
+static int et_ctas_per_sm(int regs, int smem, int tmem_cols) {
     const int warp_regs = (regs * 32 + 255) / 256 * 256;
     const int by_regs = 65536 / (warp_regs * (ET_M / 32));
     const int by_smem = (228 * 1024) / (smem + 1024);
-    return std::max(1, std::min(std::min(by_regs, by_smem), 512 / 32));
+    return std::max(1, std::min(std::min(by_regs, by_smem), 512 / tmem_cols));
 }
 
 cudaError_t launch_encode_tc(const EncodeArgs& a, int C, const void* wtc, int* err, cudaStream_t st) {
@@ -286,12 +292,13 @@ cudaError_t launch_encode_tc(const EncodeArgs& a, int C, const void* wtc, int* e
         cudaFuncAttributes fa{};                                                                       \
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);                                       \
         if (e != cudaSuccess) return e;                                                                \
-        const int per_sm = et_ctas_per_sm(fa.numRegs, EtSmem<CV>::total);                               \
+        const int per_sm = et_ctas_per_sm(fa.numRegs, EtSmem<CV>::total, (int)EtSmem<CV>::tmem_cols);                               \
         const int grid = (int)std::min<long>(ntiles, (long)per_sm * sms);                              \
         k<<<grid, ET_M, EtSmem<CV>::total, st>>>(a, wtc, err, tiles_x, tiles_y);                       \
     } while (0)
     if (C == 16) QK_ET_LAUNCH(16);
     else if (C == 32) QK_ET_LAUNCH(32);
+    else if (C == 64) QK_ET_LAUNCH(64);
     else return cudaErrorInvalidValue;
 #undef QK_ET_LAUNCH
     return cudaGetLastError();

@@ -316,6 +316,7 @@ cudaError_t launch_mlp_block(const ConvArgs& a, int C, bool bf16, cudaStream_t s
         const unsigned g = (unsigned)((E + MB_THREADS - 1) / MB_THREADS);
         if (C == 16) mlp_block_kernel<16><<<g, MB_THREADS, 0, st>>>(a);
         else if (C == 32) mlp_block_kernel<32><<<g, MB_THREADS, 0, st>>>(a);
+        else if (C == 64) mlp_block_kernel<64><<<g, MB_THREADS, 0, st>>>(a);
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
@@ -329,7 +330,8 @@ cudaError_t launch_mlp_block(const ConvArgs& a, int C, bool bf16, cudaStream_t s
         if (e != cudaSuccess) return e;
     }
     const long ntiles = (long)((E + MB_THREADS - 1) / MB_THREADS);
-    const unsigned grid = (unsigned)std::min<long>(ntiles, 8L * sms);  // persistent: eight CTAs per SM
+    // persistent: eight CTAs per SM, fewer where their TMEM columns (2 C each) would exceed the 512
+    const unsigned grid = (unsigned)std::min<long>(ntiles, (long)std::min(8, 256 / C) * sms);
 #define QK_MB_LAUNCH(CV)                                                                               \
     do {                                                                                               \
         auto k = mlp_block_tc_kernel<CV>;                                                              \
@@ -339,6 +341,7 @@ cudaError_t launch_mlp_block(const ConvArgs& a, int C, bool bf16, cudaStream_t s
     } while (0)
     if (C == 16) QK_MB_LAUNCH(16);
     else if (C == 32) QK_MB_LAUNCH(32);
+    else if (C == 64) QK_MB_LAUNCH(64);
     else return cudaErrorInvalidValue;
 #undef QK_MB_LAUNCH
     return cudaGetLastError();

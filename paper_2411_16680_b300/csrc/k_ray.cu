@@ -98,6 +98,7 @@ cudaError_t launch_ray_add(const RayArgs& a, const void* feat, void* out, bool b
     if ((size_t)a.V * a.h * a.w == 0) return cudaSuccess;
     if (a.C == 16) return bf16 ? launch_add_t<__nv_bfloat16, 16>(a, feat, out, st) : launch_add_t<float, 16>(a, feat, out, st);
     if (a.C == 32) return bf16 ? launch_add_t<__nv_bfloat16, 32>(a, feat, out, st) : launch_add_t<float, 32>(a, feat, out, st);
+    if (a.C == 64) return bf16 ? launch_add_t<__nv_bfloat16, 64>(a, feat, out, st) : launch_add_t<float, 64>(a, feat, out, st);
     return cudaErrorInvalidValue;
 }
 

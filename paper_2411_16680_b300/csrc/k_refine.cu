@@ -132,6 +132,7 @@ cudaError_t launch_refine_add(const RefineArgs& a, bool bf16, cudaStream_t st) {
     if ((size_t)a.V * a.h * a.w == 0) return cudaSuccess;
     if (a.C == 16) return bf16 ? launch_refine_t<__nv_bfloat16, 16>(a, st) : launch_refine_t<float, 16>(a, st);
     if (a.C == 32) return bf16 ? launch_refine_t<__nv_bfloat16, 32>(a, st) : launch_refine_t<float, 32>(a, st);
+    if (a.C == 64) return bf16 ? launch_refine_t<__nv_bfloat16, 64>(a, st) : launch_refine_t<float, 64>(a, st);
     return cudaErrorInvalidValue;
 }
 

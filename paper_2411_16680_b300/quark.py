@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as ct
 import os
+import weakref
 from typing import Dict, List, Optional, Sequence
 
 import numpy as np
@@ -267,6 +268,7 @@ def _stream(stream) -> Optional[int]:
 class Pyramid:
     def __init__(self, ctx: "Context", handle: ct.c_void_p, V: int):
         self.ctx, self.handle, self.V = ctx, handle, V
+        ctx._handles.add(self)
 
     def read_level(self, k: int, dst):
         """Copy level k into dst (a tensor or array of exactly the level's size)."""
@@ -274,9 +276,10 @@ class Pyramid:
         _check(lib().quark_pyramid_read(self.handle, k, _ptr(dst), n), self.ctx.handle)
 
     def release(self):
-        if self.handle:
+        # a pyramid outlives no context: Context.close() releases it first
+        if self.handle and getattr(self.ctx, "handle", None):
             lib().quark_release_pyramid(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -288,6 +291,7 @@ class Pyramid:
 class LDM:
     def __init__(self, ctx: "Context", handle: ct.c_void_p):
         self.ctx, self.handle = ctx, handle
+        ctx._handles.add(self)
 
     def keep_steps(self, keep: bool = True):
         """quark_ldm_keep_steps: keep every step's volumes for the backward pass."""
@@ -303,9 +307,9 @@ class LDM:
         return out if shape is None else out.reshape(shape)
 
     def release(self):
-        if self.handle:
+        if self.handle and getattr(self.ctx, "handle", None):
             lib().quark_release_ldm(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -319,13 +323,18 @@ class Context:
 
     def __init__(self, cfg, device: int = 0, hbm_cap_bytes: int = 0):
         self.cfg = cfg
+        self._handles = weakref.WeakSet()  # live Pyramid / LDM objects, released by close()
         self._ccfg = make_config(cfg, hbm_cap_bytes)
         h = ct.c_void_p()
         _check(lib().quark_create(ct.byref(self._ccfg), device, ct.byref(h)))
         self.handle = h
 
     def close(self):
+        """quark_destroy, after releasing every pyramid and LDM made from this context (the library
+        refuses to destroy a context whose handles are alive)."""
         if getattr(self, "handle", None):
+            for h in list(getattr(self, "_handles", ())):
+                h.release()
             lib().quark_destroy(self.handle)
             self.handle = None
 

@@ -289,3 +289,21 @@ def test_maximum_view_count(precision):
         assert e.value.status == quark.EINVAL
     finally:
         ctx.close()
+
+
+def test_destroy_refuses_while_handles_live():
+    """A context is not destroyed under its pyramids and LDMs (their release would touch freed
+    state): quark_destroy returns EBUSY until they are released; Context.close() releases them."""
+    cfg = synth.config_small()
+    ctx = quark.Context(cfg)
+    ctx.load_weights(synth.make_weights(cfg))
+    sc = synth.scene_small()
+    pyr = ctx.encode_pyramid(torch.tensor(sc.images, device="cuda"), sc.cams)
+    ldm = ctx.ldm_create(sc.target)
+    assert quark.lib().quark_destroy(ctx.handle) == quark.EBUSY
+    ldm.release()
+    assert quark.lib().quark_destroy(ctx.handle) == quark.EBUSY
+    pyr2 = ctx.encode_pyramid(torch.tensor(sc.images, device="cuda"), sc.cams)
+    ctx.close()  # releases pyr and pyr2, then destroys
+    assert ctx.handle is None and pyr.handle is None and pyr2.handle is None
+    pyr.release()  # a no-op once the context is gone
