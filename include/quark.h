@@ -342,8 +342,10 @@ quark_status quark_sample_coords(quark_ctx* ctx, const quark_camera* target, dou
 /* Output tile of the conv-block kernel of the context's precision form for an L x H x W volume
  * (inspection, so that tests can place windows on its tile seams; Sec. 3.3 conv block): tiles of
  * *tile_rows rows by *tile_cols columns start at multiples of those in y and x (the last ones
- * ragged).  FP32 form: the fixed 16 x 8 tile; BF16 form: the tile the tensor-core kernel chooses
- * for this plane size on the context's device. */
+ * ragged).  The tile the tensor-core kernel chooses for this plane size on the context's device
+ * (BF16 form, and the FP32 form's split-operand kernel); the fixed 16 x 8 tile where the FP32
+ * form runs the SIMT kernel (C = 64, or weights outside the split's range).  Call after
+ * quark_load_weights. */
 quark_status quark_conv_tiles(quark_ctx* ctx, int L, int H, int W, int* tile_cols, int* tile_rows);
 
 quark_status quark_release_pyramid(quark_pyramid* pyr);

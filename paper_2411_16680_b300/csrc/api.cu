@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "quark_internal.cuh"
 #include "api_internal.h"
 
@@ -330,6 +332,41 @@ static void pack_conv_weights_bf16(const float* w, int C, uint16_t* dst) {
                     to_bf16_bits(w[((size_t)tap * C + ci) * C + co]);
 }
 
+// FP32 form on the tensor cores: the same B layout as pack_conv_weights_bf16 in FP16, the rounded
+// weights (hi) and then the scaled remainders fp16((w - hi) 2^11) (lo), 9 C C elements each.
+static void pack_conv_weights_f16split(const float* w, int C, uint16_t* hi, uint16_t* lo) {
+    for (int tap = 0; tap < 9; ++tap)
+        for (int ci = 0; ci < C; ++ci)
+            for (int co = 0; co < C; ++co) {
+                const float x = w[((size_t)tap * C + ci) * C + co];
+                const __half h = __float2half_rn(x);
+                const size_t i = (size_t)tap * C * C + (ci / 8) * C * 8 + co * 8 + ci % 8;
+                hi[i] = __half_as_ushort(h);
+                lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(h)) * 2048.f));
+            }
+}
+
+// Whether every FP16 part the split conv block forms stays below 2^15, for any volume: the
+// normalised input is at most sqrt(C) max|g| per channel (RMSNorm), conv1's output at most
+// sum |w1| times that plus |b1| (and gelu(y) <= max(|y|, 0.17)), the weights themselves; the
+// remainders are 2^-11 of their values, scaled by 2^11.
+static bool conv_split_in_range(const float* g, const float* w1, const float* b1, const float* w2, int C) {
+    constexpr double kMax = 32768.0;
+    double gmax = 0.0;
+    for (int c = 0; c < C; ++c) gmax = std::max(gmax, (double)std::fabs(g[c]));
+    const double xmax = std::sqrt((double)C) * gmax;
+    if (!(xmax < kMax)) return false;
+    for (int co = 0; co < C; ++co) {
+        double s = std::fabs((double)b1[co]);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int ci = 0; ci < C; ++ci) s += std::fabs((double)w1[((size_t)tap * C + ci) * C + co]) * xmax;
+        if (!(s < kMax)) return false;
+    }
+    for (size_t i = 0; i < 9 * (size_t)C * C; ++i)
+        if (!(std::fabs(w1[i]) < kMax && std::fabs(w2[i]) < kMax)) return false;
+    return true;
+}
+
 static int level_index(int k) { return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3; }
 
 extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* w) {
@@ -497,7 +534,30 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
     quark_status s = qk_alloc(ctx, (void**)&ctx->wdev, ctx->wbytes);
     if (s != QUARK_OK) return s;
     QK_CUDA(ctx, cudaMemcpy(ctx->wdev, blob.data(), ctx->wbytes, cudaMemcpyHostToDevice));
-    if (c.precision == QUARK_BF16) {
+    if (c.precision != QUARK_BF16) {
+        // FP32 form: the conv blocks on the tensor cores through split FP16 operands (C <= 32, 3 x 3
+        // kernels, every step's weights in the split's range), else the SIMT kernel (wtc stays NULL)
+        qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
+        ctx->wtc = nullptr;
+        ctx->wtc_bytes = 0;
+        bool split = C <= 32 && c.conv_kernel != 1;
+        for (int j = 0; j < c.n_scales && split; ++j)
+            split = conv_split_in_range(w->conv_g[j], cw1[j], w->conv1_b[j], cw2[j], C);
+        if (split) {
+            ctx->wtc_step_bytes = 4 * 9 * (size_t)C * C * sizeof(uint16_t);
+            std::vector<uint16_t> tc(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
+            const size_t n = 9 * (size_t)C * C;
+            for (int j = 0; j < c.n_scales; ++j) {
+                uint16_t* d = tc.data() + (size_t)j * 4 * n;
+                pack_conv_weights_f16split(cw1[j], C, d, d + n);
+                pack_conv_weights_f16split(cw2[j], C, d + 2 * n, d + 3 * n);
+            }
+            ctx->wtc_bytes = tc.size() * sizeof(uint16_t);
+            s = qk_alloc(ctx, &ctx->wtc, ctx->wtc_bytes);
+            if (s != QUARK_OK) return s;
+            QK_CUDA(ctx, cudaMemcpy(ctx->wtc, tc.data(), ctx->wtc_bytes, cudaMemcpyHostToDevice));
+        }
+    } else {
         ctx->wtc_step_bytes = 2 * 9 * (size_t)C * C * sizeof(uint16_t);
         std::vector<uint16_t> tc(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
         for (int j = 0; j < c.n_scales; ++j) {

@@ -69,13 +69,14 @@ extern "C" quark_status quark_sample_coords(quark_ctx* ctx, const quark_camera* 
 extern "C" quark_status quark_conv_tiles(quark_ctx* ctx, int L, int H, int W, int* tile_cols, int* tile_rows) {
     if (!ctx || !tile_cols || !tile_rows) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
     if (L <= 0 || H <= 0 || W <= 0) return qk_fail(ctx, QUARK_EINVAL, "non-positive volume size");
-    if (ctx->cfg.precision != QUARK_BF16) {
-        *tile_cols = 16;  // the FP32 conv block's fixed 16 x 8 pixel tile
+    const bool split = ctx->cfg.precision != QUARK_BF16;
+    if (split && !ctx->wtc) {
+        *tile_cols = 16;  // the FP32 SIMT conv block's fixed 16 x 8 pixel tile
         *tile_rows = 8;
         return QUARK_OK;
     }
     cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess) e = conv_tc_tile_shape(ctx->cfg.C, W, H, L, tile_cols, tile_rows);
+    if (e == cudaSuccess) e = conv_tc_tile_shape(ctx->cfg.C, split, W, H, L, tile_cols, tile_rows);
     if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "conv tile geometry: %s", cudaGetErrorString(e));
     return QUARK_OK;
 }

@@ -260,10 +260,13 @@ static cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// FP32 form: this SIMT kernel.  BF16 form: the tcgen05 kernel (k_conv_tc.cu).  1x1 kernels: k_mlp.cu.
+// BF16 form: the tcgen05 kernel (k_conv_tc.cu).  FP32 form: the same kernel on split FP16 operands
+// when the context packed them (C <= 32, weights within the split's range), else this SIMT kernel.
+// 1x1 kernels: k_mlp.cu.
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st) {
     if (a.ks == 1) return launch_mlp_block(a, C, bf16, st);  // 1x1 convolutions: per element
-    if (bf16) return launch_conv_block_tc(a, C, st);
+    if (bf16) return launch_conv_block_tc(a, C, false, st);
+    if (a.wtc && C <= 32) return launch_conv_block_tc(a, C, true, st);
     if (C == 16) return launch_t<float, 16>(a, st);
     if (C == 32) return launch_t<float, 32>(a, st);
     if (C == 64) return launch_t<float, 64>(a, st);

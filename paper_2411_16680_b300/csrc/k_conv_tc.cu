@@ -27,6 +27,19 @@
 //                       the residual and the stores of conv2,
 // so the loads of one tile, the MMAs of the next and the epilogues of the previous overlap.  The
 // packed weights are staged once.  mbarriers order the roles; every wait is bounded.
+//
+// FP32 form (SPLIT): the same kernel with every operand x split into two FP16 parts, the rounded
+// value x_h = fp16(x) and the scaled remainder x_l = fp16((x - x_h) 2^11), and each product taken
+// as x_h w_h + 2^-11 (x_h w_l + x_l w_h) on kind::f16 MMAs (three per K step, into a high and a
+// low accumulator per block): each partial product of 11-bit significands is exact in the FP32
+// accumulator and the dropped x_l w_l term is 2^-22 of the product, so the convolutions keep FP32
+// accuracy at tensor-core rates.  The volume is FP32 in and out, the normalisation, gelu (erf form)
+// and residual run in FP32, and the two halves of an operand take twice the bytes of a BF16 one
+// (smaller tiles).  FP16's range bounds the parts: the launcher takes this path only when the
+// weights bound every normalised input and every conv1 output below 2^15 (a check on the host,
+// whatever the volume); otherwise the SIMT kernel (k_conv.cu) runs.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "device_common.cuh"
@@ -46,19 +59,21 @@ struct ConvTile {
     int P, R, nb1, nb2, tiles_x, tiles_y;
 };
 
-template <int C>
+template <int C, bool SPLIT>
 struct TcSmem {
     static constexpr int G = C / 8;
+    static constexpr int PLANES = SPLIT ? 2 : 1;  // operand parts: BF16, or FP16 high and scaled low
     // pixels of an input / mid tile buffer (two buffers and both convs' weights in 227 KB; at
     // C = 64 the weights alone take 144 KB)
-    static constexpr int NPIX = C == 64 ? 312 : C == 32 ? 1152 : 2304;
-    static constexpr int NB_MAX = 256 / C;              // MMA blocks per conv in half the TMEM
+    static constexpr int NPIX = SPLIT ? (C == 32 ? 600 : 1600) : (C == 64 ? 312 : C == 32 ? 1152 : 2304);
+    static constexpr int NB_MAX = 256 / (PLANES * C);   // MMA blocks per conv in half the TMEM
     // a tile's mid tile reuses its input buffer: conv1 has finished reading it when the epilogue
-    // writes gelu(conv1)
-    static constexpr int buf_bytes = G * NPIX * 16;     // input buffers b = 0, 1 at b * buf_bytes
+    // writes gelu(conv1).  Channel group g of part q at (q G + g) NPIX 16.
+    static constexpr int buf_bytes = PLANES * G * NPIX * 16;  // input buffers b = 0, 1 at b * buf_bytes
+    static constexpr int wconv_bytes = PLANES * 9 * C * C * 2;  // one conv's packed weights (parts in turn)
     static constexpr int w1_off = 2 * buf_bytes;
-    static constexpr int w2_off = w1_off + 9 * C * C * 2;
-    static constexpr int misc_off = w2_off + 9 * C * C * 2;
+    static constexpr int w2_off = w1_off + wconv_bytes;
+    static constexpr int misc_off = w2_off + wconv_bytes;
     static constexpr int misc_n = 8 * C + 8;
     // barriers: input full [2], input free [2], conv1 done, conv2 done, conv1 read, conv2 read, drain
     static constexpr int bar_off = (misc_off + misc_n * 4 + 7) / 8 * 8;
@@ -79,6 +94,28 @@ __device__ __forceinline__ void store_pixel_bf16(uint8_t* base, int npix, int p,
     }
 }
 
+// FP32 form: a pixel's channels as the FP16 high parts (groups 0 .. G - 1) and the scaled
+// remainders (groups G .. 2G - 1).  x - fp16(x) is exact in FP32, and x 2^11 is exact.
+template <int C>
+__device__ __forceinline__ void store_pixel_split(uint8_t* base, int npix, int p, const float (&v)[C]) {
+#pragma unroll
+    for (int g = 0; g < C / 8; ++g) {
+        uint4 uh, ul;
+        __half2* hh = reinterpret_cast<__half2*>(&uh);
+        __half2* hl = reinterpret_cast<__half2*>(&ul);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float x0 = v[8 * g + 2 * j], x1 = v[8 * g + 2 * j + 1];
+            const __half2 h = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h);
+            hh[j] = h;
+            hl[j] = __floats2half2_rn((x0 - hf.x) * 2048.f, (x1 - hf.y) * 2048.f);
+        }
+        *reinterpret_cast<uint4*>(base + ((size_t)g * npix + p) * 16) = uh;
+        *reinterpret_cast<uint4*>(base + ((size_t)(C / 8 + g) * npix + p) * 16) = ul;
+    }
+}
+
 template <int C>
 __device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[C]) {
     if constexpr (C == 64) {
@@ -91,9 +128,9 @@ __device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[C]) {
     }
 }
 
-template <int C>
+template <int C, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const ConvArgs a, const ConvTile tg) {
-    using S = TcSmem<C>;
+    using S = TcSmem<C, SPLIT>;
     const ConvLayout lay{C};
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_w1 = sm + S::w1_off;
@@ -116,8 +153,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     const size_t plane = (size_t)H * W;
     const int ntiles = tg.tiles_x * tg.tiles_y * L;
     constexpr int NLOAD = 32 * TC_LOAD_WARPS, NEPI = 32 * TC_EPI_WARPS;
+    constexpr int NACC = S::PLANES * C;  // TMEM columns of one block: the accumulator(s)
 
-    // ---- constants and packed BF16 weights ----
+    // ---- constants and packed weights (BF16, or the FP16 parts) ----
     for (int i = tid; i < C; i += TC_THREADS) {
         misc[i] = a.w[lay.g() + i];
         misc[C + i] = a.w[lay.b1() + i];
@@ -131,7 +169,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
         const uint4* src = reinterpret_cast<const uint4*>(a.wtc);
         uint4* d1 = reinterpret_cast<uint4*>(s_w1);
         uint4* d2 = reinterpret_cast<uint4*>(s_w2);
-        constexpr int n = 9 * C * C * 2 / 16;
+        constexpr int n = S::wconv_bytes / 16;
         for (int i = tid; i < n; i += TC_THREADS) {
             d1[i] = __ldg(src + i);
             d2[i] = __ldg(src + n + i);
@@ -155,10 +193,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(TC_M, C);
+    constexpr uint32_t idesc = SPLIT ? umma::idesc_f16_f32(TC_M, C) : umma::idesc_bf16_f32(TC_M, C);
     constexpr uint32_t LBO_W = C * 16;        // B: N = C rows of 16 B per core-matrix column
     constexpr uint32_t LBO_A = S::NPIX * 16;  // A: channel-group stride of an input / mid tile
     constexpr uint32_t TB = 256;              // TMEM column of conv2's accumulators
+    // SPLIT: the low parts, as descriptor start-address offsets (16-byte units)
+    constexpr uint32_t A_LO = (S::G * LBO_A) >> 4, W_LO = (9 * C * C * 2) >> 4;
 
     if (warp < TC_LOAD_WARPS) {
         // ---- loader: normalised input tile k into buffer k % 2 ----
@@ -173,23 +213,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
             uint8_t* s_in = sm + (size_t)b * S::buf_bytes;
             const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
             const int li = tile / (tg.tiles_x * tg.tiles_y);
-            const __nv_bfloat16* vin = reinterpret_cast<const __nv_bfloat16*>(a.in) + (size_t)li * plane * C;
             // rows y0-2 .. y0+R+1, columns x0-2 .. x0+OW+1 (pitch P); two pixels in flight per thread
             const int NIN = (R + 4) * P;
             for (int p0 = tid; p0 < NIN; p0 += 2 * NLOAD) {
-                uint4 raw[2][C / 8];
+                // a pixel's channels in 256-bit loads (whole sectors), from the clamped address
+                constexpr int NV = SPLIT ? C / 4 : C / 8;  // 16-byte words of a pixel
+                uint4 raw[2][NV];
                 bool in[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int p = p0 + u * NLOAD;
                     const int gy = y0 - 2 + p / P, gx = x0 - 2 + p % P;
                     in[u] = p < NIN && gy >= 0 && gy < H && gx >= 0 && gx < W;
-                    // a pixel's channels in 256-bit loads (whole sectors), from the clamped address
-                    const __nv_bfloat16* src = vin + ((size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0)) * C;
+                    const size_t pix = (size_t)li * plane + (size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0);
+                    const uint8_t* src = reinterpret_cast<const uint8_t*>(a.in) + pix * NV * 16;
 #pragma unroll
-                    for (int g = 0; g < C / 16; ++g) ldg256(src + 16 * g, raw[u][2 * g], raw[u][2 * g + 1]);
+                    for (int g = 0; g < NV / 2; ++g) ldg256(src + 32 * g, raw[u][2 * g], raw[u][2 * g + 1]);
 #pragma unroll
-                    for (int g = 0; g < C / 8; ++g)
+                    for (int g = 0; g < NV; ++g)
                         if (!in[u]) raw[u][g] = make_uint4(0, 0, 0, 0);
                 }
 #pragma unroll
@@ -197,14 +238,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                     const int p = p0 + u * NLOAD;
                     if (p >= NIN) break;
                     float v[C];
+                    if constexpr (SPLIT) {
 #pragma unroll
-                    for (int g = 0; g < C / 8; ++g) {
-                        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw[u][g]);
+                        for (int g = 0; g < NV; ++g) {
+                            v[4 * g] = __uint_as_float(raw[u][g].x);
+                            v[4 * g + 1] = __uint_as_float(raw[u][g].y);
+                            v[4 * g + 2] = __uint_as_float(raw[u][g].z);
+                            v[4 * g + 3] = __uint_as_float(raw[u][g].w);
+                        }
+                    } else {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float2 f = __bfloat1622float2(h[j]);
-                            v[8 * g + 2 * j] = f.x;
-                            v[8 * g + 2 * j + 1] = f.y;
+                        for (int g = 0; g < NV; ++g) {
+                            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw[u][g]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float2 f = __bfloat1622float2(h[j]);
+                                v[8 * g + 2 * j] = f.x;
+                                v[8 * g + 2 * j + 1] = f.y;
+                            }
                         }
                     }
                     float ms = 0.f;
@@ -213,7 +264,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                     const float r = in[u] ? 1.0f / sqrtf(ms / C + 1e-6f) : 0.f;
 #pragma unroll
                     for (int c = 0; c < C; ++c) v[c] = v[c] * r * misc[c];
-                    store_pixel_bf16<C>(s_in, S::NPIX, p, v);
+                    if constexpr (SPLIT) store_pixel_split<C>(s_in, S::NPIX, p, v);
+                    else store_pixel_bf16<C>(s_in, S::NPIX, p, v);
                 }
             }
             umma::fence_smem_to_async();  // these writes, before the MMAs that read them
@@ -222,6 +274,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     } else if (warp == TC_MMA_WARP) {
         // ---- MMA issue (one thread) ----
         if (lane == 0) {
+            // descriptors built once per conv; each MMA adds its start offset (16-byte units: one
+            // pixel) to the start-address field, which stays below 2^14.  BF16: one MMA per K step;
+            // SPLIT: x_h w_h into the block's high accumulator, x_h w_l and x_l w_h into its low one.
+            auto conv = [&](uint64_t ad0, uint64_t bd0, uint32_t d0, int nb) {
+                for (int i = 0; i < nb; ++i) {
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                        for (int kk = 0; kk < C / 16; ++kk) {
+                            const int dy = tap / 3, dx = tap % 3;
+                            const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
+                            const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
+                            const uint32_t d = d0 + i * NACC;
+                            umma::mma_bf16(d, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
+                            if constexpr (SPLIT) {
+                                umma::mma_bf16(d + C, ad0 + ao, bd0 + bo + W_LO, idesc, (tap | kk) != 0);
+                                umma::mma_bf16(d + C, ad0 + ao + A_LO, bd0 + bo, idesc, 1);
+                            }
+                        }
+                }
+            };
             int k = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
@@ -231,45 +304,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                      (k == 0 || umma::mbar_wait(e1done, (k - 1) & 1, TC_WAIT_NS));
                 if (!ok) break;
                 umma::fence_after_sync();
-                {
-                    // descriptors built once; each MMA adds its start offset (16-byte units: one
-                    // pixel) to the start-address field, which stays below 2^14
-                    const uint64_t ad0 = umma::desc(umma::smem_u32(s_in), LBO_A, 128);
-                    const uint64_t bd0 = umma::desc(umma::smem_u32(s_w1), LBO_W, 128);
-                    for (int i = 0; i < tg.nb1; ++i) {
-#pragma unroll
-                        for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-                            for (int kk = 0; kk < C / 16; ++kk) {
-                                const int dy = tap / 3, dx = tap % 3;
-                                const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
-                                const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
-                                umma::mma_bf16(tmem + i * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
-                            }
-                    }
-                    umma::commit(c1done);
-                }
+                conv(umma::desc(umma::smem_u32(s_in), LBO_A, 128), umma::desc(umma::smem_u32(s_w1), LBO_W, 128), tmem,
+                     tg.nb1);
+                umma::commit(c1done);
                 ok = umma::mbar_wait(e1done, k & 1, TC_WAIT_NS) &&
                      (k == 0 || umma::mbar_wait(e2done, (k - 1) & 1, TC_WAIT_NS));
                 if (!ok) break;
                 umma::fence_after_sync();
-                {
-                    const uint64_t ad0 = umma::desc(umma::smem_u32(s_in), LBO_A, 128);  // the mid tile
-                    const uint64_t bd0 = umma::desc(umma::smem_u32(s_w2), LBO_W, 128);
-                    for (int i = 0; i < tg.nb2; ++i) {
-#pragma unroll
-                        for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-                            for (int kk = 0; kk < C / 16; ++kk) {
-                                const int dy = tap / 3, dx = tap % 3;
-                                const uint32_t ao = (uint32_t)(i * TC_M + dy * P + dx) + ((2 * kk * LBO_A) >> 4);
-                                const uint32_t bo = (tap * C * C * 2 + 2 * kk * LBO_W) >> 4;
-                                umma::mma_bf16(tmem + TB + i * C, ad0 + ao, bd0 + bo, idesc, (tap | kk) != 0);
-                            }
-                    }
-                    umma::commit(c2done);
-                    umma::commit(freed + b);  // the buffer is free once conv2 has read the mid tile
-                }
+                // the mid tile, in the input buffer
+                conv(umma::desc(umma::smem_u32(s_in), LBO_A, 128), umma::desc(umma::smem_u32(s_w2), LBO_W, 128),
+                     tmem + TB, tg.nb2);
+                umma::commit(c2done);
+                umma::commit(freed + b);  // the buffer is free once conv2 has read the mid tile
             }
             if (!ok) atomicOr(s_err, 2);
             // nothing of ours may still run on the tensor cores when TMEM is released
@@ -282,33 +328,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
         static_assert(TC_EPI_WARPS % 4 == 0, "the epilogue warps cover the four TMEM lane quarters evenly");
         const int q = warp & 3, grp = (warp - TC_MMA_WARP - 1) >> 2;
         const int col = q * 32 + lane;  // the pixel of a block (TMEM lane) this thread reads
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
+        // a block's accumulated conv output (SPLIT: high + 2^-11 low)
+        auto load_acc = [&](uint32_t c0, float (&v)[C]) {
+            tmem_load_row<C>(tmem + lanes + c0, v);
+            if constexpr (SPLIT) {
+                float lo[C];
+                tmem_load_row<C>(tmem + lanes + c0 + C, lo);
+#pragma unroll
+                for (int c = 0; c < C; ++c) v[c] = fmaf(lo[c], 1.0f / 2048.f, v[c]);
+            }
+        };
         int k = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
             const int b = k & 1;
             uint8_t* s_mid = sm + (size_t)b * S::buf_bytes;
             const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
             const int li = tile / (tg.tiles_x * tg.tiles_y);
-            const __nv_bfloat16* vin = reinterpret_cast<const __nv_bfloat16*>(a.in) + (size_t)li * plane * C;
             if (!umma::mbar_wait(c1done, k & 1, TC_WAIT_NS)) {
                 atomicOr(s_err, 4);
                 break;
             }
             umma::fence_after_sync();
-            // gelu(conv1 + b1) -> BF16 mid tile, zero outside the plane and on the discarded pixels
+            // gelu(conv1 + b1) -> mid tile, zero outside the plane and on the discarded pixels
             for (int i = grp; i < tg.nb1; i += NGRP) {
                 float v[C];
-                tmem_load_row<C>(tmem + ((uint32_t)(q * 32) << 16) + i * C, v);
+                load_acc(i * NACC, v);
                 const int idx = i * TC_M + col;
                 const int row = idx / P, cx = idx - row * P;
                 const int gy = y0 - 1 + row, gx = x0 - 1 + cx;
                 const bool inside = row < R + 2 && cx < OW + 2 && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                if constexpr (SPLIT) {
+                    // the FP32 form's gelu: the erf form
 #pragma unroll
-                for (int c = 0; c < C; c += 2) {
-                    const float2 g = gelu_tanh2(__fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(misc[C + c], misc[C + c + 1])));
-                    v[c] = inside ? g.x : 0.f;
-                    v[c + 1] = inside ? g.y : 0.f;
+                    for (int c = 0; c < C; ++c) v[c] = inside ? gelu_erf(v[c] + misc[C + c]) : 0.f;
+                    store_pixel_split<C>(s_mid, S::NPIX, idx, v);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; c += 2) {
+                        const float2 g =
+                            gelu_tanh2(__fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(misc[C + c], misc[C + c + 1])));
+                        v[c] = inside ? g.x : 0.f;
+                        v[c + 1] = inside ? g.y : 0.f;
+                    }
+                    store_pixel_bf16<C>(s_mid, S::NPIX, idx, v);
                 }
-                store_pixel_bf16<C>(s_mid, S::NPIX, idx, v);
             }
             umma::fence_smem_to_async();
             umma::fence_before_sync();
@@ -321,7 +385,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
             // residual, V_out, decode
             for (int i = grp; i < tg.nb2; i += NGRP) {
                 float v[C];
-                tmem_load_row<C>(tmem + ((uint32_t)(q * 32) << 16) + TB + i * C, v);
+                load_acc(TB + i * NACC, v);
                 const int idx = i * TC_M + col;
                 const int row = idx / P, cx = idx - row * P;
                 const int gy = y0 + row, gx = x0 + cx;
@@ -329,34 +393,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                 const size_t pix = (size_t)gy * W + gx;
                 const size_t el = (size_t)li * plane + pix;
                 float t = misc[8 * C + 3], s = misc[8 * C + 4];
-                __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.out) + el * C;
+                if constexpr (SPLIT) {
+                    const float* vin = reinterpret_cast<const float*>(a.in) + el * C;
+                    float* out = reinterpret_cast<float*>(a.out) + el * C;
 #pragma unroll
-                for (int c0 = 0; c0 < C; c0 += 16) {
-                    // the residual's 16 channels in one 256-bit load, V' in one 256-bit store
-                    float rr[16];
-                    {
+                    for (int c0 = 0; c0 < C; c0 += 8) {
+                        // eight channels: the residual in one 256-bit load, V' in one 256-bit store
                         uint4 r0, r1;
-                        ldg256(vin + pix * C + c0, r0, r1);
-                        const uint32_t pk[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                        ldg256(vin + c0, r0, r1);
+                        const float rr[8] = {__uint_as_float(r0.x), __uint_as_float(r0.y), __uint_as_float(r0.z),
+                                             __uint_as_float(r0.w), __uint_as_float(r1.x), __uint_as_float(r1.y),
+                                             __uint_as_float(r1.z), __uint_as_float(r1.w)};
+                        float o[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            rr[2 * j] = __uint_as_float(pk[j] << 16);
-                            rr[2 * j + 1] = __uint_as_float(pk[j] & 0xffff0000u);
+                            const int c = c0 + j;
+                            o[j] = rr[j] + v[c] + misc[2 * C + c];
+                            t = fmaf(o[j], misc[3 * C + c], t);
+                            s = fmaf(o[j], misc[4 * C + c], s);
                         }
+                        stg256(out + c0, make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                                                    __float_as_uint(o[3])),
+                               make_uint4(__float_as_uint(o[4]), __float_as_uint(o[5]), __float_as_uint(o[6]),
+                                          __float_as_uint(o[7])));
                     }
-                    uint4 u[2];
-                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
+                } else {
+                    const __nv_bfloat16* vin = reinterpret_cast<const __nv_bfloat16*>(a.in) + (size_t)li * plane * C;
+                    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.out) + el * C;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int c = c0 + 2 * j;
-                        hh[j] = __floats2bfloat162_rn(rr[2 * j] + v[c] + misc[2 * C + c],
-                                                      rr[2 * j + 1] + v[c + 1] + misc[2 * C + c + 1]);
-                        // the logits from V' as stored, as the on-demand decode computes them
-                        const float2 o = __bfloat1622float2(hh[j]);
-                        t = fmaf(o.y, misc[3 * C + c + 1], fmaf(o.x, misc[3 * C + c], t));
-                        s = fmaf(o.y, misc[4 * C + c + 1], fmaf(o.x, misc[4 * C + c], s));
+                    for (int c0 = 0; c0 < C; c0 += 16) {
+                        // the residual's 16 channels in one 256-bit load, V' in one 256-bit store
+                        float rr[16];
+                        {
+                            uint4 r0, r1;
+                            ldg256(vin + pix * C + c0, r0, r1);
+                            const uint32_t pk[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                rr[2 * j] = __uint_as_float(pk[j] << 16);
+                                rr[2 * j + 1] = __uint_as_float(pk[j] & 0xffff0000u);
+                            }
+                        }
+                        uint4 u[2];
+                        __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(u);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int c = c0 + 2 * j;
+                            hh[j] = __floats2bfloat162_rn(rr[2 * j] + v[c] + misc[2 * C + c],
+                                                          rr[2 * j + 1] + v[c + 1] + misc[2 * C + c + 1]);
+                            // the logits from V' as stored, as the on-demand decode computes them
+                            const float2 o = __bfloat1622float2(hh[j]);
+                            t = fmaf(o.y, misc[3 * C + c + 1], fmaf(o.x, misc[3 * C + c], t));
+                            s = fmaf(o.y, misc[4 * C + c + 1], fmaf(o.x, misc[4 * C + c], s));
+                        }
+                        stg256(out + c0, u[0], u[1]);
                     }
-                    stg256(out + c0, u[0], u[1]);
                 }
                 if (a.t_raw) {
                     a.t_raw[pix * L + li] = t;
@@ -380,9 +471,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
 // TMEM, the cost is the tiles per CTA times (NB1 + NB2 + 3), the 3 standing for a tile's load and
 // epilogue overheads.  (Weighting the pipeline's fill and drain, which favours more and smaller
 // tiles on small planes, measured slower.)
-template <int C>
+template <int C, bool SPLIT>
 static ConvTile choose_tile(int W, int H, int L, int slots) {
-    using S = TcSmem<C>;
+    using S = TcSmem<C, SPLIT>;
     ConvTile best{0, 0, 0, 0, 0, 0};
     long best_cost = -1, best_total = -1;
     int last_ow = -1;
@@ -408,7 +499,7 @@ static ConvTile choose_tile(int W, int H, int L, int slots) {
     return best;
 }
 
-template <int C>
+template <int C, bool SPLIT>
 static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
     static int sms = 0;
     if (!sms) {
@@ -417,8 +508,8 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = TcSmem<C>::total;
-    auto k = conv_block_tc_kernel<C>;
+    const size_t smem = TcSmem<C, SPLIT>::total;
+    auto k = conv_block_tc_kernel<C, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // the geometry of the last few plane sizes, per host thread
@@ -432,7 +523,7 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
     for (const Entry& c : cache)
         if (c.t.P && c.W == a.W && c.H == a.H && c.L == a.L) tg = c.t;
     if (!tg.P) {
-        tg = choose_tile<C>(a.W, a.H, a.L, sms);
+        tg = choose_tile<C, SPLIT>(a.W, a.H, a.L, sms);
         if (!tg.P) return cudaErrorInvalidValue;
         cache[next] = Entry{a.W, a.H, a.L, tg};
         next = (next + 1) % 8;
@@ -443,28 +534,38 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t conv_tc_tile_shape(int C, int W, int H, int L, int* cols, int* rows) {
+cudaError_t conv_tc_tile_shape(int C, bool split, int W, int H, int L, int* cols, int* rows) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     ConvTile t{};
-    if (C == 16) t = choose_tile<16>(W, H, L, sms);
-    else if (C == 32) t = choose_tile<32>(W, H, L, sms);
-    else if (C == 64) t = choose_tile<64>(W, H, L, sms);
+    if (split) {
+        if (C == 16) t = choose_tile<16, true>(W, H, L, sms);
+        else if (C == 32) t = choose_tile<32, true>(W, H, L, sms);
+    } else {
+        if (C == 16) t = choose_tile<16, false>(W, H, L, sms);
+        else if (C == 32) t = choose_tile<32, false>(W, H, L, sms);
+        else if (C == 64) t = choose_tile<64, false>(W, H, L, sms);
+    }
     if (!t.P) return cudaErrorInvalidValue;
     *cols = t.P - 4;
     *rows = t.R;
     return cudaSuccess;
 }
 
-cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, cudaStream_t st) {
+cudaError_t launch_conv_block_tc(const ConvArgs& a, int C, bool split, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
     // 256-bit pixel loads and stores
     if (reinterpret_cast<uintptr_t>(a.in) % 32 || reinterpret_cast<uintptr_t>(a.out) % 32) return cudaErrorMisalignedAddress;
-    if (C == 16) return launch_tc<16>(a, st);
-    if (C == 32) return launch_tc<32>(a, st);
-    if (C == 64) return launch_tc<64>(a, st);
+    if (split) {
+        if (C == 16) return launch_tc<16, true>(a, st);
+        if (C == 32) return launch_tc<32, true>(a, st);
+        return cudaErrorInvalidValue;
+    }
+    if (C == 16) return launch_tc<16, false>(a, st);
+    if (C == 32) return launch_tc<32, false>(a, st);
+    if (C == 64) return launch_tc<64, false>(a, st);
     return cudaErrorInvalidValue;
 }
 

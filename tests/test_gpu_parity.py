@@ -247,12 +247,14 @@ def test_1080p_sampled_outputs(precision):
     """V=8 1920x1080 views, scales (8,32),(4,16),(2,8),(1,4), C=32, h=2, 1080p output, in the
     launch configuration the bench times; the oracle computes output windows from scratch through
     every scale: corners and the centre of the frame, windows across the attention kernel's tile
-    corners, and windows across the conv-block kernel's tile corners at every step (the BF16
-    kernel picks its tile per plane size, so these windows sit where its tiling changes)."""
+    corners, and windows across the conv-block kernel's tile corners at every step (the tensor-core
+    conv kernel of either form picks its tile per plane size, so these windows sit where its tiling
+    changes)."""
     cfg = synth.config_1080p().replace(precision=precision)
     scene = synth.scene_1080p()
     W = synth.make_weights(cfg, sharp=True)
     ctx = quark.Context(cfg)
+    ctx.load_weights(W)  # the FP32 form's conv kernel (and tile) depends on the weights
     rects = FULL_RECTS + ATTEND_SEAM_RECTS + conv_seam_rects(ctx, cfg)
     ctx.close()
     out, _, _ = run_gpu(cfg, W, scene, per_step=False)
