@@ -348,6 +348,14 @@ quark_status quark_sample_coords(quark_ctx* ctx, const quark_camera* target, dou
  * quark_load_weights. */
 quark_status quark_conv_tiles(quark_ctx* ctx, int L, int H, int W, int* tile_cols, int* tile_rows);
 
+/* Which kernels the context runs on the 5th-generation tensor cores (inspection): *attend = 1 when
+ * the one-to-many sampling kernel's query and output projections do (BF16 form; FP32 form with
+ * C <= 32 through split FP16 operands, when the weights bound the normalised input and the
+ * weights below 2^15), *conv = 1 when the conv block's convolutions do (BF16 form; FP32 form with
+ * C <= 32 and 3 x 3 kernels through split FP16 operands, when the weights bound every operand part
+ * below 2^15).  0 where the SIMT kernels run.  EINVAL before quark_load_weights. */
+quark_status quark_tensor_core_paths(quark_ctx* ctx, int* attend, int* conv);
+
 quark_status quark_release_pyramid(quark_pyramid* pyr);
 quark_status quark_release_ldm(quark_ldm* ldm);
 

@@ -557,6 +557,61 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             if (s != QUARK_OK) return s;
             QK_CUDA(ctx, cudaMemcpy(ctx->wtc, tc.data(), ctx->wtc_bytes, cudaMemcpyHostToDevice));
         }
+        // the one-to-many attention's projections likewise (C <= 32): [W^q | W^beta] and W^O in the
+        // BF16 form's element order and logit-scale folding, as FP16 high parts then scaled
+        // remainders.  Range: the normalised input is at most sqrt(C) max|g| per channel, the
+        // weights are the weights; the head outputs are scaled per element in the kernel.
+        qk_free(ctx, ctx->wat, ctx->wat_bytes);
+        ctx->wat = nullptr;
+        ctx->wat_bytes = 0;
+        const double qs = 1.0 / std::sqrt((double)C), log2e = 1.4426950408889634;
+        bool asplit = C <= 32 && c.attn_mode == QUARK_ATTN_ONE_TO_MANY;
+        auto small = [](double v) { return std::fabs(v) < 32768.0; };
+        for (int j = 0; j < c.n_scales && asplit; ++j) {
+            const int h = qk_heads(c, j);
+            if (h == 0) continue;
+            double gmax = 0.0;
+            for (int i = 0; i < C; ++i) gmax = std::max(gmax, (double)std::fabs(w->attn_g[j][i]));
+            asplit = small(std::sqrt((double)C) * gmax);
+            for (size_t i = 0; i < (size_t)C * h * C && asplit; ++i)
+                asplit = small(w->Wq[j][i] * qs * log2e) && small(w->Wo[j][i]);
+            for (size_t i = 0; i < (size_t)C * C && asplit; ++i) asplit = small(w->W_beta[i] * qs);
+        }
+        if (asplit) {
+            size_t total = 0;
+            for (int j = 0; j < c.n_scales; ++j) {
+                const int h = qk_heads(c, j);
+                ctx->off_wat[j] = total * sizeof(uint16_t);
+                total += h > 0 ? 2 * ((size_t)(h * C + C) * C + (size_t)C * h * C) : 0;
+            }
+            std::vector<uint16_t> at(std::max<size_t>(total, 8));
+            auto put_split = [](uint16_t* hi, uint16_t* lo, size_t i, double v) {
+                const float x = (float)v;
+                const __half hh = __float2half_rn(x);
+                hi[i] = __half_as_ushort(hh);
+                lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(hh)) * 2048.f));
+            };
+            for (int j = 0; j < c.n_scales; ++j) {
+                const int h = qk_heads(c, j), NQ = h * C + C;
+                if (h == 0) continue;
+                uint16_t* bq = at.data() + ctx->off_wat[j] / sizeof(uint16_t);
+                uint16_t* bq_lo = bq + (size_t)NQ * C;
+                uint16_t* bo = bq_lo + (size_t)NQ * C;
+                uint16_t* bo_lo = bo + (size_t)C * h * C;
+                for (int n = 0; n < NQ; ++n)
+                    for (int k = 0; k < C; ++k)
+                        put_split(bq, bq_lo, (size_t)(k / 8) * NQ * 8 + n * 8 + k % 8,
+                                  n < h * C ? w->Wq[j][(size_t)k * h * C + n] * qs * log2e
+                                            : w->W_beta[(size_t)k * C + (n - h * C)] * qs);
+                for (int n = 0; n < C; ++n)
+                    for (int k = 0; k < h * C; ++k)
+                        put_split(bo, bo_lo, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->Wo[j][(size_t)k * C + n]);
+            }
+            ctx->wat_bytes = at.size() * sizeof(uint16_t);
+            s = qk_alloc(ctx, &ctx->wat, ctx->wat_bytes);
+            if (s != QUARK_OK) return s;
+            QK_CUDA(ctx, cudaMemcpy(ctx->wat, at.data(), ctx->wat_bytes, cudaMemcpyHostToDevice));
+        }
     } else {
         ctx->wtc_step_bytes = 2 * 9 * (size_t)C * C * sizeof(uint16_t);
         std::vector<uint16_t> tc(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
@@ -1358,7 +1413,7 @@ quark_status qk_decode(quark_ctx* ctx, int scale, const void* vol, int L, int H,
 
 // Packed BF16 collapse weights of step `scale` (after the step's attention packs), or NULL.
 const void* qk_collapse_wtc(const quark_ctx* ctx, int scale) {
-    if (!ctx->wat) return nullptr;
+    if (!ctx->wat || ctx->cfg.precision != QUARK_BF16) return nullptr;
     const quark_config& c = ctx->cfg;
     const int h = qk_heads(c, scale);
     const size_t att_bytes = h > 0 ? ((size_t)(h * c.C + c.C) * c.C + (size_t)c.C * h * c.C) * 2 : 0;

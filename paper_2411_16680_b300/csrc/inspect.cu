@@ -80,3 +80,14 @@ extern "C" quark_status quark_conv_tiles(quark_ctx* ctx, int L, int H, int W, in
     if (e != cudaSuccess) return qk_fail(ctx, QUARK_ECUDA, "conv tile geometry: %s", cudaGetErrorString(e));
     return QUARK_OK;
 }
+
+extern "C" quark_status quark_tensor_core_paths(quark_ctx* ctx, int* attend, int* conv) {
+    if (!ctx || !attend || !conv) return qk_fail(ctx, QUARK_EINVAL, "NULL argument");
+    if (!ctx->weights_loaded) return qk_fail(ctx, QUARK_EINVAL, "weights not loaded");
+    const quark_config& c = ctx->cfg;
+    const bool bf16 = c.precision == QUARK_BF16;
+    // the dispatch rules of launch_attend and launch_conv_block for this context's packed weights
+    *attend = c.attn_mode == QUARK_ATTN_ONE_TO_MANY && (bf16 || (ctx->wat != nullptr && c.C <= 32));
+    *conv = bf16 || (c.conv_kernel != 1 && ctx->wtc != nullptr && c.C <= 32);
+    return QUARK_OK;
+}

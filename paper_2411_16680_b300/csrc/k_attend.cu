@@ -124,10 +124,13 @@ cudaError_t launch_attend_std(const AttendArgs& a, int C, int heads, Transition 
     return cudaErrorInvalidValue;
 }
 
-// FP32 form: this SIMT kernel.  BF16 form: projections on tcgen05 (k_attend_tc.cu).
+// BF16 form: projections on tcgen05 (k_attend_tc.cu).  FP32 form: the same kernel with split FP16
+// operands when the context packed them (C <= 32, weights within the split's range), else this
+// SIMT kernel.
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                           cudaStream_t st) {
-    if (bf16) return launch_attend_tc(a, C, heads, tr, last, st);
+    if (bf16) return launch_attend_tc(a, C, heads, tr, last, false, st);
+    if (a.wtc && C <= 32) return launch_attend_tc(a, C, heads, tr, last, true, st);
     if (reinterpret_cast<uintptr_t>(a.feat) % 32) return cudaErrorMisalignedAddress;  // 256-bit tap loads
     if (C == 16) return attend_fp32_c16(a, heads, tr, last, st);
     if (C == 32) return attend_fp32_c32(a, heads, tr, last, st);

@@ -16,6 +16,8 @@
 //   4. The head outputs O (BF16) go back to shared memory as an A operand; one MMA chain
 //      O W^O (N = C, K = hC) into TMEM; residual add in FP32; V_attn stored as BF16.
 // Completion of each MMA chain is signalled through an mbarrier; every wait is bounded.
+#include <cuda_fp16.h>
+
 #include "device_common.cuh"
 #include "umma.cuh"
 
@@ -29,24 +31,37 @@ constexpr float AT_SLACK = 20.f;  // log2 units: a factor of about 1e6
 // Shared memory of one CTA.  Only the query columns in use are copied (the blend query exists
 // on the last step only) and the blend logits are staged for the V views present, so that the
 // rest of the SM's unified L1 stays free to cache the sampled texels.
-template <int C, int NH, bool LAST>
+//
+// FP32 form (SPLIT): the X and O operands and the packed weights come in two FP16 parts, the
+// rounded value and the scaled remainder fp16((x - fp16(x)) 2^11), and each projection is
+// x_h w_h + 2^-11 (x_h w_l + x_l w_h) on three kind::f16 MMAs per K step into a high and a low
+// accumulator (FP32 accuracy: the dropped x_l w_l term is 2^-22 of a product).  The X tile (both
+// parts) later holds the FP32 entering volume; the O tile (both parts) takes the Q copy's bytes
+// once every thread has left the view loop.  O is scaled per element by a power of two into
+// [-1, 1) before the split (any feature magnitude), and the output row scaled back.
+template <int C, int NH, bool LAST, bool SPLIT>
 struct AtSmem {
+    static constexpr int PARTS = SPLIT ? 2 : 1;
     static constexpr int NQ = NH * C + C;        // packed query columns incl. the blend query
     static constexpr int NQ_USED = LAST ? NQ : NH * C;
     static constexpr int QS = NQ_USED + 4;       // padded fp32 row stride of the Q copy
-    static constexpr int x_off = 0;                               // A: 128 x C bf16
-    static constexpr int o_off = x_off + AT_M * C * 2;            // A: 128 x hC bf16
-    static constexpr int wq_off = o_off + AT_M * NH * C * 2;      // B: NQ x C bf16
-    static constexpr int wo_off = wq_off + NQ * C * 2;            // B: C x hC bf16
-    static constexpr int q_off = wo_off + C * NH * C * 2;         // fp32 128 x QS (Q copy, then output copy)
+    static constexpr int o_bytes = PARTS * AT_M * NH * C * 2;
+    static constexpr int x_off = 0;                               // A: 128 x C (per part)
+    static constexpr int o_sep = x_off + PARTS * AT_M * C * 2;    // A: 128 x hC (BF16 form)
+    static constexpr int wq_off = o_sep + (SPLIT ? 0 : o_bytes);  // B: NQ x C (per part)
+    static constexpr int wo_off = wq_off + PARTS * NQ * C * 2;    // B: C x hC (per part)
+    static constexpr int q_off = wo_off + PARTS * C * NH * C * 2; // fp32 128 x QS (Q copy, then output copy)
+    static constexpr int o_off = SPLIT ? q_off : o_sep;
     static constexpr int misc_off = q_off + AT_M * QS * 4;        // v0, g, w_d, b_d
     static constexpr int bar_off = misc_off + 4 * C * 4;
-    static constexpr int beta_off = bar_off + 16;                 // fp32 128 x V blend logits (last step)
+    static constexpr int oexp_off = bar_off + 16;                 // SPLIT: O's per-element exponent
+    static constexpr int beta_off = oexp_off + (SPLIT ? AT_M * 4 : 0);  // fp32 128 x V blend logits (last step)
     static int total(int V) { return beta_off + (LAST ? AT_M * V * 4 : 0); }
-    static constexpr int tmem_cols = NQ <= 32 ? 32 : NQ <= 64 ? 64 : NQ <= 128 ? 128 : 256;
+    static constexpr int tmem_need = PARTS * NQ;
+    static constexpr int tmem_cols = tmem_need <= 32 ? 32 : tmem_need <= 64 ? 64 : tmem_need <= 128 ? 128 : tmem_need <= 256 ? 256 : 512;
+    static constexpr uint32_t LO_COL = tmem_cols / 2;            // SPLIT: the low accumulators
+    static_assert(!SPLIT || o_bytes <= AT_M * QS * 4, "the O tile fits the Q copy's bytes");
 };
-
-
 
 // Bilinear interpolation on packed BF16 pairs: each 32-bit word of a tap holds two channels, and
 // one fma.rn.bf16x2 adds both channels' weighted taps (BF16 products and sums, one rounding per
@@ -95,13 +110,49 @@ __device__ __forceinline__ void unpack16(const uint32_t (&H)[8], float2 (&D)[8])
 #pragma unroll
     for (int j = 0; j < 8; ++j) D[j] = make_float2(__uint_as_float(H[j] << 16), __uint_as_float(H[j] & 0xffff0000u));
 }
+// FP32 form: D += w * texel for 16 FP32 channels at p (32-byte aligned): two 256-bit loads
+__device__ __forceinline__ void fma_tap16_f32(const float* p, float w, float2 (&D)[8]) {
+    uint4 t[4];
+    ldg256(p, t[0], t[1]);
+    ldg256(p + 8, t[2], t[3]);
+    const float2 w2 = make_float2(w, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        D[2 * i] = __ffma2_rn(make_float2(__uint_as_float(t[i].x), __uint_as_float(t[i].y)), w2, D[2 * i]);
+        D[2 * i + 1] = __ffma2_rn(make_float2(__uint_as_float(t[i].z), __uint_as_float(t[i].w)), w2, D[2 * i + 1]);
+    }
+}
+// FP32 form: eight channels as their FP16 parts (x - fp16(x) is exact in FP32, x 2^11 exact)
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+    __half2* h = reinterpret_cast<__half2*>(&hi);
+    __half2* l = reinterpret_cast<__half2*>(&lo);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __half2 hh = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+        const float2 f = __half22float2(hh);
+        h[j] = hh;
+        l[j] = __floats2half2_rn((v[2 * j] - f.x) * 2048.f, (v[2 * j + 1] - f.y) * 2048.f);
+    }
+}
+// A TMEM row chunk of 16 columns of the high (and, SPLIT, the low) accumulator: high + 2^-11 low
+template <bool SPLIT, uint32_t LO>
+__device__ __forceinline__ void tmem_acc16(uint32_t taddr, float (&v)[16]) {
+    umma::ld_32x32b_x16(taddr, v);
+    if constexpr (SPLIT) {
+        float lo[16];
+        umma::ld_32x32b_x16(taddr + LO, lo);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaf(lo[i], 1.0f / 2048.f, v[i]);
+    }
+}
+
 // The softmax below works in log2 units, so that each weight is one ex2 (ex2_approx); the
 // reprojection divides with one reciprocal (reproject_rcp).
-template <int C, int NH, int TR, bool LAST>
+template <int C, int NH, int TR, bool LAST, bool SPLIT>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;
     constexpr int NT = AT_M * TPE;
-    using S = AtSmem<C, NH, LAST>;
+    using S = AtSmem<C, NH, LAST, SPLIT>;
     constexpr int NQ_USED = S::NQ_USED;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_x = sm + S::x_off;
@@ -127,7 +178,8 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         const uint4* src = reinterpret_cast<const uint4*>(a.wtc);
         uint4* dq = reinterpret_cast<uint4*>(s_wq);
         constexpr int nq = S::NQ * C * 2 / 16, no = C * NH * C * 2 / 16;
-        for (int i = tid; i < nq + no; i += NT) dq[i] = __ldg(src + i);  // wq then wo, contiguous
+        // wq then wo (each part by part), contiguous
+        for (int i = tid; i < S::PARTS * (nq + no); i += NT) dq[i] = __ldg(src + i);
     }
     for (int i = tid; i < 4 * C; i += NT) misc[i] = a.w[i];  // v0 [C], g [C], w_d [C], b_d (padded)
 
@@ -144,6 +196,43 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     if (TR == TR_INIT) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) vres[i] = misc[c0 + i];
+    } else if (SPLIT && TR == TR_SAME) {
+        // FP32 form: the thread's 16 FP32 channels in two 256-bit loads
+        uint4 t[4];
+        const float* p = reinterpret_cast<const float*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0;
+        ldg256(p, t[0], t[1]);
+        ldg256(p + 8, t[2], t[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            vres[4 * i] = __uint_as_float(t[i].x);
+            vres[4 * i + 1] = __uint_as_float(t[i].y);
+            vres[4 * i + 2] = __uint_as_float(t[i].z);
+            vres[4 * i + 3] = __uint_as_float(t[i].w);
+        }
+    } else if (SPLIT) {
+        // FP32 form: x2 bilinear upsample in FP32
+        int ya, yb, xa, xb;
+        float wy, wx;
+        resize_taps(yc, 2, a.Hp, ya, yb, wy);
+        resize_taps(xc, 2, a.Wp, xa, xb, wx);
+        const float* base = reinterpret_cast<const float*>(a.prev) + (size_t)li * a.Hp * a.Wp * C + c0;
+        const float* q[4] = {base + ((size_t)ya * a.Wp + xa) * C, base + ((size_t)ya * a.Wp + xb) * C,
+                             base + ((size_t)yb * a.Wp + xa) * C, base + ((size_t)yb * a.Wp + xb) * C};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint4 r[4][2];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) ldg256(q[t] + 8 * h, r[t][0], r[t][1]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float f[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) f[t] = __uint_as_float((&r[t][i / 4].x)[i % 4]);
+                const float top = f[0] + wx * (f[1] - f[0]);
+                const float bot = f[2] + wx * (f[3] - f[2]);
+                vres[8 * h + i] = top + wy * (bot - top);
+            }
+        }
     } else if (TR == TR_SAME) {
         uint4 u0, u1;
         ldg256(reinterpret_cast<const __nv_bfloat16*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0, u0, u1);
@@ -207,7 +296,21 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         else if (a.depth_out && live && sub == 0) a.depth_out[de] = d;
     }
     const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
-    {
+    if constexpr (SPLIT) {
+        // this thread's 16 channels of X = N(V_in) as FP16 parts: two 8-channel groups per part,
+        // K-major A layout (group g of row m at g * 128 * 16 + m * 16, the low part's groups after
+        // the high part's C / 8)
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float xv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) xv[i] = vres[8 * g + i] * rinv * misc[C + c0 + 8 * g + i];
+            uint4 hi, lo;
+            split8(xv, hi, lo);
+            *reinterpret_cast<uint4*>(s_x + ((size_t)(c0 / 8 + g) * AT_M + e) * 16) = hi;
+            *reinterpret_cast<uint4*>(s_x + ((size_t)(C / 8 + c0 / 8 + g) * AT_M + e) * 16) = lo;
+        }
+    } else {
         // this thread's 16 channels of X = N(V_in): two 8-channel groups, K-major A layout
         // (group g of row m at g * 128 * 16 + m * 16)
 #pragma unroll
@@ -236,24 +339,37 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     const bool test_skip = a.test_wait_ns != 0;
     const uint64_t wait_ns = test_skip ? a.test_wait_ns : AT_WAIT_NS;
     if (tid == 0 && !test_skip) {
-        constexpr uint32_t idesc = umma::idesc_bf16_f32(AT_M, NQ_USED);
+        constexpr uint32_t idesc = SPLIT ? umma::idesc_f16_f32(AT_M, NQ_USED) : umma::idesc_bf16_f32(AT_M, NQ_USED);
         const uint32_t a0 = umma::smem_u32(s_x), b0 = umma::smem_u32(s_wq);
         constexpr uint32_t LBO_A = AT_M * 16, LBO_B = S::NQ * 16;
+        constexpr uint32_t A_LO = (C / 8) * LBO_A, B_LO = S::NQ * C * 2;  // the low parts (bytes)
 #pragma unroll
-        for (int kk = 0; kk < C / 16; ++kk)
-            umma::mma_bf16(tmem, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128), umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128),
-                           idesc, kk > 0);
+        for (int kk = 0; kk < C / 16; ++kk) {
+            const uint32_t ak = a0 + 2 * kk * LBO_A, bk = b0 + 2 * kk * LBO_B;
+            umma::mma_bf16(tmem, umma::desc(ak, LBO_A, 128), umma::desc(bk, LBO_B, 128), idesc, kk > 0);
+            if constexpr (SPLIT) {
+                umma::mma_bf16(tmem + S::LO_COL, umma::desc(ak, LBO_A, 128), umma::desc(bk + B_LO, LBO_B, 128), idesc, kk > 0);
+                umma::mma_bf16(tmem + S::LO_COL, umma::desc(ak + A_LO, LBO_A, 128), umma::desc(bk, LBO_B, 128), idesc, 1);
+            }
+        }
         umma::commit(mbar);
     }
     bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, wait_ns));
     uint32_t failed_phase = 0;
     umma::fence_after_sync();
     if (TR != TR_INIT && !failed) {
-        // X has been read by the MMA: its tile now keeps the entering volume's BF16 pairs (element
-        // e's channels at (e C + c) x 2 bytes) for the residual of the output epilogue
-        uint4* dst = reinterpret_cast<uint4*>(s_x + ((size_t)e * C + c0) * 2);
-        dst[0] = make_uint4(vpk[0], vpk[1], vpk[2], vpk[3]);
-        dst[1] = make_uint4(vpk[4], vpk[5], vpk[6], vpk[7]);
+        // X has been read by the MMA: its tile now keeps the entering volume for the residual of the
+        // output epilogue, element e's channels at (e C + c) x 2 bytes as BF16 pairs (BF16 form) or
+        // at (e C + c) x 4 bytes in FP32 (FP32 form)
+        if constexpr (SPLIT) {
+            float4* dst = reinterpret_cast<float4*>(s_x + ((size_t)e * C + c0) * 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(vres[4 * i], vres[4 * i + 1], vres[4 * i + 2], vres[4 * i + 3]);
+        } else {
+            uint4* dst = reinterpret_cast<uint4*>(s_x + ((size_t)e * C + c0) * 2);
+            dst[0] = make_uint4(vpk[0], vpk[1], vpk[2], vpk[3]);
+            dst[1] = make_uint4(vpk[4], vpk[5], vpk[6], vpk[7]);
+        }
     }
     if (!failed) {
         // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16.  The logit
@@ -262,7 +378,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         const int q = warp & 3, grp = warp >> 2;
         for (int ch = grp; ch < NQ_USED / 16; ch += TPE) {
             float v[16];
-            umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+            tmem_acc16<SPLIT, S::LO_COL>(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
             float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
 #pragma unroll
             for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -293,17 +409,30 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         const int vstride = a.fh * a.fw * C;  // < 2^31 for every accepted level size
         // Bilinear sample of view m: the four taps are always fetched (clamped into the map, weight
         // zero outside it), with no branch, so all the loads of the view are in flight together.
+        // (FP32 form: FP32 features, FP32 taps, the reprojection with an IEEE divide.)
         auto sample = [&](int m, float2 (&D)[8]) {
             float u = 0.f, v = 0.f;
-            const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
-            const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
-            const __nv_bfloat16* f = feat0 + (size_t)m * vstride;
-            uint32_t Hs[8];
-            mul_taps16(f + tp.i00 * C, tp.w00, Hs);
-            fma_taps16(f + tp.i01 * C, tp.w01, Hs);
-            fma_taps16(f + tp.i10 * C, tp.w10, Hs);
-            fma_taps16(f + tp.i11 * C, tp.w11, Hs);
-            unpack16(Hs, D);
+            if constexpr (SPLIT) {
+                const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
+                const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
+                const float* f = reinterpret_cast<const float*>(a.feat) + c0 + (size_t)m * vstride;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) D[j] = make_float2(0.f, 0.f);
+                fma_tap16_f32(f + tp.i00 * C, tp.w00, D);
+                fma_tap16_f32(f + tp.i01 * C, tp.w01, D);
+                fma_tap16_f32(f + tp.i10 * C, tp.w10, D);
+                fma_tap16_f32(f + tp.i11 * C, tp.w11, D);
+            } else {
+                const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
+                const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
+                const __nv_bfloat16* f = feat0 + (size_t)m * vstride;
+                uint32_t Hs[8];
+                mul_taps16(f + tp.i00 * C, tp.w00, Hs);
+                fma_taps16(f + tp.i01 * C, tp.w01, Hs);
+                fma_taps16(f + tp.i10 * C, tp.w10, Hs);
+                fma_taps16(f + tp.i11 * C, tp.w11, Hs);
+                unpack16(Hs, D);
+            }
         };
         // One online-softmax step of head h: logit s (log2 units, this element's full sum), sample D.
         // The softmax is invariant to the reference subtracted from its logits, so the reference
@@ -333,8 +462,9 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // Views in pairs: each query float4 is read from shared memory once for two samples (the
         // shared-memory reads of the queries were the larger part of the L1 data-pipe traffic).
         // Each view's arithmetic, and the order of the softmax steps, is that of one view at a time.
+        // (FP32 form: one view at a time, whose FP32 taps take twice the registers.)
         int m = 0;
-        for (; m + 1 < a.V; m += 2) {
+        for (; !SPLIT && m + 1 < a.V; m += 2) {
             float2 Da[8], Db[8];
             sample(m, Da);
             sample(m + 1, Db);
@@ -371,7 +501,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 }
             }
         }
-        if (m < a.V) {  // the last view of an odd count
+        for (; m < a.V; ++m) {  // the last view of an odd count (FP32 form: every view)
             float2 D[8];
             sample(m, D);
 #pragma unroll
@@ -397,18 +527,53 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 if (sub == 0) s_beta[e * a.V + m] = sa;
             }
         }
-        // head outputs -> BF16 A operand (K = h * C + channel)
+        if constexpr (SPLIT) {
+            // head outputs -> FP16 parts of the A operand (K = h * C + channel), scaled by 2^-x with
+            // x the exponent of the element's largest output (the row is scaled back after W^O).
+            // The O tile takes the Q copy's bytes: every thread must be done reading its queries.
+            float il[NH], mo = 0.f;
 #pragma unroll
-        for (int h = 0; h < NH; ++h) {
-            const float il = 1.0f / l[h];
+            for (int h = 0; h < NH; ++h) {
+                il[h] = 1.0f / l[h];
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                uint4 u;
-                __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+                for (int j = 0; j < 8; ++j) mo = fmaxf(mo, fmaxf(fabsf(o[h][j].x), fabsf(o[h][j].y)) * il[h]);
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    hh[j] = __floats2bfloat162_rn(o[h][4 * g + j].x * il, o[h][4 * g + j].y * il);
-                *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = u;
+            for (int off = 1; off < TPE; off <<= 1) mo = fmaxf(mo, __shfl_xor_sync(0xffffffffu, mo, off));
+            int ex = 0;
+            frexpf(mo, &ex);
+            if (sub == 0) reinterpret_cast<int*>(sm + S::oexp_off)[e] = ex;
+            __syncthreads();
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    float ov[8];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        ov[2 * j] = ldexpf(o[h][4 * g + j].x * il[h], -ex);
+                        ov[2 * j + 1] = ldexpf(o[h][4 * g + j].y * il[h], -ex);
+                    }
+                    uint4 hi, lo;
+                    split8(ov, hi, lo);
+                    *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = hi;
+                    *reinterpret_cast<uint4*>(s_o + ((size_t)((NH * C + h * C + c0) / 8 + g) * AT_M + e) * 16) = lo;
+                }
+            }
+        } else {
+            // head outputs -> BF16 A operand (K = h * C + channel)
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+                const float il = 1.0f / l[h];
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    uint4 u;
+                    __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        hh[j] = __floats2bfloat162_rn(o[h][4 * g + j].x * il, o[h][4 * g + j].y * il);
+                    *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = u;
+                }
             }
         }
     }
@@ -420,13 +585,20 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     if (!failed) {
         // ---- O W^O into TMEM columns [0, C) ----
         if (tid == 0) {
-            constexpr uint32_t idesc = umma::idesc_bf16_f32(AT_M, C);
+            constexpr uint32_t idesc = SPLIT ? umma::idesc_f16_f32(AT_M, C) : umma::idesc_bf16_f32(AT_M, C);
             const uint32_t a0 = umma::smem_u32(s_o), b0 = umma::smem_u32(s_wo);
             constexpr uint32_t LBO_A = AT_M * 16, LBO_B = C * 16;
+            constexpr uint32_t A_LO = (NH * C / 8) * LBO_A, B_LO = C * NH * C * 2;  // the low parts (bytes)
 #pragma unroll
-            for (int kk = 0; kk < NH * C / 16; ++kk)
-                umma::mma_bf16(tmem, umma::desc(a0 + 2 * kk * LBO_A, LBO_A, 128),
-                               umma::desc(b0 + 2 * kk * LBO_B, LBO_B, 128), idesc, kk > 0);
+            for (int kk = 0; kk < NH * C / 16; ++kk) {
+                const uint32_t ak = a0 + 2 * kk * LBO_A, bk = b0 + 2 * kk * LBO_B;
+                umma::mma_bf16(tmem, umma::desc(ak, LBO_A, 128), umma::desc(bk, LBO_B, 128), idesc, kk > 0);
+                if constexpr (SPLIT) {
+                    umma::mma_bf16(tmem + S::LO_COL, umma::desc(ak, LBO_A, 128), umma::desc(bk + B_LO, LBO_B, 128), idesc,
+                                   kk > 0);
+                    umma::mma_bf16(tmem + S::LO_COL, umma::desc(ak + A_LO, LBO_A, 128), umma::desc(bk, LBO_B, 128), idesc, 1);
+                }
+            }
             umma::commit(mbar);
         }
         failed = __syncthreads_or(!umma::mbar_wait(mbar, 1, AT_WAIT_NS));
@@ -440,7 +612,28 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             const int ex = blockIdx.y * AT_TW + er % AT_TW, ey = blockIdx.z * AT_TH + er / AT_TW;
             for (int ch = grp; ch < C / 16; ch += TPE) {
                 float v[16];
-                umma::ld_32x32b_x16(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+                tmem_acc16<SPLIT, S::LO_COL>(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+                if constexpr (SPLIT) {
+                    // FP32 form: the row scaled back (exactly: a power of two), the FP32 residual from
+                    // the X tile (or v0), V_attn stored in FP32
+                    if (ex < W && ey < H) {
+                        const int oe = reinterpret_cast<const int*>(sm + S::oexp_off)[er];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            v[i] = ldexpf(v[i], oe) +
+                                   (TR == TR_INIT ? misc[ch * 16 + i]
+                                                  : reinterpret_cast<const float*>(s_x)[(size_t)er * C + ch * 16 + i]);
+                        float* dst = reinterpret_cast<float*>(a.out) + (((size_t)li * H + ey) * W + ex) * C + ch * 16;
+                        uint4 u[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            u[i] = make_uint4(__float_as_uint(v[4 * i]), __float_as_uint(v[4 * i + 1]),
+                                              __float_as_uint(v[4 * i + 2]), __float_as_uint(v[4 * i + 3]));
+                        stcs256(dst, u[0], u[1]);
+                        stcs256(dst + 8, u[2], u[3]);
+                    }
+                    continue;
+                }
                 if (ex < W && ey < H) {
                     if (TR == TR_INIT) {
 #pragma unroll
@@ -487,14 +680,14 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     if (warp == 0) umma::tmem_dealloc(tmem, S::tmem_cols);
 }
 
-template <int C, int NH>
+template <int C, int NH, bool SPLIT>
 static cudaError_t launch_tc_nh(const AttendArgs& a, Transition tr, bool last, cudaStream_t st) {
     dim3 grid(a.L, (a.W + AT_TW - 1) / AT_TW, (a.H + AT_TH - 1) / AT_TH);
     const int threads = AT_M * (C / 16);
 #define QK_TC_LAUNCH(TRV, LASTV)                                                                       \
     do {                                                                                               \
-        const size_t smem = AtSmem<C, NH, LASTV>::total(a.V);                                          \
-        auto k = attend_tc_kernel<C, NH, TRV, LASTV>;                                                  \
+        const size_t smem = AtSmem<C, NH, LASTV, SPLIT>::total(a.V);                                   \
+        auto k = attend_tc_kernel<C, NH, TRV, LASTV, SPLIT>;                                           \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                \
         k<<<grid, threads, smem, st>>>(a);                                                             \
@@ -510,27 +703,33 @@ static cudaError_t launch_tc_nh(const AttendArgs& a, Transition tr, bool last, c
     return cudaGetLastError();
 }
 
-template <int C>
+template <int C, bool SPLIT>
 static cudaError_t launch_tc_c(const AttendArgs& a, int heads, Transition tr, bool last, cudaStream_t st) {
-    if (heads == 1) return launch_tc_nh<C, 1>(a, tr, last, st);
-    if (heads == 2) return launch_tc_nh<C, 2>(a, tr, last, st);
+    if (heads == 1) return launch_tc_nh<C, 1, SPLIT>(a, tr, last, st);
+    if (heads == 2) return launch_tc_nh<C, 2, SPLIT>(a, tr, last, st);
     // four heads: (4 + 1) C query columns; at C = 64 that is 320, above the 256 columns of one
     // M = 128 MMA (and its shared memory above 227 KB), so that configuration is not built
     if constexpr (C <= 32) {
-        if (heads == 4) return launch_tc_nh<C, 4>(a, tr, last, st);
+        if (heads == 4) return launch_tc_nh<C, 4, SPLIT>(a, tr, last, st);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st) {
+cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool split, cudaStream_t st) {
     if (!a.wtc || !a.err) return cudaErrorInvalidValue;
     // 256-bit loads of the taps and of the entering volume, 256-bit stores of V_attn
     if (reinterpret_cast<uintptr_t>(a.feat) % 32 || reinterpret_cast<uintptr_t>(a.prev) % 32 ||
         reinterpret_cast<uintptr_t>(a.out) % 32)
         return cudaErrorMisalignedAddress;
-    if (C == 16) return launch_tc_c<16>(a, heads, tr, last, st);
-    if (C == 32) return launch_tc_c<32>(a, heads, tr, last, st);
-    if (C == 64) return launch_tc_c<64>(a, heads, tr, last, st);
+    if (split) {
+        // FP32 form (C <= 32): the FP16 parts of the operands take twice the shared memory
+        if (C == 16) return launch_tc_c<16, true>(a, heads, tr, last, st);
+        if (C == 32) return launch_tc_c<32, true>(a, heads, tr, last, st);
+        return cudaErrorInvalidValue;
+    }
+    if (C == 16) return launch_tc_c<16, false>(a, heads, tr, last, st);
+    if (C == 32) return launch_tc_c<32, false>(a, heads, tr, last, st);
+    if (C == 64) return launch_tc_c<64, false>(a, heads, tr, last, st);
     return cudaErrorInvalidValue;
 }
 

@@ -197,7 +197,9 @@ cudaError_t launch_mlp_block(const ConvArgs& a, int C, bool bf16, cudaStream_t s
 // Output tile (columns, rows) the tensor-core conv block uses for an L x H x W volume.
 cudaError_t conv_tc_tile_shape(int C, bool split, int W, int H, int L, int* cols, int* rows);
 cudaError_t launch_decode(const DecodeArgs& a, int C, bool bf16, cudaStream_t st);
-cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, cudaStream_t st);
+// split: the FP32 form on FP16 operand parts (AttendArgs.wtc packed by pack_attention_f16split)
+cudaError_t launch_attend_tc(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool split,
+                             cudaStream_t st);
 cudaError_t launch_kv_project(const void* feat, size_t texels, int C, const float* wkv, void* out, bool with_f, bool bf16,
                               cudaStream_t st);
 cudaError_t launch_attend_std(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,

@@ -176,6 +176,7 @@ def lib():
             "quark_encode_pyramid_bwd": ([vp, vp, ct.POINTER(vp), ct.POINTER(Grads), vp], ct.c_int),
             "quark_conv_tiles": ([vp, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)],
                                  ct.c_int),
+            "quark_tensor_core_paths": ([vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)], ct.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -475,6 +476,13 @@ class Context:
         cols, rows = ct.c_int(0), ct.c_int(0)
         _check(lib().quark_conv_tiles(self.handle, L, H, W, ct.byref(cols), ct.byref(rows)), self.handle)
         return cols.value, rows.value
+
+    def tensor_core_paths(self):
+        """quark_tensor_core_paths: (attend, conv) -- whether the sampling kernel's projections and the
+        conv block's convolutions run on the tensor cores for the loaded weights."""
+        at, cv = ct.c_int(0), ct.c_int(0)
+        _check(lib().quark_tensor_core_paths(self.handle, ct.byref(at), ct.byref(cv)), self.handle)
+        return bool(at.value), bool(cv.value)
 
     def test_wait_timeout(self):
         """quark_test_wait_timeout: the next BF16 sampling launch's bounded wait runs out (error-path test)."""
