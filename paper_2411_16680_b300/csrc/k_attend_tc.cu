@@ -462,9 +462,8 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // Views in pairs: each query float4 is read from shared memory once for two samples (the
         // shared-memory reads of the queries were the larger part of the L1 data-pipe traffic).
         // Each view's arithmetic, and the order of the softmax steps, is that of one view at a time.
-        // (FP32 form: one view at a time, whose FP32 taps take twice the registers.)
         int m = 0;
-        for (; !SPLIT && m + 1 < a.V; m += 2) {
+        for (; m + 1 < a.V; m += 2) {
             float2 Da[8], Db[8];
             sample(m, Da);
             sample(m + 1, Db);
@@ -501,7 +500,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 }
             }
         }
-        for (; m < a.V; ++m) {  // the last view of an odd count (FP32 form: every view)
+        if (m < a.V) {  // the last view of an odd count
             float2 D[8];
             sample(m, D);
 #pragma unroll
