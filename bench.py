@@ -205,6 +205,7 @@ def run_form(cfg, W, scene, steps, warmup, rank, world, dev, peaks, flush_bytes=
     torch.cuda.set_device(dev)
     ctx = quark.Context(cfg, device=dev)
     ctx.load_weights(W)
+    tc_paths = ctx.tensor_core_paths()
     stream = torch.cuda.Stream(dev)
     images = torch.tensor(scene.images, device=f"cuda:{dev}")
     out = torch.empty(cfg.out_h, cfg.out_w, 4, device=f"cuda:{dev}")
@@ -299,7 +300,7 @@ def run_form(cfg, W, scene, steps, warmup, rank, world, dev, peaks, flush_bytes=
     ldm.release()
     ctx.close()
     return {
-        "total_ms": total_ms, "lat": lat, "launches": launches, "ktimes": ktimes, "clocks": clk.summary(),
+        "total_ms": total_ms, "lat": lat, "launches": launches, "ktimes": ktimes, "clocks": clk.summary(), "tc_paths": tc_paths,
         "e2e_s": e2e_s, "serial_s": serial_s, "h2d": int(scene.images.nbytes), "d2h": int(cfg.out_h * cfg.out_w * 16), "rgba": rgba,
     }
 
@@ -323,7 +324,7 @@ def measured_traffic(fam, cfg, bytes_per_launch):
 
 
 def roofline(cfg, V, img_h, img_w, res, peaks):
-    work = accounting.per_view_work(cfg, V, img_h, img_w)
+    work = accounting.per_view_work(cfg, V, img_h, img_w, res.get("tc_paths"))
     steps_done = None
     fam, (n, ms) = max(res["ktimes"].items(), key=lambda kv: kv[1][1])
     # frames timed: the render runs once per frame
@@ -351,9 +352,11 @@ def roofline(cfg, V, img_h, img_w, res, peaks):
         "alu": (alu_flops / (alu_peak * 1e12), alu_flops / sec / 1e12, round(alu_peak, 1), "TFLOP/s", alu_src),
     }
     if tensor_flops > 0:
-        tp = peaks["bf16_tflops_sustained"]
-        cands["tensor"] = (tensor_flops / (tp * 1e12), tensor_flops / sec / 1e12, tp, "TFLOP/s",
-                           f"{peaks['source']} BF16 dense, sustained")
+        # FP32 form: three FP16 products (the FP16 dense rate is the BF16 one) per FLOP of the definition
+        parts = w.get("tensor_products", 1)
+        tp = round(peaks["bf16_tflops_sustained"] / parts, 1)
+        src = f"{peaks['source']} BF16 dense, sustained" + (f" / {parts} (split FP16 products per FP32 product)" if parts > 1 else "")
+        cands["tensor"] = (tensor_flops / (tp * 1e12), tensor_flops / sec / 1e12, tp, "TFLOP/s", src)
     binding = max(cands, key=lambda k: cands[k][0])
     bound = ("tensor" if "tensor" in cands else "alu") if fam == "conv_block" else "hbm"
     _, ach, peak, unit, src = cands[bound]

@@ -11,14 +11,20 @@ from __future__ import annotations
 from typing import Dict
 
 
-def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, float]]:
+def per_view_work(cfg, V: int, img_h: int, img_w: int, tc_paths=None) -> Dict[str, Dict[str, float]]:
+    """tc_paths: (attend, conv) on the tensor cores, as quark_tensor_core_paths reports them for the
+    loaded weights; default: both in the BF16 form, neither in the FP32 form."""
     C = cfg.C
-    elt = 2 if cfg.precision == 1 else 4
-    # "tensor_flops": the part of "flops" that runs on the tensor cores (BF16 form); the rest runs
-    # on the FP32 SIMT pipes
-    out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "tensor_flops": 0.0, "launches": 0}
+    bf16 = cfg.precision == 1
+    elt = 2 if bf16 else 4
+    # "tensor_flops": the part of "flops" that runs on the tensor cores; the rest runs on the FP32
+    # SIMT pipes.  "tensor_products": tensor-core products per FLOP of the definition: 1 in the BF16
+    # form, 3 where the FP32 form splits each operand into two FP16 parts (x_h w_h, x_h w_l, x_l w_h)
+    out: Dict[str, Dict[str, float]] = {k: {"bytes": 0.0, "flops": 0.0, "tensor_flops": 0.0, "launches": 0,
+                                            "tensor_products": 1 if bf16 else 3}
                                         for k in ("encode", "collapse", "attend", "conv_block", "render", "refine")}
-    tc = cfg.precision == 1
+    attend_tc, conv_tc = (bf16, bf16) if tc_paths is None else (bool(tc_paths[0]), bool(tc_paths[1]))
+    tc = bf16
     # encode: images in, every used level out, RGBA copy out
     e = out["encode"]
     e["bytes"] += V * img_h * img_w * (3 * 4 + 16)
@@ -45,7 +51,7 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
         cb = out["conv_block"]
         cb["bytes"] += 2 * E * C * elt + (2 * E * 4 if last else 0)  # V in and out; raw logits of the last step
         cb["flops"] += 2 * (18 * C * C + 5 * C) * E
-        cb["tensor_flops"] += 2 * 18 * C * C * E if tc else 0
+        cb["tensor_flops"] += 2 * 18 * C * C * E if conv_tc else 0
         cb["launches"] += 1
         if h == 0:
             continue  # a block without attention: its conv block only
@@ -86,12 +92,12 @@ def per_view_work(cfg, V: int, img_h: int, img_w: int) -> Dict[str, Dict[str, fl
         else:
             a["bytes"] += vin + texels * C * elt + E * C * elt + (E * V * 4 if last else 0)
             # per element: the projections X W^q (+ the blend query X W^beta) and O W^O (tensor cores
-            # in the BF16 form), per view the bilinear sample, h logits, h weighted sums and the
+            # when attend_tc), per view the bilinear sample, h logits, h weighted sums and the
             # blend logit (SIMT)
             proj = 2 * h * C * C + (C * C if last else 0)
             macs = proj + 2 * V * h * C + 4 * V * C + (V * C if last else 0)
             a["flops"] += 2 * macs * E
-            a["tensor_flops"] += 2 * proj * E if tc else 0
+            a["tensor_flops"] += 2 * proj * E if attend_tc else 0
             a["launches"] += 1
     L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
     r = out["render"]

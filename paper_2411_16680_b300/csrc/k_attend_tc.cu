@@ -27,6 +27,10 @@ constexpr int AT_M = 128;
 constexpr int AT_TW = 16, AT_TH = 8;  // pixel tile of the 128 elements
 constexpr uint64_t AT_WAIT_NS = 1000000000ull;
 constexpr float AT_SLACK = 20.f;  // log2 units: a factor of about 1e6
+// Leading byte offset of the X and O operand tiles (distance between K-adjacent 8-channel columns of
+// core matrices): 128 rows of 16 bytes plus 32, so that the two threads of an element, which write
+// columns two apart, and eight consecutive rows fall on distinct banks.
+constexpr int AT_LBO = AT_M * 16 + 32;
 
 // Shared memory of one CTA.  Only the query columns in use are copied (the blend query exists
 // on the last step only) and the blend logits are staged for the V views present, so that the
@@ -45,9 +49,9 @@ struct AtSmem {
     static constexpr int NQ = NH * C + C;        // packed query columns incl. the blend query
     static constexpr int NQ_USED = LAST ? NQ : NH * C;
     static constexpr int QS = NQ_USED + 4;       // padded fp32 row stride of the Q copy
-    static constexpr int o_bytes = PARTS * AT_M * NH * C * 2;
+    static constexpr int o_bytes = PARTS * (NH * C / 8) * AT_LBO;
     static constexpr int x_off = 0;                               // A: 128 x C (per part)
-    static constexpr int o_sep = x_off + PARTS * AT_M * C * 2;    // A: 128 x hC (BF16 form)
+    static constexpr int o_sep = x_off + PARTS * (C / 8) * AT_LBO;  // A: 128 x hC (BF16 form)
     static constexpr int wq_off = o_sep + (SPLIT ? 0 : o_bytes);  // B: NQ x C (per part)
     static constexpr int wo_off = wq_off + PARTS * NQ * C * 2;    // B: C x hC (per part)
     static constexpr int q_off = wo_off + PARTS * C * NH * C * 2; // fp32 128 x QS (Q copy, then output copy)
@@ -307,8 +311,8 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             for (int i = 0; i < 8; ++i) xv[i] = vres[8 * g + i] * rinv * misc[C + c0 + 8 * g + i];
             uint4 hi, lo;
             split8(xv, hi, lo);
-            *reinterpret_cast<uint4*>(s_x + ((size_t)(c0 / 8 + g) * AT_M + e) * 16) = hi;
-            *reinterpret_cast<uint4*>(s_x + ((size_t)(C / 8 + c0 / 8 + g) * AT_M + e) * 16) = lo;
+            *reinterpret_cast<uint4*>(s_x + (size_t)(c0 / 8 + g) * AT_LBO + e * 16) = hi;
+            *reinterpret_cast<uint4*>(s_x + (size_t)(C / 8 + c0 / 8 + g) * AT_LBO + e * 16) = lo;
         }
     } else {
         // this thread's 16 channels of X = N(V_in): two 8-channel groups, K-major A layout
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 const int i = 8 * g + 2 * j;
                 hh[j] = __floats2bfloat162_rn(vres[i] * rinv * misc[C + c0 + i], vres[i + 1] * rinv * misc[C + c0 + i + 1]);
             }
-            *reinterpret_cast<uint4*>(s_x + ((size_t)(c0 / 8 + g) * AT_M + e) * 16) = u;
+            *reinterpret_cast<uint4*>(s_x + (size_t)(c0 / 8 + g) * AT_LBO + e * 16) = u;
         }
     }
     if (warp == 0) umma::tmem_alloc(tslot, S::tmem_cols);
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     if (tid == 0 && !test_skip) {
         constexpr uint32_t idesc = SPLIT ? umma::idesc_f16_f32(AT_M, NQ_USED) : umma::idesc_bf16_f32(AT_M, NQ_USED);
         const uint32_t a0 = umma::smem_u32(s_x), b0 = umma::smem_u32(s_wq);
-        constexpr uint32_t LBO_A = AT_M * 16, LBO_B = S::NQ * 16;
+        constexpr uint32_t LBO_A = AT_LBO, LBO_B = S::NQ * 16;
         constexpr uint32_t A_LO = (C / 8) * LBO_A, B_LO = S::NQ * C * 2;  // the low parts (bytes)
 #pragma unroll
         for (int kk = 0; kk < C / 16; ++kk) {
@@ -359,16 +363,16 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     umma::fence_after_sync();
     if (TR != TR_INIT && !failed) {
         // X has been read by the MMA: its tile now keeps the entering volume for the residual of the
-        // output epilogue, element e's channels at (e C + c) x 2 bytes as BF16 pairs (BF16 form) or
-        // at (e C + c) x 4 bytes in FP32 (FP32 form)
+        // output epilogue, in 16-byte columns of the operand layout (8 BF16 channels, BF16 form; 4
+        // FP32 channels, FP32 form): column k of element e at k * AT_LBO + e * 16
         if constexpr (SPLIT) {
-            float4* dst = reinterpret_cast<float4*>(s_x + ((size_t)e * C + c0) * 4);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dst[i] = make_float4(vres[4 * i], vres[4 * i + 1], vres[4 * i + 2], vres[4 * i + 3]);
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<float4*>(s_x + (size_t)(c0 / 4 + i) * AT_LBO + e * 16) =
+                    make_float4(vres[4 * i], vres[4 * i + 1], vres[4 * i + 2], vres[4 * i + 3]);
         } else {
-            uint4* dst = reinterpret_cast<uint4*>(s_x + ((size_t)e * C + c0) * 2);
-            dst[0] = make_uint4(vpk[0], vpk[1], vpk[2], vpk[3]);
-            dst[1] = make_uint4(vpk[4], vpk[5], vpk[6], vpk[7]);
+            *reinterpret_cast<uint4*>(s_x + (size_t)(c0 / 8) * AT_LBO + e * 16) = make_uint4(vpk[0], vpk[1], vpk[2], vpk[3]);
+            *reinterpret_cast<uint4*>(s_x + (size_t)(c0 / 8 + 1) * AT_LBO + e * 16) = make_uint4(vpk[4], vpk[5], vpk[6], vpk[7]);
         }
     }
     if (!failed) {
@@ -494,10 +498,9 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                     bb = __ffma2_rn(make_float2(q4.z, q4.w), Db[2 * i + 1], bb);
                 }
                 const float sa = group_sum(ba.x + ba.y), sb = group_sum(bb.x + bb.y);
-                if (sub == 0) {
-                    s_beta[e * a.V + m] = sa;
-                    s_beta[e * a.V + m + 1] = sb;
-                }
+                // the element's first and last threads store one each (fewer bank conflicts)
+                if (sub == 0) s_beta[e * a.V + m] = sa;
+                if (sub == TPE - 1) s_beta[e * a.V + m + 1] = sb;
             }
         }
         if (m < a.V) {  // the last view of an odd count
@@ -555,8 +558,8 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                     }
                     uint4 hi, lo;
                     split8(ov, hi, lo);
-                    *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = hi;
-                    *reinterpret_cast<uint4*>(s_o + ((size_t)((NH * C + h * C + c0) / 8 + g) * AT_M + e) * 16) = lo;
+                    *reinterpret_cast<uint4*>(s_o + (size_t)((h * C + c0) / 8 + g) * AT_LBO + e * 16) = hi;
+                    *reinterpret_cast<uint4*>(s_o + (size_t)((NH * C + h * C + c0) / 8 + g) * AT_LBO + e * 16) = lo;
                 }
             }
         } else {
@@ -571,7 +574,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         hh[j] = __floats2bfloat162_rn(o[h][4 * g + j].x * il, o[h][4 * g + j].y * il);
-                    *reinterpret_cast<uint4*>(s_o + ((size_t)((h * C + c0) / 8 + g) * AT_M + e) * 16) = u;
+                    *reinterpret_cast<uint4*>(s_o + (size_t)((h * C + c0) / 8 + g) * AT_LBO + e * 16) = u;
                 }
             }
         }
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         if (tid == 0) {
             constexpr uint32_t idesc = SPLIT ? umma::idesc_f16_f32(AT_M, C) : umma::idesc_bf16_f32(AT_M, C);
             const uint32_t a0 = umma::smem_u32(s_o), b0 = umma::smem_u32(s_wo);
-            constexpr uint32_t LBO_A = AT_M * 16, LBO_B = C * 16;
+            constexpr uint32_t LBO_A = AT_LBO, LBO_B = C * 16;
             constexpr uint32_t A_LO = (NH * C / 8) * LBO_A, B_LO = C * NH * C * 2;  // the low parts (bytes)
 #pragma unroll
             for (int kk = 0; kk < NH * C / 16; ++kk) {
@@ -618,10 +621,15 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                     if (ex < W && ey < H) {
                         const int oe = reinterpret_cast<const int*>(sm + S::oexp_off)[er];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            v[i] = ldexpf(v[i], oe) +
-                                   (TR == TR_INIT ? misc[ch * 16 + i]
-                                                  : reinterpret_cast<const float*>(s_x)[(size_t)er * C + ch * 16 + i]);
+                        for (int i = 0; i < 4; ++i) {
+                            float4 r = make_float4(misc[ch * 16 + 4 * i], misc[ch * 16 + 4 * i + 1],
+                                                   misc[ch * 16 + 4 * i + 2], misc[ch * 16 + 4 * i + 3]);
+                            if (TR != TR_INIT) r = *reinterpret_cast<const float4*>(s_x + (size_t)(4 * ch + i) * AT_LBO + er * 16);
+                            v[4 * i] = ldexpf(v[4 * i], oe) + r.x;
+                            v[4 * i + 1] = ldexpf(v[4 * i + 1], oe) + r.y;
+                            v[4 * i + 2] = ldexpf(v[4 * i + 2], oe) + r.z;
+                            v[4 * i + 3] = ldexpf(v[4 * i + 3], oe) + r.w;
+                        }
                         float* dst = reinterpret_cast<float*>(a.out) + (((size_t)li * H + ey) * W + ex) * C + ch * 16;
                         uint4 u[4];
 #pragma unroll
@@ -638,8 +646,8 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] += misc[ch * 16 + i];
                     } else {
-                        const uint4* src = reinterpret_cast<const uint4*>(s_x + ((size_t)er * C + ch * 16) * 2);
-                        const uint4 p0 = src[0], p1 = src[1];
+                        const uint4 p0 = *reinterpret_cast<const uint4*>(s_x + (size_t)(2 * ch) * AT_LBO + er * 16);
+                        const uint4 p1 = *reinterpret_cast<const uint4*>(s_x + (size_t)(2 * ch + 1) * AT_LBO + er * 16);
                         const uint32_t pk[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {

@@ -30,12 +30,27 @@ def test_sampling_flops_split_into_projections_and_per_view_work():
     assert w["flops"] - w["tensor_flops"] == simt
 
 
-def test_fp32_form_has_no_tensor_flops():
-    work = accounting.per_view_work(_cfg(synth.PREC_FP32), 8, 1080, 1920)
+def test_fp32_form_tensor_flops_follow_its_paths():
+    # SIMT kernels only: no tensor FLOPs
+    work = accounting.per_view_work(_cfg(synth.PREC_FP32), 8, 1080, 1920, (False, False))
     assert all(v["tensor_flops"] == 0 for v in work.values())
     conv = accounting.per_view_work(_cfg(synth.PREC_BF16), 8, 1080, 1920)["conv_block"]
     E = sum(L * (1080 // k) * (1920 // k) for k, L in _cfg(1).scales)
-    assert conv["tensor_flops"] == 2 * 18 * 32 * 32 * E
+    assert conv["tensor_flops"] == 2 * 18 * 32 * 32 * E and conv["tensor_products"] == 1
+    # split FP16 operands: the same definition FLOPs on the tensor cores, three products each
+    split = accounting.per_view_work(_cfg(synth.PREC_FP32), 8, 1080, 1920, (True, True))
+    bf = accounting.per_view_work(_cfg(synth.PREC_BF16), 8, 1080, 1920)
+    for fam in ("attend", "conv_block"):
+        assert split[fam]["tensor_flops"] == bf[fam]["tensor_flops"] > 0
+        assert split[fam]["tensor_products"] == 3
+    assert split["collapse"]["tensor_flops"] == 0 and split["encode"]["tensor_flops"] == 0
+
+
+def test_split_roofline_takes_a_third_of_the_dense_peak():
+    cfg = _cfg(synth.PREC_FP32)
+    res = {"ktimes": {"conv_block": (4, 4.0), "render": (1, 0.3)}, "tc_paths": (True, True)}
+    r = bench.roofline(cfg, 8, 1080, 1920, res, PEAKS)
+    assert r["bound"] == "tensor" and r["peak"] == round(PEAKS["bf16_tflops_sustained"] / 3, 1)
 
 
 @pytest.mark.parametrize("fam,precision,bound", [("attend", synth.PREC_BF16, "hbm"),
@@ -43,7 +58,7 @@ def test_fp32_form_has_no_tensor_flops():
                                                  ("conv_block", synth.PREC_FP32, "alu")])
 def test_roofline_reports_the_stated_bound_and_names_the_binding_one(fam, precision, bound):
     cfg = _cfg(precision)
-    res = {"ktimes": {fam: (4, 4.0), "render": (1, 0.3)}}
+    res = {"ktimes": {fam: (4, 4.0), "render": (1, 0.3)}}  # FP32: the SIMT kernels (no tc_paths)
     r = bench.roofline(cfg, 8, 1080, 1920, res, PEAKS)
     assert r["kernel"] == fam and r["bound"] == bound
     assert r["frac"] == r["fractions"][bound]
