@@ -23,15 +23,20 @@ namespace quark {
 constexpr int ET_W = 16, ET_H = 8, ET_M = ET_W * ET_H;  // tile (pixels) = M
 constexpr int ET_PW = ET_W + 2, ET_PH = ET_H + 2;       // image patch incl. the 1-pixel halo
 constexpr int ET_K = 32;                                // 27 taps x channels, zero-padded
+// Row stride of the image patch in shared memory, in floats: 80 = 16 (mod 32), so that the two tile
+// rows of a warp (16 pixels at a 3-float stride each) read 32 distinct banks
+constexpr int ET_PROW = 80;
 constexpr uint64_t ET_WAIT_NS = 1000000000ull;
 
 template <int C>
 struct EtSmem {
     static constexpr int a_off = 0;                                 // A: 128 x 32 bf16, K-major
     static constexpr int b_off = a_off + ET_M * ET_K * 2;           // B: C x 32 bf16
-    static constexpr int patch_off = b_off + C * ET_K * 2;          // fp32 [2][10][18][3]
-    static constexpr int l2_off = patch_off + 2 * ET_PH * ET_PW * 3 * 4;  // fp32 level-2 texels [4][8][C]
-    static constexpr int l4_off = l2_off + 4 * 8 * C * 4;           // fp32 level-4 texels [2][4][C]
+    static constexpr int patch_off = b_off + C * ET_K * 2;          // fp32 [2][10][ET_PROW] (18 x 3 used)
+    // level-2 texels at a stride of C + 4 floats: the eight texels a warp stages fall on distinct banks
+    static constexpr int L2S = C + 4;
+    static constexpr int l2_off = patch_off + 2 * ET_PH * ET_PROW * 4;  // fp32 level-2 texels [4][8][L2S]
+    static constexpr int l4_off = l2_off + 4 * 8 * L2S * 4;         // fp32 level-4 texels [2][4][C]
     static constexpr int bias_off = l4_off + 2 * 4 * C * 4;         // fp32 [C]
     static constexpr int bar_off = (bias_off + C * 4 + 7) / 8 * 8;
     static constexpr int total = bar_off + 16;
@@ -53,7 +58,7 @@ __device__ __forceinline__ void et_fetch_patch(const EncodeArgs& a, int tile, in
         const int c = i % 3, px = (i / 3) % ET_PW, py = i / (3 * ET_PW);
         const int gy = Y0 - 1 + py, gx = X0 - 1 + px;
         const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-        et_cp_async4(patch + i, in ? img + ((size_t)gy * a.W + gx) * 3 + c : img, in);
+        et_cp_async4(patch + py * ET_PROW + px * 3 + c, in ? img + ((size_t)gy * a.W + gx) * 3 + c : img, in);
     }
 }
 
@@ -105,9 +110,9 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
     if (tile < ntiles) et_fetch_patch(a, tile, tiles_x, tiles_y, s_patch);
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        float* patch = s_patch + (it & 1) * (ET_PH * ET_PW * 3);
+        float* patch = s_patch + (it & 1) * (ET_PH * ET_PROW);
         if (tile + (int)gridDim.x < ntiles)
-            et_fetch_patch(a, tile + gridDim.x, tiles_x, tiles_y, s_patch + ((it + 1) & 1) * (ET_PH * ET_PW * 3));
+            et_fetch_patch(a, tile + gridDim.x, tiles_x, tiles_y, s_patch + ((it + 1) & 1) * (ET_PH * ET_PROW));
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's patch has landed
         __syncthreads();
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                    for (int ci = 0; ci < 3; ++ci) k[(dy * 3 + dx) * 3 + ci] = patch[((py + dy) * ET_PW + px + dx) * 3 + ci];
+                    for (int ci = 0; ci < 3; ++ci) k[(dy * 3 + dx) * 3 + ci] = patch[(py + dy) * ET_PROW + (px + dx) * 3 + ci];
 #pragma unroll
             for (int i = 27; i < ET_K; ++i) k[i] = 0.f;
 #pragma unroll
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
             }
 #pragma unroll
             for (int c = 0; c < C; c += 4)
-                *reinterpret_cast<float4*>(s_l2 + (y2 * 8 + x2) * C + c) = make_float4(f[c], f[c + 1], f[c + 2], f[c + 3]);
+                *reinterpret_cast<float4*>(s_l2 + (y2 * 8 + x2) * S::L2S + c) = make_float4(f[c], f[c + 1], f[c + 2], f[c + 3]);
         }
         // this tile's TMEM reads, before the next tile's MMA; the level-2 texels for the next means
         umma::fence_before_sync();
@@ -212,9 +217,9 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
                 for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 2; ++dx) {
-                        const float* p = s_l2 + ((2 * y4 + dy) * 8 + 2 * x4 + dx) * C + cp;
-                        s.x += p[0];
-                        s.y += p[1];
+                        const float2 t = *reinterpret_cast<const float2*>(s_l2 + ((2 * y4 + dy) * 8 + 2 * x4 + dx) * S::L2S + cp);
+                        s.x += t.x;
+                        s.y += t.y;
                     }
                 s = make_float2(0.25f * s.x, 0.25f * s.y);
                 s_l4[(y4 * 4 + x4) * C + cp] = s.x;
