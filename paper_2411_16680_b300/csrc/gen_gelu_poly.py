@@ -1,12 +1,13 @@
-"""Coefficients of the polynomial GELU used by the BF16 tensor-core kernels (gelu_poly2 in
-device_common.cuh).
+"""Coefficients of the polynomial GELUs in device_common.cuh: gelu_poly2 (B = 5, degree 11, for
+the BF16 form's layer collapse) and gelu_fine2 (B = 6, degree 16, for the FP32 form: its error is
+FP32 rounding, about 2 ulp).
 
 gelu(x) = x Phi(x) with Phi(x) = 0.5 + x S(x^2) and S(u) = erf(sqrt(u / 2)) / (2 sqrt(u)).
 S is fitted by weighted least squares on Chebyshev nodes of u in [0, B^2], as a polynomial of
 degree DEG in t = 2 u / B^2 - 1 (a well-conditioned basis on [-1, 1]).  The kernel clamps u to
 B^2 and saturates Phi to [0, 1], so |x| > B gives gelu = x or 0.  Printed: the coefficients
 (lowest order first) and the maximum absolute error of an FP32 evaluation against the exact
-erf form on [-12, 12].  Run: python gen_gelu_poly.py
+erf form on [-12, 12], for both fits.  Run: python gen_gelu_poly.py
 """
 import numpy as np
 from scipy.special import erf
@@ -35,8 +36,11 @@ def eval_f32(co, x):
 
 
 if __name__ == "__main__":
-    co = fit()
-    x = np.linspace(-12, 12, 600001)
-    err = np.abs(eval_f32(co, x) - 0.5 * x * (1 + erf(x / np.sqrt(2)))).max()
-    print("B =", B, "degree", DEG, "max abs error", f"{err:.2e}")
-    print(", ".join(f"{float(np.float32(c)):.9e}f" for c in co))
+    for B, DEG in ((5.0, 11), (6.0, 16)):
+        co = fit()
+        x = np.linspace(-12, 12, 600001)
+        ref = 0.5 * x * (1 + erf(x / np.sqrt(2)))
+        err = np.abs(eval_f32(co, x) - ref)
+        print("B =", B, "degree", DEG, "max abs error", f"{err.max():.2e}",
+              "max error relative to max(1, |x|)", f"{np.max(err / np.maximum(1.0, np.abs(x))):.2e}")
+        print(", ".join(f"{float(np.float32(c)):.9e}f" for c in co))

@@ -52,25 +52,48 @@ __global__ void __launch_bounds__(128) collapse_kernel(CollapseArgs a) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) vb[c0 + i] = t[i];
     }
-    float h[C];
+    // packed FP32x2 arithmetic on rows of weights read as float4 (the weight rows are 16-byte
+    // aligned: C is a multiple of 16 and every block of the layout starts at a multiple of C)
+    float2 h[C / 2];
 #pragma unroll
-    for (int c = 0; c < C; ++c) h[c] = w[lay.b1() + c];
+    for (int c = 0; c < C; c += 2) h[c / 2] = make_float2(w[lay.b1() + c], w[lay.b1() + c + 1]);
 #pragma unroll
     for (int i = 0; i < C; ++i) {
-        const float* r0 = &w[lay.w1() + i * C];
-        const float* r1 = &w[lay.w1() + (C + i) * C];
+        const float4* r0 = reinterpret_cast<const float4*>(&w[lay.w1() + i * C]);
+        const float4* r1 = reinterpret_cast<const float4*>(&w[lay.w1() + (C + i) * C]);
+        const float2 xa = make_float2(va[i], va[i]), xb = make_float2(vb[i], vb[i]);
 #pragma unroll
-        for (int c = 0; c < C; ++c) h[c] = fmaf(va[i], r0[c], fmaf(vb[i], r1[c], h[c]));
+        for (int c4 = 0; c4 < C / 4; ++c4) {
+            const float4 p = r0[c4], q = r1[c4];
+            h[2 * c4] = __ffma2_rn(xa, make_float2(p.x, p.y), __ffma2_rn(xb, make_float2(q.x, q.y), h[2 * c4]));
+            h[2 * c4 + 1] = __ffma2_rn(xa, make_float2(p.z, p.w), __ffma2_rn(xb, make_float2(q.z, q.w), h[2 * c4 + 1]));
+        }
+    }
+    float2 o2[C / 2];
+#pragma unroll
+    for (int c = 0; c < C; c += 2)
+        o2[c / 2] = make_float2(0.5f * (va[c] + vb[c]) + w[lay.b2() + c], 0.5f * (va[c + 1] + vb[c + 1]) + w[lay.b2() + c + 1]);
+#pragma unroll
+    for (int i2 = 0; i2 < C / 2; ++i2) {
+        const float2 g = gelu_fine2(h[i2]);  // the erf form to FP32 rounding
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float gk = k ? g.y : g.x;
+            const float2 gg = make_float2(gk, gk);
+            const float4* r = reinterpret_cast<const float4*>(&w[lay.w2() + (2 * i2 + k) * C]);
+#pragma unroll
+            for (int c4 = 0; c4 < C / 4; ++c4) {
+                const float4 p = r[c4];
+                o2[2 * c4] = __ffma2_rn(gg, make_float2(p.x, p.y), o2[2 * c4]);
+                o2[2 * c4 + 1] = __ffma2_rn(gg, make_float2(p.z, p.w), o2[2 * c4 + 1]);
+            }
+        }
     }
     float o[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) o[c] = 0.5f * (va[c] + vb[c]) + w[lay.b2() + c];
-#pragma unroll
-    for (int i = 0; i < C; ++i) {
-        float g = gelu_erf(h[i]);
-        const float* r = &w[lay.w2() + i * C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) o[c] = fmaf(g, r[c], o[c]);
+    for (int c = 0; c < C; c += 2) {
+        o[c] = o2[c / 2].x;
+        o[c + 1] = o2[c / 2].y;
     }
     T* po = reinterpret_cast<T*>(a.out) + e * C;
 #pragma unroll

@@ -33,8 +33,8 @@
 // as x_h w_h + 2^-11 (x_h w_l + x_l w_h) on kind::f16 MMAs (three per K step, into a high and a
 // low accumulator per block): each partial product of 11-bit significands is exact in the FP32
 // accumulator and the dropped x_l w_l term is 2^-22 of the product, so the convolutions keep FP32
-// accuracy at tensor-core rates.  The volume is FP32 in and out, the normalisation, gelu (erf form)
-// and residual run in FP32, and the two halves of an operand take twice the bytes of a BF16 one
+// accuracy at tensor-core rates.  The volume is FP32 in and out, the normalisation, gelu (the erf
+// form to FP32 rounding, gelu_fine2) and residual run in FP32, and the two halves of an operand take twice the bytes of a BF16 one
 // (smaller tiles).  FP16's range bounds the parts: the launcher takes this path only when the
 // weights bound every normalised input and every conv1 output below 2^15 (a check on the host,
 // whatever the volume); otherwise the SIMT kernel (k_conv.cu) runs.
@@ -359,9 +359,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                 const int gy = y0 - 1 + row, gx = x0 - 1 + cx;
                 const bool inside = row < R + 2 && cx < OW + 2 && gy >= 0 && gy < H && gx >= 0 && gx < W;
                 if constexpr (SPLIT) {
-                    // the FP32 form's gelu: the erf form
+                    // the FP32 form's gelu: the erf form to FP32 rounding, on packed pairs
 #pragma unroll
-                    for (int c = 0; c < C; ++c) v[c] = inside ? gelu_erf(v[c] + misc[C + c]) : 0.f;
+                    for (int c = 0; c < C; c += 2) {
+                        const float2 g = gelu_fine2(__fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(misc[C + c], misc[C + c + 1])));
+                        v[c] = inside ? g.x : 0.f;
+                        v[c + 1] = inside ? g.y : 0.f;
+                    }
                     store_pixel_split<C>(s_mid, S::NPIX, idx, v);
                 } else {
 #pragma unroll
