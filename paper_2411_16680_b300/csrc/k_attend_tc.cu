@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         if (a.depth_in) d = __ldg(a.depth_in + de);
         else if (a.depth_out && live && sub == 0) a.depth_out[de] = d;
     }
-    const float rinv = 1.0f / sqrtf(ms / C + 1e-6f);
+    const float rinv = rsqrtf(ms / C + 1e-6f);  // 2 ulp, on the special-function unit
     if constexpr (SPLIT) {
         // this thread's 16 channels of X = N(V_in) as FP16 parts: two 8-channel groups per part,
         // K-major A layout (group g of row m at g * 128 * 16 + m * 16, the low part's groups after

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
                     float ms = 0.f;
 #pragma unroll
                     for (int c = 0; c < C; ++c) ms = fmaf(v[c], v[c], ms);
-                    const float r = in[u] ? 1.0f / sqrtf(ms / C + 1e-6f) : 0.f;
+                    // rsqrt on the special-function unit (2 ulp): the per-pixel chain stays short
+                    const float r = in[u] ? rsqrtf(ms / C + 1e-6f) : 0.f;
 #pragma unroll
                     for (int c = 0; c < C; ++c) v[c] = v[c] * r * misc[c];
                     if constexpr (SPLIT) store_pixel_split<C>(s_in, S::NPIX, p, v);
