@@ -540,11 +540,11 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
         ctx->wtc = nullptr;
         ctx->wtc_bytes = 0;
+        ctx->wtc_step_bytes = 4 * 9 * (size_t)C * C * sizeof(uint16_t);
         bool split = C <= 32 && c.conv_kernel != 1;
         for (int j = 0; j < c.n_scales && split; ++j)
             split = conv_split_in_range(w->conv_g[j], cw1[j], w->conv1_b[j], cw2[j], C);
         if (split) {
-            ctx->wtc_step_bytes = 4 * 9 * (size_t)C * C * sizeof(uint16_t);
             std::vector<uint16_t> tc(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
             const size_t n = 9 * (size_t)C * C;
             for (int j = 0; j < c.n_scales; ++j) {
@@ -556,6 +556,27 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             s = qk_alloc(ctx, &ctx->wtc, ctx->wtc_bytes);
             if (s != QUARK_OK) return s;
             QK_CUDA(ctx, cudaMemcpy(ctx->wtc, tc.data(), ctx->wtc_bytes, cudaMemcpyHostToDevice));
+        }
+        // render-and-refine: the Update Blocks' residual CNN likewise, per step at j * wtc_step_bytes
+        qk_free(ctx, ctx->wupd, ctx->wupd_bytes);
+        ctx->wupd = nullptr;
+        ctx->wupd_bytes = 0;
+        bool usplit = C <= 32 && c.render_refine;
+        for (int j = 0; j < c.n_scales && usplit; ++j)
+            if (qk_refines(c, j)) usplit = conv_split_in_range(w->upd_g[j], w->upd1_w[j], w->upd1_b[j], w->upd2_w[j], C);
+        if (usplit) {
+            std::vector<uint16_t> up(ctx->wtc_step_bytes / sizeof(uint16_t) * c.n_scales);
+            const size_t n = 9 * (size_t)C * C;
+            for (int j = 0; j < c.n_scales; ++j) {
+                if (!qk_refines(c, j)) continue;
+                uint16_t* d = up.data() + (size_t)j * 4 * n;
+                pack_conv_weights_f16split(w->upd1_w[j], C, d, d + n);
+                pack_conv_weights_f16split(w->upd2_w[j], C, d + 2 * n, d + 3 * n);
+            }
+            ctx->wupd_bytes = up.size() * sizeof(uint16_t);
+            s = qk_alloc(ctx, &ctx->wupd, ctx->wupd_bytes);
+            if (s != QUARK_OK) return s;
+            QK_CUDA(ctx, cudaMemcpy(ctx->wupd, up.data(), ctx->wupd_bytes, cudaMemcpyHostToDevice));
         }
         // the one-to-many attention's projections likewise (C <= 32): [W^q | W^beta] and W^O in the
         // BF16 form's element order and logit-scale folding, as FP16 high parts then scaled

@@ -34,7 +34,7 @@ struct quark_ctx {
     size_t off_std[QUARK_MAX_SCALES] = {};  // standard attention weights (StdLayout), or (size_t)-1
     size_t off_ray[4] = {};                   // ray encoding projection per level index, or (size_t)-1
     size_t off_upd[QUARK_MAX_SCALES] = {};    // Update Block (ConvLayout, then W_r, b_r), or (size_t)-1
-    void* wupd = nullptr;                     // BF16 form: Update Block convs packed as tcgen05 B operands
+    void* wupd = nullptr;                     // Update Block convs packed as tcgen05 B operands (FP32 form: split)
     size_t wupd_bytes = 0;
     // BF16 form: conv weights packed as tcgen05 B operands, per step W1 then W2
     void* wtc = nullptr;
