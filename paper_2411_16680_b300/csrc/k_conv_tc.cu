@@ -18,12 +18,16 @@
 // (OW, R) per plane size to minimise MMA blocks per output (tall narrow tiles waste least: two
 // columns per row instead of a part-empty last block), with enough tiles for every SM.
 //
-// One persistent CTA per SM, warp-specialised, strides over the tiles with two input buffers:
-//   loader warps (4)    normalise tile k into buffer k % 2 once conv2 of tile k - 2 has released it;
-//   MMA warp (1 thread) conv1 of tile k into TMEM columns [0, 256) once its input is ready and the
-//                       epilogue has read conv1 of tile k - 1; conv2 into columns [256, 512) once
-//                       the mid tile is written and the epilogue has read conv2 of tile k - 1;
-//   epilogue warps (8)  gelu(conv1) -> mid tile (in the input buffer, which conv1 has read), then
+// Persistent warp-specialised CTAs stride over the tiles with two input buffers each: two per SM in
+// the BF16 form at C <= 32 (2 loader and 4 epilogue warps and half the TMEM each, so that one CTA's
+// GELU and stores overlap the other's MMAs: 1080p conv block 1.51 -> 1.40 ms), one per SM where the
+// weights fill the shared memory (the FP32 form's split operands, C = 64; 4 loader and 8 epilogue
+// warps):
+//   loader warps        normalise tile k into buffer k % 2 once conv2 of tile k - 2 has released it;
+//   MMA warp (1 thread) conv1 of tile k into the first half of the CTA's TMEM columns once its input
+//                       is ready and the epilogue has read conv1 of tile k - 1; conv2 into the second
+//                       half once the mid tile is written and the epilogue has read conv2 of tile k - 1;
+//   epilogue warps      gelu(conv1) -> mid tile (in the input buffer, which conv1 has read), then
 //                       the residual and the stores of conv2,
 // so the loads of one tile, the MMAs of the next and the epilogues of the previous overlap.  The
 // packed weights are staged once.  mbarriers order the roles; every wait is bounded.
@@ -48,9 +52,6 @@
 namespace quark {
 
 constexpr int TC_M = 128;
-constexpr int TC_LOAD_WARPS = 4, TC_EPI_WARPS = 8;
-constexpr int TC_MMA_WARP = TC_LOAD_WARPS;  // the warp after the loaders
-constexpr int TC_THREADS = 32 * (TC_LOAD_WARPS + 1 + TC_EPI_WARPS);
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s bound on every wait
 
 // Tile geometry of one launch (host-chosen): pitch P = OW + 4, R output rows, NB1 / NB2 MMA blocks
@@ -63,10 +64,15 @@ template <int C, bool SPLIT>
 struct TcSmem {
     static constexpr int G = C / 8;
     static constexpr int PLANES = SPLIT ? 2 : 1;  // operand parts: BF16, or FP16 high and scaled low
-    // pixels of an input / mid tile buffer (two buffers and both convs' weights in 227 KB; at
-    // C = 64 the weights alone take 144 KB)
-    static constexpr int NPIX = SPLIT ? (C == 32 ? 600 : 1600) : (C == 64 ? 312 : C == 32 ? 1152 : 2304);
-    static constexpr int NB_MAX = 256 / (PLANES * C);   // MMA blocks per conv in half the TMEM
+    static constexpr int CTAS = (!SPLIT && C <= 32) ? 2 : 1;  // CTAs per SM
+    static constexpr int LOAD_WARPS = CTAS == 2 ? 2 : 4, EPI_WARPS = CTAS == 2 ? 4 : 8;
+    static constexpr int MMA_WARP = LOAD_WARPS;  // the warp after the loaders
+    static constexpr int THREADS = 32 * (LOAD_WARPS + 1 + EPI_WARPS);
+    static constexpr int TMEM_COLS = 512 / CTAS;  // conv1 in the first half, conv2 in the second
+    // pixels of an input / mid tile buffer (two buffers and both convs' weights in the CTA's share of
+    // the 228 KB; at C = 64 the weights alone take 144 KB)
+    static constexpr int NPIX = SPLIT ? (C == 32 ? 600 : 1600) : (C == 64 ? 312 : C == 32 ? 576 : 1152);
+    static constexpr int NB_MAX = TMEM_COLS / 2 / (PLANES * C);  // MMA blocks per conv in half the TMEM
     // a tile's mid tile reuses its input buffer: conv1 has finished reading it when the epilogue
     // writes gelu(conv1).  Channel group g of part q at (q G + g) NPIX 16.
     static constexpr int buf_bytes = PLANES * G * NPIX * 16;  // input buffers b = 0, 1 at b * buf_bytes
@@ -79,7 +85,7 @@ struct TcSmem {
     static constexpr int bar_off = (misc_off + misc_n * 4 + 7) / 8 * 8;
     static constexpr int err_off = bar_off + 9 * 8;
     static constexpr int total = err_off + 16;
-    static_assert(total + 1024 <= 233472, "one CTA per SM");
+    static_assert(CTAS * (total + 1024) <= 233472, "the CTAs of an SM fit its shared memory");
 };
 
 template <int C>
@@ -129,8 +135,11 @@ __device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[C]) {
 }
 
 template <int C, bool SPLIT>
-__global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const ConvArgs a, const ConvTile tg) {
+__global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::CTAS)
+    conv_block_tc_kernel(const ConvArgs a, const ConvTile tg) {
     using S = TcSmem<C, SPLIT>;
+    constexpr int TC_LOAD_WARPS = S::LOAD_WARPS, TC_EPI_WARPS = S::EPI_WARPS, TC_MMA_WARP = S::MMA_WARP;
+    constexpr int TC_THREADS = S::THREADS;
     const ConvLayout lay{C};
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_w1 = sm + S::w1_off;
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
             d2[i] = __ldg(src + n + i);
         }
     }
-    if (warp == 0) umma::tmem_alloc(tslot, 512);
+    if (warp == 0) umma::tmem_alloc(tslot, S::TMEM_COLS);
     if (tid == 0) {
         umma::mbar_init(full, NLOAD);
         umma::mbar_init(full + 1, NLOAD);
@@ -196,7 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     constexpr uint32_t idesc = SPLIT ? umma::idesc_f16_f32(TC_M, C) : umma::idesc_bf16_f32(TC_M, C);
     constexpr uint32_t LBO_W = C * 16;        // B: N = C rows of 16 B per core-matrix column
     constexpr uint32_t LBO_A = S::NPIX * 16;  // A: channel-group stride of an input / mid tile
-    constexpr uint32_t TB = 256;              // TMEM column of conv2's accumulators
+    constexpr uint32_t TB = S::TMEM_COLS / 2;  // TMEM column of conv2's accumulators
     // SPLIT: the low parts, as descriptor start-address offsets (16-byte units)
     constexpr uint32_t A_LO = (S::G * LBO_A) >> 4, W_LO = (9 * C * C * 2) >> 4;
 
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_block_tc_kernel(const Conv
     __syncthreads();
     umma::fence_after_sync();
     if (tid == 0 && *s_err) atomicExch(a.err, *s_err & 2 ? 2 : 1);
-    if (warp == 0) umma::tmem_dealloc(tmem, 512);
+    if (warp == 0) umma::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 // Tile geometry for a W x H plane (L planes) that minimises the MMA blocks of the busiest CTA: for
@@ -528,14 +537,14 @@ static cudaError_t launch_tc(const ConvArgs& a, cudaStream_t st) {
     for (const Entry& c : cache)
         if (c.t.P && c.W == a.W && c.H == a.H && c.L == a.L) tg = c.t;
     if (!tg.P) {
-        tg = choose_tile<C, SPLIT>(a.W, a.H, a.L, sms);
+        tg = choose_tile<C, SPLIT>(a.W, a.H, a.L, TcSmem<C, SPLIT>::CTAS * sms);
         if (!tg.P) return cudaErrorInvalidValue;
         cache[next] = Entry{a.W, a.H, a.L, tg};
         next = (next + 1) % 8;
     }
     const long ntiles = (long)tg.tiles_x * tg.tiles_y * a.L;
-    const int grid = (int)std::min<long>(ntiles, (long)sms);
-    k<<<grid, TC_THREADS, smem, st>>>(a, tg);
+    const int grid = (int)std::min<long>(ntiles, (long)TcSmem<C, SPLIT>::CTAS * sms);
+    k<<<grid, TcSmem<C, SPLIT>::THREADS, smem, st>>>(a, tg);
     return cudaGetLastError();
 }
 
@@ -546,12 +555,12 @@ cudaError_t conv_tc_tile_shape(int C, bool split, int W, int H, int L, int* cols
     if (e != cudaSuccess) return e;
     ConvTile t{};
     if (split) {
-        if (C == 16) t = choose_tile<16, true>(W, H, L, sms);
-        else if (C == 32) t = choose_tile<32, true>(W, H, L, sms);
+        if (C == 16) t = choose_tile<16, true>(W, H, L, TcSmem<16, true>::CTAS * sms);
+        else if (C == 32) t = choose_tile<32, true>(W, H, L, TcSmem<32, true>::CTAS * sms);
     } else {
-        if (C == 16) t = choose_tile<16, false>(W, H, L, sms);
-        else if (C == 32) t = choose_tile<32, false>(W, H, L, sms);
-        else if (C == 64) t = choose_tile<64, false>(W, H, L, sms);
+        if (C == 16) t = choose_tile<16, false>(W, H, L, TcSmem<16, false>::CTAS * sms);
+        else if (C == 32) t = choose_tile<32, false>(W, H, L, TcSmem<32, false>::CTAS * sms);
+        else if (C == 64) t = choose_tile<64, false>(W, H, L, TcSmem<64, false>::CTAS * sms);
     }
     if (!t.P) return cudaErrorInvalidValue;
     *cols = t.P - 4;
