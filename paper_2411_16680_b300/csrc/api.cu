@@ -302,6 +302,7 @@ extern "C" quark_status quark_destroy(quark_ctx* ctx) {
     qk_free(ctx, ctx->wdev, ctx->wbytes);
     qk_free(ctx, ctx->wtc, ctx->wtc_bytes);
     qk_free(ctx, ctx->wat, ctx->wat_bytes);
+    qk_free(ctx, ctx->wcol, ctx->wcol_bytes);
     qk_free(ctx, ctx->wupd, ctx->wupd_bytes);
     qk_free(ctx, ctx->wenc, ctx->wenc_bytes);
     qk_free(ctx, ctx->dev_err, sizeof(int));
@@ -556,6 +557,52 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
             s = qk_alloc(ctx, &ctx->wtc, ctx->wtc_bytes);
             if (s != QUARK_OK) return s;
             QK_CUDA(ctx, cudaMemcpy(ctx->wtc, tc.data(), ctx->wtc_bytes, cudaMemcpyHostToDevice));
+        }
+        // the layer collapses' MLP likewise (C <= 32): W1 (N = C, K = 2C) and W2 (K = C) in the BF16
+        // form's element order, FP16 high parts then scaled remainders; the kernel scales each
+        // element's activations by a power of two, so only the weights bound the parts
+        qk_free(ctx, ctx->wcol, ctx->wcol_bytes);
+        ctx->wcol = nullptr;
+        ctx->wcol_bytes = 0;
+        {
+            bool csplit = C <= 32, any = false;
+            auto small = [](double v) { return std::fabs(v) < 32768.0; };
+            for (int j = 0; j < c.n_scales && csplit; ++j) {
+                if (ctx->off_collapse[j] == (size_t)-1) continue;
+                any = true;
+                for (size_t i = 0; i < 2 * (size_t)C * C && csplit; ++i) csplit = small(w->col_w1[j][i]);
+                for (size_t i = 0; i < (size_t)C * C && csplit; ++i) csplit = small(w->col_w2[j][i]);
+            }
+            if (csplit && any) {
+                size_t total = 0;
+                for (int j = 0; j < c.n_scales; ++j) {
+                    ctx->off_wcol[j] = total * sizeof(uint16_t);
+                    if (ctx->off_collapse[j] != (size_t)-1) total += 2 * 3 * (size_t)C * C;
+                }
+                std::vector<uint16_t> cb(total);
+                auto put_split = [](uint16_t* hi, uint16_t* lo, size_t i, float x) {
+                    const __half hh = __float2half_rn(x);
+                    hi[i] = __half_as_ushort(hh);
+                    lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(hh)) * 2048.f));
+                };
+                for (int j = 0; j < c.n_scales; ++j) {
+                    if (ctx->off_collapse[j] == (size_t)-1) continue;
+                    uint16_t* b1 = cb.data() + ctx->off_wcol[j] / sizeof(uint16_t);
+                    uint16_t* b1l = b1 + 2 * (size_t)C * C;
+                    uint16_t* b2 = b1l + 2 * (size_t)C * C;
+                    uint16_t* b2l = b2 + (size_t)C * C;
+                    for (int n = 0; n < C; ++n) {
+                        for (int k = 0; k < 2 * C; ++k)
+                            put_split(b1, b1l, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->col_w1[j][(size_t)k * C + n]);
+                        for (int k = 0; k < C; ++k)
+                            put_split(b2, b2l, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->col_w2[j][(size_t)k * C + n]);
+                    }
+                }
+                ctx->wcol_bytes = cb.size() * sizeof(uint16_t);
+                s = qk_alloc(ctx, &ctx->wcol, ctx->wcol_bytes);
+                if (s != QUARK_OK) return s;
+                QK_CUDA(ctx, cudaMemcpy(ctx->wcol, cb.data(), ctx->wcol_bytes, cudaMemcpyHostToDevice));
+            }
         }
         // render-and-refine: the Update Blocks' residual CNN likewise, per step at j * wtc_step_bytes
         qk_free(ctx, ctx->wupd, ctx->wupd_bytes);
@@ -1432,9 +1479,13 @@ quark_status qk_decode(quark_ctx* ctx, int scale, const void* vol, int L, int H,
     return qk_launch(ctx, st, KF_CONV, [&] { return launch_decode(da, c.C, c.precision == QUARK_BF16, st); });
 }
 
-// Packed BF16 collapse weights of step `scale` (after the step's attention packs), or NULL.
+// Packed collapse weights of step `scale`: BF16 (after the step's attention packs), or the FP32
+// form's split parts; NULL where the step has none (or the FP32 form keeps the SIMT kernel).
 const void* qk_collapse_wtc(const quark_ctx* ctx, int scale) {
-    if (!ctx->wat || ctx->cfg.precision != QUARK_BF16) return nullptr;
+    if (ctx->cfg.precision != QUARK_BF16)
+        return ctx->wcol && ctx->off_collapse[scale] != (size_t)-1 ? (const uint8_t*)ctx->wcol + ctx->off_wcol[scale]
+                                                                    : nullptr;
+    if (!ctx->wat) return nullptr;
     const quark_config& c = ctx->cfg;
     const int h = qk_heads(c, scale);
     const size_t att_bytes = h > 0 ? ((size_t)(h * c.C + c.C) * c.C + (size_t)c.C * h * c.C) * 2 : 0;

@@ -44,6 +44,10 @@ struct quark_ctx {
     // operands, per step at byte offset off_wat[j]
     void* wat = nullptr;
     size_t wat_bytes = 0;
+    // FP32 form: the layer collapses' MLP as split FP16 B operands, per step at byte offset off_wcol[j]
+    void* wcol = nullptr;
+    size_t wcol_bytes = 0;
+    size_t off_wcol[QUARK_MAX_SCALES] = {};
     size_t off_wat[QUARK_MAX_SCALES] = {};
     // BF16 form: the encoder conv packed as a tcgen05 B operand (C x 32)
     void* wenc = nullptr;

@@ -105,9 +105,11 @@ __global__ void __launch_bounds__(128) collapse_kernel(CollapseArgs a) {
     }
 }
 
-// FP32 form: this SIMT kernel.  BF16 form: both MLP layers on tcgen05 (k_collapse_tc.cu).
+// BF16 form: both MLP layers on tcgen05 (k_collapse_tc.cu).  FP32 form: the same kernel on split
+// FP16 operands when the context packed them (C <= 32), else this SIMT kernel.
 cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st) {
-    if (bf16) return launch_collapse_tc(a, C, st);
+    if (bf16) return launch_collapse_tc(a, C, false, st);
+    if (a.wtc && C <= 32) return launch_collapse_tc(a, C, true, st);
     size_t n = (size_t)a.L * a.H * a.W;
     unsigned grid = (unsigned)((n + 127) / 128);
     auto run = [&](auto k, int Cv) {

@@ -187,7 +187,8 @@ struct CollapseLayout {
 cudaError_t launch_encode(const EncodeArgs& a, int C, bool bf16, cudaStream_t st);
 cudaError_t launch_encode_tc(const EncodeArgs& a, int C, const void* wtc, int* err, cudaStream_t st);
 cudaError_t launch_collapse(const CollapseArgs& a, int C, bool bf16, cudaStream_t st);
-cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, cudaStream_t st);
+// split: the FP32 form on FP16 operand parts (CollapseArgs.wtc from the context's split packs)
+cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, bool split, cudaStream_t st);
 cudaError_t launch_attend(const AttendArgs& a, int C, int heads, Transition tr, bool last, bool bf16,
                           cudaStream_t st);
 cudaError_t launch_conv_block(const ConvArgs& a, int C, bool bf16, cudaStream_t st);
