@@ -63,6 +63,38 @@ Rect = Tuple[int, int, int, int]  # y0, y1, x0, x1 (half-open), in plane coordin
 
 
 # ---------------------------------------------------------------------------------------------
+# LDM grids (Sec. 3.2: the step's grid factor relative to the output; Sec. 4: for outputs whose
+# aspect differs from the model's, the LDM keeps its pixel count and the final upsample adapts)
+# ---------------------------------------------------------------------------------------------
+
+def ldm_shape(cfg, j: int) -> Tuple[int, int, int]:
+    """(L, H, W) of step j's LDM.  By default H = out_h / f_j and W = out_w / f_j for the step's
+    grid factor f_j.  With a model size (model_w x model_h, aspect-adaptive): the coarsest grid has
+    the model's area per layer at the output's aspect, h0 = round(sqrt(area / aspect)) and
+    w0 = round(h0 * aspect), and step j's grid is that times f_0 / f_j (the finer grids are its x2
+    multiples)."""
+    L = cfg.scales[j][1]
+    f = cfg.f_of(j)
+    if cfg.model_w:
+        f0 = cfg.f_of(0)
+        area = (cfg.model_h / f0) * (cfg.model_w / f0)
+        aspect = cfg.out_w / cfg.out_h
+        h0 = max(1, int(math.floor(math.sqrt(area / aspect) + 0.5)))
+        w0 = max(1, int(math.floor(h0 * aspect + 0.5)))
+        m = int(round(f0 / f))
+        return L, h0 * m, w0 * m
+    H, W = int(round(cfg.out_h / f)), int(round(cfg.out_w / f))
+    assert abs(H * f - cfg.out_h) < 1e-6 and abs(W * f - cfg.out_w) < 1e-6, "output not divisible by f"
+    return L, H, W
+
+
+def grid_factors(cfg, j: int) -> Tuple[float, float]:
+    """Step j's grid factors (rows, columns): the output size over the grid size."""
+    _, H, W = ldm_shape(cfg, j)
+    return cfg.out_h / H, cfg.out_w / W
+
+
+# ---------------------------------------------------------------------------------------------
 # Elementwise definitions
 # ---------------------------------------------------------------------------------------------
 
@@ -422,8 +454,8 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
     or, with render-and-refine, the Update Block's output (delta_fetch, one fetcher per view)."""
     f64 = lambda a: np.asarray(a, np.float64)
     k, L = cfg.scales[j]          # pyramid level of the views, layers
-    f = cfg.fyx_of(j)             # LDM grid factors (rows, columns) relative to the output
-    _, H, Wd = cfg.ldm_shape(j)
+    f = grid_factors(cfg, j)      # LDM grid factors (rows, columns) relative to the output
+    _, H, Wd = ldm_shape(cfg, j)
     heads = cfg.heads_of(j)
     C = cfg.C
     ys = np.arange(rect_attn[0], rect_attn[1])[:, None]
@@ -436,7 +468,7 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
         V_in = np.broadcast_to(f64(W["v0"]), (L, h, w, C)).copy()
         d = np.broadcast_to(1.0 / ((ell - 0.5) / L * (1 / cfg.near - 1 / cfg.far) + 1 / cfg.far), (L, h, w)).copy()
     else:
-        Lp, Hp, Wp = cfg.ldm_shape(j - 1)
+        Lp, Hp, Wp = ldm_shape(cfg, j - 1)
         Vp, rp = prev.V_out, prev.rect_out
         if Lp == 2 * L:
             Vp = layer_collapse(Vp, f64(W[f"col_w1_{j}"]), f64(W[f"col_b1_{j}"]),
@@ -502,8 +534,8 @@ def update_fuse_step(cfg, W, scene, fetchers, j, prev: Optional[StepResult],
 
 def render_rect(cfg, scene, last: StepResult, out_rect: Rect, return_layers: bool = False):
     """RGBA of the novel view on out_rect (full output resolution)."""
-    L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
-    s = cfg.upsample_syx
+    L, Hl, Wl = ldm_shape(cfg, cfg.n_scales - 1)
+    s = grid_factors(cfg, cfg.n_scales - 1)
     rect_beta = last.rect_attn
     ob = (last.rect_out[0] - rect_beta[0], last.rect_out[2] - rect_beta[2])
     hb, wb = last.V_out.shape[1], last.V_out.shape[2]
@@ -550,8 +582,8 @@ def render_depth_rect(cfg, last: StepResult, out_rect: Rect):
     last LDM are upsampled and activated exactly as for the colour render; then, front (l = L) to
     back, D += T alpha_l d_l and T *= 1 - alpha_l, with 0 behind the last layer.  Reading: the
     over-composite itself, not normalised by the accumulated alpha."""
-    L, Hl, Wl = cfg.ldm_shape(cfg.n_scales - 1)
-    s = cfg.upsample_syx
+    L, Hl, Wl = ldm_shape(cfg, cfg.n_scales - 1)
+    s = grid_factors(cfg, cfg.n_scales - 1)
     t_up = resize_rect(last.t[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
     s_up = resize_rect(last.s[..., None], last.rect_out, Hl, Wl, s, out_rect)[..., 0]
     ell = np.arange(1, L + 1, dtype=np.float64)[:, None, None]
@@ -690,7 +722,7 @@ def refine_features(cfg, W, scene, fetchers, j, prev: StepResult):
     if Lp == 2 * L:
         Vc = layer_collapse(Vc, f64(W[f"col_w1_{j}"]), f64(W[f"col_b1_{j}"]), f64(W[f"col_w2_{j}"]),
                             f64(W[f"col_b2_{j}"]))
-    It = render_to_views(cfg, W, scene, Vc, cfg.fyx_of(j - 1), kp)
+    It = render_to_views(cfg, W, scene, Vc, grid_factors(cfg, j - 1), kp)
     out = []
     for m, lf in enumerate(fetchers[k]):
         lf.prepare([np.array([0, lf.h - 1])], [np.array([0, lf.w - 1])])  # the whole level (+ gamma)
@@ -705,8 +737,8 @@ def refine_features(cfg, W, scene, fetchers, j, prev: StepResult):
 def plan_rects(cfg, out_rect: Rect):
     """Windows each scale must compute so that out_rect of the final render is exact."""
     n = cfg.n_scales
-    _, Hl, Wl = cfg.ldm_shape(n - 1)
-    sy, sx = cfg.upsample_syx
+    _, Hl, Wl = ldm_shape(cfg, n - 1)
+    sy, sx = grid_factors(cfg, n - 1)
     ys = np.arange(out_rect[0], out_rect[1])
     xs = np.arange(out_rect[2], out_rect[3])
     y0, y1, _ = resize_taps(ys, sy, Hl)
@@ -715,11 +747,11 @@ def plan_rects(cfg, out_rect: Rect):
     rect_out = [None] * n
     rect_attn = [None] * n
     for j in range(n - 1, -1, -1):
-        _, H, W = cfg.ldm_shape(j)
+        _, H, W = ldm_shape(cfg, j)
         rect_out[j] = need
         rect_attn[j] = grow(need, 2, H, W)
         if j > 0:
-            _, Hp, Wp = cfg.ldm_shape(j - 1)
+            _, Hp, Wp = ldm_shape(cfg, j - 1)
             ratio = H // Hp
             ys = np.arange(rect_attn[j][0], rect_attn[j][1])
             xs = np.arange(rect_attn[j][2], rect_attn[j][3])

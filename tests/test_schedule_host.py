@@ -1,8 +1,11 @@
 """Model schedules on the host: the Quark workload follows the paper's model table (appendix,
-table "Model description for Quark"), and the C ABI rejects schedules its steps cannot run."""
+table "Model description for Quark"), the LDM grid rule of the oracle (Sec. 3.2; Sec. 4 for the
+aspect-adaptive reading) gives those tables' grids and equals the sizes the input module uses,
+and the C ABI rejects schedules its steps cannot run."""
 import pytest
 import torch
 
+from oracle import quark_oracle as O
 from paper_2411_16680_b300 import quark, synth
 
 
@@ -17,7 +20,7 @@ def test_quark_workload_matches_the_model_table():
     table_feat = [(36, 60), (36, 60), (72, 120), (72, 120), (144, 240), (288, 480)]
     table_blocks = [[4, 0, 4, 0, 4, 0]] * 3 + [[4, 4], [2, 2], [1, 1]]
     for (a, b), out, feat, blocks in zip(groups, table_out, table_feat, table_blocks):
-        assert all(cfg.ldm_shape(j) == out for j in range(a, b))
+        assert all(O.ldm_shape(cfg, j) == out for j in range(a, b))
         assert all((288 // cfg.scales[j][0], 480 // cfg.scales[j][0]) == feat for j in range(a, b))
         assert [cfg.heads_of(j) for j in range(a, b)] == blocks
         # one set of update features per step: only the step's first block decodes depths
@@ -75,3 +78,36 @@ def test_valid_schedules_pass_validation():
         with pytest.raises(quark.QuarkError) as e:
             quark.Context(cfg)
         assert e.value.status == quark.ECUDA  # past validation, stopped only by the missing device
+
+
+@pytest.mark.parametrize("cfg", [
+    synth.config_1080p(), synth.config_small(), synth.config_grad(), synth.config_quark(), synth.config_quarkplus(),
+    synth.config_quark(out_w=1024, out_h=768).replace(model_w=1920, model_h=1080),
+    synth.config_quark(out_w=2048, out_h=1536).replace(model_w=1920, model_h=1080),
+    synth.config_quarkplus(out_w=1024, out_h=768).replace(model_w=1920, model_h=1080),
+    synth.config_quark(out_w=200, out_h=130).replace(model_w=240, model_h=120),
+], ids=["1080p", "small", "grad", "quark", "quarkplus", "quark_1024x768", "quark_2048x1536", "quarkplus_1024x768",
+        "anisotropic_200x130"])
+def test_input_sizes_follow_the_oracle_grid_rule(cfg):
+    """The input module sizes buffers and reads with its own copy of the grid rule; it must give the
+    oracle's grids and factors at every step (the CUDA path computes them a third time, in the ABI)."""
+    for j in range(cfg.n_scales):
+        assert cfg.ldm_shape(j) == O.ldm_shape(cfg, j)
+        assert cfg.fyx_of(j) == pytest.approx(O.grid_factors(cfg, j), rel=0, abs=0)
+
+
+def test_aspect_adaptive_grids_keep_the_model_area():
+    """Sec. 4: at another aspect the LDM keeps the model's pixel count per layer (to rounding) and
+    its grids stay x2 multiples of the coarsest; at the model's own size the rule is the identity."""
+    model = synth.config_quark()
+    for w, h in ((1024, 768), (2048, 1536), (1280, 720), (3840, 2160)):
+        cfg = synth.config_quark(out_w=w, out_h=h).replace(model_w=1920, model_h=1080)
+        for j in range(cfg.n_scales):
+            _, H, W = O.ldm_shape(cfg, j)
+            _, Hm, Wm = O.ldm_shape(model, j)
+            assert abs(H * W - Hm * Wm) / (Hm * Wm) < 0.05
+            assert abs(W / H - w / h) < 0.05 * w / h
+            _, H0, W0 = O.ldm_shape(cfg, 0)
+            assert H % H0 == 0 and W % W0 == 0 and H // H0 == W // W0
+    same = synth.config_quark().replace(model_w=1920, model_h=1080)
+    assert [O.ldm_shape(same, j) for j in range(same.n_scales)] == [O.ldm_shape(model, j) for j in range(model.n_scales)]
