@@ -72,9 +72,14 @@ typedef struct {
  *              f_j = ldm_f[j], or k[j] where ldm_f[j] is 0; f[j-1]/f[j] in {1,2} (x2 spatial
  *              upsample).  The final render upsamples by s = f of the last step (e.g. 3.75).
  *   near_m, far_m  near and far planes eta and f of Eq. (depth_activation), 0 < near < far
- *   precision  QUARK_FP32 (all storage and arithmetic FP32) or QUARK_BF16 (pyramid and
- *              feature volume stored in BF16, contractions on tensor cores with FP32
- *              accumulation; geometry, softmax and transmittance stay FP32)
+ *   precision  QUARK_FP32 (all storage FP32, arithmetic to FP32 accuracy: the conv blocks, the
+ *              sampling kernel's projections, the layer collapse and the Update Block run on
+ *              tensor cores with each operand split into two FP16 parts and three products per
+ *              FP32 product -- error at FP32 rounding -- where the weights keep every part in
+ *              FP16 range (C <= 32), on SIMT kernels otherwise; see quark_tensor_core_paths) or
+ *              QUARK_BF16 (pyramid and feature volume stored in BF16, contractions on tensor
+ *              cores with BF16 operands and FP32 accumulation; geometry, softmax and
+ *              transmittance stay FP32)
  *   attn_mode  QUARK_ATTN_ONE_TO_MANY (the paper's optimized attention: no K/V projections)
  *              or QUARK_ATTN_STANDARD (textbook multi-head cross attention, Sec. 3.3 Eq.
  *              MultiHead: keys and values are the sampled features times W^k and W^val, here
