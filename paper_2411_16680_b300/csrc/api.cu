@@ -333,18 +333,25 @@ static void pack_conv_weights_bf16(const float* w, int C, uint16_t* dst) {
                     to_bf16_bits(w[((size_t)tap * C + ci) * C + co]);
 }
 
-// FP32 form on the tensor cores: the same B layout as pack_conv_weights_bf16 in FP16, the rounded
-// weights (hi) and then the scaled remainders fp16((w - hi) 2^11) (lo), 9 C C elements each.
+// FP32 form on the tensor cores: a value as its FP16 parts, the rounded value hi[i] = fp16(x) and the
+// scaled remainder lo[i] = fp16((x - hi) 2^11) (x - hi is exact in FP32, the scaling too).  The
+// parts stay finite while |x| < kSplitMax; the kernels take x_h w_h + 2^-11 (x_h w_l + x_l w_h).
+constexpr double kSplitMax = 32768.0;
+static void put_f16split(uint16_t* hi, uint16_t* lo, size_t i, float x) {
+    const __half h = __float2half_rn(x);
+    hi[i] = __half_as_ushort(h);
+    lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(h)) * 2048.f));
+}
+static bool in_split_range(double v) { return std::fabs(v) < kSplitMax; }
+
+// The same B layout as pack_conv_weights_bf16 in FP16 parts: the rounded weights (hi), then the
+// scaled remainders (lo), 9 C C elements each.
 static void pack_conv_weights_f16split(const float* w, int C, uint16_t* hi, uint16_t* lo) {
     for (int tap = 0; tap < 9; ++tap)
         for (int ci = 0; ci < C; ++ci)
-            for (int co = 0; co < C; ++co) {
-                const float x = w[((size_t)tap * C + ci) * C + co];
-                const __half h = __float2half_rn(x);
-                const size_t i = (size_t)tap * C * C + (ci / 8) * C * 8 + co * 8 + ci % 8;
-                hi[i] = __half_as_ushort(h);
-                lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(h)) * 2048.f));
-            }
+            for (int co = 0; co < C; ++co)
+                put_f16split(hi, lo, (size_t)tap * C * C + (ci / 8) * C * 8 + co * 8 + ci % 8,
+                             w[((size_t)tap * C + ci) * C + co]);
 }
 
 // Whether every FP16 part the split conv block forms stays below 2^15, for any volume: the
@@ -352,19 +359,18 @@ static void pack_conv_weights_f16split(const float* w, int C, uint16_t* hi, uint
 // sum |w1| times that plus |b1| (and gelu(y) <= max(|y|, 0.17)), the weights themselves; the
 // remainders are 2^-11 of their values, scaled by 2^11.
 static bool conv_split_in_range(const float* g, const float* w1, const float* b1, const float* w2, int C) {
-    constexpr double kMax = 32768.0;
     double gmax = 0.0;
     for (int c = 0; c < C; ++c) gmax = std::max(gmax, (double)std::fabs(g[c]));
     const double xmax = std::sqrt((double)C) * gmax;
-    if (!(xmax < kMax)) return false;
+    if (!in_split_range(xmax)) return false;
     for (int co = 0; co < C; ++co) {
         double s = std::fabs((double)b1[co]);
         for (int tap = 0; tap < 9; ++tap)
             for (int ci = 0; ci < C; ++ci) s += std::fabs((double)w1[((size_t)tap * C + ci) * C + co]) * xmax;
-        if (!(s < kMax)) return false;
+        if (!in_split_range(s)) return false;
     }
     for (size_t i = 0; i < 9 * (size_t)C * C; ++i)
-        if (!(std::fabs(w1[i]) < kMax && std::fabs(w2[i]) < kMax)) return false;
+        if (!in_split_range(w1[i]) || !in_split_range(w2[i])) return false;
     return true;
 }
 
@@ -566,12 +572,11 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         ctx->wcol_bytes = 0;
         {
             bool csplit = C <= 32, any = false;
-            auto small = [](double v) { return std::fabs(v) < 32768.0; };
             for (int j = 0; j < c.n_scales && csplit; ++j) {
                 if (ctx->off_collapse[j] == (size_t)-1) continue;
                 any = true;
-                for (size_t i = 0; i < 2 * (size_t)C * C && csplit; ++i) csplit = small(w->col_w1[j][i]);
-                for (size_t i = 0; i < (size_t)C * C && csplit; ++i) csplit = small(w->col_w2[j][i]);
+                for (size_t i = 0; i < 2 * (size_t)C * C && csplit; ++i) csplit = in_split_range(w->col_w1[j][i]);
+                for (size_t i = 0; i < (size_t)C * C && csplit; ++i) csplit = in_split_range(w->col_w2[j][i]);
             }
             if (csplit && any) {
                 size_t total = 0;
@@ -580,11 +585,6 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
                     if (ctx->off_collapse[j] != (size_t)-1) total += 2 * 3 * (size_t)C * C;
                 }
                 std::vector<uint16_t> cb(total);
-                auto put_split = [](uint16_t* hi, uint16_t* lo, size_t i, float x) {
-                    const __half hh = __float2half_rn(x);
-                    hi[i] = __half_as_ushort(hh);
-                    lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(hh)) * 2048.f));
-                };
                 for (int j = 0; j < c.n_scales; ++j) {
                     if (ctx->off_collapse[j] == (size_t)-1) continue;
                     uint16_t* b1 = cb.data() + ctx->off_wcol[j] / sizeof(uint16_t);
@@ -593,9 +593,9 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
                     uint16_t* b2l = b2 + (size_t)C * C;
                     for (int n = 0; n < C; ++n) {
                         for (int k = 0; k < 2 * C; ++k)
-                            put_split(b1, b1l, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->col_w1[j][(size_t)k * C + n]);
+                            put_f16split(b1, b1l, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->col_w1[j][(size_t)k * C + n]);
                         for (int k = 0; k < C; ++k)
-                            put_split(b2, b2l, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->col_w2[j][(size_t)k * C + n]);
+                            put_f16split(b2, b2l, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->col_w2[j][(size_t)k * C + n]);
                     }
                 }
                 ctx->wcol_bytes = cb.size() * sizeof(uint16_t);
@@ -634,16 +634,15 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
         ctx->wat_bytes = 0;
         const double qs = 1.0 / std::sqrt((double)C), log2e = 1.4426950408889634;
         bool asplit = C <= 32 && c.attn_mode == QUARK_ATTN_ONE_TO_MANY;
-        auto small = [](double v) { return std::fabs(v) < 32768.0; };
         for (int j = 0; j < c.n_scales && asplit; ++j) {
             const int h = qk_heads(c, j);
             if (h == 0) continue;
             double gmax = 0.0;
             for (int i = 0; i < C; ++i) gmax = std::max(gmax, (double)std::fabs(w->attn_g[j][i]));
-            asplit = small(std::sqrt((double)C) * gmax);
+            asplit = in_split_range(std::sqrt((double)C) * gmax);
             for (size_t i = 0; i < (size_t)C * h * C && asplit; ++i)
-                asplit = small(w->Wq[j][i] * qs * log2e) && small(w->Wo[j][i]);
-            for (size_t i = 0; i < (size_t)C * C && asplit; ++i) asplit = small(w->W_beta[i] * qs);
+                asplit = in_split_range(w->Wq[j][i] * qs * log2e) && in_split_range(w->Wo[j][i]);
+            for (size_t i = 0; i < (size_t)C * C && asplit; ++i) asplit = in_split_range(w->W_beta[i] * qs);
         }
         if (asplit) {
             size_t total = 0;
@@ -653,12 +652,6 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
                 total += h > 0 ? 2 * ((size_t)(h * C + C) * C + (size_t)C * h * C) : 0;
             }
             std::vector<uint16_t> at(std::max<size_t>(total, 8));
-            auto put_split = [](uint16_t* hi, uint16_t* lo, size_t i, double v) {
-                const float x = (float)v;
-                const __half hh = __float2half_rn(x);
-                hi[i] = __half_as_ushort(hh);
-                lo[i] = __half_as_ushort(__float2half_rn((x - __half2float(hh)) * 2048.f));
-            };
             for (int j = 0; j < c.n_scales; ++j) {
                 const int h = qk_heads(c, j), NQ = h * C + C;
                 if (h == 0) continue;
@@ -668,12 +661,12 @@ extern "C" quark_status quark_load_weights(quark_ctx* ctx, const quark_weights* 
                 uint16_t* bo_lo = bo + (size_t)C * h * C;
                 for (int n = 0; n < NQ; ++n)
                     for (int k = 0; k < C; ++k)
-                        put_split(bq, bq_lo, (size_t)(k / 8) * NQ * 8 + n * 8 + k % 8,
+                        put_f16split(bq, bq_lo, (size_t)(k / 8) * NQ * 8 + n * 8 + k % 8,
                                   n < h * C ? w->Wq[j][(size_t)k * h * C + n] * qs * log2e
                                             : w->W_beta[(size_t)k * C + (n - h * C)] * qs);
                 for (int n = 0; n < C; ++n)
                     for (int k = 0; k < h * C; ++k)
-                        put_split(bo, bo_lo, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->Wo[j][(size_t)k * C + n]);
+                        put_f16split(bo, bo_lo, (size_t)(k / 8) * C * 8 + n * 8 + k % 8, w->Wo[j][(size_t)k * C + n]);
             }
             ctx->wat_bytes = at.size() * sizeof(uint16_t);
             s = qk_alloc(ctx, &ctx->wat, ctx->wat_bytes);
