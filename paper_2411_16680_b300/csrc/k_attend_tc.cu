@@ -16,6 +16,8 @@
 //   4. The head outputs O (BF16) go back to shared memory as an A operand; one MMA chain
 //      O W^O (N = C, K = hC) into TMEM; residual add in FP32; V_attn stored as BF16.
 // Completion of each MMA chain is signalled through an mbarrier; every wait is bounded.
+// The same kernel serves the FP32 form (template SPLIT): X, O and the packed weights as FP16
+// parts, three MMAs per K step, FP32 features, taps, residual and V_attn (see AtSmem).
 #include <cuda_fp16.h>
 
 #include "device_common.cuh"
