@@ -180,26 +180,48 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
 #pragma unroll
             for (int c0 = 0; c0 < C; c0 += 16) et_store16(l1 + c0, f + c0);
         }
+        // The 2x2 block's four lanes split its sums: the x partners (lane ^ 1) exchange halves of the
+        // channels, then the y partners (lane ^ 16) halves of those halves, so that each lane ends
+        // with a quarter of the channels of the block's sum (C / 2 + C / 4 shuffles instead of 2 C;
+        // the pairings, and so the rounded sums, are those of (f00 + f01) + (f10 + f11)).
+        constexpr int HC = C / 2, QC = C / 4;
+        const bool xo = px & 1, yo = lane & 16;
+        float g[HC];
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            float s = f[c] + __shfl_xor_sync(0xffffffffu, f[c], 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 16);
-            f[c] = 0.25f * s;
+        for (int i = 0; i < HC; ++i) {
+            const float r = __shfl_xor_sync(0xffffffffu, xo ? f[i] : f[HC + i], 1);
+            g[i] = (xo ? f[HC + i] : f[i]) + r;
         }
-        // lanes with an even x of the warp's first row hold the level-2 texels of this tile row pair
-        const bool l2_owner = !(px & 1) && !(lane & 16);
+        float q[QC];
+#pragma unroll
+        for (int i = 0; i < QC; ++i) {
+            const float r = __shfl_xor_sync(0xffffffffu, yo ? g[i] : g[QC + i], 16);
+            q[i] = 0.25f * ((yo ? g[QC + i] : g[i]) + r);
+        }
+        // every lane of the block stores its quarter of the level-2 texel (channels cq .. cq + C / 4)
+        const int cq = (xo ? HC : 0) + (yo ? QC : 0);
         const int x2 = px >> 1, y2 = warp;  // level-2 texel within the tile (8 x 4)
-        if (l2_owner) {
+        {
             const int X2 = X0 / 2 + x2, Y2 = Y0 / 2 + y2;
             if (a.level[1] && X2 < W / 2 && Y2 < H / 2) {
                 __nv_bfloat16* l2 =
-                    reinterpret_cast<__nv_bfloat16*>(a.level[1]) + (((size_t)v * (H / 2) + Y2) * (W / 2) + X2) * C;
+                    reinterpret_cast<__nv_bfloat16*>(a.level[1]) + (((size_t)v * (H / 2) + Y2) * (W / 2) + X2) * C + cq;
+                if constexpr (QC == 16) {
+                    et_store16(l2, q);
+                } else {
+                    uint32_t u[QC / 2];
 #pragma unroll
-                for (int c0 = 0; c0 < C; c0 += 16) et_store16(l2 + c0, f + c0);
+                    for (int j = 0; j < QC / 2; ++j) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(q[2 * j], q[2 * j + 1]);
+                        u[j] = *reinterpret_cast<const uint32_t*>(&h);
+                    }
+                    if constexpr (QC == 8) *reinterpret_cast<uint4*>(l2) = make_uint4(u[0], u[1], u[2], u[3]);
+                    else *reinterpret_cast<uint2*>(l2) = make_uint2(u[0], u[1]);
+                }
             }
 #pragma unroll
-            for (int c = 0; c < C; c += 4)
-                *reinterpret_cast<float4*>(s_l2 + (y2 * 8 + x2) * S::L2S + c) = make_float4(f[c], f[c + 1], f[c + 2], f[c + 3]);
+            for (int c = 0; c < QC; c += 4)
+                *reinterpret_cast<float4*>(s_l2 + (y2 * 8 + x2) * S::L2S + cq + c) = make_float4(q[c], q[c + 1], q[c + 2], q[c + 3]);
         }
         // this tile's TMEM reads, before the next tile's MMA; the level-2 texels for the next means
         umma::fence_before_sync();

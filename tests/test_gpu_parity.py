@@ -178,6 +178,40 @@ def test_bf16_form(sharp):
         assert psnr(out, ref) >= PSNR_MIN_BF16
 
 
+@pytest.mark.parametrize("C", [16, 32, 64])
+def test_bf16_pyramid_levels(C):
+    """Every level of the BF16 form's pyramid against the oracle's (Sec. 3.2.1: F_1 the 3x3 conv of
+    the image, F_2k the 2x2 means of F_k), on three views of 72 x 56 pixels (the largest factor, 8,
+    divides the view): ragged 16 x 8 encoder tiles in x and a 9 x 7 level 8.  Per texel |gpu - oracle| <= 2^-8 (S + |oracle|) + 1e-6, S the same
+    conv and means of |I| with |W| and no bias: the BF16 rounding of the image and weight operands
+    (2^-9 each) and of the stored texel (2^-9).  A texel, channel or block misplaced by the
+    pooling's lane exchanges is an error of the size of the features themselves."""
+    H, Wd, V = 56, 72, 3
+    cfg = synth.QuarkConfig(C=C, heads=1, scales=[(8, 4), (4, 4), (2, 2), (1, 2)], near=1.0, far=40.0,
+                            out_h=H, out_w=Wd, precision=synth.PREC_BF16)
+    sc = synth.scene_raycast(seed=31, V=V, W=Wd, H=H, f=50.0, arc=0.3)
+    for sharp in (False, True):
+        W = synth.make_weights(cfg, seed=12, sharp=sharp)
+        ctx = quark.Context(cfg)
+        ctx.load_weights(W)
+        pyr = ctx.encode_pyramid(torch.tensor(sc.images, device="cuda"), sc.cams)
+        for k in (1, 2, 4, 8):
+            ref = np.stack([O.encode_level(sc.images[m], W["enc_w"], W["enc_b"], k) for m in range(V)])
+            mag = np.stack([O.encode_level(np.abs(sc.images[m]), np.abs(W["enc_w"]), np.zeros_like(W["enc_b"]), k)
+                            for m in range(V)])
+            raw = np.zeros(ref.shape, np.uint16)
+            pyr.read_level(k, raw)
+            got = (raw.astype(np.uint32) << 16).view(np.float32)  # BF16 is the high half of an FP32 word
+            err = np.abs(got.astype(np.float64) - ref)
+            tol = 2.0 ** -8 * (mag + np.abs(ref)) + 1e-6
+            bad = np.argwhere(err > tol)
+            assert bad.size == 0, (f"C={C} sharp={sharp} level {k}: {len(bad)} texels out of bound, first "
+                                   f"{tuple(bad[0])}: gpu {got[tuple(bad[0])]:.6g} oracle {ref[tuple(bad[0])]:.6g}")
+        ctx.check_device()
+        pyr.release()
+        ctx.close()
+
+
 def test_invalid_arguments_are_rejected():
     cfg = synth.config_small()
     ctx = quark.Context(cfg)
