@@ -179,15 +179,43 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     const bool live = x < W && y < H;
     const int xc = min(x, W - 1), yc = min(y, H - 1);
 
-    // ---- weights: packed BF16 B operands, FP32 misc ----
+    // ---- weights: packed BF16 B operands, FP32 misc; in the BF16 form the entering volume's words
+    // too.  Every global load of the prologue is issued before the first barrier, so that their
+    // latencies overlap instead of adding up. ----
+    constexpr int NWQ = S::PARTS * (S::NQ * C * 2 / 16 + C * NH * C * 2 / 16);  // 16-byte words: wq then wo
+    constexpr int WPT = (NWQ + NT - 1) / NT;
+    uint4 wreg[WPT];
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.wtc);
-        uint4* dq = reinterpret_cast<uint4*>(s_wq);
-        constexpr int nq = S::NQ * C * 2 / 16, no = C * NH * C * 2 / 16;
-        // wq then wo (each part by part), contiguous
-        for (int i = tid; i < S::PARTS * (nq + no); i += NT) dq[i] = __ldg(src + i);
+#pragma unroll
+        for (int j = 0; j < WPT; ++j)
+            if (tid + j * NT < NWQ) wreg[j] = __ldg(src + tid + j * NT);
     }
-    for (int i = tid; i < 4 * C; i += NT) misc[i] = a.w[i];  // v0 [C], g [C], w_d [C], b_d (padded)
+    const float mreg = tid < 4 * C ? a.w[tid] : 0.f;  // v0 [C], g [C], w_d [C], b_d (padded); 4C <= NT
+    // BF16 form: this element's 16 channels (same resolution), or the four x2-upsample taps' words
+    uint4 vraw[TR == TR_UP2 ? 4 : 1][2];
+    int ya = 0, yb = 0, xa = 0, xb = 0;
+    float wy = 0.f, wx = 0.f;
+    if constexpr (!SPLIT && TR == TR_SAME) {
+        ldg256(reinterpret_cast<const __nv_bfloat16*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0,
+               vraw[0][0], vraw[0][1]);
+    } else if constexpr (!SPLIT && TR == TR_UP2) {
+        resize_taps(yc, 2, a.Hp, ya, yb, wy);
+        resize_taps(xc, 2, a.Wp, xa, xb, wx);
+        const __nv_bfloat16* base =
+            reinterpret_cast<const __nv_bfloat16*>(a.prev) + (size_t)li * a.Hp * a.Wp * C + c0;
+        ldg256(base + ((size_t)ya * a.Wp + xa) * C, vraw[0][0], vraw[0][1]);
+        ldg256(base + ((size_t)ya * a.Wp + xb) * C, vraw[1][0], vraw[1][1]);
+        ldg256(base + ((size_t)yb * a.Wp + xa) * C, vraw[2][0], vraw[2][1]);
+        ldg256(base + ((size_t)yb * a.Wp + xb) * C, vraw[3][0], vraw[3][1]);
+    }
+    {
+        uint4* dq = reinterpret_cast<uint4*>(s_wq);
+#pragma unroll
+        for (int j = 0; j < WPT; ++j)
+            if (tid + j * NT < NWQ) dq[tid + j * NT] = wreg[j];
+        if (tid < 4 * C) misc[tid] = mreg;
+    }
 
     // ---- volume entering the step, depth, RMSNorm ----
     // Each thread of an element's group holds its own 16 channels (vres); the depth logit and the
@@ -240,8 +268,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             }
         }
     } else if (TR == TR_SAME) {
-        uint4 u0, u1;
-        ldg256(reinterpret_cast<const __nv_bfloat16*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0, u0, u1);
+        const uint4 u0 = vraw[0][0], u1 = vraw[0][1];  // loaded before the barrier
         vpk[0] = u0.x; vpk[1] = u0.y; vpk[2] = u0.z; vpk[3] = u0.w;
         vpk[4] = u1.x; vpk[5] = u1.y; vpk[6] = u1.z; vpk[7] = u1.w;
 #pragma unroll
@@ -250,23 +277,13 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             vres[2 * j + 1] = __uint_as_float(vpk[j] & 0xffff0000u);
         }
     } else {
-        int ya, yb, xa, xb;
-        float wy, wx;
-        resize_taps(yc, 2, a.Hp, ya, yb, wy);
-        resize_taps(xc, 2, a.Wp, xa, xb, wx);
-        const __nv_bfloat16* base =
-            reinterpret_cast<const __nv_bfloat16*>(a.prev) + (size_t)li * a.Hp * a.Wp * C + c0;
-        uint4 r[4][2];
-        ldg256(base + ((size_t)ya * a.Wp + xa) * C, r[0][0], r[0][1]);
-        ldg256(base + ((size_t)ya * a.Wp + xb) * C, r[1][0], r[1][1]);
-        ldg256(base + ((size_t)yb * a.Wp + xa) * C, r[2][0], r[2][1]);
-        ldg256(base + ((size_t)yb * a.Wp + xb) * C, r[3][0], r[3][1]);
+        // the four x2-upsample taps, loaded before the barrier (vraw; weights wx, wy)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             float t[4][2];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t w = (&r[q][j / 4].x)[j % 4];
+                const uint32_t w = (&vraw[q][j / 4].x)[j % 4];
                 t[q][0] = __uint_as_float(w << 16);
                 t[q][1] = __uint_as_float(w & 0xffff0000u);
             }
@@ -360,6 +377,43 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         }
         umma::commit(mbar);
     }
+    // ---- the first pair of views' samples, before the wait: their gathers need only the depth, so
+    // their latency overlaps the MMA chain, the query copy and the barrier that follow ----
+    const float pxc = xc + 0.5f, pyc = yc + 0.5f;
+    const __nv_bfloat16* feat0 = reinterpret_cast<const __nv_bfloat16*>(a.feat) + c0;
+    const int vstride = a.fh * a.fw * C;  // < 2^31 for every accepted level size
+    // Bilinear sample of view m: the four taps are always fetched (clamped into the map, weight
+    // zero outside it), with no branch, so all the loads of the view are in flight together.
+    // (FP32 form: FP32 features, FP32 taps, the reprojection with an IEEE divide.)
+    auto sample = [&](int m, float2 (&D)[8]) {
+        float u = 0.f, v = 0.f;
+        if constexpr (SPLIT) {
+            const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
+            const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
+            const float* f = reinterpret_cast<const float*>(a.feat) + c0 + (size_t)m * vstride;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) D[j] = make_float2(0.f, 0.f);
+            fma_tap16_f32(f + tp.i00 * C, tp.w00, D);
+            fma_tap16_f32(f + tp.i01 * C, tp.w01, D);
+            fma_tap16_f32(f + tp.i10 * C, tp.w10, D);
+            fma_tap16_f32(f + tp.i11 * C, tp.w11, D);
+        } else {
+            const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
+            const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
+            const __nv_bfloat16* f = feat0 + (size_t)m * vstride;
+            uint32_t Hs[8];
+            mul_taps16(f + tp.i00 * C, tp.w00, Hs);
+            fma_taps16(f + tp.i01 * C, tp.w01, Hs);
+            fma_taps16(f + tp.i10 * C, tp.w10, Hs);
+            fma_taps16(f + tp.i11 * C, tp.w11, Hs);
+            unpack16(Hs, D);
+        }
+    };
+    float2 Da[8], Db[8];
+    if (a.V >= 2) {
+        sample(0, Da);
+        sample(1, Db);
+    }
     bool failed = __syncthreads_or(!umma::mbar_wait(mbar, 0, wait_ns));
     uint32_t failed_phase = 0;
     umma::fence_after_sync();
@@ -401,7 +455,6 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         const float4* qb4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
 
         // ---- views: sample, online softmax (log2 units), weighted sum (FP32) ----
-        const float pxc = xc + 0.5f, pyc = yc + 0.5f;
         float mx[NH], l[NH];
         float2 o[NH][8];
 #pragma unroll
@@ -411,35 +464,6 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) o[h][j] = make_float2(0.f, 0.f);
         }
-        const __nv_bfloat16* feat0 = reinterpret_cast<const __nv_bfloat16*>(a.feat) + c0;
-        const int vstride = a.fh * a.fw * C;  // < 2^31 for every accepted level size
-        // Bilinear sample of view m: the four taps are always fetched (clamped into the map, weight
-        // zero outside it), with no branch, so all the loads of the view are in flight together.
-        // (FP32 form: FP32 features, FP32 taps, the reprojection with an IEEE divide.)
-        auto sample = [&](int m, float2 (&D)[8]) {
-            float u = 0.f, v = 0.f;
-            if constexpr (SPLIT) {
-                const bool ok = reproject(a.geo.v[m], pxc, pyc, d, u, v);
-                const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
-                const float* f = reinterpret_cast<const float*>(a.feat) + c0 + (size_t)m * vstride;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) D[j] = make_float2(0.f, 0.f);
-                fma_tap16_f32(f + tp.i00 * C, tp.w00, D);
-                fma_tap16_f32(f + tp.i01 * C, tp.w01, D);
-                fma_tap16_f32(f + tp.i10 * C, tp.w10, D);
-                fma_tap16_f32(f + tp.i11 * C, tp.w11, D);
-            } else {
-                const bool ok = reproject_rcp(a.geo.v[m], pxc, pyc, d, u, v);
-                const Taps4 tp = bilinear_taps4(ok, u, v, a.fh, a.fw);
-                const __nv_bfloat16* f = feat0 + (size_t)m * vstride;
-                uint32_t Hs[8];
-                mul_taps16(f + tp.i00 * C, tp.w00, Hs);
-                fma_taps16(f + tp.i01 * C, tp.w01, Hs);
-                fma_taps16(f + tp.i10 * C, tp.w10, Hs);
-                fma_taps16(f + tp.i11 * C, tp.w11, Hs);
-                unpack16(Hs, D);
-            }
-        };
         // One online-softmax step of head h: logit s (log2 units, this element's full sum), sample D.
         // The softmax is invariant to the reference subtracted from its logits, so the reference
         // moves only when a logit passes it by AT_SLACK (log2 units): taken at the first view and
@@ -470,9 +494,10 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // Each view's arithmetic, and the order of the softmax steps, is that of one view at a time.
         int m = 0;
         for (; m + 1 < a.V; m += 2) {
-            float2 Da[8], Db[8];
-            sample(m, Da);
-            sample(m + 1, Db);
+            if (m > 0) {
+                sample(m, Da);
+                sample(m + 1, Db);
+            }
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
                 float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
