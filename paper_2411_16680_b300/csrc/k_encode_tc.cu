@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
                 umma::mma_bf16(tmem, ad + ((2 * kk * LBO_A) >> 4), bd + ((2 * kk * LBO_B) >> 4), idesc, kk > 0);
             umma::commit(mbar);
         }
-        failed = __syncthreads_or(!umma::mbar_wait(mbar, phase, ET_WAIT_NS));
+        // one thread polls the MMA's mbarrier; the others wait at the CTA barrier, leaving the issue
+        // slots to the SM's other CTAs (the fence after the barrier orders their TMEM reads)
+        failed = __syncthreads_or(tid == 0 && !umma::mbar_wait(mbar, phase, ET_WAIT_NS));
         umma::fence_after_sync();
         if (failed) break;
         phase ^= 1;
