@@ -227,10 +227,10 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
     __syncthreads();
     float vres[16];
     uint32_t vpk[8];
-    if (TR == TR_INIT) {
+    if constexpr (TR == TR_INIT) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) vres[i] = misc[c0 + i];
-    } else if (SPLIT && TR == TR_SAME) {
+    } else if constexpr (SPLIT && TR == TR_SAME) {
         // FP32 form: the thread's 16 FP32 channels in two 256-bit loads
         uint4 t[4];
         const float* p = reinterpret_cast<const float*>(a.prev) + (((size_t)li * H + yc) * W + xc) * C + c0;
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
             vres[4 * i + 2] = __uint_as_float(t[i].z);
             vres[4 * i + 3] = __uint_as_float(t[i].w);
         }
-    } else if (SPLIT) {
+    } else if constexpr (SPLIT) {
         // FP32 form: x2 bilinear upsample in FP32
         int ya, yb, xa, xb;
         float wy, wx;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 vres[8 * h + i] = top + wy * (bot - top);
             }
         }
-    } else if (TR == TR_SAME) {
+    } else if constexpr (TR == TR_SAME) {
         const uint4 u0 = vraw[0][0], u1 = vraw[0][1];  // loaded before the barrier
         vpk[0] = u0.x; vpk[1] = u0.y; vpk[2] = u0.z; vpk[3] = u0.w;
         vpk[4] = u1.x; vpk[5] = u1.y; vpk[6] = u1.z; vpk[7] = u1.w;
@@ -421,7 +421,9 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // X has been read by the MMA: its tile now keeps the entering volume for the residual of the
         // output epilogue, in 16-byte columns of the operand layout (8 BF16 channels, BF16 form; 4
         // FP32 channels, FP32 form): column k of element e at k * AT_LBO + e * 16
-        if constexpr (SPLIT) {
+        if constexpr (TR == TR_INIT) {
+            // (not reached: the first step's residual is v0, read from shared memory)
+        } else if constexpr (SPLIT) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 *reinterpret_cast<float4*>(s_x + (size_t)(c0 / 4 + i) * AT_LBO + e * 16) =

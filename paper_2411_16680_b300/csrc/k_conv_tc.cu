@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
             const int b = k & 1;
             // the buffer's previous tile (k - 2) is complete; the first two waits pass at once
-            if (!umma::mbar_wait(freed + b, ((k >> 1) & 1) ^ 1, TC_WAIT_NS)) {
+            if (!umma::mbar_wait_suspend(freed + b, ((k >> 1) & 1) ^ 1, TC_WAIT_NS)) {
                 atomicOr(s_err, 1);
                 break;
             }
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
                 const int b = k & 1;
                 uint8_t* s_in = sm + (size_t)b * S::buf_bytes;
-                ok = umma::mbar_wait(full + b, (k >> 1) & 1, TC_WAIT_NS);
+                ok = umma::mbar_wait_suspend(full + b, (k >> 1) & 1, TC_WAIT_NS);
                 if (!ok) break;
                 umma::fence_after_sync();
                 const uint64_t ad = umma::desc(umma::smem_u32(s_in), LBO_A, 128);
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
                 const uint64_t bd2 = umma::desc(umma::smem_u32(s_w2), LBO_W, 128);
                 for (int i = 0; i < tg.nb1 && ok; ++i) {
                     if (k > 0) {
-                        ok = umma::mbar_wait(e1done + i, (k - 1) & 1, TC_WAIT_NS);
+                        ok = umma::mbar_wait_suspend(e1done + i, (k - 1) & 1, TC_WAIT_NS);
                         if (!ok) break;
                         umma::fence_after_sync();
                     }
@@ -344,9 +344,9 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
                     const int need = min(tg.nb1 - 1, (i * TC_M + TC_M + 2 * P + 1) / TC_M);
                     while (ok && ready < need) {
                         ++ready;
-                        ok = umma::mbar_wait(e1done + ready, k & 1, TC_WAIT_NS);
+                        ok = umma::mbar_wait_suspend(e1done + ready, k & 1, TC_WAIT_NS);
                     }
-                    if (ok && k > 0) ok = umma::mbar_wait(e2done + i, (k - 1) & 1, TC_WAIT_NS);
+                    if (ok && k > 0) ok = umma::mbar_wait_suspend(e2done + i, (k - 1) & 1, TC_WAIT_NS);
                     if (!ok) break;
                     umma::fence_after_sync();
                     conv_block(ad, bd2, tmem + TB, i);
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
             if (!ok) atomicOr(s_err, 2);
             // nothing of ours may still run on the tensor cores when TMEM is released
             umma::commit(drain);
-            if (!umma::mbar_wait(drain, 0, TC_WAIT_NS)) atomicOr(s_err, 2);
+            if (!umma::mbar_wait_suspend(drain, 0, TC_WAIT_NS)) atomicOr(s_err, 2);
         }
     } else {
         // ---- epilogues: TC_EPI_WARPS / 4 warps per TMEM lane quarter ----
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
             // gelu(conv1 + b1) -> mid tile, zero outside the plane and on the discarded pixels, each
             // block as soon as its MMAs complete
             for (int i = grp; i < tg.nb1; i += NGRP) {
-                if (!umma::mbar_wait(c1done + i, k & 1, TC_WAIT_NS)) {
+                if (!umma::mbar_wait_suspend(c1done + i, k & 1, TC_WAIT_NS)) {
                     atomicOr(s_err, 4);
                     stop = true;
                     break;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
             if (stop) break;
             // residual, V_out, decode, each block as soon as its MMAs complete
             for (int i = grp; i < tg.nb2; i += NGRP) {
-                if (!umma::mbar_wait(c2done + i, k & 1, TC_WAIT_NS)) {
+                if (!umma::mbar_wait_suspend(c2done + i, k & 1, TC_WAIT_NS)) {
                     atomicOr(s_err, 4);
                     stop = true;
                     break;

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
         }
         // one thread polls the MMA's mbarrier; the others wait at the CTA barrier, leaving the issue
         // slots to the SM's other CTAs (the fence after the barrier orders their TMEM reads)
-        failed = __syncthreads_or(tid == 0 && !umma::mbar_wait(mbar, phase, ET_WAIT_NS));
+        failed = __syncthreads_or(tid == 0 && !umma::mbar_wait_suspend(mbar, phase, ET_WAIT_NS));
         umma::fence_after_sync();
         if (failed) break;
         phase ^= 1;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (failed) {
         if (tid == 0) atomicExch(err, 9);
-        umma::mbar_wait(mbar, phase, ET_WAIT_NS);  // nothing of ours may still run when TMEM is freed
+        umma::mbar_wait_suspend(mbar, phase, ET_WAIT_NS);  // nothing of ours may still run when TMEM is freed
     }
     umma::fence_before_sync();
     __syncthreads();

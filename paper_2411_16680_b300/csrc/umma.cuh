@@ -84,6 +84,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint6
     }
 }
 
+// The same bounded wait, with each poll suspending the thread (up to a hint of 20 us) until the
+// phase completes instead of returning at once, so a waiting warp neither re-polls through the L1
+// pipe nor takes issue slots from the SM's other warps.
+__device__ __forceinline__ bool mbar_wait_suspend(uint64_t* mbar, uint32_t parity, uint64_t limit_ns) {
+    const uint32_t a = smem_u32(mbar);
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity), "r"(20000u));
+        if (done) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // Arrive on the mbarrier (one of the arrivals its phase expects).
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
