@@ -43,17 +43,41 @@ struct EtSmem {
     static constexpr uint32_t tmem_cols = C <= 32 ? 32 : 64;
 };
 
+// n / d for 0 <= n < 2^31 by a multiply-high with a magic number m and shift l computed on the host
+// for the divisor d (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1), so that a tile
+// index splits into view, row and column without a runtime integer division.
+struct EtDiv {
+    uint32_t d, m, l;
+};
+static EtDiv et_make_div(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const uint64_t m = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1;
+    return EtDiv{d, (uint32_t)m, l};
+}
+__device__ __forceinline__ int et_div(int n, const EtDiv& q) {
+    return (int)((__umulhi((uint32_t)n, q.m) + (uint32_t)n) >> q.l);
+}
+// a tile's view and pixel origin
+struct EtTile {
+    int v, X0, Y0;
+};
+__device__ __forceinline__ EtTile et_tile(int tile, const EtDiv& per_view, const EtDiv& tiles_x) {
+    const int v = et_div(tile, per_view), r = tile - v * (int)per_view.d;
+    const int ty = et_div(r, tiles_x);
+    return EtTile{v, (r - ty * (int)tiles_x.d) * ET_W, ty * ET_H};
+}
+
 __device__ __forceinline__ void et_cp_async4(float* smem, const float* gmem, bool valid) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
 }
 
 // the tile's image patch (rows Y0-1 .. Y0+8, columns X0-1 .. X0+16, zero outside the image)
-__device__ __forceinline__ void et_fetch_patch(const EncodeArgs& a, int tile, int tiles_x, int tiles_y, float* patch) {
-    const int per_view = tiles_x * tiles_y;
-    const int v = tile / per_view, r = tile % per_view;
-    const int X0 = (r % tiles_x) * ET_W, Y0 = (r / tiles_x) * ET_H;
-    const float* img = a.images + (size_t)v * a.H * a.W * 3;
+__device__ __forceinline__ void et_fetch_patch(const EncodeArgs& a, const EtTile& t, float* patch) {
+    const int X0 = t.X0, Y0 = t.Y0;
+    const float* img = a.images + (size_t)t.v * a.H * a.W * 3;
     for (int i = threadIdx.x; i < ET_PH * ET_PW * 3; i += ET_M) {
         const int c = i % 3, px = (i / 3) % ET_PW, py = i / (3 * ET_PW);
         const int gy = Y0 - 1 + py, gx = X0 - 1 + px;
@@ -72,8 +96,8 @@ __device__ __forceinline__ void et_store16(__nv_bfloat16* p, const float* v) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const EncodeArgs a, const void* wtc, int* err, int tiles_x,
-                                                         int tiles_y) {
+__global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const EncodeArgs a, const void* wtc, int* err,
+                                                                          const EtDiv per_view, const EtDiv tiles_x) {
     using S = EtSmem<C>;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_a = sm + S::a_off;
@@ -86,7 +110,7 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int H = a.H, W = a.W;
-    const int ntiles = tiles_x * tiles_y * a.V;
+    const int ntiles = (int)per_view.d * a.V;
     {
         const uint4* src = reinterpret_cast<const uint4*>(wtc);
         uint4* dst = reinterpret_cast<uint4*>(sm + S::b_off);
@@ -107,17 +131,17 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
     bool failed = false;
 
     int tile = blockIdx.x;
-    if (tile < ntiles) et_fetch_patch(a, tile, tiles_x, tiles_y, s_patch);
+    EtTile cur = et_tile(tile, per_view, tiles_x);
+    if (tile < ntiles) et_fetch_patch(a, cur, s_patch);
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
         float* patch = s_patch + (it & 1) * (ET_PH * ET_PROW);
-        if (tile + (int)gridDim.x < ntiles)
-            et_fetch_patch(a, tile + gridDim.x, tiles_x, tiles_y, s_patch + ((it + 1) & 1) * (ET_PH * ET_PROW));
+        const EtTile nxt = et_tile(tile + gridDim.x, per_view, tiles_x);
+        if (tile + (int)gridDim.x < ntiles) et_fetch_patch(a, nxt, s_patch + ((it + 1) & 1) * (ET_PH * ET_PROW));
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's patch has landed
         __syncthreads();
-        const int v = tile / (tiles_x * tiles_y), r = tile % (tiles_x * tiles_y);
-        const int X0 = (r % tiles_x) * ET_W, Y0 = (r / tiles_x) * ET_H;
+        const int v = cur.v, X0 = cur.X0, Y0 = cur.Y0;
         const int X = X0 + px, Y = Y0 + py;
         const bool inside = X < W && Y < H;
 
@@ -277,6 +301,7 @@ __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const 
             }
         }
         __syncthreads();  // the patch buffer and the staged texels are reused by the next tile
+        cur = nxt;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (failed) {
@@ -323,7 +348,8 @@ cudaError_t launch_encode_tc(const EncodeArgs& a, int C, const void* wtc, int* e
         if (e != cudaSuccess) return e;                                                                \
         const int per_sm = et_ctas_per_sm(fa.numRegs, EtSmem<CV>::total, (int)EtSmem<CV>::tmem_cols);                               \
         const int grid = (int)std::min<long>(ntiles, (long)per_sm * sms);                              \
-        k<<<grid, ET_M, EtSmem<CV>::total, st>>>(a, wtc, err, tiles_x, tiles_y);                       \
+        k<<<grid, ET_M, EtSmem<CV>::total, st>>>(a, wtc, err, et_make_div((uint32_t)(tiles_x * tiles_y)), \
+                                                 et_make_div((uint32_t)tiles_x));                      \
     } while (0)
     if (C == 16) QK_ET_LAUNCH(16);
     else if (C == 32) QK_ET_LAUNCH(32);
