@@ -10,6 +10,24 @@
 
 namespace quark {
 
+// ---- division by a launch constant -----------------------------------------------------------
+// n / d for 0 <= n < 2^31 by a multiply-high with a magic number m and shift l computed on the host
+// for the divisor d (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1), instead of a
+// runtime integer division (a few instructions against a couple of dozen).
+struct FastDiv {
+    uint32_t d, m, l;
+};
+static inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{d, (uint32_t)m, l};
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv& q) {
+    return (int)((__umulhi((uint32_t)n, q.m) + (uint32_t)n) >> q.l);
+}
+
 // ---- 16-channel vector loads/stores in the storage type --------------------------------------
 
 // 32 bytes of read-only data in one 256-bit load (sm_100 family; global memory only; `p` 32-byte

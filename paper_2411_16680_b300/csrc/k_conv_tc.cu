@@ -62,7 +62,16 @@ constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s bound on every wait
 // of conv1 / conv2.
 struct ConvTile {
     int P, R, nb1, nb2, tiles_x, tiles_y;
+    FastDiv dP, dtx, dty;  // division by P, tiles_x, tiles_y (set by with_divs)
 };
+static ConvTile with_divs(ConvTile t) {
+    if (t.P > 0) {
+        t.dP = make_fastdiv((uint32_t)t.P);
+        t.dtx = make_fastdiv((uint32_t)t.tiles_x);
+        t.dty = make_fastdiv((uint32_t)t.tiles_y);
+    }
+    return t;
+}
 
 template <int C, bool SPLIT>
 struct TcSmem {
@@ -228,8 +237,8 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
                 break;
             }
             uint8_t* s_in = sm + (size_t)b * S::buf_bytes;
-            const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
-            const int li = tile / (tg.tiles_x * tg.tiles_y);
+            const int tq = fdiv(tile, tg.dtx), li = fdiv(tq, tg.dty);
+            const int x0 = (tile - tq * tg.tiles_x) * OW, y0 = (tq - li * tg.tiles_y) * R;
             // rows y0-2 .. y0+R+1, columns x0-2 .. x0+OW+1 (pitch P); two pixels in flight per thread
             const int NIN = (R + 4) * P;
             for (int p0 = tid; p0 < NIN; p0 += 2 * NLOAD) {
@@ -240,7 +249,8 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int p = p0 + u * NLOAD;
-                    const int gy = y0 - 2 + p / P, gx = x0 - 2 + p % P;
+                    const int pr = fdiv(p, tg.dP);
+                    const int gy = y0 - 2 + pr, gx = x0 - 2 + (p - pr * P);
                     in[u] = p < NIN && gy >= 0 && gy < H && gx >= 0 && gx < W;
                     const size_t pix = (size_t)li * plane + (size_t)(in[u] ? gy : 0) * W + (in[u] ? gx : 0);
                     const uint8_t* src = reinterpret_cast<const uint8_t*>(a.in) + pix * NV * 16;
@@ -381,8 +391,8 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
             const int b = k & 1;
             uint8_t* s_mid = sm + (size_t)b * S::buf_bytes;
-            const int x0 = (tile % tg.tiles_x) * OW, y0 = ((tile / tg.tiles_x) % tg.tiles_y) * R;
-            const int li = tile / (tg.tiles_x * tg.tiles_y);
+            const int tq = fdiv(tile, tg.dtx), li = fdiv(tq, tg.dty);
+            const int x0 = (tile - tq * tg.tiles_x) * OW, y0 = (tq - li * tg.tiles_y) * R;
             bool stop = false;
             // gelu(conv1 + b1) -> mid tile, zero outside the plane and on the discarded pixels, each
             // block as soon as its MMAs complete
@@ -396,7 +406,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
                 float v[C];
                 load_acc(i * NACC, v);
                 const int idx = i * TC_M + col;
-                const int row = idx / P, cx = idx - row * P;
+                const int row = fdiv(idx, tg.dP), cx = idx - row * P;
                 const int gy = y0 - 1 + row, gx = x0 - 1 + cx;
                 const bool inside = row < R + 2 && cx < OW + 2 && gy >= 0 && gy < H && gx >= 0 && gx < W;
                 if constexpr (SPLIT) {
@@ -437,7 +447,7 @@ __global__ void __launch_bounds__(TcSmem<C, SPLIT>::THREADS, TcSmem<C, SPLIT>::C
                 umma::fence_before_sync();
                 umma::mbar_arrive(e2done + i);
                 const int idx = i * TC_M + col;
-                const int row = idx / P, cx = idx - row * P;
+                const int row = fdiv(idx, tg.dP), cx = idx - row * P;
                 const int gy = y0 + row, gx = x0 + cx;
                 if (row >= R || cx >= OW || gy >= H || gx >= W) continue;
                 const size_t pix = (size_t)gy * W + gx;
@@ -545,7 +555,7 @@ static ConvTile choose_tile(int W, int H, int L, int slots) {
         }
         if (ow <= 8) break;
     }
-    return best;
+    return with_divs(best);
 }
 
 template <int C, bool SPLIT>

@@ -43,29 +43,13 @@ struct EtSmem {
     static constexpr uint32_t tmem_cols = C <= 32 ? 32 : 64;
 };
 
-// n / d for 0 <= n < 2^31 by a multiply-high with a magic number m and shift l computed on the host
-// for the divisor d (Granlund and Montgomery, "Division by invariant integers using
-// multiplication", PLDI 1994: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1), so that a tile
-// index splits into view, row and column without a runtime integer division.
-struct EtDiv {
-    uint32_t d, m, l;
-};
-static EtDiv et_make_div(uint32_t d) {
-    uint32_t l = 0;
-    while ((1ull << l) < d) ++l;
-    const uint64_t m = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1;
-    return EtDiv{d, (uint32_t)m, l};
-}
-__device__ __forceinline__ int et_div(int n, const EtDiv& q) {
-    return (int)((__umulhi((uint32_t)n, q.m) + (uint32_t)n) >> q.l);
-}
-// a tile's view and pixel origin
+// a tile's view and pixel origin (divisions by the launch's tile counts: FastDiv)
 struct EtTile {
     int v, X0, Y0;
 };
-__device__ __forceinline__ EtTile et_tile(int tile, const EtDiv& per_view, const EtDiv& tiles_x) {
-    const int v = et_div(tile, per_view), r = tile - v * (int)per_view.d;
-    const int ty = et_div(r, tiles_x);
+__device__ __forceinline__ EtTile et_tile(int tile, const FastDiv& per_view, const FastDiv& tiles_x) {
+    const int v = fdiv(tile, per_view), r = tile - v * (int)per_view.d;
+    const int ty = fdiv(r, tiles_x);
     return EtTile{v, (r - ty * (int)tiles_x.d) * ET_W, ty * ET_H};
 }
 
@@ -97,7 +81,7 @@ __device__ __forceinline__ void et_store16(__nv_bfloat16* p, const float* v) {
 
 template <int C>
 __global__ void __launch_bounds__(ET_M, C == 64 ? 4 : 8) encode_tc_kernel(const EncodeArgs a, const void* wtc, int* err,
-                                                                          const EtDiv per_view, const EtDiv tiles_x) {
+                                                                          const FastDiv per_view, const FastDiv tiles_x) {
     using S = EtSmem<C>;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_a = sm + S::a_off;
@@ -348,8 +332,8 @@ cudaError_t launch_encode_tc(const EncodeArgs& a, int C, const void* wtc, int* e
         if (e != cudaSuccess) return e;                                                                \
         const int per_sm = et_ctas_per_sm(fa.numRegs, EtSmem<CV>::total, (int)EtSmem<CV>::tmem_cols);                               \
         const int grid = (int)std::min<long>(ntiles, (long)per_sm * sms);                              \
-        k<<<grid, ET_M, EtSmem<CV>::total, st>>>(a, wtc, err, et_make_div((uint32_t)(tiles_x * tiles_y)), \
-                                                 et_make_div((uint32_t)tiles_x));                      \
+        k<<<grid, ET_M, EtSmem<CV>::total, st>>>(a, wtc, err, make_fastdiv((uint32_t)(tiles_x * tiles_y)), \
+                                                 make_fastdiv((uint32_t)tiles_x));                      \
     } while (0)
     if (C == 16) QK_ET_LAUNCH(16);
     else if (C == 32) QK_ET_LAUNCH(32);
