@@ -61,7 +61,7 @@ __device__ __forceinline__ void tmem_row16(uint32_t tmem, int warp, int col, flo
 }
 
 template <int C, bool SPLIT>
-__global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a) {
+__global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a, const FastDiv tiles_p_div) {
     using S = ClSmem<C, SPLIT>;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_x = sm + S::x_off;
@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(CL_M) collapse_tc_kernel(const CollapseArgs a)
 
     // persistent: tiles of 128 pixels of one output layer j, the layer pair (2j, 2j+1) in
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int j = tile / tiles_p;
-        const size_t pix = (size_t)(tile % tiles_p) * CL_M + tid;
+        const int j = fdiv(tile, tiles_p_div);
+        const size_t pix = (size_t)(tile - j * tiles_p) * CL_M + tid;
         const bool live = pix < plane;
         const size_t pixc = live ? pix : plane - 1;
         // X row of this element: channel group g (8 bf16) of row m at g * 128 * 16 + m * 16
@@ -360,7 +360,7 @@ cudaError_t launch_collapse_tc(const CollapseArgs& a, int C, bool split, cudaStr
         auto k = collapse_tc_kernel<CV, SV>;                                                           \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ClSmem<CV, SV>::total); \
         if (e != cudaSuccess) return e;                                                                \
-        k<<<grid, CL_M, ClSmem<CV, SV>::total, st>>>(a);                                               \
+        k<<<grid, CL_M, ClSmem<CV, SV>::total, st>>>(a, make_fastdiv((uint32_t)((plane + CL_M - 1) / CL_M))); \
     } while (0)
     if (split) {
         if (C == 16) QK_CL_LAUNCH(16, true);

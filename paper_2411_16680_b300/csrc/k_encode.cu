@@ -57,11 +57,19 @@ __device__ __forceinline__ void quad_mean(float2 (&t)[8], int dx, int dy) {
     }
 }
 
+// the view and pixel origin of a tile (divisions by the launch's tile counts: FastDiv)
+__device__ __forceinline__ void tile_origin(int tile, const FastDiv& per_view, const FastDiv& tiles_x, int& v, int& X0, int& Y0) {
+    v = fdiv(tile, per_view);
+    const int r = tile - v * (int)per_view.d, ty = fdiv(r, tiles_x);
+    X0 = (r - ty * (int)tiles_x.d) * ENC_T;
+    Y0 = ty * ENC_T;
+}
+
 template <int NT>
-__device__ __forceinline__ void fetch_patch(const EncodeArgs& a, int tile, int tiles_x, int tiles_y, float (*patch)[ENC_P][3]) {
-    const int per_view = tiles_x * tiles_y;
-    const int v = tile / per_view, r = tile % per_view;
-    const int X0 = (r % tiles_x) * ENC_T, Y0 = (r / tiles_x) * ENC_T;
+__device__ __forceinline__ void fetch_patch(const EncodeArgs& a, int tile, const FastDiv& per_view, const FastDiv& tiles_x,
+                                            float (*patch)[ENC_P][3]) {
+    int v, X0, Y0;
+    tile_origin(tile, per_view, tiles_x, v, X0, Y0);
     const float* img = a.images + (size_t)v * a.H * a.W * 3;
     for (int i = threadIdx.x; i < ENC_P * ENC_P * 3; i += NT) {
         const int c = i % 3, px = (i / 3) % ENC_P, py = i / (3 * ENC_P);
@@ -72,14 +80,14 @@ __device__ __forceinline__ void fetch_patch(const EncodeArgs& a, int tile, int t
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(64 * (C / 16), C == 64 ? 2 : 4) encode_kernel(EncodeArgs a, int tiles_x, int tiles_y) {
+__global__ void __launch_bounds__(64 * (C / 16), C == 64 ? 2 : 4) encode_kernel(EncodeArgs a, FastDiv per_view, FastDiv tiles_x) {
     constexpr int NT = 64 * (C / 16);
     __shared__ float patch_buf[2][ENC_P][ENC_P][3];
     __shared__ __align__(16) float w[28 * C];  // [tap = (dy * 3 + dx) * 3 + ci][C], then bias [C]
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int H = a.H, W = a.W;
-    const int ntiles = tiles_x * tiles_y * a.V;
+    const int ntiles = (int)per_view.d * a.V;
     for (int i = tid; i < 28 * C; i += NT) w[i] = a.w[i];
 
     // quad (qx, qy) of the 8 x 8 quads of the tile; warp w % 4 holds quad rows 4 (w % 4) .. + 3
@@ -88,16 +96,16 @@ __global__ void __launch_bounds__(64 * (C / 16), C == 64 ? 2 : 4) encode_kernel(
     const int px0 = 2 * qx, py0 = 2 * qy;
 
     int tile = blockIdx.x;
-    if (tile < ntiles) fetch_patch<NT>(a, tile, tiles_x, tiles_y, patch_buf[0]);
+    if (tile < ntiles) fetch_patch<NT>(a, tile, per_view, tiles_x, patch_buf[0]);
     cp_async_commit();
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        if (tile + (int)gridDim.x < ntiles) fetch_patch<NT>(a, tile + gridDim.x, tiles_x, tiles_y, patch_buf[(it + 1) & 1]);
+        if (tile + (int)gridDim.x < ntiles) fetch_patch<NT>(a, tile + gridDim.x, per_view, tiles_x, patch_buf[(it + 1) & 1]);
         cp_async_commit();
         cp_async_wait_prior();  // this tile's patch has landed
         __syncthreads();
         float (*patch)[ENC_P][3] = patch_buf[it & 1];
-        const int v = tile / (tiles_x * tiles_y), r = tile % (tiles_x * tiles_y);
-        const int X0 = (r % tiles_x) * ENC_T, Y0 = (r / tiles_x) * ENC_T;
+        int v, X0, Y0;
+        tile_origin(tile, per_view, tiles_x, v, X0, Y0);
 
         // RGBA copy of the tile
         for (int i = tid; i < ENC_T * ENC_T; i += NT) {
@@ -198,7 +206,7 @@ static cudaError_t launch_t(const EncodeArgs& a, cudaStream_t st) {
     const int tiles_x = (a.W + ENC_T - 1) / ENC_T, tiles_y = (a.H + ENC_T - 1) / ENC_T;
     const long ntiles = (long)tiles_x * tiles_y * a.V;
     const int grid = (int)std::min<long>(ntiles, (long)sms * ctas_per_sm);
-    encode_kernel<T, C><<<grid, 64 * (C / 16), 0, st>>>(a, tiles_x, tiles_y);
+    encode_kernel<T, C><<<grid, 64 * (C / 16), 0, st>>>(a, make_fastdiv((uint32_t)(tiles_x * tiles_y)), make_fastdiv((uint32_t)tiles_x));
     return cudaGetLastError();
 }
 

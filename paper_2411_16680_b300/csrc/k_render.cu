@@ -70,7 +70,7 @@ template <bool VEC4>
 __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)a.Hout * a.Wout) return;
-    const int X = (int)(idx % a.Wout), Y = (int)(idx / a.Wout);
+    const int X = (int)((uint32_t)idx % (uint32_t)a.Wout), Y = (int)((uint32_t)idx / (uint32_t)a.Wout);  // < 2^32 pixels
     const int L = a.L, V = a.V;
     const float pxc = X + 0.5f, pyc = Y + 0.5f;
     float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(RD_THREADS) render_kernel(const RenderArgs a) 
 __global__ void __launch_bounds__(RD_THREADS) render_depth_kernel(const RenderArgs a, float* __restrict__ depth) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)a.Hout * a.Wout) return;
-    const int X = (int)(idx % a.Wout), Y = (int)(idx / a.Wout);
+    const int X = (int)((uint32_t)idx % (uint32_t)a.Wout), Y = (int)((uint32_t)idx / (uint32_t)a.Wout);  // < 2^32 pixels
     const int L = a.L;
     float D = 0.f, T = 1.f;
     if (a.sx == 1.f && a.sy == 1.f) {
