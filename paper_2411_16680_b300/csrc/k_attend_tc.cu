@@ -154,11 +154,14 @@ __device__ __forceinline__ void tmem_acc16(uint32_t taddr, float (&v)[16]) {
 
 // The softmax below works in log2 units, so that each weight is one ex2 (ex2_approx); the
 // reprojection divides with one reciprocal (reproject_rcp).
-template <int C, int NH, int TR, bool LAST, bool SPLIT>
+template <int C, int NH, int TR, bool LAST, bool SPLIT, int VT>
 __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1) attend_tc_kernel(const AttendArgs a) {
     constexpr int TPE = C / 16;
     constexpr int NT = AT_M * TPE;
     using S = AtSmem<C, NH, LAST, SPLIT>;
+    // views: VT when the launch fixes the count (the view loop then unrolls, each view's map a
+    // constant-bank operand), else the argument
+    const int NV = VT > 0 ? VT : a.V;
     constexpr int NQ_USED = S::NQ_USED;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t* s_x = sm + S::x_off;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         }
     };
     float2 Da[8], Db[8];
-    if (a.V >= 2) {
+    if (NV >= 2) {
         sample(0, Da);
         sample(1, Db);
     }
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // shared-memory reads of the queries were the larger part of the L1 data-pipe traffic).
         // Each view's arithmetic, and the order of the softmax steps, is that of one view at a time.
         int m = 0;
-        for (; m + 1 < a.V; m += 2) {
+        auto pair_step = [&](int m) {
             if (m > 0) {
                 sample(m, Da);
                 sample(m + 1, Db);
@@ -528,11 +531,17 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                 }
                 const float sa = group_sum(ba.x + ba.y), sb = group_sum(bb.x + bb.y);
                 // the element's first and last threads store one each (fewer bank conflicts)
-                if (sub == 0) s_beta[e * a.V + m] = sa;
-                if (sub == TPE - 1) s_beta[e * a.V + m + 1] = sb;
+                if (sub == 0) s_beta[e * NV + m] = sa;
+                if (sub == TPE - 1) s_beta[e * NV + m + 1] = sb;
             }
+        };
+        if constexpr (VT > 0) {
+#pragma unroll
+            for (; m + 1 < VT; m += 2) pair_step(m);
+        } else {
+            for (; m + 1 < NV; m += 2) pair_step(m);
         }
-        if (m < a.V) {  // the last view of an odd count
+        if (m < NV) {  // the last view of an odd count
             float2 D[8];
             sample(m, D);
 #pragma unroll
@@ -555,7 +564,7 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
                     ba = __ffma2_rn(make_float2(q4.z, q4.w), D[2 * i + 1], ba);
                 }
                 const float sa = group_sum(ba.x + ba.y);
-                if (sub == 0) s_beta[e * a.V + m] = sa;
+                if (sub == 0) s_beta[e * NV + m] = sa;
             }
         }
         if constexpr (SPLIT) {
@@ -697,13 +706,13 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         if constexpr (LAST) {
             // blend logits of the element, contiguous [m] in the [H][W][L][V] layout
             if (!failed && live) {
-                float* dst = a.beta + (((size_t)y * W + x) * L + li) * a.V;
-                const float* src = s_beta + e * a.V;
-                if (a.V % (4 * TPE) == 0) {  // 16-byte runs: the element's views split across its lanes
-                    for (int m = 4 * sub; m < a.V; m += 4 * TPE)
+                float* dst = a.beta + (((size_t)y * W + x) * L + li) * NV;
+                const float* src = s_beta + e * NV;
+                if (NV % (4 * TPE) == 0) {  // 16-byte runs: the element's views split across its lanes
+                    for (int m = 4 * sub; m < NV; m += 4 * TPE)
                         __stcs(reinterpret_cast<float4*>(dst + m), *reinterpret_cast<const float4*>(src + m));
                 } else {
-                    for (int m = sub; m < a.V; m += TPE) __stcs(dst + m, src[m]);
+                    for (int m = sub; m < NV; m += TPE) __stcs(dst + m, src[m]);
                 }
             }
         }
@@ -720,13 +729,21 @@ template <int C, int NH, bool SPLIT>
 static cudaError_t launch_tc_nh(const AttendArgs& a, Transition tr, bool last, cudaStream_t st) {
     dim3 grid(a.L, (a.W + AT_TW - 1) / AT_TW, (a.H + AT_TH - 1) / AT_TH);
     const int threads = AT_M * (C / 16);
-#define QK_TC_LAUNCH(TRV, LASTV)                                                                       \
+    // FP32 form, eight views at C = 32 with up to two heads (the 1080p workload): the view count fixed
+    // at compile time (measured faster there; the BF16 form's unrolled loop spills at its register cap)
+    constexpr bool FIX8 = SPLIT && C == 32 && NH <= 2;
+#define QK_TC_LAUNCH_V(TRV, LASTV, VTV)                                                                \
     do {                                                                                               \
         const size_t smem = AtSmem<C, NH, LASTV, SPLIT>::total(a.V);                                   \
-        auto k = attend_tc_kernel<C, NH, TRV, LASTV, SPLIT>;                                           \
+        auto k = attend_tc_kernel<C, NH, TRV, LASTV, SPLIT, VTV>;                                      \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                \
         k<<<grid, threads, smem, st>>>(a);                                                             \
+    } while (0)
+#define QK_TC_LAUNCH(TRV, LASTV)                                                                       \
+    do {                                                                                               \
+        if (FIX8 && a.V == 8) QK_TC_LAUNCH_V(TRV, LASTV, FIX8 ? 8 : 0);                                \
+        else QK_TC_LAUNCH_V(TRV, LASTV, 0);                                                            \
     } while (0)
     if (tr == TR_INIT) {
         if (last) QK_TC_LAUNCH(TR_INIT, true); else QK_TC_LAUNCH(TR_INIT, false);
@@ -736,6 +753,7 @@ static cudaError_t launch_tc_nh(const AttendArgs& a, Transition tr, bool last, c
         if (last) QK_TC_LAUNCH(TR_UP2, true); else QK_TC_LAUNCH(TR_UP2, false);
     }
 #undef QK_TC_LAUNCH
+#undef QK_TC_LAUNCH_V
     return cudaGetLastError();
 }
 
