@@ -440,13 +440,20 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
         // TMEM -> shared: warp w reads lanes 32 (w % 4) .. + 31, column chunks of 16.  The logit
         // scale 1/sqrt(C), and for the attention heads log2(e) (the softmax below runs on ex2), is
         // folded into the packed W^q and W^beta.
+        // On the first step every element's queries are those of the constant v0 (identical X rows,
+        // so identical Q rows): row 0 alone is copied and read by every element (a shared-memory
+        // broadcast in the view loop).
         const int q = warp & 3, grp = warp >> 2;
-        for (int ch = grp; ch < NQ_USED / 16; ch += TPE) {
-            float v[16];
-            tmem_acc16<SPLIT, S::LO_COL>(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
-            float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
+        if (TR != TR_INIT || q == 0) {
+            for (int ch = grp; ch < NQ_USED / 16; ch += TPE) {
+                float v[16];
+                tmem_acc16<SPLIT, S::LO_COL>(tmem + ((uint32_t)(q * 32) << 16) + ch * 16, v);
+                if (TR != TR_INIT || lane == 0) {
+                    float4* dst = reinterpret_cast<float4*>(s_q + (size_t)(q * 32 + lane) * S::QS + ch * 16);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+            }
         }
     }
     umma::fence_before_sync();
@@ -455,9 +462,10 @@ __global__ void __launch_bounds__(AT_M * (C / 16), (C == 32 && NH <= 2) ? 2 : 1)
 
     if (!failed) {
         // the queries stay in shared memory (read once per pair of views) to keep registers for the gathers
-        const float4* qh4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + c0);
+        const int qrow = TR == TR_INIT ? 0 : e;  // the first step's queries: one row for all
+        const float4* qh4 = reinterpret_cast<const float4*>(s_q + (size_t)qrow * S::QS + c0);
         // the blend query likewise
-        const float4* qb4 = reinterpret_cast<const float4*>(s_q + (size_t)e * S::QS + NH * C + c0);
+        const float4* qb4 = reinterpret_cast<const float4*>(s_q + (size_t)qrow * S::QS + NH * C + c0);
 
         // ---- views: sample, online softmax (log2 units), weighted sum (FP32) ----
         float mx[NH], l[NH];
